@@ -1,0 +1,358 @@
+"""Benchmark: Pauli-string commutator hot path on GB300.
+
+Timed step: one Lanczos step (A = [H, O_n] - b_n O_{n-1}, b_{n+1} = ||A||,
+O_{n+1} = top-2^22(A / b_{n+1})) of the open XXZ chain on 64 sites,
+H = sum X X + Y Y + 0.5 Z Z (189 strings), O_0 = sum X_i / 8, once the
+operator has reached the 2^22-string cap.  `value` is [H,O] Pauli products
+(|H| x |O| string products per commutator) per second; the JSON line also
+carries merged strings/s, RK4 steps/s on the N=10 chain workload, the
+roofline of the dominant kernel, the oracle's CPU rate and an end-to-end
+figure measured through host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (torchrun), each rank runs an independent replica (the path does not
+shard: weak scaling); value = products of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "[H,O] Pauli products/s + RK4 steps/s at ≤1e-6 rel error vs FP64 oracle"
+N_SITES = 64
+TOP_K = 1 << 22
+WORKLOAD = ("Lanczos on the open XXZ chain N=64 (H = sum XX+YY+0.5ZZ, 189 strings), O_0 = sum X_i/8, "
+            "top 2^22 strings kept after each step; timed steps start once |O| has reached 2^22")
+RK4_WORKLOAD = "RK4 on the open N=10 chain sum ZZ + 1.05 sum X + 0.5 sum Z, O(0)=Z_1, dt=0.05, 40 steps, weight<=6 then |c|<1e-10"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--top-k", type=int, default=TOP_K)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], f[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+def workload_arrays():
+    from paper_2410_09654_gb300 import inputs as I
+    return I.xxz_chain(N_SITES, 0.5).arrays(), I.uniform_sum(N_SITES, "X").arrays()
+
+
+def oracle_rate(top_k: int, steps: int, warmup: int, budget_s: float = 25.0):
+    """The CPU oracle on a bounded sample of the same workload: the same Lanczos recursion
+    with the cap lowered so that one step takes about a second; returns per-step timings."""
+    import oracle as orc
+    Ha, O0a = workload_arrays()
+    H = orc.Op(N_SITES, *Ha)
+    prev, cur, b = orc.Op.empty(N_SITES), orc.Op(N_SITES, *O0a), 0.0
+    n = 0
+    while len(cur) < top_k and n < 40:  # ramp (untimed)
+        b, nxt = orc.lanczos_step(H, prev, cur, b, top_k=top_k)
+        prev, cur = cur, nxt
+        n += 1
+    rec = []
+    t_all = time.perf_counter()
+    for i in range(warmup + steps):
+        t = time.perf_counter()
+        prods = len(H) * len(cur)
+        b, nxt = orc.lanczos_step(H, prev, cur, b, top_k=top_k)
+        dt = time.perf_counter() - t
+        prev, cur = cur, nxt
+        if i >= warmup:
+            rec.append((prods, dt))
+        if time.perf_counter() - t_all > budget_s and len(rec) >= 1:
+            break
+    return rec
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample_k = 1 << 16
+    rec = oracle_rate(sample_k, args.steps, args.warmup, budget_s=150.0)
+    prods = sum(p for p, _ in rec)
+    secs = sum(t for _, t in rec)
+    value = prods / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Pauli products/s", "n_gpus": args.gpus,
+        "steps": len(rec), "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(rec), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"same recursion with the cap lowered to 2^16 strings"},
+        "cpu_baseline": {"value": value, "unit": "Pauli products/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(rec)} oracle Lanczos steps at |O| = 2^16 (single-threaded C++ oracle)"},
+        "e2e": {"value": value, "unit": "Pauli products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2410_09654_gb300 import inputs as I
+    from paper_2410_09654_gb300 import paulistr as ps
+    ps.load(build_if_missing=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    Ha, O0a = workload_arrays()
+    H = ps.PauliSum.from_arrays(N_SITES, *Ha)
+    nH = len(Ha[0])
+    pol = ps.policy(top_k=args.top_k)
+    prev, cur = ps.PauliSum(N_SITES), ps.PauliSum.from_arrays(N_SITES, *O0a)
+    b = 0.0
+    n_done = 0
+    # ramp: untimed steps until the operator has reached the cap
+    while len(cur) < args.top_k and n_done < 30:
+        b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
+        n_done += 1
+    ramp_steps = n_done
+    for _ in range(args.warmup):
+        b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
+        n_done += 1
+
+    # snapshot of the state for the end-to-end leg
+    snap_cur = cur.download() if not args.no_e2e else None
+    snap_prev = prev.download() if not args.no_e2e else None
+    snap_b = b
+
+    # ---------------------------------------------------------------- timed region
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    products = 0
+    merged = 0
+    contributions = 0
+    bs = []
+    ps.pauli_profile_enable(True)
+    barrier()
+    clocks.start()
+    launches0 = ps.pauli_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        products += nH * len(cur)
+        b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
+        st = ps.pauli_last_merge_stats()
+        merged += st["merged"]
+        contributions += st["contributions"]
+        bs.append(b)
+    ev1.record(stream)
+    barrier()
+    launches = ps.pauli_launch_count() - launches0
+    clk = clocks.stop()
+    prof = ps.pauli_profile_report()
+    ps.pauli_profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms)
+    products_all = sum_over_ranks(products)
+    value = products_all / (ms_max / 1e3)
+    merged_rate = sum_over_ranks(merged) / (ms_max / 1e3)
+
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (1, 1.0))
+    kname, (klaunch, kms) = top
+    avg_s = kms / 1e3 / max(klaunch, 1)
+    roof = {"kernel": kname, "share": kms / max(sum(v[1] for v in prof.values()), 1e-9)}
+    per_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in prof.items()}
+    if kname == "k_merge":
+        # algorithmic bytes per launch: each entry (8 B) read once, its product operand (32 B)
+        # gathered once, each merged output string (32 B) written once
+        alg = (contributions / args.steps) * (8 + 32) + (merged / args.steps) * 32
+        roof.update({"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"})
+    elif kname == "k_emit_products":
+        alg = (products / args.steps) / max(klaunch / args.steps, 1)
+        pair_peak = POPC_PEAK_PAIRS_PER_S
+        roof.update({"bound": "alu", "achieved": alg / avg_s / 1e9, "peak": pair_peak / 1e9, "unit": "Gpairtests/s",
+                     "peak_kind": "integer popcount issue rate (see DESIGN.md)"})
+    else:
+        roof.update({"bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s"})
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if snap_cur is not None:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hc = [pin(x) for x in snap_cur]
+        hp = [pin(x) for x in snap_prev]
+        e_prev, e_cur = ps.PauliSum(N_SITES, len(hp[0])), ps.PauliSum(N_SITES, len(hc[0]))
+        n_e2e = max(1, min(args.steps, 4))
+        barrier()
+        t0 = time.perf_counter()
+        e_prod = 0
+        for _ in range(n_e2e):
+            e_prev.upload(*hp)
+            e_cur.upload(*hc)
+            e_prod += nH * len(hc[0])
+            bb = ps.pauli_lanczos_step(H, e_prev, e_cur, snap_b, pol)  # b_n read back to the host
+        barrier()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": sum_over_ranks(e_prod) / t_e2e, "unit": "Pauli products/s",
+               "h2d_bytes_per_step": int(32 * (len(hc[0]) + len(hp[0]))), "d2h_bytes_per_step": 8,
+               "api": "pauli_sum_upload x2 (pinned host arrays) + pauli_lanczos_step (b_n to host)"}
+
+    # ---------------------------------------------------------------- RK4 steps/s (N=10 chain)
+    n10 = 10
+    Hr = ps.PauliSum.from_arrays(n10, *I.tilted_ising_chain(n10).arrays())
+    Z1 = I.single(n10, "Z", 1).arrays()
+    rk_pol = ps.policy(max_weight=6, cutoff=1e-10)
+    Or = ps.PauliSum.from_arrays(n10, *Z1)
+    for _ in range(3):
+        ps.pauli_rk4_step(Hr, Or, 0.05, rk_pol)
+    Or = ps.PauliSum.from_arrays(n10, *Z1)
+    Z1s = ps.PauliSum.from_arrays(n10, *Z1)
+    barrier()
+    t0 = time.perf_counter()
+    obs = []
+    for _ in range(40):
+        ps.pauli_rk4_step(Hr, Or, 0.05, rk_pol)
+        obs.append(ps.pauli_trace_product(Or, Z1s).real)
+    barrier()
+    t_rk = max_over_ranks(time.perf_counter() - t0)
+    rk4 = {"steps_per_s": sum_over_ranks(40) / t_rk, "workload": RK4_WORKLOAD, "final_size": len(Or),
+           "observable_t2": obs[-1]}
+
+    # ---------------------------------------------------------------- CPU oracle baseline
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rec = oracle_rate(1 << 16, 4, 1, budget_s=20.0)
+        cp = sum(p for p, _ in rec) / sum(t for _, t in rec)
+        cpu = {"value": cp, "unit": "Pauli products/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(rec)} Lanczos steps of the same recursion with the cap lowered to 2^16 strings "
+                         f"(single-threaded C++ oracle)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Pauli products/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_sites": N_SITES, "H_strings": nH, "top_k": args.top_k,
+                       "ramp_steps": ramp_steps, "l2": "inputs larger than L2 (|O| = 2^22 strings x 32 B = 134 MB; "
+                       "the merge bins are several GB)", "parallelism": "replicas" if world > 1 else "single"},
+            "merged_strings_per_s": merged_rate,
+            "contributions_per_step": contributions / args.steps,
+            "b_n_timed": bs,
+            "rk4": rk4,
+            "roofline": roof,
+            "kernels_per_step_ms": {k: round(v[1], 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1][1])},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# Pair-test peak used for an ALU-bound emission kernel: one 64-bit popcount (two 32-bit
+# POPC) per pair; 152 SMs x 16 POPC/clk/SM x 2.07 GHz / 2.
+POPC_PEAK_PAIRS_PER_S = 152 * 16 * 2.07e9 / 2
+
+if __name__ == "__main__":
+    main()

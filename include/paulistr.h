@@ -1,0 +1,186 @@
+/* paulistr.h -- C ABI of the GB300 (sm_103a) Pauli-string commutator library.
+ *
+ * The library implements the hot path of the binary Pauli-string method
+ * (Loizeau, Peacock, Sels, "Quantum many-body simulations with
+ * PauliStrings.jl", arXiv:2410.09654): the commutator [H, O] of two Pauli
+ * sums with duplicate merging (Alg. 1 adapted with eq. eps_com), truncation
+ * (trim / cutoff / long-string discarding / depolarising noise), one RK4 step
+ * of the Heisenberg equation dO/dt = i[H, O] and one Lanczos step of the
+ * recursion method, plus the trace products and norms they need.
+ *
+ * Conventions (paper, Methods, eqs. v12, w12, eps12, eps_com):
+ *   - A Pauli string on n_sites <= 64 sites is a pair of uint64 masks (v, w).
+ *     Bit i-1 is site i; v is the Z bit and w the X bit (tau table).  Bits at or
+ *     above n_sites must be zero.
+ *   - A coefficient multiplies the Hermitian string
+ *     P(v,w) = (-i)^{popcount(v & w)} Z^v X^w  (site letters I, X, Y, Z).
+ *   - Coefficients are complex FP64, passed as separate real and imaginary arrays.
+ *
+ * Memory and streams:
+ *   - A pauli_sum is device resident and owned by the library (stream-ordered
+ *     allocations on the sum's stream).  Host arrays passed in or out are owned
+ *     by the caller and are only read or written during the call.
+ *   - Every call is ordered on the stream given at creation (a cudaStream_t,
+ *     e.g. PyTorch's current stream; NULL is the legacy default stream).  Calls
+ *     that return a host value (sizes, norms, b_n, trace products) synchronise
+ *     that stream; the others may synchronise it to size their outputs.
+ *   - All sums passed to one call must share n_sites and should share the stream.
+ *
+ * Errors: every entry point returns a status (PS_OK = 0).  On error, output
+ * sums are left empty or unchanged and nothing aborts; no device code traps.
+ * pauli_status_string() gives a description.
+ *
+ * Determinism: for every string, the contributions to its coefficient are added
+ * in the same order as in Alg. 1 with H in the outer loop (H's term order as
+ * uploaded), with separately rounded FP64 products and sums and no FMA; norms
+ * and trace products are the exactly rounded values of the exact sums.  The
+ * results are therefore independent of the storage order of the strings and of
+ * the GPU scheduling, and equal those of a plain sequential implementation.
+ * Storage order inside a sum is unspecified; pauli_sum_download returns the
+ * canonical order (v ascending, then w ascending, unsigned).
+ */
+#ifndef PAULISTR_H
+#define PAULISTR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define PS_OK 0
+#define PS_ERR_INVALID 1          /* bad argument: null, n_sites out of range, key bits >= n_sites, ... */
+#define PS_ERR_CAPACITY 2         /* a caller-provided capacity is too small (download) */
+#define PS_ERR_TABLE_FULL 3       /* a merge table could not be resolved even after splitting */
+#define PS_ERR_CUDA 4             /* a CUDA runtime call failed; see pauli_last_cuda_error() */
+#define PS_ERR_TIMEOUT 5          /* a bounded device-side wait gave up */
+#define PS_ERR_KRYLOV_EXHAUSTED 6 /* Lanczos: b_n == 0 (the Krylov space closed); b_out is 0 */
+#define PS_ERR_NOMEM 7            /* device allocation failed */
+#define PS_ERR_UNCERTAIN 8        /* reserved */
+
+const char* pauli_status_string(int status);
+/* Text of the last CUDA error seen by the library on this thread ("" if none). */
+const char* pauli_last_cuda_error(void);
+
+/* ------------------------------------------------------------------ sums */
+typedef struct pauli_sum pauli_sum; /* opaque, device resident */
+
+/* Create an empty sum on n_sites (1..64) sites.  capacity is a hint (strings);
+ * sums grow as needed.  cuda_stream: cudaStream_t the sum's work is ordered on. */
+int pauli_sum_create(int n_sites, int64_t capacity, void* cuda_stream, pauli_sum** out);
+int pauli_sum_destroy(pauli_sum* s);
+
+/* Replace the contents of s with n strings from HOST arrays v, w, re, im
+ * (caller-owned, read during the call).  Strings must be distinct (a repeated
+ * string is PS_ERR_INVALID) and have no bits at or above n_sites.  The given
+ * order is kept; for a sum used as the left operand H of a commutator this is
+ * the order of the outer loop of Alg. 1.  Exact-zero coefficients are kept. */
+int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re,
+                     const double* im, int64_t n);
+
+/* Same as pauli_sum_upload but v, w, re, im are DEVICE pointers (n elements each);
+ * only the bit-range check is done (on the device); distinctness is the caller's
+ * responsibility. */
+int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re,
+                            const double* im, int64_t n);
+
+/* Number of strings (synchronises the stream). */
+int pauli_sum_size(const pauli_sum* s, int64_t* n);
+int pauli_sum_n_sites(const pauli_sum* s, int* n_sites);
+
+/* Copy the sum to HOST arrays of capacity cap in canonical order (v, then w,
+ * ascending).  *n receives the size; PS_ERR_CAPACITY (nothing written) if cap < size. */
+int pauli_sum_download(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im,
+                       int64_t cap, int64_t* n);
+
+/* Copy the sum to DEVICE arrays in storage order (unspecified order). */
+int pauli_sum_download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im,
+                              int64_t cap, int64_t* n);
+
+int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst);
+
+/* ------------------------------------------------------------------ algebra */
+
+/* out = [H, O] = H O - O H  (Alg. 1 with eq. eps_com): all-pairs string
+ * products (XOR of the masks, eqs. v12/w12), anticommutation test and popcount
+ * phase, coefficient 2 i^k h o for anticommuting pairs, duplicates merged,
+ * exact zeros dropped.  out must be distinct from H and O. */
+int pauli_commutator(const pauli_sum* H, const pauli_sum* O, pauli_sum* out);
+
+/* out = A + alpha * B over the union of supports (absent strings are zero),
+ * exact zeros dropped.  out must be distinct from A and B. */
+int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_sum* B, pauli_sum* out);
+
+/* Truncation policy (paper: trim(O, M; keep), cutoff(O, eps), discarding long
+ * strings, add_noise(O, eps*dt)). */
+typedef struct {
+  int max_weight;   /* drop strings of Pauli weight > max_weight; < 0: off */
+  double cutoff;    /* drop |c| < cutoff, tested as re*re + im*im < cutoff*cutoff; <= 0: off */
+  int64_t top_k;    /* keep the top_k strings by |c|^2, exact ties to the smaller (v, w); <= 0: off */
+  double gamma;     /* depolarising transmission exp(-(gamma*dt) * weight); 0: off */
+  int trim_stages;  /* RK4 only: also cut each stage derivative k_j to its top_k */
+} pauli_trunc_policy;
+
+/* In place: (1) c *= exp(-(gamma*dt)*wt), wt = popcount(v|w); (2) drop wt > max_weight;
+ * (3) drop |c|^2 < cutoff^2; (4) keep the top_k by |c|^2 (ties: smaller key), never
+ * dropping a string that is present in keep (keep may be NULL; only its strings
+ * matter).  Exact zeros are dropped. */
+int pauli_truncate(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt);
+
+/* One classical RK4 step of dO/dt = i[H, O] (paper, Heisenberg time evolution):
+ *   k1 = i[H,O]; k2 = i[H, O + dt/2 k1]; k3 = i[H, O + dt/2 k2]; k4 = i[H, O + dt k3];
+ *   S = k1 + 2 k2; S = S + 2 k3; S = S + k4;  O <- O + (dt/6) S;
+ * then pauli_truncate(O, policy, keep, dt).  policy may be NULL (no truncation). */
+int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
+                   const pauli_sum* keep);
+
+/* One step of the Lanczos recursion (paper, Krylov subspace expansion):
+ *   A = [H, O_cur] - b_prev O_prev;  b_n = ||A|| = sqrt(sum |c|^2);  O_n = trunc(A / b_n)
+ * and the sums rotate: O_prev <- O_cur, O_cur <- O_n.  For the first step pass an
+ * empty O_prev (and b_prev = 0): then b_1 = ||[H, O_0]||.  *b_out receives b_n.
+ * If b_n == 0 the sums are left unchanged and PS_ERR_KRYLOV_EXHAUSTED is returned.
+ * policy may be NULL (no truncation); its gamma and trim_stages are ignored. */
+int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev,
+                       const pauli_trunc_policy* policy, double* b_out);
+
+/* Tr(A B) / 2^N = sum over strings present in both of a_s b_s (eq. correlator with
+ * the Hermitian, trace-orthonormal strings); each component exactly rounded. */
+int pauli_trace_product(const pauli_sum* A, const pauli_sum* B, double* re, double* im);
+
+/* ||O|| = sqrt(sum |c|^2) = sqrt(Tr(O^dag O) / 2^N) (the norm of the Krylov section,
+ * read with the square root), from the exactly rounded sum of squares. */
+int pauli_norm(const pauli_sum* O, double* out);
+
+/* ------------------------------------------------------------------ statistics */
+/* Counters of the last pauli_commutator / merge on this sum's stream: pair tests
+ * (|H|*|O|), anticommuting contributions, merged output strings. */
+typedef struct {
+  int64_t pair_tests;
+  int64_t contributions;
+  int64_t merged;
+  int64_t groups;
+  int64_t split_groups;
+} pauli_merge_stats;
+int pauli_last_merge_stats(pauli_merge_stats* out);
+
+/* ------------------------------------------------------------------ profiling */
+/* Enable (1) or disable (0) per-kernel timing: every kernel launch of the library is
+ * bracketed by CUDA events recorded on its launching stream.  Enabling clears the totals. */
+int pauli_profile_enable(int on);
+/* Write the totals as JSON {"kernel": [launches, total_ms], ...} into buf (len bytes,
+ * NUL-terminated); waits for the recorded events.  *needed receives the size required;
+ * PS_ERR_CAPACITY if len is too small. */
+int pauli_profile_report(char* buf, int64_t len, int64_t* needed);
+/* Number of kernels the library has launched since it was loaded. */
+int64_t pauli_launch_count(void);
+
+/* ------------------------------------------------------------------ testing hooks */
+/* Make the next n-th device allocation of the library fail (n >= 1; 0 disables).
+ * Host-side fault injection for tests; it never touches the GPU. */
+int pauli_debug_fail_alloc_after(int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAULISTR_H */

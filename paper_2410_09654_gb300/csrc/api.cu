@@ -1,0 +1,167 @@
+// C ABI entry points: commutator, add, truncate, RK4 step, Lanczos step, trace product, norm.
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "common.cuh"
+
+using namespace ps;
+
+namespace {
+
+bool same_sites(const pauli_sum* a, const pauli_sum* b) { return !a || !b || a->n_sites == b->n_sites; }
+
+// A library-internal temporary sum on a given stream.
+struct Tmp {
+  pauli_sum s;
+  explicit Tmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0} {}
+  ~Tmp() { dev_free(s.d, s.stream); }
+  Tmp(const Tmp&) = delete;
+  Tmp& operator=(const Tmp&) = delete;
+};
+
+void swap_contents(pauli_sum* a, pauli_sum* b) {
+  std::swap(a->d, b->d);
+  std::swap(a->cap, b->cap);
+  std::swap(a->n, b->n);
+}
+
+// k = i[H, X] (rot = 1) or [H, X] (rot = 0) into out.
+int commutator_into(const pauli_sum* H, const pauli_sum* X, int rot, pauli_sum* out) {
+  MergeSpec sp;
+  sp.H = H->d;
+  sp.nH = (int)H->n;
+  sp.X = X->d;
+  sp.nX = X->n;
+  sp.rot = rot;
+  return merge_run(sp, out->stream, out);
+}
+
+bool policy_valid(const pauli_trunc_policy* p) {
+  if (!p) return true;
+  return std::isfinite(p->cutoff) && std::isfinite(p->gamma) && p->max_weight <= 64;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pauli_commutator(const pauli_sum* H, const pauli_sum* O, pauli_sum* out) {
+  if (!H || !O || !out || out == H || out == O) return PS_ERR_INVALID;
+  if (!same_sites(H, O) || !same_sites(O, out)) return PS_ERR_INVALID;
+  if (H->n > 0xEFFF) return PS_ERR_INVALID;
+  if (H->stream != out->stream) PS_CUDA(cudaStreamSynchronize(H->stream));
+  if (O->stream != out->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
+  return commutator_into(H, O, 0, out);
+}
+
+int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_sum* B, pauli_sum* out) {
+  if (!A || !B || !out || out == A || out == B) return PS_ERR_INVALID;
+  if (!same_sites(A, B) || !same_sites(A, out)) return PS_ERR_INVALID;
+  MergeSpec sp;
+  sp.src[0] = MergeSource{A->d, A->n, Cx{1.0, 0.0}};
+  sp.src[1] = MergeSource{B->d, B->n, Cx{alpha_re, alpha_im}};
+  sp.nsrc = 2;
+  return merge_run(sp, out->stream, out);
+}
+
+int pauli_truncate(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt) {
+  if (!O || !same_sites(O, keep) || !policy_valid(policy) || !std::isfinite(dt)) return PS_ERR_INVALID;
+  return truncate_run(O, policy, keep, dt, nullptr);
+}
+
+int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
+                   const pauli_sum* keep) {
+  if (!H || !O || H == O || !same_sites(H, O) || !same_sites(O, keep)) return PS_ERR_INVALID;
+  if (!policy_valid(policy) || !std::isfinite(dt) || H->n > 0xEFFF) return PS_ERR_INVALID;
+  const double h2 = dt / 2.0, h6 = dt / 6.0;
+  const bool trim = policy && policy->trim_stages && policy->top_k > 0;
+  pauli_trunc_policy stage{-1, 0.0, policy ? policy->top_k : 0, 0.0, 0};
+  Tmp k1(O), k2(O), k3(O), k4(O), X(O);
+  auto L = [&](const pauli_sum* in, pauli_sum* k) -> int {
+    PS_TRY(commutator_into(H, in, 1, k));
+    if (trim) PS_TRY(truncate_run(k, &stage, nullptr, dt, nullptr));
+    return PS_OK;
+  };
+  auto stage_input = [&](const pauli_sum* k, double a) -> int {  // X = O + a k
+    MergeSpec sp;
+    sp.src[0] = MergeSource{O->d, O->n, Cx{1.0, 0.0}};
+    sp.src[1] = MergeSource{k->d, k->n, Cx{a, 0.0}};
+    sp.nsrc = 2;
+    return merge_run(sp, O->stream, &X.s);
+  };
+  PS_TRY(L(O, &k1.s));
+  PS_TRY(stage_input(&k1.s, h2));
+  PS_TRY(L(&X.s, &k2.s));
+  PS_TRY(stage_input(&k2.s, h2));
+  PS_TRY(L(&X.s, &k3.s));
+  PS_TRY(stage_input(&k3.s, dt));
+  PS_TRY(L(&X.s, &k4.s));
+  // S = ((k1 + 2 k2) + 2 k3) + k4;  O' = O + (dt/6) S
+  MergeSpec sp;
+  sp.src[0] = MergeSource{k1.s.d, k1.s.n, Cx{1.0, 0.0}};
+  sp.src[1] = MergeSource{k2.s.d, k2.s.n, Cx{2.0, 0.0}};
+  sp.src[2] = MergeSource{k3.s.d, k3.s.n, Cx{2.0, 0.0}};
+  sp.src[3] = MergeSource{k4.s.d, k4.s.n, Cx{1.0, 0.0}};
+  sp.nsrc = 4;
+  sp.pre = O->d;
+  sp.npre = O->n;
+  sp.has_post = true;
+  sp.post = Cx{h6, 0.0};
+  PS_TRY(merge_run(sp, O->stream, &X.s));
+  PS_TRY(truncate_run(&X.s, policy, keep, dt, nullptr));
+  swap_contents(O, &X.s);
+  return PS_OK;
+}
+
+int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev,
+                       const pauli_trunc_policy* policy, double* b_out) {
+  if (!H || !O_prev || !O_cur || !b_out || O_prev == O_cur || H == O_prev || H == O_cur) return PS_ERR_INVALID;
+  if (!same_sites(H, O_cur) || !same_sites(O_prev, O_cur) || !policy_valid(policy) || !std::isfinite(b_prev))
+    return PS_ERR_INVALID;
+  if (H->n > 0xEFFF) return PS_ERR_INVALID;
+  *b_out = 0.0;
+  Tmp A(O_cur);
+  MergeSpec sp;
+  sp.H = H->d;
+  sp.nH = (int)H->n;
+  sp.X = O_cur->d;
+  sp.nX = O_cur->n;
+  if (O_prev->n > 0) {
+    sp.src[0] = MergeSource{O_prev->d, O_prev->n, Cx{-b_prev, 0.0}};
+    sp.nsrc = 1;
+  }
+  PS_TRY(merge_run(sp, O_cur->stream, &A.s));
+  double n2 = 0.0;
+  PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2));
+  double b = std::sqrt(n2);
+  *b_out = b;
+  if (b == 0.0) return PS_ERR_KRYLOV_EXHAUSTED;
+  pauli_trunc_policy p{-1, 0.0, 0, 0.0, 0};
+  if (policy) {
+    p.max_weight = policy->max_weight;
+    p.cutoff = policy->cutoff;
+    p.top_k = policy->top_k;
+  }
+  PS_TRY(truncate_run(&A.s, &p, nullptr, 0.0, &b));
+  // rotate: O_prev <- O_cur, O_cur <- O_n
+  swap_contents(O_prev, O_cur);
+  swap_contents(O_cur, &A.s);
+  return PS_OK;
+}
+
+int pauli_trace_product(const pauli_sum* A, const pauli_sum* B, double* re, double* im) {
+  if (!A || !B || !re || !im || !same_sites(A, B)) return PS_ERR_INVALID;
+  if (A->stream != B->stream) PS_CUDA(cudaStreamSynchronize(B->stream));
+  return exact_trace_product(A->d, A->n, B->d, B->n, A->stream, re, im);
+}
+
+int pauli_norm(const pauli_sum* O, double* out) {
+  if (!O || !out) return PS_ERR_INVALID;
+  double n2 = 0.0;
+  PS_TRY(exact_norm2(O->d, O->n, O->stream, &n2));
+  *out = std::sqrt(n2);
+  return PS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+// Internal definitions shared by the CUDA translation units of libpaulistr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <cstring>
+#include <string>
+
+#include "../../include/paulistr.h"
+
+namespace ps {
+
+// One string with its complex FP64 coefficient: 32 bytes, one DRAM sector.
+struct __align__(16) Rec {
+  uint64_t v, w;
+  double re, im;
+};
+
+struct Cx {
+  double re, im;
+};
+
+// ----------------------------------------------------------------------------- errors
+void set_cuda_error(cudaError_t e, const char* where);
+#define PS_CUDA(call)                                 \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) {                          \
+      ::ps::set_cuda_error(_e, #call);                \
+      return PS_ERR_CUDA;                             \
+    }                                                 \
+  } while (0)
+#define PS_TRY(expr)               \
+  do {                             \
+    int _s = (expr);               \
+    if (_s != PS_OK) return _s;    \
+  } while (0)
+
+// ----------------------------------------------------------------------------- memory
+// Stream-ordered device allocation (cudaMallocAsync on the stream's pool).  The
+// test hook pauli_debug_fail_alloc_after makes a chosen allocation fail on the host.
+int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// RAII scratch buffer freed in stream order.
+template <class T>
+struct Buf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { reset(); }
+  int alloc(size_t count, cudaStream_t stream) {
+    reset();
+    s = stream;
+    n = count;
+    if (count == 0) return PS_OK;
+    return dev_alloc((void**)&p, count * sizeof(T), stream);
+  }
+  void reset() {
+    if (p) dev_free(p, s);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+}  // namespace ps
+
+// The opaque sum (device resident).  `n` is the authoritative size; it is kept
+// current on the host after every call (calls that change it synchronise).
+struct pauli_sum {
+  int n_sites;
+  cudaStream_t stream;
+  ps::Rec* d;
+  int64_t cap;
+  int64_t n;
+};
+
+namespace ps {
+
+int sum_reserve(pauli_sum* s, int64_t cap, bool keep_contents);
+int sum_adopt(pauli_sum* s, Rec* d, int64_t cap, int64_t n);  // take ownership of a buffer
+uint64_t key_mask(int n_sites);
+
+// ----------------------------------------------------------------------------- output hash
+// F: a GF(2)-linear map from a 128-bit key to 32 bits, F_j(v,w) = parity((v & A_j) ^ (w & B_j)).
+// Linearity gives F(a ^ b) = F(a) ^ F(b): the bin of a product string is the XOR of the
+// bins of its factors, so products can be routed to bins without forming the key first.
+constexpr int kHashRows = 32;
+uint32_t host_hash(uint64_t v, uint64_t w, int bits);
+void host_hash_rows(const uint64_t** a, const uint64_t** b);
+// A key whose hash (low `bits` bits) is exactly `target`; the map has full rank.
+void host_key_with_hash(uint32_t target, int bits, uint64_t* v, uint64_t* w);
+int upload_hash_tables();  // merge.cu: copies the rows to its __constant__ tables
+
+// ----------------------------------------------------------------------------- Pauli algebra
+// Strings a, b anticommute iff popcount(wa&vb) + popcount(va&wb) is odd (eq. eps_com);
+// the parity of a sum of popcounts is the popcount parity of the XOR.
+__device__ __forceinline__ bool anticommute(uint64_t va, uint64_t wa, uint64_t vb, uint64_t wb) {
+  return (__popcll((wa & vb) ^ (va & wb)) & 1) != 0;
+}
+
+// P_a P_b = i^k P_{a^b} in the Hermitian basis P(v,w) = (-i)^{pop(v&w)} Z^v X^w:
+// k = pop(vc&wc) - pop(va&wa) - pop(vb&wb) + 2 pop(wa&vb) (mod 4)  (eq. eps12 rewritten).
+__device__ __forceinline__ int product_phase(uint64_t va, uint64_t wa, uint64_t vb, uint64_t wb) {
+  uint64_t vc = va ^ vb, wc = wa ^ wb;
+  int k = __popcll(vc & wc) - __popcll(va & wa) - __popcll(vb & wb) + 2 * __popcll(wa & vb);
+  return k & 3;
+}
+
+// Exactly-rounded FP64 operations without contraction into FMA.
+__device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+
+// 2*x, exact (exponent increment); falls back to x+x for zero, subnormal, huge or non-finite x.
+__device__ __forceinline__ double twice(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  if (e != 0u && e < 0x7FEu) return __longlong_as_double((long long)(b + (1ull << 52)));
+  return __dadd_rn(x, x);
+}
+
+// (a.re b.re - a.im b.im, a.re b.im + a.im b.re) with separately rounded products and sums.
+// Products with an exactly-zero factor are skipped: they are +-0 and do not change a
+// non-zero partial result, so every non-zero component is bit-identical to the full formula.
+__device__ __forceinline__ Cx cmul(Cx a, Cx b) {
+  double rr = (is_zero(a.re) || is_zero(b.re)) ? 0.0 : __dmul_rn(a.re, b.re);
+  double ii = (is_zero(a.im) || is_zero(b.im)) ? 0.0 : __dmul_rn(a.im, b.im);
+  double ri = (is_zero(a.re) || is_zero(b.im)) ? 0.0 : __dmul_rn(a.re, b.im);
+  double ir = (is_zero(a.im) || is_zero(b.re)) ? 0.0 : __dmul_rn(a.im, b.re);
+  Cx r;
+  r.re = is_zero(ii) ? rr : (is_zero(rr) ? -ii : __dsub_rn(rr, ii));
+  r.im = is_zero(ir) ? ri : (is_zero(ri) ? ir : __dadd_rn(ri, ir));
+  return r;
+}
+
+__device__ __forceinline__ Cx rot(Cx a, int k) {  // multiply by i^k (exact)
+  switch (k & 3) {
+    case 0: return a;
+    case 1: return Cx{-a.im, a.re};
+    case 2: return Cx{-a.re, -a.im};
+    default: return Cx{a.im, -a.re};
+  }
+}
+
+__device__ __forceinline__ double add_rn(double a, double b) {
+  if (is_zero(b)) return a;
+  if (is_zero(a)) return b;
+  return __dadd_rn(a, b);
+}
+
+// ----------------------------------------------------------------------------- profiling
+// Scoped around one kernel launch: counts the launch and, when profiling is enabled,
+// records CUDA events on the launching stream before and after it.
+class KTimer {
+ public:
+  KTimer(const char* name, cudaStream_t s);
+  ~KTimer();
+  KTimer(const KTimer&) = delete;
+  KTimer& operator=(const KTimer&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  void* a_;
+};
+#define PS_LAUNCH(name, stream, ...) \
+  do {                               \
+    ::ps::KTimer _kt(name, stream);  \
+    __VA_ARGS__;                     \
+  } while (0)
+
+// ----------------------------------------------------------------------------- misc
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int num_sms();
+int check_keys_device(const Rec* d, int64_t n, uint64_t mask, cudaStream_t s, bool* ok);
+int check_distinct_device(const Rec* d, int64_t n, cudaStream_t s, bool* ok);
+
+// Exclusive prefix sum of n unsigned values into out[0..n]; out[n] = total (device only).
+int scan_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s);
+int scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, cudaStream_t s);
+
+// Merge engine (merge.cu).  For every output string c the engine forms
+//   acc(c) = sequential sum, in order, of: the products 2 i^(k+rot) h x for each H term h
+//            (H order) with x in X and h^x = c, anticommuting; then alpha_s * y_s(c) for
+//            each extra source s in order;
+// and returns out(c) = acc(c)                    (no post scale), or
+//              out(c) = pre(c) + post * acc(c)    (with post; absent terms are zero).
+// Exact zeros are dropped.  This covers [H,X], A + alpha B, the Lanczos combination
+// [H,O] - b O_prev and the RK4 stage combinations.
+struct MergeSource {
+  const Rec* rec;
+  int64_t n;
+  Cx alpha;
+};
+struct MergeSpec {
+  const Rec* H = nullptr;
+  int nH = 0;
+  const Rec* X = nullptr;
+  int64_t nX = 0;
+  int rot = 0;
+  MergeSource src[4];
+  int nsrc = 0;
+  const Rec* pre = nullptr;
+  int64_t npre = 0;
+  bool has_post = false;
+  Cx post{1.0, 0.0};
+};
+int merge_run(const MergeSpec& spec, cudaStream_t s, pauli_sum* out);
+void record_merge_stats(const pauli_merge_stats& st);
+
+// truncate.cu / reduce.cu
+int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor);
+int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out);
+int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cudaStream_t s, double* re, double* im);
+
+}  // namespace ps

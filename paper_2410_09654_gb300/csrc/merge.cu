@@ -1,0 +1,672 @@
+// The merge engine: all-pairs H x X string products (Alg. 1 with eq. eps_com),
+// duplicate merging with the paper's summation order, and linear combinations.
+//
+// Data flow for one call (all on one stream):
+//   1. bins: every output string c goes to bin F(c) (low b bits of a GF(2)-linear
+//      hash).  For a product c = h ^ x, F(c) = F(h) ^ F(x), so the bin is known from
+//      the factors.  A per-bin upper bound (histogram of F(x) XOR-convolved with the
+//      F(h) of all H terms, plus the extra sources) gives each bin a fixed region.
+//   2. emit: one thread per x streams X once, tests it against every H term held in
+//      shared memory (XOR, AND, popcount parity) and appends a compact 8-byte entry
+//      (x index, h index) to the bin of each anticommuting product.  Extra sources
+//      append (index, source id) to bin F(y).
+//   3. group: consecutive bins are grouped so that a group holds <= kCap entries.
+//   4. merge: one CTA per group (persistent loop) rebuilds each contribution, inserts
+//      the product keys in a shared-memory hash table, counts per key, scatters the
+//      entries per key and sums each key's contributions in increasing order (H order,
+//      then the sources in order).  That is exactly the order in which Alg. 1 with H
+//      in the outer loop adds them, so the result is independent of scheduling.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ps {
+
+__constant__ uint64_t c_hashA[kHashRows];
+__constant__ uint64_t c_hashB[kHashRows];
+
+int upload_hash_tables() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    const uint64_t *a, *b;
+    host_hash_rows(&a, &b);
+    err = cudaMemcpyToSymbol(c_hashA, a, kHashRows * sizeof(uint64_t));
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_hashB, b, kHashRows * sizeof(uint64_t));
+  });
+  if (err != cudaSuccess) {
+    set_cuda_error(err, "cudaMemcpyToSymbol(hash rows)");
+    return PS_ERR_CUDA;
+  }
+  return PS_OK;
+}
+
+// Rows [lo, lo+bits) of the output hash.
+__device__ __forceinline__ uint32_t dev_hash(uint64_t v, uint64_t w, int lo, int bits) {
+  uint32_t f = 0;
+  for (int j = 0; j < bits; ++j) {
+    uint64_t t = (v & c_hashA[lo + j]) ^ (w & c_hashB[lo + j]);
+    f |= (uint32_t)(__popcll(t) & 1) << j;
+  }
+  return f;
+}
+
+namespace {
+
+constexpr int kCap = 2048;       // entries per merge pass
+constexpr int kTable = 2048;     // shared-memory hash slots (power of two)
+constexpr int kMergeThreads = 256;
+constexpr int kMaxProbe = 128;
+constexpr uint32_t kCodeSrc = 0xF000u;  // entry code of extra source s: kCodeSrc + s
+constexpr uint32_t kCodePre = 0xFFFFu;  // entry code of the `pre` operand
+constexpr int kMaxH = 0xEFFF;
+constexpr int kHChunk = 2048;    // H terms per emission launch (shared memory)
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t table_hash(uint64_t v, uint64_t w) {
+  uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w * 0xC2B2AE3D27D4EB4Full + 0x165667B19E3779F9ull);
+  h ^= h >> 29;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 32;
+  return (uint32_t)h;
+}
+
+__device__ __forceinline__ ulonglong2 cas128_shared(ulonglong2* p, ulonglong2 expect, ulonglong2 desired) {
+  ulonglong2 old;
+  unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile(
+      "{\n\t.reg .b128 d, b, c;\n\t"
+      "mov.b128 b, {%2, %3};\n\t"
+      "mov.b128 c, {%4, %5};\n\t"
+      "atom.shared.cas.b128 d, [%6], b, c;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(old.x), "=l"(old.y)
+      : "l"(expect.x), "l"(expect.y), "l"(desired.x), "l"(desired.y), "r"(addr)
+      : "memory");
+  return old;
+}
+
+// --------------------------------------------------------------------------- hashing
+__global__ void k_hash_hist(const Rec* __restrict__ r, int64_t n, int bits, uint32_t* __restrict__ f,
+                            uint32_t* __restrict__ hist) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) {
+    uint32_t h = dev_hash(r[i].v, r[i].w, 0, bits);
+    if (f) f[i] = h;
+    atomicAdd(&hist[h], 1u);
+  }
+}
+
+// bound[p] = histY[p] + sum_h histX[p ^ F(h)]: the number of (h, x) pairs routed to bin p,
+// plus the source entries of bin p.
+__global__ void k_bound(const uint32_t* __restrict__ histX, const uint32_t* __restrict__ histY,
+                        const uint32_t* __restrict__ fH, int nH, uint32_t nbins, uint64_t* __restrict__ bound) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nbins; p += gridDim.x * blockDim.x) {
+    uint64_t b = histY ? histY[p] : 0;
+    if (histX)
+      for (int h = 0; h < nH; ++h) b += histX[p ^ __ldg(&fH[h])];
+    bound[p] = b;
+  }
+}
+
+// --------------------------------------------------------------------------- emission
+// One thread per x; H terms [h0, h0+nh) in shared memory.
+__global__ void __launch_bounds__(256) k_emit_products(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
+                                                       int64_t nX, const Rec* __restrict__ H,
+                                                       const uint32_t* __restrict__ fH, int h0, int nh,
+                                                       const uint64_t* __restrict__ base, uint32_t* __restrict__ cnt,
+                                                       uint64_t* __restrict__ entries,
+                                                       unsigned long long* __restrict__ total) {
+  extern __shared__ unsigned char smem[];
+  ulonglong2* s_hk = reinterpret_cast<ulonglong2*>(smem);
+  uint32_t* s_hf = reinterpret_cast<uint32_t*>(smem + sizeof(ulonglong2) * nh);
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+    s_hk[i] = make_ulonglong2(H[h0 + i].v, H[h0 + i].w);
+    s_hf[i] = fH[h0 + i];
+  }
+  __syncthreads();
+  uint32_t mine = 0;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nX; i += stride) {
+    const ulonglong2 xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
+    const uint32_t fx = fX[i];
+    for (int h = 0; h < nh; ++h) {
+      const ulonglong2 hk = s_hk[h];
+      if (anticommute(hk.x, hk.y, xk.x, xk.y)) {
+        uint32_t p = fx ^ s_hf[h];
+        uint32_t pos = atomicAdd(&cnt[p], 1u);
+        entries[base[p] + pos] = ((uint64_t)i << 16) | (uint64_t)(h0 + h);
+        ++mine;
+      }
+    }
+  }
+  // block total
+  __shared__ unsigned long long s_tot;
+  if (threadIdx.x == 0) s_tot = 0;
+  __syncthreads();
+  for (int d = 16; d > 0; d >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, d);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_tot, (unsigned long long)mine);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
+}
+
+__global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, uint32_t code,
+                              const uint64_t* __restrict__ base, uint32_t* __restrict__ cnt,
+                              uint64_t* __restrict__ entries) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t p = dev_hash(Y[i].v, Y[i].w, 0, bits);
+    uint32_t pos = atomicAdd(&cnt[p], 1u);
+    entries[base[p] + pos] = ((uint64_t)i << 16) | code;
+  }
+}
+
+// --------------------------------------------------------------------------- grouping
+// Bin p opens a group when the running entry count crosses a multiple of `quota`, and at
+// the middle bin (so that no group spans both halves of the bin range).
+__global__ void k_group_flags(const uint64_t* __restrict__ cpre, uint32_t nbins, uint64_t quota,
+                              uint32_t* __restrict__ flag) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nbins; p += gridDim.x * blockDim.x) {
+    bool start = (p == 0) || (p == nbins / 2) || (cpre[p] / quota != cpre[p - 1] / quota);
+    flag[p] = start ? 1u : 0u;
+  }
+}
+
+__global__ void k_group_scatter(const uint32_t* __restrict__ flag, const uint64_t* __restrict__ fpre, uint32_t nbins,
+                                uint32_t* __restrict__ gstart, uint32_t* __restrict__ ngroups) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nbins; p += gridDim.x * blockDim.x)
+    if (flag[p]) gstart[fpre[p]] = p;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uint32_t g = (uint32_t)fpre[nbins];
+    *ngroups = g;
+    gstart[g] = nbins;
+  }
+}
+
+// --------------------------------------------------------------------------- merge
+struct MergeArgs {
+  const Rec* H;
+  int nH;
+  const Rec* X;
+  int rot;
+  const Rec* src[4];
+  Cx alpha[4];
+  const Rec* pre;
+  int has_post;
+  Cx post;
+  int bits;
+  uint32_t nbins;
+  const uint64_t* base;   // bin region starts
+  const uint32_t* cnt;    // bin fill counts
+  const uint64_t* cpre;   // exclusive prefix of cnt
+  const uint64_t* entries;
+  const uint32_t* gstart;
+  const uint32_t* ngroups;
+  unsigned* next_group;
+  Rec* out;
+  unsigned long long* out_n;
+  unsigned long long out_cap;
+  int* err;               // bit 0: capacity, bit 1: unresolved table overflow
+  unsigned* split_groups;
+  ulonglong2 sent_lo, sent_hi;  // empty-slot keys for groups in the lower / upper half
+};
+
+struct MergeSmem {
+  ulonglong2 key[kTable];
+  uint32_t cnt[kTable];
+  uint32_t off[kTable];
+  uint32_t cur[kTable];
+  uint32_t pre[kTable];
+  double ere[kCap];
+  double eim[kCap];
+  uint16_t eslot[kCap];
+  uint16_t eord[kCap];
+  uint16_t perm[kCap];
+  uint32_t wsum[kMergeThreads / 32];
+  uint32_t n_e;
+  int flags;
+  unsigned group;
+  unsigned long long out_base;
+};
+
+// Exclusive block scan of kTable counters in place (each thread owns kTable/blockDim consecutive slots).
+__device__ __forceinline__ uint32_t block_scan_table(MergeSmem& s, uint32_t* arr, uint32_t* out) {
+  constexpr int per = kTable / kMergeThreads;
+  const int t = threadIdx.x;
+  uint32_t local[per];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    local[k] = arr[t * per + k];
+    sum += local[k];
+  }
+  int lane = t & 31, warp = t >> 5;
+  uint32_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += u;
+  }
+  if (lane == 31) s.wsum[warp] = incl;
+  __syncthreads();
+  uint32_t wpre = 0, total = 0;
+  for (int k = 0; k < kMergeThreads / 32; ++k) {
+    uint32_t x = s.wsum[k];
+    if (k < warp) wpre += x;
+    total += x;
+  }
+  uint32_t run = wpre + incl - sum;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    out[t * per + k] = run;
+    run += local[k];
+  }
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ int table_insert(MergeSmem& s, ulonglong2 c, ulonglong2 sent) {
+  uint32_t slot = table_hash(c.x, c.y) & (kTable - 1);
+  for (int probe = 0; probe < kMaxProbe; ++probe) {
+    ulonglong2 k = s.key[slot];
+    if (k.x == c.x && k.y == c.y) return (int)slot;
+    if (k.x == sent.x && k.y == sent.y) {
+      ulonglong2 old = cas128_shared(&s.key[slot], sent, c);
+      if ((old.x == sent.x && old.y == sent.y) || (old.x == c.x && old.y == c.y)) return (int)slot;
+    }
+    slot = (slot + 1) & (kTable - 1);
+  }
+  return -1;
+}
+
+// Rebuild entry e of the group: its key, its contribution and its order code.
+__device__ __forceinline__ void decode_entry(const MergeArgs& a, uint64_t ent, ulonglong2& key, Cx& t,
+                                             uint32_t& code) {
+  code = (uint32_t)(ent & 0xFFFFu);
+  uint64_t idx = ent >> 16;
+  if (code < kCodeSrc) {
+    const Rec x = a.X[idx];
+    const Rec h = a.H[code];
+    key = make_ulonglong2(h.v ^ x.v, h.w ^ x.w);
+    int k = product_phase(h.v, h.w, x.v, x.w) + a.rot;
+    Cx p = cmul(Cx{h.re, h.im}, Cx{x.re, x.im});
+    t = rot(Cx{twice(p.re), twice(p.im)}, k);
+  } else if (code == kCodePre) {
+    const Rec y = a.pre[idx];
+    key = make_ulonglong2(y.v, y.w);
+    t = Cx{y.re, y.im};
+  } else {
+    uint32_t sidx = code - kCodeSrc;
+    const Rec y = a.src[sidx][idx];
+    key = make_ulonglong2(y.v, y.w);
+    t = cmul(a.alpha[sidx], Cx{y.re, y.im});
+  }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MergeSmem& s = *reinterpret_cast<MergeSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const uint32_t ngroups = *a.ngroups;
+
+  for (;;) {
+    if (tid == 0) s.group = atomicAdd(a.next_group, 1u);
+    __syncthreads();
+    const uint32_t g = s.group;
+    __syncthreads();
+    if (g >= ngroups) break;
+    const uint32_t lo = a.gstart[g], hi = a.gstart[g + 1];
+    const uint64_t e0 = a.cpre[lo];
+    const uint64_t E = a.cpre[hi] - e0;
+    if (E == 0) continue;
+    const ulonglong2 sent = (lo >= a.nbins / 2) ? a.sent_hi : a.sent_lo;
+
+    int level = 0;  // split level: sub-pass j keeps keys whose extra hash bits equal j
+    while ((uint64_t)kCap << level < 2 * E && level < 16) ++level;
+    if (a.bits + level > kHashRows) {  // cannot split this far: report, skip the group
+      if (tid == 0) atomicOr(a.err, 2);
+      continue;
+    }
+    if (level > 0 && tid == 0) atomicAdd(a.split_groups, 1u);
+
+    for (uint32_t sub = 0; sub < (1u << level);) {
+      // ---- phase 0: clear
+      for (int i = tid; i < kTable; i += kMergeThreads) {
+        s.key[i] = sent;
+        s.cnt[i] = 0;
+        s.cur[i] = 0;
+        s.pre[i] = kNone;
+      }
+      if (tid == 0) {
+        s.n_e = 0;
+        s.flags = 0;
+      }
+      __syncthreads();
+      // ---- phase 1: rebuild entries, insert keys, count per key
+      for (uint64_t j = tid; j < E; j += kMergeThreads) {
+        // locate bin of flat entry j (binary search on the prefix of bin counts)
+        uint32_t l = lo, r = hi;  // cpre[l] - e0 <= j < cpre[r] - e0
+        while (r - l > 1) {
+          uint32_t m = (l + r) >> 1;
+          if (a.cpre[m] - e0 <= j) l = m; else r = m;
+        }
+        uint64_t ent = a.entries[a.base[l] + (j - (a.cpre[l] - e0))];
+        ulonglong2 key;
+        Cx t;
+        uint32_t code;
+        decode_entry(a, ent, key, t, code);
+        if (level > 0) {
+          uint32_t fx = dev_hash(key.x, key.y, a.bits, level);
+          if (fx != sub) continue;
+        }
+        uint32_t e = atomicAdd(&s.n_e, 1u);
+        if (e >= (uint32_t)kCap) {
+          atomicOr(&s.flags, 1);
+          continue;
+        }
+        int slot = table_insert(s, key, sent);
+        if (slot < 0) {
+          atomicOr(&s.flags, 1);
+          continue;
+        }
+        s.eslot[e] = (uint16_t)slot;
+        s.ere[e] = t.re;
+        s.eim[e] = t.im;
+        if (code == kCodePre) {
+          s.eord[e] = 0xFFFF;
+          s.pre[slot] = e;
+        } else {
+          s.eord[e] = (uint16_t)code;
+          atomicAdd(&s.cnt[slot], 1u);
+        }
+      }
+      __syncthreads();
+      if (s.flags) {  // this pass did not fit: split further and restart the group
+        __syncthreads();
+        if (level >= 16 || a.bits + level + 1 > kHashRows) {
+          if (tid == 0) atomicOr(a.err, 2);
+          break;
+        }
+        if (level == 0 && tid == 0) atomicAdd(a.split_groups, 1u);
+        ++level;
+        sub = 0;
+        continue;
+      }
+      const uint32_t n_e = s.n_e;
+      // ---- phase 2: offsets of each key's entry list
+      block_scan_table(s, s.cnt, s.off);
+      // ---- phase 3: scatter entry indices per key
+      for (uint32_t e = tid; e < n_e; e += kMergeThreads) {
+        if (s.eord[e] == 0xFFFF) continue;
+        uint32_t slot = s.eslot[e];
+        uint32_t pos = s.off[slot] + atomicAdd(&s.cur[slot], 1u);
+        s.perm[pos] = (uint16_t)e;
+      }
+      __syncthreads();
+      // ---- phase 4: per key, sum contributions in increasing order code
+      for (int slot = tid; slot < kTable; slot += kMergeThreads) {
+        uint32_t n = s.cnt[slot];
+        uint32_t pe = s.pre[slot];
+        uint32_t outflag = 0, res = kNone;
+        if (n > 0 || pe != kNone) {
+          const uint32_t o = s.off[slot];
+          Cx acc{0.0, 0.0};
+          int last = -1;
+          for (uint32_t m = 0; m < n; ++m) {  // selection in (order code, entry) order
+            int best = 0x7FFFFFFF, bi = -1;
+            for (uint32_t q = 0; q < n; ++q) {
+              int e = (int)s.perm[o + q];
+              int key = ((int)s.eord[e] << 11) | e;
+              if (key > last && key < best) { best = key; bi = e; }
+            }
+            if (bi < 0) break;
+            last = best;
+            Cx t{s.ere[bi], s.eim[bi]};
+            if (m == 0) acc = t;
+            else { acc.re = add_rn(acc.re, t.re); acc.im = add_rn(acc.im, t.im); }
+          }
+          Cx r;
+          if (a.has_post) {
+            Cx sc = (n > 0) ? cmul(a.post, acc) : Cx{0.0, 0.0};
+            if (pe != kNone) {
+              Cx pv{s.ere[pe], s.eim[pe]};
+              r = (n > 0) ? Cx{add_rn(pv.re, sc.re), add_rn(pv.im, sc.im)} : pv;
+            } else {
+              r = sc;
+            }
+          } else {
+            r = acc;
+          }
+          if (!(is_zero(r.re) && is_zero(r.im))) {
+            outflag = 1;
+            res = (n > 0) ? (uint32_t)s.perm[o] : pe;
+            s.ere[res] = r.re;
+            s.eim[res] = r.im;
+          }
+        }
+        s.cur[slot] = res;
+        s.cnt[slot] = outflag;
+      }
+      __syncthreads();
+      // ---- phase 5: compact and write
+      uint32_t U = block_scan_table(s, s.cnt, s.off);
+      if (tid == 0) s.out_base = U ? atomicAdd(a.out_n, (unsigned long long)U) : 0ull;
+      __syncthreads();
+      const unsigned long long ob = s.out_base;
+      if (ob + U > a.out_cap) {
+        if (tid == 0) atomicOr(a.err, 1);
+      } else {
+        for (int slot = tid; slot < kTable; slot += kMergeThreads) {
+          if (!s.cnt[slot]) continue;
+          uint32_t res = s.cur[slot];
+          ulonglong2 k = s.key[slot];
+          a.out[ob + s.off[slot]] = Rec{k.x, k.y, s.ere[res], s.eim[res]};
+        }
+      }
+      __syncthreads();
+      ++sub;
+    }
+  }
+}
+
+int choose_bits(int64_t bound_total) {
+  int b = 4;
+  while (b < 20 && ((int64_t)1 << b) * 2048 < bound_total) ++b;
+  return b;
+}
+
+std::mutex g_stats_mu;
+pauli_merge_stats g_stats{};
+
+}  // namespace
+
+void record_merge_stats(const pauli_merge_stats& st) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  g_stats = st;
+}
+
+int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
+  PS_TRY(upload_hash_tables());
+  if (sp.nH > kMaxH || sp.nsrc > 4) return PS_ERR_INVALID;
+  const int64_t nX = (sp.X && sp.nH > 0) ? sp.nX : 0;
+  int64_t nsrc_total = sp.npre;
+  for (int i = 0; i < sp.nsrc; ++i) nsrc_total += sp.src[i].n;
+  const int64_t pairs = (int64_t)sp.nH * nX;
+  const int64_t bound_total = pairs + nsrc_total;
+  pauli_merge_stats st{};
+  st.pair_tests = pairs;
+  if (bound_total == 0) {
+    out->n = 0;
+    record_merge_stats(st);
+    return PS_OK;
+  }
+  const int bits = choose_bits(bound_total);
+  const uint32_t nbins = 1u << bits;
+  const int nsm = num_sms();
+
+  Buf<uint32_t> fX, fH, histX, histY, cnt, flag, gstart;
+  Buf<uint64_t> bound, base, cpre, fpre, entries;
+  Buf<unsigned long long> counters;  // [0] product entries, [1] out_n
+  Buf<unsigned> misc;                // [0] next_group, [1] ngroups, [2] split groups
+  Buf<int> err;
+  PS_TRY(histY.alloc(nbins, s));
+  PS_TRY(cnt.alloc(nbins, s));
+  PS_TRY(bound.alloc(nbins, s));
+  PS_TRY(base.alloc(nbins + 1, s));
+  PS_TRY(counters.alloc(2, s));
+  PS_TRY(misc.alloc(3, s));
+  PS_TRY(err.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(histY.p, 0, nbins * sizeof(uint32_t), s));
+  PS_CUDA(cudaMemsetAsync(cnt.p, 0, nbins * sizeof(uint32_t), s));
+  PS_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), s));
+  PS_CUDA(cudaMemsetAsync(misc.p, 0, 3 * sizeof(unsigned), s));
+  PS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+
+  auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
+
+  // 1. hashes, histograms and bin bounds
+  if (nX > 0) {
+    PS_TRY(fX.alloc(nX, s));
+    PS_TRY(histX.alloc(nbins, s));
+    PS_CUDA(cudaMemsetAsync(histX.p, 0, nbins * sizeof(uint32_t), s));
+    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
+    PS_CUDA(cudaGetLastError());
+    std::vector<uint32_t> hf(sp.nH);
+    std::vector<Rec> hh(sp.nH);
+    PS_CUDA(cudaMemcpyAsync(hh.data(), sp.H, sp.nH * sizeof(Rec), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < sp.nH; ++i) hf[i] = host_hash(hh[i].v, hh[i].w, bits);
+    PS_TRY(fH.alloc(sp.nH, s));
+    PS_CUDA(cudaMemcpyAsync(fH.p, hf.data(), sp.nH * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  }
+  for (int i = 0; i < sp.nsrc; ++i)
+    if (sp.src[i].n > 0) {
+      PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
+      PS_CUDA(cudaGetLastError());
+    }
+  if (sp.npre > 0) {
+    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, nullptr, histY.p));
+    PS_CUDA(cudaGetLastError());
+  }
+  {
+    int nh = nX > 0 ? sp.nH : 0;
+    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
+    PS_LAUNCH("k_bound", s, k_bound<<<blocks, 256, 0, s>>>(nX > 0 ? histX.p : nullptr, histY.p, fH.p, nh, nbins, bound.p));
+    PS_CUDA(cudaGetLastError());
+  }
+  PS_TRY(scan_u64(bound.p, base.p, nbins, s));
+  PS_TRY(entries.alloc((size_t)bound_total, s));
+
+  // 2. emission
+  if (nX > 0) {
+    for (int h0 = 0; h0 < sp.nH; h0 += kHChunk) {
+      int nh = std::min(kHChunk, sp.nH - h0);
+      size_t sm = (size_t)nh * (sizeof(ulonglong2) + sizeof(uint32_t));
+      if (sm > 48 * 1024) PS_CUDA(cudaFuncSetAttribute(k_emit_products, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      PS_LAUNCH("k_emit_products", s, k_emit_products<<<grid_for(nX), 256, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, h0, nh, base.p, cnt.p, entries.p,
+                                                     counters.p));
+      PS_CUDA(cudaGetLastError());
+    }
+  }
+  for (int i = 0; i < sp.nsrc; ++i)
+    if (sp.src[i].n > 0) {
+      PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, kCodeSrc + i, base.p,
+                                                          cnt.p, entries.p));
+      PS_CUDA(cudaGetLastError());
+    }
+  if (sp.npre > 0) {
+    PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, kCodePre, base.p, cnt.p, entries.p));
+    PS_CUDA(cudaGetLastError());
+  }
+  unsigned long long n_prod = 0;
+  PS_CUDA(cudaMemcpyAsync(&n_prod, counters.p, sizeof(n_prod), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  const int64_t total_entries = (int64_t)n_prod + nsrc_total;
+  st.contributions = (int64_t)n_prod;
+
+  // 3. groups
+  PS_TRY(cpre.alloc(nbins + 1, s));
+  PS_TRY(scan_u32_to_u64(cnt.p, cpre.p, nbins, s));
+  PS_TRY(flag.alloc(nbins, s));
+  PS_TRY(fpre.alloc(nbins + 1, s));
+  PS_TRY(gstart.alloc(nbins + 1, s));
+  {
+    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
+    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)kCap / 2, flag.p));
+    PS_CUDA(cudaGetLastError());
+    PS_TRY(scan_u32_to_u64(flag.p, fpre.p, nbins, s));
+    PS_LAUNCH("k_group_scatter", s, k_group_scatter<<<blocks, 256, 0, s>>>(flag.p, fpre.p, nbins, gstart.p, misc.p + 1));
+    PS_CUDA(cudaGetLastError());
+  }
+
+  // 4. merge into a fresh output buffer
+  int64_t out_cap = std::max<int64_t>(total_entries, 1);
+  Rec* outbuf = nullptr;
+  PS_TRY(dev_alloc((void**)&outbuf, (size_t)out_cap * sizeof(Rec), s));
+  MergeArgs a{};
+  a.H = sp.H;
+  a.nH = sp.nH;
+  a.X = sp.X;
+  a.rot = sp.rot;
+  for (int i = 0; i < sp.nsrc; ++i) {
+    a.src[i] = sp.src[i].rec;
+    a.alpha[i] = sp.src[i].alpha;
+  }
+  a.pre = sp.pre;
+  a.has_post = sp.has_post ? 1 : 0;
+  a.post = sp.post;
+  a.bits = bits;
+  a.nbins = nbins;
+  a.base = base.p;
+  a.cnt = cnt.p;
+  a.cpre = cpre.p;
+  a.entries = entries.p;
+  a.gstart = gstart.p;
+  a.ngroups = misc.p + 1;
+  a.next_group = misc.p;
+  a.out = outbuf;
+  a.out_n = counters.p + 1;
+  a.out_cap = (unsigned long long)out_cap;
+  a.err = err.p;
+  a.split_groups = misc.p + 2;
+  uint64_t kv, kw;
+  host_key_with_hash(nbins / 2, bits, &kv, &kw);  // hash in the upper half: empty key for lower-half groups
+  a.sent_lo = make_ulonglong2(kv, kw);
+  a.sent_hi = make_ulonglong2(0ull, 0ull);        // hash 0: empty key for upper-half groups
+  size_t sm = sizeof(MergeSmem);
+  PS_CUDA(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int per_sm = 0;
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge, kMergeThreads, sm));
+  int grid = std::max(1, per_sm) * nsm;
+  PS_LAUNCH("k_merge", s, k_merge<<<grid, kMergeThreads, sm, s>>>(a));
+  PS_CUDA(cudaGetLastError());
+  unsigned long long hres[2];
+  unsigned hmisc[3];
+  int herr = 0;
+  PS_CUDA(cudaMemcpyAsync(hres, counters.p, sizeof(hres), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaMemcpyAsync(hmisc, misc.p, sizeof(hmisc), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  if (herr) {
+    dev_free(outbuf, s);
+    return (herr & 2) ? PS_ERR_TABLE_FULL : PS_ERR_CAPACITY;
+  }
+  PS_TRY(sum_adopt(out, outbuf, out_cap, (int64_t)hres[1]));
+  st.merged = (int64_t)hres[1];
+  st.groups = hmisc[1];
+  st.split_groups = hmisc[2];
+  record_merge_stats(st);
+  return PS_OK;
+}
+
+}  // namespace ps
+
+extern "C" int pauli_last_merge_stats(pauli_merge_stats* out) {
+  if (!out) return PS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ps::g_stats_mu);
+  *out = ps::g_stats;
+  return PS_OK;
+}

@@ -1,0 +1,429 @@
+// Sums: creation, upload/download, memory, status strings, the output-hash tables
+// and small validation kernels.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ps {
+
+// ----------------------------------------------------------------------------- errors
+static thread_local std::string g_last_cuda_error;
+
+void set_cuda_error(cudaError_t e, const char* where) {
+  g_last_cuda_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e) + " (" + where + ")";
+}
+
+// ----------------------------------------------------------------------------- memory
+static std::atomic<int64_t> g_fail_after{0};
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  int64_t f = g_fail_after.load();
+  if (f > 0) {
+    if (g_fail_after.fetch_sub(1) == 1) return PS_ERR_NOMEM;
+  }
+  static std::once_flag once;
+  std::call_once(once, [] {
+    // Keep freed blocks in the pool instead of returning them to the driver.
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    *p = nullptr;
+    return PS_ERR_NOMEM;
+  }
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "cudaMallocAsync");
+    *p = nullptr;
+    return PS_ERR_CUDA;
+  }
+  return PS_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+uint64_t key_mask(int n_sites) { return n_sites >= 64 ? ~0ull : ((1ull << n_sites) - 1); }
+
+int sum_reserve(pauli_sum* s, int64_t cap, bool keep_contents) {
+  if (cap <= s->cap) return PS_OK;
+  int64_t nc = std::max<int64_t>(cap, 64);
+  Rec* d = nullptr;
+  PS_TRY(dev_alloc((void**)&d, (size_t)nc * sizeof(Rec), s->stream));
+  if (keep_contents && s->n > 0) PS_CUDA(cudaMemcpyAsync(d, s->d, (size_t)s->n * sizeof(Rec), cudaMemcpyDeviceToDevice, s->stream));
+  dev_free(s->d, s->stream);
+  s->d = d;
+  s->cap = nc;
+  return PS_OK;
+}
+
+int sum_adopt(pauli_sum* s, Rec* d, int64_t cap, int64_t n) {
+  dev_free(s->d, s->stream);
+  s->d = d;
+  s->cap = cap;
+  s->n = n;
+  return PS_OK;
+}
+
+// ----------------------------------------------------------------------------- output hash
+static uint64_t splitmix(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct HashRows {
+  uint64_t a[kHashRows], b[kHashRows];
+  HashRows() {
+    uint64_t s = 0x5EED2410096540ull;
+    for (int j = 0; j < kHashRows; ++j) {
+      a[j] = splitmix(s);
+      b[j] = splitmix(s);
+    }
+  }
+};
+static const HashRows g_rows;
+
+void host_hash_rows(const uint64_t** a, const uint64_t** b) {
+  *a = g_rows.a;
+  *b = g_rows.b;
+}
+
+uint32_t host_hash(uint64_t v, uint64_t w, int bits) {
+  uint32_t f = 0;
+  for (int j = 0; j < bits; ++j) {
+    uint64_t t = (v & g_rows.a[j]) ^ (w & g_rows.b[j]);
+    f |= (uint32_t)(__builtin_popcountll(t) & 1) << j;
+  }
+  return f;
+}
+
+// Solve F(v,w) = target on the low `bits` rows by Gaussian elimination over GF(2).
+void host_key_with_hash(uint32_t target, int bits, uint64_t* v, uint64_t* w) {
+  struct Row { uint64_t a, b; uint32_t rhs; };
+  std::vector<Row> rows(bits);
+  for (int j = 0; j < bits; ++j) rows[j] = {g_rows.a[j], g_rows.b[j], (target >> j) & 1u};
+  std::vector<int> pivot_col(bits, -1);
+  int r = 0;
+  for (int col = 0; col < 128 && r < bits; ++col) {
+    auto getbit = [&](const Row& x) { return col < 64 ? (x.a >> col) & 1 : (x.b >> (col - 64)) & 1; };
+    int p = -1;
+    for (int i = r; i < bits; ++i)
+      if (getbit(rows[i])) { p = i; break; }
+    if (p < 0) continue;
+    std::swap(rows[p], rows[r]);
+    for (int i = 0; i < bits; ++i)
+      if (i != r && getbit(rows[i])) {
+        rows[i].a ^= rows[r].a;
+        rows[i].b ^= rows[r].b;
+        rows[i].rhs ^= rows[r].rhs;
+      }
+    pivot_col[r] = col;
+    ++r;
+  }
+  uint64_t kv = 0, kw = 0;
+  for (int i = 0; i < r; ++i)
+    if (rows[i].rhs) {
+      int col = pivot_col[i];
+      if (col < 64) kv |= 1ull << col; else kw |= 1ull << (col - 64);
+    }
+  *v = kv;
+  *w = kw;
+}
+
+// ----------------------------------------------------------------------------- validation kernels
+__global__ void k_check_bits(const Rec* __restrict__ d, int64_t n, uint64_t inv_mask, int* bad) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride)
+    if ((d[i].v | d[i].w) & inv_mask) atomicOr(bad, 1);
+}
+
+int check_keys_device(const Rec* d, int64_t n, uint64_t mask, cudaStream_t s, bool* ok) {
+  *ok = true;
+  if (n == 0 || mask == ~0ull) return PS_OK;
+  Buf<int> bad;
+  PS_TRY(bad.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
+  PS_LAUNCH("k_check_bits", s, k_check_bits<<<blocks, 256, 0, s>>>(d, n, ~mask, bad.p));
+  PS_CUDA(cudaGetLastError());
+  int h = 0;
+  PS_CUDA(cudaMemcpyAsync(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  *ok = (h == 0);
+  return PS_OK;
+}
+
+__device__ __forceinline__ uint32_t mix32(uint64_t v, uint64_t w) {
+  uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w + 0x632BE59BD9B4E019ull);
+  h ^= h >> 32;
+  h *= 0xD6E8FEB86659FD93ull;
+  h ^= h >> 32;
+  return (uint32_t)h;
+}
+
+__device__ __forceinline__ void cas128_global(ulonglong2* p, ulonglong2 expect, ulonglong2 desired, ulonglong2& old) {
+  asm volatile(
+      "{\n\t.reg .b128 d, b, c;\n\t"
+      "mov.b128 b, {%2, %3};\n\t"
+      "mov.b128 c, {%4, %5};\n\t"
+      "atom.global.cas.b128 d, [%6], b, c;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(old.x), "=l"(old.y)
+      : "l"(expect.x), "l"(expect.y), "l"(desired.x), "l"(desired.y), "l"(p)
+      : "memory");
+}
+
+// Insert every key into an open-addressing table of 2^k slots (empty = all ones);
+// a key found already present is a duplicate.  The all-ones key itself is counted aside.
+__global__ void k_distinct(const Rec* __restrict__ d, int64_t n, ulonglong2* table, uint64_t tmask, int* dup,
+                           int* ones) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const ulonglong2 empty = make_ulonglong2(~0ull, ~0ull);
+  for (; i < n; i += stride) {
+    ulonglong2 k = make_ulonglong2(d[i].v, d[i].w);
+    if (k.x == ~0ull && k.y == ~0ull) {
+      if (atomicAdd(ones, 1) > 0) atomicOr(dup, 1);
+      continue;
+    }
+    uint64_t slot = mix32(k.x, k.y) & tmask;
+    for (uint64_t probe = 0; probe <= tmask; ++probe) {
+      ulonglong2 old;
+      cas128_global(&table[slot], empty, k, old);
+      if (old.x == empty.x && old.y == empty.y) break;     // inserted
+      if (old.x == k.x && old.y == k.y) { atomicOr(dup, 1); break; }
+      slot = (slot + 1) & tmask;
+    }
+  }
+}
+
+int check_distinct_device(const Rec* d, int64_t n, cudaStream_t s, bool* ok) {
+  *ok = true;
+  if (n <= 1) return PS_OK;
+  uint64_t slots = 1;
+  while (slots < (uint64_t)(2 * n)) slots <<= 1;
+  Buf<ulonglong2> table;
+  Buf<int> flags;
+  PS_TRY(table.alloc(slots, s));
+  PS_TRY(flags.alloc(2, s));
+  PS_CUDA(cudaMemsetAsync(table.p, 0xFF, slots * sizeof(ulonglong2), s));
+  PS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
+  int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
+  PS_LAUNCH("k_distinct", s, k_distinct<<<blocks, 256, 0, s>>>(d, n, table.p, slots - 1, flags.p, flags.p + 1));
+  PS_CUDA(cudaGetLastError());
+  int h[2];
+  PS_CUDA(cudaMemcpyAsync(h, flags.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  *ok = (h[0] == 0);
+  return PS_OK;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+// ============================================================================= C ABI
+extern "C" {
+
+const char* pauli_status_string(int status) {
+  switch (status) {
+    case PS_OK: return "ok";
+    case PS_ERR_INVALID: return "invalid argument";
+    case PS_ERR_CAPACITY: return "capacity too small";
+    case PS_ERR_TABLE_FULL: return "merge table full";
+    case PS_ERR_CUDA: return "CUDA error";
+    case PS_ERR_TIMEOUT: return "device wait timed out";
+    case PS_ERR_KRYLOV_EXHAUSTED: return "Krylov space exhausted (b_n = 0)";
+    case PS_ERR_NOMEM: return "device out of memory";
+    case PS_ERR_UNCERTAIN: return "result rounding uncertain";
+    default: return "unknown status";
+  }
+}
+
+const char* pauli_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int pauli_debug_fail_alloc_after(int64_t n) {
+  g_fail_after.store(n < 0 ? 0 : n);
+  return PS_OK;
+}
+
+int pauli_sum_create(int n_sites, int64_t capacity, void* cuda_stream, pauli_sum** out) {
+  if (!out || n_sites < 1 || n_sites > 64 || capacity < 0) return PS_ERR_INVALID;
+  *out = nullptr;
+  PS_TRY(upload_hash_tables());
+  pauli_sum* s = new pauli_sum{n_sites, (cudaStream_t)cuda_stream, nullptr, 0, 0};
+  int st = sum_reserve(s, std::max<int64_t>(capacity, 64), false);
+  if (st != PS_OK) {
+    delete s;
+    return st;
+  }
+  *out = s;
+  return PS_OK;
+}
+
+int pauli_sum_destroy(pauli_sum* s) {
+  if (!s) return PS_ERR_INVALID;
+  dev_free(s->d, s->stream);
+  delete s;
+  return PS_OK;
+}
+
+int pauli_sum_n_sites(const pauli_sum* s, int* n_sites) {
+  if (!s || !n_sites) return PS_ERR_INVALID;
+  *n_sites = s->n_sites;
+  return PS_OK;
+}
+
+int pauli_sum_size(const pauli_sum* s, int64_t* n) {
+  if (!s || !n) return PS_ERR_INVALID;
+  PS_CUDA(cudaStreamSynchronize(s->stream));
+  *n = s->n;
+  return PS_OK;
+}
+
+__global__ void k_pack(Rec* __restrict__ d, const uint64_t* __restrict__ v, const uint64_t* __restrict__ w,
+                       const double* __restrict__ re, const double* __restrict__ im, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) d[i] = Rec{v[i], w[i], re[i], im[i]};
+}
+
+int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re, const double* im,
+                     int64_t n) {
+  if (!s || n < 0 || (n > 0 && (!v || !w || !re || !im))) return PS_ERR_INVALID;
+  PS_TRY(sum_reserve(s, n, false));
+  s->n = 0;
+  if (n > 0) {
+    // four host->device copies into a staging area, then one packing kernel
+    Buf<uint64_t> stage;
+    PS_TRY(stage.alloc((size_t)n * 4, s->stream));
+    uint64_t* dv = stage.p;
+    uint64_t* dw = stage.p + n;
+    double* dre = reinterpret_cast<double*>(stage.p + 2 * n);
+    double* dim = reinterpret_cast<double*>(stage.p + 3 * n);
+    const size_t bytes = (size_t)n * sizeof(uint64_t);
+    PS_CUDA(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, s->stream));
+    PS_CUDA(cudaMemcpyAsync(dw, w, bytes, cudaMemcpyHostToDevice, s->stream));
+    PS_CUDA(cudaMemcpyAsync(dre, re, bytes, cudaMemcpyHostToDevice, s->stream));
+    PS_CUDA(cudaMemcpyAsync(dim, im, bytes, cudaMemcpyHostToDevice, s->stream));
+    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
+    PS_LAUNCH("k_pack", s->stream, k_pack<<<blocks, 256, 0, s->stream>>>(s->d, dv, dw, dre, dim, n));
+    PS_CUDA(cudaGetLastError());
+  }
+  bool ok = true;
+  PS_TRY(check_keys_device(s->d, n, key_mask(s->n_sites), s->stream, &ok));
+  if (ok) PS_TRY(check_distinct_device(s->d, n, s->stream, &ok));
+  PS_CUDA(cudaStreamSynchronize(s->stream));  // the caller's host arrays may be released on return
+  if (!ok) return PS_ERR_INVALID;
+  s->n = n;
+  return PS_OK;
+}
+
+__global__ void k_unpack(const Rec* __restrict__ d, uint64_t* __restrict__ v, uint64_t* __restrict__ w,
+                         double* __restrict__ re, double* __restrict__ im, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) {
+    Rec r = d[i];
+    v[i] = r.v;
+    w[i] = r.w;
+    re[i] = r.re;
+    im[i] = r.im;
+  }
+}
+
+int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re,
+                            const double* im, int64_t n) {
+  if (!s || n < 0 || (n > 0 && (!v || !w || !re || !im))) return PS_ERR_INVALID;
+  PS_TRY(sum_reserve(s, n, false));
+  if (n > 0) {
+    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
+    PS_LAUNCH("k_pack", s->stream, k_pack<<<blocks, 256, 0, s->stream>>>(s->d, v, w, re, im, n));
+    PS_CUDA(cudaGetLastError());
+  }
+  s->n = n;
+  bool ok = true;
+  PS_TRY(check_keys_device(s->d, n, key_mask(s->n_sites), s->stream, &ok));
+  if (!ok) {
+    s->n = 0;
+    return PS_ERR_INVALID;
+  }
+  return PS_OK;
+}
+
+int pauli_sum_download(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im, int64_t cap,
+                       int64_t* n) {
+  if (!s || !n) return PS_ERR_INVALID;
+  PS_CUDA(cudaStreamSynchronize(s->stream));
+  *n = s->n;
+  if (cap < s->n) return PS_ERR_CAPACITY;
+  if (s->n == 0) return PS_OK;
+  if (!v || !w || !re || !im) return PS_ERR_INVALID;
+  std::vector<Rec> h((size_t)s->n);
+  PS_CUDA(cudaMemcpyAsync(h.data(), s->d, (size_t)s->n * sizeof(Rec), cudaMemcpyDeviceToHost, s->stream));
+  PS_CUDA(cudaStreamSynchronize(s->stream));
+  std::sort(h.begin(), h.end(), [](const Rec& a, const Rec& b) { return a.v < b.v || (a.v == b.v && a.w < b.w); });
+  for (int64_t i = 0; i < s->n; ++i) {
+    v[i] = h[(size_t)i].v;
+    w[i] = h[(size_t)i].w;
+    re[i] = h[(size_t)i].re;
+    im[i] = h[(size_t)i].im;
+  }
+  return PS_OK;
+}
+
+int pauli_sum_download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im, int64_t cap,
+                              int64_t* n) {
+  if (!s || !n) return PS_ERR_INVALID;
+  *n = s->n;
+  if (cap < s->n) return PS_ERR_CAPACITY;
+  if (s->n == 0) return PS_OK;
+  if (!v || !w || !re || !im) return PS_ERR_INVALID;
+  int blocks = (int)std::min<int64_t>(ceil_div(s->n, 256), 8 * num_sms());
+  PS_LAUNCH("k_unpack", s->stream, k_unpack<<<blocks, 256, 0, s->stream>>>(s->d, v, w, re, im, s->n));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst) {
+  if (!src || !dst || src->n_sites != dst->n_sites) return PS_ERR_INVALID;
+  if (src == dst) return PS_OK;
+  PS_TRY(sum_reserve(dst, src->n, false));
+  if (src->n > 0) {
+    if (src->stream != dst->stream) PS_CUDA(cudaStreamSynchronize(src->stream));
+    PS_CUDA(cudaMemcpyAsync(dst->d, src->d, (size_t)src->n * sizeof(Rec), cudaMemcpyDeviceToDevice, dst->stream));
+  }
+  dst->n = src->n;
+  return PS_OK;
+}
+
+}  // extern "C"

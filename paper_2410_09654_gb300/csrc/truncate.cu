@@ -1,0 +1,311 @@
+// Truncation (paper: trim(O, M; keep), cutoff(O, eps), discarding long strings,
+// add_noise(O, eps*dt)):
+//   1. optional division by a real b (the Lanczos normalisation O = A/b);
+//   2. depolarising transmission c *= exp(-(gamma*dt) * wt), wt = popcount(v|w);
+//   3. drop wt > max_weight; drop exact zeros; drop |c|^2 < cutoff^2;
+//   4. keep the top_k by |c|^2 = re*re + im*im, exact ties to the smaller key (v, then w),
+//      never dropping a string of the keep set.
+// Step 4 is a most-significant-digit radix select over the 192-bit rank key
+// (|c|^2 bits, ~v, ~w): all rank keys are distinct, so exactly top_k strings
+// outrank the selected threshold.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr int kDigitBits = 11;
+constexpr int kBins = 1 << kDigitBits;
+constexpr int kPasses = (192 + kDigitBits - 1) / kDigitBits;  // 18
+
+struct TruncArgs {
+  int max_weight;
+  double cut2;
+  int use_cut;
+  int use_gamma;
+  int use_div;
+  double divisor;
+  const double* factor;  // exp(-(gamma*dt) w), w = 0..64
+};
+
+__device__ __forceinline__ double sq_sum(double re, double im) {
+  double a = is_zero(re) ? 0.0 : __dmul_rn(re, re);
+  double b = is_zero(im) ? 0.0 : __dmul_rn(im, im);
+  return add_rn(a, b);
+}
+
+// Steps 1-3 with compaction (order of survivors is unspecified).
+__global__ void k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a, Rec* __restrict__ out,
+                         unsigned long long* __restrict__ n_out) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t iters = ceil_div_dev(n, stride);
+  for (int64_t it = 0; it < iters; ++it) {
+    int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool keep = false;
+    Rec r;
+    if (i < n) {
+      r = in[i];
+      if (a.use_div) {
+        r.re = is_zero(r.re) ? r.re : __ddiv_rn(r.re, a.divisor);
+        r.im = is_zero(r.im) ? r.im : __ddiv_rn(r.im, a.divisor);
+      }
+      int wt = __popcll(r.v | r.w);
+      if (a.use_gamma) {
+        double f = a.factor[wt];
+        r.re = is_zero(r.re) ? r.re : __dmul_rn(r.re, f);
+        r.im = is_zero(r.im) ? r.im : __dmul_rn(r.im, f);
+      }
+      keep = !(a.max_weight >= 0 && wt > a.max_weight) && !(is_zero(r.re) && is_zero(r.im));
+      if (keep && a.use_cut) keep = !(sq_sum(r.re, r.im) < a.cut2);
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (!mask) continue;
+    int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == __ffs(mask) - 1) base = atomicAdd(n_out, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    if (keep) out[base + __popc(mask & ((1u << lane) - 1))] = r;
+  }
+}
+
+// rank key digit d (0 = most significant) of record r
+__device__ __forceinline__ uint32_t rank_digit(const Rec& r, int d) {
+  uint64_t k0 = (uint64_t)__double_as_longlong(sq_sum(r.re, r.im));
+  uint64_t k1 = ~r.v, k2 = ~r.w;
+  int hi = 192 - d * kDigitBits;           // bits [lo, hi) of the 192-bit key, counted from bit 0 = LSB of k2
+  int lo = max(hi - kDigitBits, 0);
+  uint32_t out = 0;
+  for (int b = hi - 1; b >= lo; --b) {
+    uint64_t word = b >= 128 ? k0 : (b >= 64 ? k1 : k2);
+    out = (out << 1) | (uint32_t)((word >> (b & 63)) & 1);
+  }
+  return out;
+}
+
+// Full 192-bit rank key as 3 words (k0 most significant).
+__device__ __forceinline__ void rank_key(const Rec& r, uint64_t k[3]) {
+  k[0] = (uint64_t)__double_as_longlong(sq_sum(r.re, r.im));
+  k[1] = ~r.v;
+  k[2] = ~r.w;
+}
+
+// Select state: the digits fixed so far, the rank still needed inside the current prefix.
+struct SelState {
+  uint64_t prefix[3];   // fixed high bits of the threshold (others zero)
+  unsigned long long need;
+  int done;
+  int pass;
+};
+
+__device__ __forceinline__ bool matches_prefix(const uint64_t k[3], const SelState& st, int pass) {
+  int nbits = min(pass * kDigitBits, 192);  // high bits already fixed
+  for (int w = 0; w < 3; ++w) {
+    int wb = nbits - 64 * w;  // fixed bits in this word
+    if (wb <= 0) break;
+    uint64_t m = wb >= 64 ? ~0ull : (~0ull << (64 - wb));
+    if ((k[w] & m) != (st.prefix[w] & m)) return false;
+  }
+  return true;
+}
+
+__global__ void k_sel_hist(const Rec* __restrict__ d, int64_t n, const SelState* __restrict__ st_p, int pass,
+                           unsigned* __restrict__ hist) {
+  __shared__ unsigned s_hist[kBins];
+  SelState st = *st_p;
+  if (st.done) return;
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Rec r = d[i];
+    uint64_t k[3];
+    rank_key(r, k);
+    if (!matches_prefix(k, st, pass)) continue;
+    atomicAdd(&s_hist[rank_digit(r, pass)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
+}
+
+// Pick the digit of the need-th largest key in the current prefix (single block).
+__global__ void k_sel_pick(SelState* st_p, int pass, unsigned* __restrict__ hist) {
+  __shared__ unsigned s_hist[kBins];
+  SelState st = *st_p;
+  if (st.done) return;
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
+    s_hist[i] = hist[i];
+    hist[i] = 0;  // ready for the next pass
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long cum = 0;
+    int hi = 192 - pass * kDigitBits;
+    int width = min(kDigitBits, hi);
+    int top = (1 << width) - 1;
+    int sel = 0;
+    unsigned long long above = 0;
+    for (int b = top; b >= 0; --b) {
+      if (cum + s_hist[b] >= st.need) {
+        sel = b;
+        above = cum;
+        break;
+      }
+      cum += s_hist[b];
+    }
+    // write the selected digit into the prefix: bits [hi - width, hi)
+    int lo = hi - width;
+    for (int j = 0; j < width; ++j) {
+      int b = lo + j;  // bit index counted from LSB of k2
+      if ((sel >> j) & 1) {
+        int word = b >= 128 ? 0 : (b >= 64 ? 1 : 2);
+        st_p->prefix[word] |= 1ull << (b & 63);
+      }
+    }
+    unsigned long long need = st.need - above;
+    st_p->need = need;
+    st_p->pass = pass + 1;
+    if (s_hist[sel] == need || lo == 0) st_p->done = 1;  // every key in this bin is kept (or key fully fixed)
+  }
+}
+
+// keep iff rank key >= threshold (prefix with zero low bits), or in the keep set (sorted keys)
+__global__ void k_sel_compact(const Rec* __restrict__ in, int64_t n, const SelState* __restrict__ st_p,
+                              const ulonglong2* __restrict__ keep, int64_t nkeep, Rec* __restrict__ out,
+                              unsigned long long* __restrict__ n_out) {
+  const SelState st = *st_p;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t iters = ceil_div_dev(n, stride);
+  for (int64_t it = 0; it < iters; ++it) {
+    int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool kp = false;
+    Rec r;
+    if (i < n) {
+      r = in[i];
+      uint64_t k[3];
+      rank_key(r, k);
+      kp = (k[0] > st.prefix[0]) || (k[0] == st.prefix[0] && (k[1] > st.prefix[1] || (k[1] == st.prefix[1] && k[2] >= st.prefix[2])));
+      if (!kp && nkeep > 0) {
+        int64_t l = 0, h = nkeep;
+        while (l < h) {
+          int64_t m = (l + h) >> 1;
+          ulonglong2 c = keep[m];
+          if (c.x < r.v || (c.x == r.v && c.y < r.w)) l = m + 1; else h = m;
+        }
+        kp = (l < nkeep && keep[l].x == r.v && keep[l].y == r.w);
+      }
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, kp);
+    if (!mask) continue;
+    int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == __ffs(mask) - 1) base = atomicAdd(n_out, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    if (kp) out[base + __popc(mask & ((1u << lane) - 1))] = r;
+  }
+}
+
+}  // namespace
+
+// Truncate O in place; `divisor` (if non-null) divides every coefficient first.
+int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor) {
+  cudaStream_t s = O->stream;
+  const bool use_gamma = P && P->gamma != 0.0;
+  const bool use_w = P && P->max_weight >= 0;
+  const bool use_cut = P && P->cutoff > 0.0;
+  const bool use_top = P && P->top_k > 0;
+  if (!use_gamma && !use_w && !use_cut && !use_top && !divisor) return PS_OK;
+  if (O->n == 0) return PS_OK;
+  const int nsm = num_sms();
+  auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
+
+  Buf<double> factor;
+  Buf<unsigned long long> cnt;
+  PS_TRY(cnt.alloc(2, s));
+  PS_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), s));
+  TruncArgs a{};
+  a.max_weight = use_w ? P->max_weight : -1;
+  a.use_cut = use_cut;
+  a.cut2 = use_cut ? P->cutoff * P->cutoff : 0.0;
+  a.use_gamma = use_gamma;
+  a.use_div = divisor != nullptr;
+  a.divisor = divisor ? *divisor : 1.0;
+  if (use_gamma) {
+    double h[65];
+    double x = P->gamma * dt;
+    for (int wt = 0; wt <= 64; ++wt) h[wt] = std::exp(-(x * (double)wt));
+    PS_TRY(factor.alloc(65, s));
+    PS_CUDA(cudaMemcpyAsync(factor.p, h, sizeof(h), cudaMemcpyHostToDevice, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    a.factor = factor.p;
+  }
+  Rec* cand = nullptr;
+  PS_TRY(dev_alloc((void**)&cand, (size_t)O->n * sizeof(Rec), s));
+  PS_LAUNCH("k_filter", s, k_filter<<<grid_for(O->n), 256, 0, s>>>(O->d, O->n, a, cand, cnt.p));
+  cudaError_t e = cudaGetLastError();
+  unsigned long long nc = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nc, cnt.p, sizeof(nc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    dev_free(cand, s);
+    set_cuda_error(e, "truncate filter");
+    return PS_ERR_CUDA;
+  }
+  if (!use_top || (int64_t)nc <= P->top_k) return sum_adopt(O, cand, O->n, (int64_t)nc);
+
+  // ---- top-k select
+  Buf<SelState> st;
+  Buf<unsigned> hist;
+  Buf<ulonglong2> keepk;
+  PS_TRY(st.alloc(1, s));
+  PS_TRY(hist.alloc(kBins, s));
+  SelState h0{};
+  h0.need = (unsigned long long)P->top_k;
+  PS_CUDA(cudaMemcpyAsync(st.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
+  PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
+  int64_t nkeep = 0;
+  if (keep && keep->n > 0) {
+    std::vector<Rec> hk((size_t)keep->n);
+    PS_CUDA(cudaMemcpyAsync(hk.data(), keep->d, hk.size() * sizeof(Rec), cudaMemcpyDeviceToHost, keep->stream));
+    PS_CUDA(cudaStreamSynchronize(keep->stream));
+    std::vector<ulonglong2> kk(hk.size());
+    for (size_t i = 0; i < hk.size(); ++i) kk[i] = make_ulonglong2(hk[i].v, hk[i].w);
+    std::sort(kk.begin(), kk.end(), [](const ulonglong2& x, const ulonglong2& y) { return x.x < y.x || (x.x == y.x && x.y < y.y); });
+    nkeep = (int64_t)kk.size();
+    PS_TRY(keepk.alloc(kk.size(), s));
+    PS_CUDA(cudaMemcpyAsync(keepk.p, kk.data(), kk.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, s));
+  }
+  int hb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)nc, 256), 4 * nsm));
+  // |c|^2 digits first (6 passes); the key digits only matter for exact ties
+  for (int pass = 0; pass < kPasses; ++pass) {
+    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(cand, (int64_t)nc, st.p, pass, hist.p));
+    PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, pass, hist.p));
+    if (pass == 5 || pass == kPasses - 1) {
+      SelState hs;
+      PS_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      PS_CUDA(cudaStreamSynchronize(s));
+      if (hs.done) break;
+    }
+  }
+  PS_CUDA(cudaGetLastError());
+  Rec* outb = nullptr;
+  int64_t ocap = (int64_t)nc;  // kept <= top_k + |keep| <= nc
+  PS_TRY(dev_alloc((void**)&outb, (size_t)std::max<int64_t>(ocap, 1) * sizeof(Rec), s));
+  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<grid_for((int64_t)nc), 256, 0, s>>>(cand, (int64_t)nc, st.p, keepk.p, nkeep, outb, cnt.p + 1));
+  e = cudaGetLastError();
+  unsigned long long nk = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nk, cnt.p + 1, sizeof(nk), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(cand, s);
+  if (e != cudaSuccess) {
+    dev_free(outb, s);
+    set_cuda_error(e, "truncate select");
+    return PS_ERR_CUDA;
+  }
+  return sum_adopt(O, outb, std::max<int64_t>(ocap, 1), (int64_t)nk);
+}
+
+}  // namespace ps

@@ -1,0 +1,293 @@
+"""Thin Python binding of libpaulistr (ctypes).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  The functions carry the names of the C ABI in ``include/paulistr.h``;
+``PauliSum`` owns one ``pauli_sum*``.  PyTorch is used only to pick the CUDA
+stream (``torch.cuda.current_stream()``) and to pass device tensors.
+
+There is no CPU fallback: if the compiled library is missing, or no CUDA
+device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+PS_OK = 0
+PS_ERR_INVALID = 1
+PS_ERR_CAPACITY = 2
+PS_ERR_TABLE_FULL = 3
+PS_ERR_CUDA = 4
+PS_ERR_TIMEOUT = 5
+PS_ERR_KRYLOV_EXHAUSTED = 6
+PS_ERR_NOMEM = 7
+
+_lib = None
+
+
+class PauliError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _lib
+        msg = lib.pauli_status_string(status).decode() if lib else str(status)
+        extra = ""
+        if lib and status == PS_ERR_CUDA:
+            extra = " [" + lib.pauli_last_cuda_error().decode() + "]"
+        super().__init__(f"{where}: {msg}{extra}")
+        self.status = status
+
+
+class pauli_trunc_policy(ctypes.Structure):
+    _fields_ = [("max_weight", ctypes.c_int), ("cutoff", ctypes.c_double), ("top_k", ctypes.c_int64),
+                ("gamma", ctypes.c_double), ("trim_stages", ctypes.c_int)]
+
+
+class pauli_merge_stats(ctypes.Structure):
+    _fields_ = [("pair_tests", ctypes.c_int64), ("contributions", ctypes.c_int64), ("merged", ctypes.c_int64),
+                ("groups", ctypes.c_int64), ("split_groups", ctypes.c_int64)]
+
+
+def policy(max_weight: int = -1, cutoff: float = 0.0, top_k: int = 0, gamma: float = 0.0,
+           trim_stages: int = 0) -> pauli_trunc_policy:
+    return pauli_trunc_policy(int(max_weight), float(cutoff), int(top_k), float(gamma), int(trim_stages))
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libpaulistr.so; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libpaulistr is not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    U64P = ctypes.POINTER(ctypes.c_uint64)
+    F64P = ctypes.POINTER(ctypes.c_double)
+    I64 = ctypes.c_int64
+    sig = {
+        "pauli_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "pauli_last_cuda_error": ([], ctypes.c_char_p),
+        "pauli_sum_create": ([ctypes.c_int, I64, P, ctypes.POINTER(P)], ctypes.c_int),
+        "pauli_sum_destroy": ([P], ctypes.c_int),
+        "pauli_sum_upload": ([P, U64P, U64P, F64P, F64P, I64], ctypes.c_int),
+        "pauli_sum_upload_device": ([P, P, P, P, P, I64], ctypes.c_int),
+        "pauli_sum_size": ([P, ctypes.POINTER(I64)], ctypes.c_int),
+        "pauli_sum_n_sites": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "pauli_sum_download": ([P, U64P, U64P, F64P, F64P, I64, ctypes.POINTER(I64)], ctypes.c_int),
+        "pauli_sum_download_device": ([P, P, P, P, P, I64, ctypes.POINTER(I64)], ctypes.c_int),
+        "pauli_sum_copy": ([P, P], ctypes.c_int),
+        "pauli_commutator": ([P, P, P], ctypes.c_int),
+        "pauli_add": ([P, ctypes.c_double, ctypes.c_double, P, P], ctypes.c_int),
+        "pauli_truncate": ([P, ctypes.POINTER(pauli_trunc_policy), P, ctypes.c_double], ctypes.c_int),
+        "pauli_rk4_step": ([P, P, ctypes.c_double, ctypes.POINTER(pauli_trunc_policy), P], ctypes.c_int),
+        "pauli_lanczos_step": ([P, P, P, ctypes.c_double, ctypes.POINTER(pauli_trunc_policy), F64P], ctypes.c_int),
+        "pauli_trace_product": ([P, P, F64P, F64P], ctypes.c_int),
+        "pauli_norm": ([P, F64P], ctypes.c_int),
+        "pauli_last_merge_stats": ([ctypes.POINTER(pauli_merge_stats)], ctypes.c_int),
+        "pauli_debug_fail_alloc_after": ([I64], ctypes.c_int),
+        "pauli_profile_enable": ([ctypes.c_int], ctypes.c_int),
+        "pauli_profile_report": ([ctypes.c_char_p, I64, ctypes.POINTER(I64)], ctypes.c_int),
+        "pauli_launch_count": ([], I64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    """Names of the functions declared in include/paulistr.h."""
+    import re
+    hdr = os.path.join(_build.ROOT, "include", "paulistr.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"\b(pauli_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status: int, where: str):
+    if status != PS_OK:
+        raise PauliError(status, where)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _u64(a):
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class PauliSum:
+    """A device-resident Pauli sum (owns one ``pauli_sum*``)."""
+
+    def __init__(self, n_sites: int, capacity: int = 0, stream=None):
+        lib = load()
+        self._lib = lib
+        self.n_sites = int(n_sites)
+        self.stream = _current_stream() if stream is None else ctypes.c_void_p(stream)
+        h = ctypes.c_void_p()
+        _check(lib.pauli_sum_create(self.n_sites, int(capacity), self.stream, ctypes.byref(h)), "pauli_sum_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and self._lib is not None:
+            self._lib.pauli_sum_destroy(h)
+            self.handle = None
+
+    # ------------------------------------------------------------ data movement
+    @classmethod
+    def from_arrays(cls, n_sites: int, v, w, re, im, stream=None) -> "PauliSum":
+        s = cls(n_sites, len(v), stream)
+        s.upload(v, w, re, im)
+        return s
+
+    def upload(self, v, w, re, im):
+        """Host upload (numpy arrays); order kept."""
+        v, w, re, im = _u64(v), _u64(w), _f64(re), _f64(im)
+        n = len(v)
+        U64P = ctypes.POINTER(ctypes.c_uint64)
+        F64P = ctypes.POINTER(ctypes.c_double)
+        _check(self._lib.pauli_sum_upload(self.handle, v.ctypes.data_as(U64P), w.ctypes.data_as(U64P),
+                                          re.ctypes.data_as(F64P), im.ctypes.data_as(F64P), n), "pauli_sum_upload")
+
+    def upload_device(self, v, w, re, im):
+        """Device upload from torch CUDA tensors (uint64/int64, float64)."""
+        n = int(v.numel())
+        _check(self._lib.pauli_sum_upload_device(self.handle, ctypes.c_void_p(v.data_ptr()),
+                                                 ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(re.data_ptr()),
+                                                 ctypes.c_void_p(im.data_ptr()), n), "pauli_sum_upload_device")
+
+    def __len__(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.pauli_sum_size(self.handle, ctypes.byref(n)), "pauli_sum_size")
+        return int(n.value)
+
+    def download(self):
+        """(v, w, re, im) numpy arrays in canonical order (v, then w ascending)."""
+        n = len(self)
+        v = np.empty(n, np.uint64)
+        w = np.empty(n, np.uint64)
+        re = np.empty(n, np.float64)
+        im = np.empty(n, np.float64)
+        got = ctypes.c_int64()
+        U64P = ctypes.POINTER(ctypes.c_uint64)
+        F64P = ctypes.POINTER(ctypes.c_double)
+        _check(self._lib.pauli_sum_download(self.handle, v.ctypes.data_as(U64P), w.ctypes.data_as(U64P),
+                                            re.ctypes.data_as(F64P), im.ctypes.data_as(F64P), n,
+                                            ctypes.byref(got)), "pauli_sum_download")
+        return v, w, re, im
+
+    def to_dict(self) -> dict:
+        v, w, re, im = self.download()
+        return {(int(a), int(b)): complex(c, d) for a, b, c, d in zip(v, w, re, im)}
+
+    def copy(self) -> "PauliSum":
+        out = PauliSum(self.n_sites, len(self), self.stream.value)
+        _check(self._lib.pauli_sum_copy(self.handle, out.handle), "pauli_sum_copy")
+        return out
+
+
+def _h(s):
+    return None if s is None else s.handle
+
+
+def pauli_commutator(H: PauliSum, O: PauliSum, out: PauliSum | None = None) -> PauliSum:
+    out = out or PauliSum(O.n_sites, 0, O.stream.value)
+    _check(load().pauli_commutator(H.handle, O.handle, out.handle), "pauli_commutator")
+    return out
+
+
+def pauli_add(A: PauliSum, alpha: complex, B: PauliSum, out: PauliSum | None = None) -> PauliSum:
+    out = out or PauliSum(A.n_sites, 0, A.stream.value)
+    alpha = complex(alpha)
+    _check(load().pauli_add(A.handle, alpha.real, alpha.imag, B.handle, out.handle), "pauli_add")
+    return out
+
+
+def pauli_truncate(O: PauliSum, pol: pauli_trunc_policy | None, keep: PauliSum | None = None, dt: float = 0.0):
+    _check(load().pauli_truncate(O.handle, None if pol is None else ctypes.byref(pol), _h(keep), float(dt)),
+           "pauli_truncate")
+    return O
+
+
+def pauli_rk4_step(H: PauliSum, O: PauliSum, dt: float, pol: pauli_trunc_policy | None = None,
+                   keep: PauliSum | None = None):
+    _check(load().pauli_rk4_step(H.handle, O.handle, float(dt), None if pol is None else ctypes.byref(pol),
+                                 _h(keep)), "pauli_rk4_step")
+    return O
+
+
+def pauli_lanczos_step(H: PauliSum, O_prev: PauliSum, O_cur: PauliSum, b_prev: float,
+                       pol: pauli_trunc_policy | None = None) -> float:
+    """Returns b_n (0.0 when the Krylov space closed; then the sums are unchanged)."""
+    b = ctypes.c_double()
+    st = load().pauli_lanczos_step(H.handle, O_prev.handle, O_cur.handle, float(b_prev),
+                                   None if pol is None else ctypes.byref(pol), ctypes.byref(b))
+    if st == PS_ERR_KRYLOV_EXHAUSTED:
+        return 0.0
+    _check(st, "pauli_lanczos_step")
+    return float(b.value)
+
+
+def pauli_trace_product(A: PauliSum, B: PauliSum) -> complex:
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(load().pauli_trace_product(A.handle, B.handle, ctypes.byref(re), ctypes.byref(im)), "pauli_trace_product")
+    return complex(re.value, im.value)
+
+
+def pauli_norm(O: PauliSum) -> float:
+    r = ctypes.c_double()
+    _check(load().pauli_norm(O.handle, ctypes.byref(r)), "pauli_norm")
+    return float(r.value)
+
+
+def pauli_last_merge_stats() -> dict:
+    st = pauli_merge_stats()
+    _check(load().pauli_last_merge_stats(ctypes.byref(st)), "pauli_last_merge_stats")
+    return {k: int(getattr(st, k)) for k, _ in pauli_merge_stats._fields_}
+
+
+def pauli_profile_enable(on: bool = True):
+    _check(load().pauli_profile_enable(1 if on else 0), "pauli_profile_enable")
+
+
+def pauli_profile_report() -> dict:
+    """{kernel: (launches, total_ms)} since profiling was enabled."""
+    import json
+    lib = load()
+    need = ctypes.c_int64()
+    lib.pauli_profile_report(None, 0, ctypes.byref(need))
+    buf = ctypes.create_string_buffer(int(need.value) + 64)
+    _check(lib.pauli_profile_report(buf, len(buf), ctypes.byref(need)), "pauli_profile_report")
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def pauli_launch_count() -> int:
+    return int(load().pauli_launch_count())
+
+
+def pauli_debug_fail_alloc_after(n: int):
+    _check(load().pauli_debug_fail_alloc_after(int(n)), "pauli_debug_fail_alloc_after")

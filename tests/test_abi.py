@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads and exports every symbol that include/paulistr.h
+declares (no compute calls: runs without a GPU)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2410_09654_gb300 import build as B
+from paper_2410_09654_gb300 import paulistr as ps
+
+HDR = os.path.join(B.ROOT, "include", "paulistr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    try:
+        B.build()
+    except RuntimeError as e:  # no nvcc here
+        pytest.skip(str(e))
+    return ctypes.CDLL(B.LIB)
+
+
+def test_header_declares_the_path():
+    names = ps.declared_symbols()
+    for need in ("pauli_sum_create", "pauli_commutator", "pauli_truncate", "pauli_rk4_step",
+                 "pauli_lanczos_step", "pauli_trace_product"):
+        assert need in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pauli_\w+)", out))
+    missing = [s for s in ps.declared_symbols() if s not in exported]
+    assert not missing, missing
+    for s in ps.declared_symbols():
+        getattr(lib, s)  # resolvable through dlsym
+
+
+def test_binding_signatures_cover_header(lib):
+    l = ps.load()
+    for s in ps.declared_symbols():
+        assert getattr(l, s).argtypes is not None, s
+
+
+def test_status_strings_without_gpu(lib):
+    l = ps.load()
+    assert l.pauli_status_string(0) == b"ok"
+    assert b"Krylov" in l.pauli_status_string(ps.PS_ERR_KRYLOV_EXHAUSTED)
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib):
+    l = ps.load()
+    h = ctypes.c_void_p()
+    assert l.pauli_sum_create(0, 0, None, ctypes.byref(h)) == ps.PS_ERR_INVALID
+    assert l.pauli_sum_create(65, 0, None, ctypes.byref(h)) == ps.PS_ERR_INVALID
+    assert l.pauli_commutator(None, None, None) == ps.PS_ERR_INVALID
+    assert l.pauli_lanczos_step(None, None, None, 0.0, None, None) == ps.PS_ERR_INVALID
+
+
+def test_product_path_does_not_touch_the_oracle():
+    pkg = os.path.join(B.ROOT, "paper_2410_09654_gb300")
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(root, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "liboracle" not in text, f

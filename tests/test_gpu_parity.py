@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on seeded inputs.
+
+Sizes: small cases for the edge cases, and workloads whose merge spans many
+bin groups (and forces the split path) for the tiles-and-ragged-tail cases."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2410_09654_gb300 import inputs as I
+
+from gpu_util import assert_match
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2410_09654_gb300 import paulistr as ps  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ps.load(build_if_missing=True)
+
+
+def dev(n, arrays):
+    return ps.PauliSum.from_arrays(n, *arrays)
+
+
+def ref(n, arrays):
+    return orc.Op(n, *arrays)
+
+
+# ----------------------------------------------------------------------------- commutator
+@pytest.mark.parametrize("kind", ["real", "imag", "complex"])
+@pytest.mark.parametrize("n,mh,mo,sup", [(3, 9, 17, None), (10, 29, 500, 5), (32, 60, 3000, 8), (64, 120, 5000, 10),
+                                         (64, 40, 20000, None)])
+def test_commutator_random(kind, n, mh, mo, sup):
+    Ha = I.random_sum(1000 + n, n, mh, "real" if kind != "complex" else "complex", max_support=min(3, n))
+    Oa = I.random_sum(2000 + n + mo, n, mo, kind, max_support=sup)
+    out = ps.pauli_commutator(dev(n, Ha), dev(n, Oa))
+    assert_match(out.download(), orc.commutator(ref(n, Ha), ref(n, Oa)), what="commutator")
+
+
+def test_commutator_dyadic_exact():
+    n = 12
+    Ha = I.random_sum(5, n, 40, "real", max_support=3, dyadic=True)
+    Oa = I.random_sum(6, n, 3000, "real", max_support=6, dyadic=True)
+    out = ps.pauli_commutator(dev(n, Ha), dev(n, Oa))
+    assert_match(out.download(), orc.commutator(ref(n, Ha), ref(n, Oa)), what="dyadic")
+
+
+def test_commutator_workload_many_groups():
+    # XXZ chain on 64 sites acting on a Lanczos vector of ~1e4 strings: many bins/groups
+    n = 64
+    H = I.xxz_chain(n).arrays()
+    O0 = I.uniform_sum(n, "X").arrays()
+    _, On = orc.lanczos(ref(n, H), ref(n, O0), 6)
+    Oa = (On.v, On.w, On.re, On.im)
+    out = ps.pauli_commutator(dev(n, H), dev(n, Oa))
+    st = ps.pauli_last_merge_stats()
+    assert st["groups"] > 4
+    assert_match(out.download(), orc.commutator(ref(n, H), On), what="xxz")
+
+
+def test_commutator_dense_anticommuting_forces_split():
+    # all-to-all random H on 8 sites: every output key receives many contributions and
+    # bins overflow the shared-memory pass, exercising the split path
+    n = 8
+    Ha = I.random_sum(77, n, 400, "real")
+    Oa = I.random_sum(78, n, 3000, "real")
+    out = ps.pauli_commutator(dev(n, Ha), dev(n, Oa))
+    assert_match(out.download(), orc.commutator(ref(n, Ha), ref(n, Oa)), what="dense")
+
+
+def test_commutator_edges():
+    n = 64
+    top = np.uint64(1 << 63)
+    # site 64 bits, the all-ones string, the identity
+    Ha = ([top, 0, np.uint64(~0 & (2**64 - 1))], [0, top, np.uint64(2**64 - 1)], [1.0, 0.5, 0.25], [0.0, 0.0, 0.0])
+    Oa = ([top, np.uint64(2**64 - 1), 0, 1], [top, 0, 0, 1], [1.0, -2.0, 3.0, 0.5], [0.0, 1.0, 0.0, 0.0])
+    out = ps.pauli_commutator(dev(n, Ha), dev(n, Oa))
+    assert_match(out.download(), orc.commutator(ref(n, Ha), ref(n, Oa)), what="edges")
+    # empty operands
+    e = ps.PauliSum(n)
+    assert len(ps.pauli_commutator(e, dev(n, Oa))) == 0
+    assert len(ps.pauli_commutator(dev(n, Ha), e)) == 0
+    # commuting operands give an empty result ([XXZ, sum Z] = 0)
+    H = dev(16, I.xxz_chain(16).arrays())
+    assert len(ps.pauli_commutator(H, dev(16, I.uniform_sum(16, "Z", 1.0).arrays()))) == 0
+
+
+def test_commutator_n1():
+    Ha = ([1], [0], [0.7], [0.0])
+    Oa = ([0, 1], [1, 1], [1.0, 0.25], [0.0, -0.5])
+    out = ps.pauli_commutator(dev(1, Ha), dev(1, Oa))
+    assert_match(out.download(), orc.commutator(ref(1, Ha), ref(1, Oa)), what="n1")
+
+
+# ----------------------------------------------------------------------------- add / truncate
+def test_add():
+    n = 20
+    A = I.random_sum(31, n, 4000, "complex", max_support=6)
+    B = (A[0][:2000], A[1][:2000], -A[2][:2000], A[3][:2000] * 0.5)  # overlap, with cancellations
+    B = (np.concatenate([B[0], I.random_sum(32, n, 3000, "complex", max_support=6)[0]]),
+         np.concatenate([B[1], I.random_sum(32, n, 3000, "complex", max_support=6)[1]]),
+         np.concatenate([B[2], I.random_sum(32, n, 3000, "complex", max_support=6)[2]]),
+         np.concatenate([B[3], I.random_sum(32, n, 3000, "complex", max_support=6)[3]]))
+    # drop duplicate strings inside B
+    keys = list(zip(B[0].tolist(), B[1].tolist()))
+    _, first = np.unique(np.array(keys, dtype=np.uint64), axis=0, return_index=True)
+    first = np.sort(first)
+    B = tuple(x[first] for x in B)
+    for alpha in (1.0, -0.37 + 1.25j, 2.0):
+        out = ps.pauli_add(dev(n, A), alpha, dev(n, B))
+        assert_match(out.download(), orc.axpy(ref(n, A), alpha, ref(n, B)), what=f"add {alpha}")
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_truncate(case):
+    rng = np.random.default_rng(500 + case)
+    n = 16
+    m = 20000
+    v, w = I.random_strings(rng, n, m)
+    vals = np.array([1.0, -1.0, 0.5, 0.25, 1e-11, 3e-3, -3e-3, 0.0, 0.125])
+    re = vals[rng.integers(0, len(vals), m)]
+    im = vals[rng.integers(0, len(vals), m)] * (case % 2)
+    keep_idx = rng.choice(m, 5, replace=False)
+    keep = (v[keep_idx], w[keep_idx], np.ones(5), np.zeros(5)) if case >= 3 else None
+    params = [dict(max_weight=6, cutoff=1e-10, top_k=0, gamma=0.0, dt=0.05),
+              dict(max_weight=-1, cutoff=0.0, top_k=3700, gamma=0.0, dt=0.05),
+              dict(max_weight=12, cutoff=1e-3, top_k=5000, gamma=0.1, dt=0.02),
+              dict(max_weight=-1, cutoff=0.0, top_k=2000, gamma=0.0, dt=0.05),
+              dict(max_weight=-1, cutoff=0.0, top_k=1, gamma=0.3, dt=0.1),
+              dict(max_weight=9, cutoff=2e-3, top_k=100, gamma=0.0, dt=0.0)][case]
+    O = dev(n, (v, w, re, im))
+    # drop exact zeros on the input side, as a commutator output never holds them
+    pol = ps.policy(params["max_weight"], params["cutoff"], params["top_k"], params["gamma"])
+    ps.pauli_truncate(O, pol, None if keep is None else dev(n, keep), params["dt"])
+    want = orc.truncate(ref(n, (v, w, re, im)), keep=None if keep is None else ref(n, keep), **params)
+    assert_match(O.download(), want, what=f"truncate {case}")
+
+
+def test_truncate_all_ties():
+    # every coefficient equal: the top-k is decided by the key order alone
+    n = 30
+    rng = np.random.default_rng(9)
+    v, w = I.random_strings(rng, n, 5000)
+    re = np.full(5000, 0.5)
+    im = np.zeros(5000)
+    O = dev(n, (v, w, re, im))
+    ps.pauli_truncate(O, ps.policy(top_k=1234))
+    assert_match(O.download(), orc.truncate(ref(n, (v, w, re, im)), top_k=1234), what="ties")
+
+
+# ----------------------------------------------------------------------------- reductions
+def test_norm_and_trace_exact():
+    rng = np.random.default_rng(21)
+    n = 64
+    m = 30000
+    v, w = I.random_strings(rng, n, m)
+    re = rng.standard_normal(m) * 10.0 ** rng.integers(-60, 20, m)
+    im = rng.standard_normal(m) * 10.0 ** rng.integers(-60, 20, m)
+    A = (v, w, re, im)
+    dA = dev(n, A)
+    assert ps.pauli_norm(dA) == orc.norm(ref(n, A))
+    B = (np.concatenate([v[:20000], v[20000:] ^ np.uint64(1 << 40)]), w, rng.standard_normal(m), -im)
+    assert ps.pauli_trace_product(dA, dev(n, B)) == orc.trace_product(ref(n, A), ref(n, B))
+    # cancellation to exactly zero
+    C = (v[:4], w[:4], np.array([1e20, 1.0, -1e20, -1.0]), np.zeros(4))
+    D = (v[:4], w[:4], np.ones(4), np.zeros(4))
+    assert ps.pauli_trace_product(dev(n, C), dev(n, D)) == 0
+    assert ps.pauli_norm(ps.PauliSum(n)) == 0.0
+
+
+# ----------------------------------------------------------------------------- RK4
+def test_rk4_chain_n10_config_shape():
+    # the RK4 workload: N=10 tilted Ising chain, O(0)=Z_1, dt=0.05, weight <= 6 then cutoff 1e-10
+    n = 10
+    Ha = I.tilted_ising_chain(n).arrays()
+    O = dev(n, I.single(n, "Z", 1).arrays())
+    Or = ref(n, I.single(n, "Z", 1).arrays())
+    H, Hr = dev(n, Ha), ref(n, Ha)
+    pol = ps.policy(max_weight=6, cutoff=1e-10)
+    Z1 = dev(n, I.single(n, "Z", 1).arrays())
+    for step in range(12):
+        ps.pauli_rk4_step(H, O, 0.05, pol)
+        Or = orc.rk4_step(Hr, Or, 0.05, max_weight=6, cutoff=1e-10)
+        assert_match(O.download(), Or, what=f"rk4 step {step}")
+        assert ps.pauli_trace_product(O, Z1) == orc.trace_product(Or, ref(n, I.single(n, "Z", 1).arrays()))
+
+
+def test_rk4_dissipation_topk_keep():
+    n = 16
+    Ha = I.heisenberg_2d(4, 4).arrays()
+    O0 = I.single(n, "Z", 6).arrays()
+    H, Hr = dev(n, Ha), ref(n, Ha)
+    O, Or = dev(n, O0), ref(n, O0)
+    keep, keepr = dev(n, O0), ref(n, O0)
+    pol = ps.policy(top_k=300, gamma=0.1)
+    for step in range(6):
+        ps.pauli_rk4_step(H, O, 0.02, pol, keep)
+        Or = orc.rk4_step(Hr, Or, 0.02, top_k=300, gamma=0.1, keep=keepr)
+        assert_match(O.download(), Or, what=f"rk4 diss step {step}")
+
+
+def test_rk4_trim_stages():
+    n = 16
+    Ha = I.heisenberg_2d(4, 4).arrays()
+    O0 = I.single(n, "Z", 6).arrays()
+    H, Hr = dev(n, Ha), ref(n, Ha)
+    O, Or = dev(n, O0), ref(n, O0)
+    pol = ps.policy(top_k=200, gamma=0.1, trim_stages=1)
+    for step in range(5):
+        ps.pauli_rk4_step(H, O, 0.02, pol)
+        Or = orc.rk4_step(Hr, Or, 0.02, top_k=200, gamma=0.1, trim_stages=1)
+        assert_match(O.download(), Or, what=f"rk4 trim step {step}")
+
+
+# ----------------------------------------------------------------------------- Lanczos
+def test_lanczos_paper_example():
+    n = 10
+    hb = I.xx_chain(n)
+    hb.add(1.0, "X", 4)
+    H, Hr = dev(n, hb.arrays()), ref(n, hb.arrays())
+    O0 = I.single(n, "X", 1).arrays()
+    prev, cur = ps.PauliSum(n), dev(n, O0)
+    rprev, rcur = orc.Op.empty(n), ref(n, O0)
+    b = rb = 0.0
+    pol = ps.policy(cutoff=1e-10)
+    for step in range(10):
+        b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
+        rb, nxt = orc.lanczos_step(Hr, rprev, rcur, rb, cutoff=1e-10)
+        rprev, rcur = rcur, nxt
+        assert b == rb
+        assert_match(cur.download(), rcur, what=f"lanczos {step}")
+        assert_match(prev.download(), rprev, what=f"lanczos prev {step}")
+
+
+def test_lanczos_xxz64_topk():
+    # the Lanczos workload at reduced size: XXZ N=64, O_0 = sum X_i / 8, top-k cap
+    n = 64
+    Ha = I.xxz_chain(n).arrays()
+    O0 = I.uniform_sum(n, "X").arrays()
+    H, Hr = dev(n, Ha), ref(n, Ha)
+    prev, cur = ps.PauliSum(n), dev(n, O0)
+    rprev, rcur = orc.Op.empty(n), ref(n, O0)
+    b = rb = 0.0
+    pol = ps.policy(top_k=4000)
+    for step in range(9):
+        b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
+        rb, nxt = orc.lanczos_step(Hr, rprev, rcur, rb, top_k=4000)
+        rprev, rcur = rcur, nxt
+        assert b == rb, (step, b, rb)
+        assert_match(cur.download(), rcur, what=f"xxz lanczos {step}")
+
+
+def test_lanczos_literal_sum_z_is_exhausted():
+    # O_0 = sum Z_i commutes with the XXZ chain: b_1 = 0, the Krylov space is closed
+    n = 64
+    H = dev(n, I.xxz_chain(n).arrays())
+    prev, cur = ps.PauliSum(n), dev(n, I.uniform_sum(n, "Z").arrays())
+    b = ps.pauli_lanczos_step(H, prev, cur, 0.0, ps.policy(top_k=1 << 22))
+    assert b == 0.0
+    assert len(cur) == n and len(prev) == 0  # left unchanged
+
+
+def test_lanczos_open_xx_closed_form():
+    n = 12
+    H = dev(n, I.xx_chain(n).arrays())
+    prev, cur = ps.PauliSum(n), dev(n, I.single(n, "X", 1).arrays())
+    b = 0.0
+    bs = []
+    for _ in range(n + 1):
+        b = ps.pauli_lanczos_step(H, prev, cur, b)
+        bs.append(b)
+        if b == 0.0:
+            break
+    assert bs[: n - 1] == [2.0] * (n - 1) and bs[n - 1] == 0.0
