@@ -56,7 +56,7 @@ __device__ __forceinline__ uint32_t dev_hash(uint64_t v, uint64_t w, int lo, int
 namespace {
 
 constexpr int kCap = 2048;       // entries per merge pass
-constexpr int kTable = 2048;     // shared-memory hash slots (power of two)
+constexpr int kTable = 1024;     // shared-memory hash slots (power of two)
 constexpr int kMergeThreads = 256;
 constexpr int kMaxProbe = 128;
 constexpr uint32_t kCodeSrc = 0xF000u;  // entry code of extra source s: kCodeSrc + s
@@ -64,6 +64,9 @@ constexpr uint32_t kCodePre = 0xFFFFu;  // entry code of the `pre` operand
 constexpr int kMaxH = 0xEFFF;
 constexpr int kHChunk = 2048;    // H terms per emission launch (shared memory)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint16_t kNone16 = 0xFFFFu;
+constexpr int kMaxGroupBins = 512;  // bins per group (a group also starts every kMaxGroupBins bins)
+constexpr int kBatch = 4;           // entries per thread with loads in flight together
 
 __device__ __forceinline__ uint32_t table_hash(uint64_t v, uint64_t w) {
   uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w * 0xC2B2AE3D27D4EB4Full + 0x165667B19E3779F9ull);
@@ -170,7 +173,7 @@ __global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, ui
 __global__ void k_group_flags(const uint64_t* __restrict__ cpre, uint32_t nbins, uint64_t quota,
                               uint32_t* __restrict__ flag) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nbins; p += gridDim.x * blockDim.x) {
-    bool start = (p == 0) || (p == nbins / 2) || (cpre[p] / quota != cpre[p - 1] / quota);
+    bool start = (p == 0) || (p == nbins / 2) || (p % kMaxGroupBins == 0) || (cpre[p] / quota != cpre[p - 1] / quota);
     flag[p] = start ? 1u : 0u;
   }
 }
@@ -215,32 +218,43 @@ struct MergeArgs {
 };
 
 struct MergeSmem {
+  // hash table over the group's output strings
   ulonglong2 key[kTable];
-  uint32_t cnt[kTable];
-  uint32_t off[kTable];
-  uint32_t cur[kTable];
-  uint32_t pre[kTable];
+  uint32_t cnt[kTable];      // contributions per slot (the pre operand not counted)
+  uint16_t pre[kTable];      // entry holding the pre operand of the slot, or kNone16
+  uint16_t upos[kTable];     // position of the slot in the key list
+  // the occupied slots as a list of keys (insertion order); phases 2-5 run over it
+  uint16_t ulist[kTable];
+  uint32_t uoff[kTable];     // per key: start of its entry run, then its output rank
+  uint32_t ucur[kTable];     // per key: scatter cursor, then its output flag
+  uint16_t ures[kTable];     // per key: entry that holds its result
+  // the entries of the current pass
   double ere[kCap];
   double eim[kCap];
   uint16_t eslot[kCap];
   uint16_t eord[kCap];
   uint16_t perm[kCap];
+  // the group's bins
+  unsigned long long gbase[kMaxGroupBins];
+  uint32_t gpre[kMaxGroupBins + 1];
   uint32_t wsum[kMergeThreads / 32];
-  uint32_t n_e;
+  uint32_t n_e, n_u;
   int flags;
   unsigned group;
   unsigned long long out_base;
+  ulonglong2 cur_sent;
 };
 
-// Exclusive block scan of kTable counters in place (each thread owns kTable/blockDim consecutive slots).
-__device__ __forceinline__ uint32_t block_scan_table(MergeSmem& s, uint32_t* arr, uint32_t* out) {
+// Exclusive block scan of arr[0..n) into out[0..n) (n <= kTable); returns the total.
+__device__ __forceinline__ uint32_t block_scan(MergeSmem& s, const uint32_t* arr, uint32_t* out, uint32_t n) {
   constexpr int per = kTable / kMergeThreads;
   const int t = threadIdx.x;
   uint32_t local[per];
   uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < per; ++k) {
-    local[k] = arr[t * per + k];
+    uint32_t i = t * per + k;
+    local[k] = i < n ? arr[i] : 0u;
     sum += local[k];
   }
   int lane = t & 31, warp = t >> 5;
@@ -253,6 +267,7 @@ __device__ __forceinline__ uint32_t block_scan_table(MergeSmem& s, uint32_t* arr
   if (lane == 31) s.wsum[warp] = incl;
   __syncthreads();
   uint32_t wpre = 0, total = 0;
+#pragma unroll
   for (int k = 0; k < kMergeThreads / 32; ++k) {
     uint32_t x = s.wsum[k];
     if (k < warp) wpre += x;
@@ -261,49 +276,71 @@ __device__ __forceinline__ uint32_t block_scan_table(MergeSmem& s, uint32_t* arr
   uint32_t run = wpre + incl - sum;
 #pragma unroll
   for (int k = 0; k < per; ++k) {
-    out[t * per + k] = run;
+    uint32_t i = t * per + k;
+    if (i < n) out[i] = run;
     run += local[k];
   }
   __syncthreads();
   return total;
 }
 
-__device__ __forceinline__ int table_insert(MergeSmem& s, ulonglong2 c, ulonglong2 sent) {
+// Insert key c (or find it).  fresh = this thread claimed the empty slot.
+__device__ __forceinline__ int table_insert(MergeSmem& s, ulonglong2 c, ulonglong2 sent, bool& fresh) {
+  fresh = false;
   uint32_t slot = table_hash(c.x, c.y) & (kTable - 1);
   for (int probe = 0; probe < kMaxProbe; ++probe) {
     ulonglong2 k = s.key[slot];
     if (k.x == c.x && k.y == c.y) return (int)slot;
     if (k.x == sent.x && k.y == sent.y) {
       ulonglong2 old = cas128_shared(&s.key[slot], sent, c);
-      if ((old.x == sent.x && old.y == sent.y) || (old.x == c.x && old.y == c.y)) return (int)slot;
+      if (old.x == sent.x && old.y == sent.y) {
+        fresh = true;
+        return (int)slot;
+      }
+      if (old.x == c.x && old.y == c.y) return (int)slot;
     }
     slot = (slot + 1) & (kTable - 1);
   }
   return -1;
 }
 
-// Rebuild entry e of the group: its key, its contribution and its order code.
-__device__ __forceinline__ void decode_entry(const MergeArgs& a, uint64_t ent, ulonglong2& key, Cx& t,
-                                             uint32_t& code) {
-  code = (uint32_t)(ent & 0xFFFFu);
-  uint64_t idx = ent >> 16;
+// Key and contribution of an entry whose operand record y has been loaded: for a product
+// (code = H index) the string h^y with 2 i^(k+rot) (h y); for a source, alpha_s y; for
+// the pre operand, y itself.
+__device__ __forceinline__ void build_contribution(const MergeArgs& a, uint32_t code, const Rec& y, ulonglong2& key,
+                                                   Cx& t) {
   if (code < kCodeSrc) {
-    const Rec x = a.X[idx];
     const Rec h = a.H[code];
-    key = make_ulonglong2(h.v ^ x.v, h.w ^ x.w);
-    int k = product_phase(h.v, h.w, x.v, x.w) + a.rot;
-    Cx p = cmul(Cx{h.re, h.im}, Cx{x.re, x.im});
+    key = make_ulonglong2(h.v ^ y.v, h.w ^ y.w);
+    int k = product_phase(h.v, h.w, y.v, y.w) + a.rot;
+    Cx p = cmul(Cx{h.re, h.im}, Cx{y.re, y.im});
     t = rot(Cx{twice(p.re), twice(p.im)}, k);
   } else if (code == kCodePre) {
-    const Rec y = a.pre[idx];
     key = make_ulonglong2(y.v, y.w);
     t = Cx{y.re, y.im};
   } else {
-    uint32_t sidx = code - kCodeSrc;
-    const Rec y = a.src[sidx][idx];
     key = make_ulonglong2(y.v, y.w);
-    t = cmul(a.alpha[sidx], Cx{y.re, y.im});
+    t = cmul(a.alpha[code - kCodeSrc], Cx{y.re, y.im});
   }
+}
+
+// Return the table to empty after a pass (only the slots the pass used).
+__device__ __forceinline__ void release_keys(MergeSmem& s, ulonglong2 sent) {
+  const uint32_t n_u = s.n_u;
+  for (uint32_t u = threadIdx.x; u < n_u; u += kMergeThreads) {
+    uint32_t slot = s.ulist[u];
+    s.key[slot] = sent;
+    s.cnt[slot] = 0;
+    s.pre[slot] = kNone16;
+    s.ucur[u] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s.n_u = 0;
+    s.n_e = 0;
+    s.flags = 0;
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
@@ -311,6 +348,20 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
   MergeSmem& s = *reinterpret_cast<MergeSmem*>(smem_raw);
   const int tid = threadIdx.x;
   const uint32_t ngroups = *a.ngroups;
+  // full initialisation once; afterwards each pass releases only what it used
+  for (int i = tid; i < kTable; i += kMergeThreads) {
+    s.key[i] = a.sent_lo;
+    s.cnt[i] = 0;
+    s.pre[i] = kNone16;
+    s.ucur[i] = 0;
+  }
+  if (tid == 0) {
+    s.n_u = 0;
+    s.n_e = 0;
+    s.flags = 0;
+    s.cur_sent = a.sent_lo;
+  }
+  __syncthreads();
 
   for (;;) {
     if (tid == 0) s.group = atomicAdd(a.next_group, 1u);
@@ -322,152 +373,215 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
     const uint64_t e0 = a.cpre[lo];
     const uint64_t E = a.cpre[hi] - e0;
     if (E == 0) continue;
-    const ulonglong2 sent = (lo >= a.nbins / 2) ? a.sent_hi : a.sent_lo;
-
-    int level = 0;  // split level: sub-pass j keeps keys whose extra hash bits equal j
-    while ((uint64_t)kCap << level < 2 * E && level < 16) ++level;
-    if (a.bits + level > kHashRows) {  // cannot split this far: report, skip the group
+    const uint32_t nb = hi - lo;  // <= kMaxGroupBins by the grouping rule
+    if (nb > (uint32_t)kMaxGroupBins) {
       if (tid == 0) atomicOr(a.err, 2);
       continue;
     }
-    if (level > 0 && tid == 0) atomicAdd(a.split_groups, 1u);
+    const ulonglong2 sent = (lo >= a.nbins / 2) ? a.sent_hi : a.sent_lo;
+    if (sent.x != s.cur_sent.x || sent.y != s.cur_sent.y) {  // groups of the other half: new empty key
+      __syncthreads();
+      for (int i = tid; i < kTable; i += kMergeThreads) s.key[i] = sent;
+      __syncthreads();
+      if (tid == 0) s.cur_sent = sent;
+    }
+    for (uint32_t i = tid; i <= nb; i += kMergeThreads) s.gpre[i] = (uint32_t)(a.cpre[lo + i] - e0);
+    for (uint32_t i = tid; i < nb; i += kMergeThreads) s.gbase[i] = a.base[lo + i];
+    __syncthreads();
 
-    for (uint32_t sub = 0; sub < (1u << level);) {
-      // ---- phase 0: clear
-      for (int i = tid; i < kTable; i += kMergeThreads) {
-        s.key[i] = sent;
-        s.cnt[i] = 0;
-        s.cur[i] = 0;
-        s.pre[i] = kNone;
-      }
-      if (tid == 0) {
-        s.n_e = 0;
-        s.flags = 0;
+    int level0 = 0;  // split level: a pass (level, sub) keeps keys whose next `level` hash bits equal sub
+    while (((uint64_t)kCap << level0) < E + E / 4 && level0 < 16) ++level0;
+    if (a.bits + level0 > kHashRows) {  // cannot split this far: report, skip the group
+      if (tid == 0) atomicOr(a.err, 2);
+      continue;
+    }
+    if (level0 > 0 && tid == 0) atomicAdd(a.split_groups, 1u);
+
+    for (uint32_t sub0 = 0; sub0 < (1u << level0); ++sub0) {
+     // a pass that does not fit is replaced by its two halves (next hash bit 0 / 1)
+     int stk_level[2 * kHashRows + 2];
+     uint32_t stk_sub[2 * kHashRows + 2];
+     int sp = 1;
+     stk_level[0] = level0;
+     stk_sub[0] = sub0;
+     while (sp > 0) {
+      --sp;
+      const int level = stk_level[sp];
+      const uint32_t sub = stk_sub[sp];
+      // ---- phase 1: rebuild entries, insert keys, count per key.  Each thread keeps
+      // kBatch entry loads and then kBatch operand gathers in flight together.
+      for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)kBatch * kMergeThreads) {
+        uint64_t ent[kBatch];
+        Rec rec[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          uint64_t j = j0 + (uint64_t)k * kMergeThreads + tid;
+          ent[k] = ~0ull;
+          if (j < E) {
+            uint32_t l = 0, r = nb;  // gpre[l] <= j < gpre[r]
+            while (r - l > 1) {
+              uint32_t m = (l + r) >> 1;
+              if (s.gpre[m] <= j) l = m; else r = m;
+            }
+            ent[k] = a.entries[s.gbase[l] + (j - s.gpre[l])];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          if (ent[k] == ~0ull) continue;
+          uint32_t code = (uint32_t)(ent[k] & 0xFFFFu);
+          uint64_t idx = ent[k] >> 16;
+          const Rec* base = code < kCodeSrc ? a.X : (code == kCodePre ? a.pre : a.src[code - kCodeSrc]);
+          rec[k] = base[idx];
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          bool keep = ent[k] != ~0ull;
+          ulonglong2 key = make_ulonglong2(0, 0);
+          Cx t{0.0, 0.0};
+          uint32_t code = 0;
+          if (keep) {
+            code = (uint32_t)(ent[k] & 0xFFFFu);
+            build_contribution(a, code, rec[k], key, t);
+            if (level > 0) keep = dev_hash(key.x, key.y, a.bits, level) == sub;
+          }
+          // warp-aggregated entry index for the kept entries
+          unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (!m) continue;
+          const int lane = tid & 31, leader = __ffs(m) - 1;
+          uint32_t eb = 0;
+          if (lane == leader) eb = atomicAdd(&s.n_e, (uint32_t)__popc(m));
+          eb = __shfl_sync(0xffffffffu, eb, leader);
+          if (!keep) continue;
+          uint32_t e = eb + __popc(m & ((1u << lane) - 1));
+          if (e >= (uint32_t)kCap) {
+            atomicOr(&s.flags, 1);
+            continue;
+          }
+          bool fresh;
+          int slot = table_insert(s, key, sent, fresh);
+          if (slot < 0) {
+            atomicOr(&s.flags, 1);
+            continue;
+          }
+          if (fresh) {
+            uint32_t u = atomicAdd(&s.n_u, 1u);
+            s.ulist[u] = (uint16_t)slot;
+            s.upos[slot] = (uint16_t)u;
+          }
+          s.eslot[e] = (uint16_t)slot;
+          s.ere[e] = t.re;
+          s.eim[e] = t.im;
+          if (code == kCodePre) {
+            s.eord[e] = 0xFFFF;
+            s.pre[slot] = (uint16_t)e;
+          } else {
+            s.eord[e] = (uint16_t)code;
+            atomicAdd(&s.cnt[slot], 1u);
+          }
+        }
       }
       __syncthreads();
-      // ---- phase 1: rebuild entries, insert keys, count per key
-      for (uint64_t j = tid; j < E; j += kMergeThreads) {
-        // locate bin of flat entry j (binary search on the prefix of bin counts)
-        uint32_t l = lo, r = hi;  // cpre[l] - e0 <= j < cpre[r] - e0
-        while (r - l > 1) {
-          uint32_t m = (l + r) >> 1;
-          if (a.cpre[m] - e0 <= j) l = m; else r = m;
-        }
-        uint64_t ent = a.entries[a.base[l] + (j - (a.cpre[l] - e0))];
-        ulonglong2 key;
-        Cx t;
-        uint32_t code;
-        decode_entry(a, ent, key, t, code);
-        if (level > 0) {
-          uint32_t fx = dev_hash(key.x, key.y, a.bits, level);
-          if (fx != sub) continue;
-        }
-        uint32_t e = atomicAdd(&s.n_e, 1u);
-        if (e >= (uint32_t)kCap) {
-          atomicOr(&s.flags, 1);
-          continue;
-        }
-        int slot = table_insert(s, key, sent);
-        if (slot < 0) {
-          atomicOr(&s.flags, 1);
-          continue;
-        }
-        s.eslot[e] = (uint16_t)slot;
-        s.ere[e] = t.re;
-        s.eim[e] = t.im;
-        if (code == kCodePre) {
-          s.eord[e] = 0xFFFF;
-          s.pre[slot] = e;
-        } else {
-          s.eord[e] = (uint16_t)code;
-          atomicAdd(&s.cnt[slot], 1u);
-        }
-      }
-      __syncthreads();
-      if (s.flags) {  // this pass did not fit: split further and restart the group
-        __syncthreads();
-        if (level >= 16 || a.bits + level + 1 > kHashRows) {
+      if (s.flags) {  // this pass did not fit: process its two halves instead
+        release_keys(s, sent);
+        if (level >= 16 || a.bits + level + 1 > kHashRows || sp + 2 > 2 * kHashRows + 2) {
           if (tid == 0) atomicOr(a.err, 2);
-          break;
+          continue;
         }
         if (level == 0 && tid == 0) atomicAdd(a.split_groups, 1u);
-        ++level;
-        sub = 0;
+        stk_level[sp] = level + 1;
+        stk_sub[sp] = sub + (1u << level);
+        stk_level[sp + 1] = level + 1;
+        stk_sub[sp + 1] = sub;
+        sp += 2;
         continue;
       }
-      const uint32_t n_e = s.n_e;
-      // ---- phase 2: offsets of each key's entry list
-      block_scan_table(s, s.cnt, s.off);
+      const uint32_t n_e = s.n_e, n_u = s.n_u;
+      // ---- phase 2: start of each key's entry run
+      {
+        // gather per-key counts in list order into ucur (still zero), scan into uoff
+        for (uint32_t u = tid; u < n_u; u += kMergeThreads) s.ucur[u] = s.cnt[s.ulist[u]];
+        __syncthreads();
+        block_scan(s, s.ucur, s.uoff, n_u);
+        for (uint32_t u = tid; u < n_u; u += kMergeThreads) s.ucur[u] = 0;
+        __syncthreads();
+      }
       // ---- phase 3: scatter entry indices per key
       for (uint32_t e = tid; e < n_e; e += kMergeThreads) {
         if (s.eord[e] == 0xFFFF) continue;
-        uint32_t slot = s.eslot[e];
-        uint32_t pos = s.off[slot] + atomicAdd(&s.cur[slot], 1u);
+        uint32_t u = s.upos[s.eslot[e]];
+        uint32_t pos = s.uoff[u] + atomicAdd(&s.ucur[u], 1u);
         s.perm[pos] = (uint16_t)e;
       }
       __syncthreads();
-      // ---- phase 4: per key, sum contributions in increasing order code
-      for (int slot = tid; slot < kTable; slot += kMergeThreads) {
-        uint32_t n = s.cnt[slot];
-        uint32_t pe = s.pre[slot];
-        uint32_t outflag = 0, res = kNone;
-        if (n > 0 || pe != kNone) {
-          const uint32_t o = s.off[slot];
-          Cx acc{0.0, 0.0};
-          int last = -1;
-          for (uint32_t m = 0; m < n; ++m) {  // selection in (order code, entry) order
-            int best = 0x7FFFFFFF, bi = -1;
-            for (uint32_t q = 0; q < n; ++q) {
-              int e = (int)s.perm[o + q];
-              int key = ((int)s.eord[e] << 11) | e;
-              if (key > last && key < best) { best = key; bi = e; }
+      // ---- phase 4: per key, sum its contributions in increasing order code
+      for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
+        const uint32_t slot = s.ulist[u];
+        const uint32_t n = s.cnt[slot];
+        const uint32_t pe = s.pre[slot];
+        const uint32_t o = s.uoff[u];
+        Cx acc{0.0, 0.0};
+        int last = -1;
+        for (uint32_t m = 0; m < n; ++m) {  // selection in (order code, entry) order
+          int best = 0x7FFFFFFF, bi = -1;
+          for (uint32_t q = 0; q < n; ++q) {
+            int e = (int)s.perm[o + q];
+            int key = ((int)s.eord[e] << 11) | e;
+            if (key > last && key < best) {
+              best = key;
+              bi = e;
             }
-            if (bi < 0) break;
-            last = best;
-            Cx t{s.ere[bi], s.eim[bi]};
-            if (m == 0) acc = t;
-            else { acc.re = add_rn(acc.re, t.re); acc.im = add_rn(acc.im, t.im); }
           }
-          Cx r;
-          if (a.has_post) {
-            Cx sc = (n > 0) ? cmul(a.post, acc) : Cx{0.0, 0.0};
-            if (pe != kNone) {
-              Cx pv{s.ere[pe], s.eim[pe]};
-              r = (n > 0) ? Cx{add_rn(pv.re, sc.re), add_rn(pv.im, sc.im)} : pv;
-            } else {
-              r = sc;
-            }
-          } else {
-            r = acc;
-          }
-          if (!(is_zero(r.re) && is_zero(r.im))) {
-            outflag = 1;
-            res = (n > 0) ? (uint32_t)s.perm[o] : pe;
-            s.ere[res] = r.re;
-            s.eim[res] = r.im;
+          if (bi < 0) break;
+          last = best;
+          Cx t{s.ere[bi], s.eim[bi]};
+          if (m == 0) acc = t;
+          else {
+            acc.re = add_rn(acc.re, t.re);
+            acc.im = add_rn(acc.im, t.im);
           }
         }
-        s.cur[slot] = res;
-        s.cnt[slot] = outflag;
+        Cx r;
+        if (a.has_post) {
+          Cx sc = (n > 0) ? cmul(a.post, acc) : Cx{0.0, 0.0};
+          if (pe != kNone16) {
+            Cx pv{s.ere[pe], s.eim[pe]};
+            r = (n > 0) ? Cx{add_rn(pv.re, sc.re), add_rn(pv.im, sc.im)} : pv;
+          } else {
+            r = sc;
+          }
+        } else {
+          r = acc;
+        }
+        uint32_t flag = 0;
+        if (!(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16)) {
+          flag = 1;
+          uint32_t res = (n > 0) ? (uint32_t)s.perm[o] : pe;
+          s.ere[res] = r.re;
+          s.eim[res] = r.im;
+          s.ures[u] = (uint16_t)res;
+        }
+        s.ucur[u] = flag;
       }
       __syncthreads();
       // ---- phase 5: compact and write
-      uint32_t U = block_scan_table(s, s.cnt, s.off);
+      uint32_t U = block_scan(s, s.ucur, s.uoff, n_u);
       if (tid == 0) s.out_base = U ? atomicAdd(a.out_n, (unsigned long long)U) : 0ull;
       __syncthreads();
       const unsigned long long ob = s.out_base;
       if (ob + U > a.out_cap) {
         if (tid == 0) atomicOr(a.err, 1);
       } else {
-        for (int slot = tid; slot < kTable; slot += kMergeThreads) {
-          if (!s.cnt[slot]) continue;
-          uint32_t res = s.cur[slot];
-          ulonglong2 k = s.key[slot];
-          a.out[ob + s.off[slot]] = Rec{k.x, k.y, s.ere[res], s.eim[res]};
+        for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
+          if (!s.ucur[u]) continue;
+          ulonglong2 k = s.key[s.ulist[u]];
+          uint32_t res = s.ures[u];
+          a.out[ob + s.uoff[u]] = Rec{k.x, k.y, s.ere[res], s.eim[res]};
         }
       }
       __syncthreads();
-      ++sub;
+      release_keys(s, sent);
+     }
     }
   }
 }

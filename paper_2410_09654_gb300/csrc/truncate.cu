@@ -38,15 +38,23 @@ __device__ __forceinline__ double sq_sum(double re, double im) {
   return add_rn(a, b);
 }
 
-// Steps 1-3 with compaction (order of survivors is unspecified).
+// Steps 1-3 with compaction (order of survivors is unspecified).  For a later top-k
+// select it also stores each survivor's |c|^2 bit pattern (non-negative doubles order
+// like their bit patterns) and histograms its top kDigitBits bits.
 __global__ void k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a, Rec* __restrict__ out,
-                         unsigned long long* __restrict__ n_out) {
+                         uint64_t* __restrict__ ab, unsigned* __restrict__ hist0, unsigned long long* __restrict__ n_out) {
+  __shared__ unsigned s_hist[kBins];
+  if (hist0) {
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+  }
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t iters = ceil_div_dev(n, stride);
   for (int64_t it = 0; it < iters; ++it) {
     int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool keep = false;
     Rec r;
+    uint64_t a2 = 0;
     if (i < n) {
       r = in[i];
       if (a.use_div) {
@@ -60,7 +68,11 @@ __global__ void k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a, Rec
         r.im = is_zero(r.im) ? r.im : __dmul_rn(r.im, f);
       }
       keep = !(a.max_weight >= 0 && wt > a.max_weight) && !(is_zero(r.re) && is_zero(r.im));
-      if (keep && a.use_cut) keep = !(sq_sum(r.re, r.im) < a.cut2);
+      if (keep && (a.use_cut || ab)) {
+        double q = sq_sum(r.re, r.im);
+        a2 = (uint64_t)__double_as_longlong(q);
+        if (a.use_cut) keep = !(q < a.cut2);
+      }
     }
     unsigned mask = __ballot_sync(0xffffffffu, keep);
     if (!mask) continue;
@@ -68,29 +80,39 @@ __global__ void k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a, Rec
     unsigned long long base = 0;
     if (lane == __ffs(mask) - 1) base = atomicAdd(n_out, (unsigned long long)__popc(mask));
     base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
-    if (keep) out[base + __popc(mask & ((1u << lane) - 1))] = r;
+    if (keep) {
+      unsigned long long o = base + __popc(mask & ((1u << lane) - 1));
+      out[o] = r;
+      if (ab) {
+        ab[o] = a2;
+        atomicAdd(&s_hist[a2 >> (64 - kDigitBits)], 1u);
+      }
+    }
+  }
+  if (hist0) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x)
+      if (s_hist[i]) atomicAdd(&hist0[i], s_hist[i]);
   }
 }
 
-// rank key digit d (0 = most significant) of record r
-__device__ __forceinline__ uint32_t rank_digit(const Rec& r, int d) {
-  uint64_t k0 = (uint64_t)__double_as_longlong(sq_sum(r.re, r.im));
-  uint64_t k1 = ~r.v, k2 = ~r.w;
-  int hi = 192 - d * kDigitBits;           // bits [lo, hi) of the 192-bit key, counted from bit 0 = LSB of k2
+// Digit d (0 = most significant) of the 192-bit rank key (k0, k1, k2), kDigitBits wide.
+__device__ __forceinline__ uint32_t rank_digit(const uint64_t k[3], int d) {
+  int hi = 192 - d * kDigitBits;  // bits [lo, hi), bit 0 = LSB of k2
   int lo = max(hi - kDigitBits, 0);
   uint32_t out = 0;
   for (int b = hi - 1; b >= lo; --b) {
-    uint64_t word = b >= 128 ? k0 : (b >= 64 ? k1 : k2);
+    uint64_t word = b >= 128 ? k[0] : (b >= 64 ? k[1] : k[2]);
     out = (out << 1) | (uint32_t)((word >> (b & 63)) & 1);
   }
   return out;
 }
 
-// Full 192-bit rank key as 3 words (k0 most significant).
-__device__ __forceinline__ void rank_key(const Rec& r, uint64_t k[3]) {
-  k[0] = (uint64_t)__double_as_longlong(sq_sum(r.re, r.im));
-  k[1] = ~r.v;
-  k[2] = ~r.w;
+// Rank key: (|c|^2 bits, ~v, ~w); larger key = kept first (larger |c|, then smaller v, w).
+__device__ __forceinline__ void rank_key(uint64_t a2, const Rec* r, uint64_t k[3]) {
+  k[0] = a2;
+  k[1] = r ? ~r->v : 0;
+  k[2] = r ? ~r->w : 0;
 }
 
 // Select state: the digits fixed so far, the rank still needed inside the current prefix.
@@ -112,52 +134,75 @@ __device__ __forceinline__ bool matches_prefix(const uint64_t k[3], const SelSta
   return true;
 }
 
-__global__ void k_sel_hist(const Rec* __restrict__ d, int64_t n, const SelState* __restrict__ st_p, int pass,
-                           unsigned* __restrict__ hist) {
+__global__ void k_sel_hist(const Rec* __restrict__ d, const uint64_t* __restrict__ ab, int64_t n,
+                           const SelState* __restrict__ st_p, int pass, unsigned* __restrict__ hist) {
   __shared__ unsigned s_hist[kBins];
   SelState st = *st_p;
   if (st.done) return;
+  const bool need_key = (pass + 1) * kDigitBits > 64;  // this pass reads bits of ~v / ~w
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    Rec r = d[i];
     uint64_t k[3];
-    rank_key(r, k);
+    Rec r;
+    if (need_key) r = d[i];
+    rank_key(ab[i], need_key ? &r : nullptr, k);
     if (!matches_prefix(k, st, pass)) continue;
-    atomicAdd(&s_hist[rank_digit(r, pass)], 1u);
+    atomicAdd(&s_hist[rank_digit(k, pass)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kBins; i += blockDim.x)
     if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
 }
 
-// Pick the digit of the need-th largest key in the current prefix (single block).
-__global__ void k_sel_pick(SelState* st_p, int pass, unsigned* __restrict__ hist) {
-  __shared__ unsigned s_hist[kBins];
-  SelState st = *st_p;
+// Pick the digit of the need-th largest key in the current prefix (one block of 256
+// threads): a block-wide scan of the histogram from the top bin down finds the one bin
+// b with above(b) < need <= above(b) + hist(b).
+__global__ void __launch_bounds__(256) k_sel_pick(SelState* st_p, int pass, unsigned* __restrict__ hist) {
+  constexpr int per = kBins / 256;
+  __shared__ unsigned long long s_w[8];
+  __shared__ int s_sel;
+  __shared__ unsigned long long s_above;
+  const SelState st = *st_p;
   if (st.done) return;
-  for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
-    s_hist[i] = hist[i];
-    hist[i] = 0;  // ready for the next pass
+  const int hi = 192 - pass * kDigitBits;
+  const int width = min(kDigitBits, hi);
+  const int top = (1 << width) - 1;
+  const int t = threadIdx.x;
+  // thread t owns ranks r = t*per .. t*per+per-1, rank r = bin (top - r)
+  unsigned h[per];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    int b = top - (t * per + k);
+    h[k] = b >= 0 ? hist[b] : 0u;
+    sum += h[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long cum = 0;
-    int hi = 192 - pass * kDigitBits;
-    int width = min(kDigitBits, hi);
-    int top = (1 << width) - 1;
-    int sel = 0;
-    unsigned long long above = 0;
-    for (int b = top; b >= 0; --b) {
-      if (cum + s_hist[b] >= st.need) {
-        sel = b;
-        above = cum;
-        break;
-      }
-      cum += s_hist[b];
+  for (int i = t; i < kBins; i += 256) hist[i] = 0;  // ready for the next pass
+  int lane = t & 31, warp = t >> 5;
+  unsigned long long incl = sum;
+  for (int d = 1; d < 32; d <<= 1) {
+    unsigned long long u = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += u;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  if (t == 0) s_sel = -1;
+  __syncthreads();
+  unsigned long long run = incl - sum;
+  for (int k = 0; k < warp; ++k) run += s_w[k];
+  for (int k = 0; k < per; ++k) {
+    int b = top - (t * per + k);
+    if (b >= 0 && run < st.need && st.need <= run + h[k]) {
+      s_sel = b;
+      s_above = run;
     }
-    // write the selected digit into the prefix: bits [hi - width, hi)
-    int lo = hi - width;
+    run += h[k];
+  }
+  __syncthreads();
+  if (t == 0 && s_sel >= 0) {
+    const int sel = s_sel;
+    const int lo = hi - width;
     for (int j = 0; j < width; ++j) {
       int b = lo + j;  // bit index counted from LSB of k2
       if ((sel >> j) & 1) {
@@ -165,15 +210,23 @@ __global__ void k_sel_pick(SelState* st_p, int pass, unsigned* __restrict__ hist
         st_p->prefix[word] |= 1ull << (b & 63);
       }
     }
-    unsigned long long need = st.need - above;
-    st_p->need = need;
+    st_p->need = st.need - s_above;
     st_p->pass = pass + 1;
-    if (s_hist[sel] == need || lo == 0) st_p->done = 1;  // every key in this bin is kept (or key fully fixed)
+  }
+  __syncthreads();
+  // the selected bin's count decides whether every key in it is kept
+  for (int k = 0; k < per; ++k) {
+    int b = top - (t * per + k);
+    if (b >= 0 && b == s_sel) {
+      const int lo = hi - width;
+      if (h[k] == st.need - s_above || lo == 0) st_p->done = 1;
+    }
   }
 }
 
 // keep iff rank key >= threshold (prefix with zero low bits), or in the keep set (sorted keys)
-__global__ void k_sel_compact(const Rec* __restrict__ in, int64_t n, const SelState* __restrict__ st_p,
+__global__ void k_sel_compact(const Rec* __restrict__ in, const uint64_t* __restrict__ ab, int64_t n,
+                              const SelState* __restrict__ st_p,
                               const ulonglong2* __restrict__ keep, int64_t nkeep, Rec* __restrict__ out,
                               unsigned long long* __restrict__ n_out) {
   const SelState st = *st_p;
@@ -186,7 +239,7 @@ __global__ void k_sel_compact(const Rec* __restrict__ in, int64_t n, const SelSt
     if (i < n) {
       r = in[i];
       uint64_t k[3];
-      rank_key(r, k);
+      rank_key(ab[i], &r, k);
       kp = (k[0] > st.prefix[0]) || (k[0] == st.prefix[0] && (k[1] > st.prefix[1] || (k[1] == st.prefix[1] && k[2] >= st.prefix[2])));
       if (!kp && nkeep > 0) {
         int64_t l = 0, h = nkeep;
@@ -244,7 +297,14 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   }
   Rec* cand = nullptr;
   PS_TRY(dev_alloc((void**)&cand, (size_t)O->n * sizeof(Rec), s));
-  PS_LAUNCH("k_filter", s, k_filter<<<grid_for(O->n), 256, 0, s>>>(O->d, O->n, a, cand, cnt.p));
+  Buf<uint64_t> ab;
+  Buf<unsigned> hist;
+  if (use_top && O->n > P->top_k) {
+    PS_TRY(ab.alloc((size_t)O->n, s));
+    PS_TRY(hist.alloc(kBins, s));
+    PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
+  }
+  PS_LAUNCH("k_filter", s, k_filter<<<grid_for(O->n), 256, 0, s>>>(O->d, O->n, a, cand, ab.p, hist.p, cnt.p));
   cudaError_t e = cudaGetLastError();
   unsigned long long nc = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nc, cnt.p, sizeof(nc), cudaMemcpyDeviceToHost, s);
@@ -258,14 +318,11 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
 
   // ---- top-k select
   Buf<SelState> st;
-  Buf<unsigned> hist;
   Buf<ulonglong2> keepk;
   PS_TRY(st.alloc(1, s));
-  PS_TRY(hist.alloc(kBins, s));
   SelState h0{};
   h0.need = (unsigned long long)P->top_k;
   PS_CUDA(cudaMemcpyAsync(st.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
-  PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
   int64_t nkeep = 0;
   if (keep && keep->n > 0) {
     std::vector<Rec> hk((size_t)keep->n);
@@ -281,7 +338,8 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   int hb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)nc, 256), 4 * nsm));
   // |c|^2 digits first (6 passes); the key digits only matter for exact ties
   for (int pass = 0; pass < kPasses; ++pass) {
-    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(cand, (int64_t)nc, st.p, pass, hist.p));
+    if (pass > 0)  // the first histogram came with the filter
+      PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(cand, ab.p, (int64_t)nc, st.p, pass, hist.p));
     PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, pass, hist.p));
     if (pass == 5 || pass == kPasses - 1) {
       SelState hs;
@@ -294,7 +352,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   Rec* outb = nullptr;
   int64_t ocap = (int64_t)nc;  // kept <= top_k + |keep| <= nc
   PS_TRY(dev_alloc((void**)&outb, (size_t)std::max<int64_t>(ocap, 1) * sizeof(Rec), s));
-  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<grid_for((int64_t)nc), 256, 0, s>>>(cand, (int64_t)nc, st.p, keepk.p, nkeep, outb, cnt.p + 1));
+  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<grid_for((int64_t)nc), 256, 0, s>>>(cand, ab.p, (int64_t)nc, st.p, keepk.p, nkeep, outb, cnt.p + 1));
   e = cudaGetLastError();
   unsigned long long nk = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nk, cnt.p + 1, sizeof(nk), cudaMemcpyDeviceToHost, s);
