@@ -257,7 +257,7 @@ def main():
     avg_s = kms / 1e3 / max(klaunch, 1)
     roof = {"kernel": kname, "share": kms / max(sum(v[1] for v in prof.values()), 1e-9)}
     per_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in prof.items()}
-    if kname == "k_merge":
+    if kname in ("k_merge", "k_merge_s"):
         # algorithmic bytes per launch: each entry (8 B) read once, its product operand (32 B)
         # gathered once, each merged output string (32 B) written once
         alg = (contributions / args.steps) * (8 + 32) + (merged / args.steps) * 32

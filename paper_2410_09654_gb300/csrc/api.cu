@@ -14,7 +14,7 @@ bool same_sites(const pauli_sum* a, const pauli_sum* b) { return !a || !b || a->
 // A library-internal temporary sum on a given stream.
 struct Tmp {
   pauli_sum s;
-  explicit Tmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0} {}
+  explicit Tmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0, 0} {}
   ~Tmp() { dev_free(s.d, s.stream); }
   Tmp(const Tmp&) = delete;
   Tmp& operator=(const Tmp&) = delete;
@@ -24,6 +24,13 @@ void swap_contents(pauli_sum* a, pauli_sum* b) {
   std::swap(a->d, b->d);
   std::swap(a->cap, b->cap);
   std::swap(a->n, b->n);
+  std::swap(a->cls, b->cls);
+}
+
+MergeSource source(const pauli_sum* p, Cx alpha) {
+  MergeSource m{p->d, p->n, alpha};
+  m.cls = p->cls;
+  return m;
 }
 
 // k = i[H, X] (rot = 1) or [H, X] (rot = 0) into out.
@@ -34,6 +41,8 @@ int commutator_into(const pauli_sum* H, const pauli_sum* X, int rot, pauli_sum* 
   sp.X = X->d;
   sp.nX = X->n;
   sp.rot = rot;
+  sp.clsH = H->cls;
+  sp.clsX = X->cls;
   return merge_run(sp, out->stream, out);
 }
 
@@ -59,8 +68,8 @@ int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_
   if (!A || !B || !out || out == A || out == B) return PS_ERR_INVALID;
   if (!same_sites(A, B) || !same_sites(A, out)) return PS_ERR_INVALID;
   MergeSpec sp;
-  sp.src[0] = MergeSource{A->d, A->n, Cx{1.0, 0.0}};
-  sp.src[1] = MergeSource{B->d, B->n, Cx{alpha_re, alpha_im}};
+  sp.src[0] = source(A, Cx{1.0, 0.0});
+  sp.src[1] = source(B, Cx{alpha_re, alpha_im});
   sp.nsrc = 2;
   return merge_run(sp, out->stream, out);
 }
@@ -85,8 +94,8 @@ int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trun
   };
   auto stage_input = [&](const pauli_sum* k, double a) -> int {  // X = O + a k
     MergeSpec sp;
-    sp.src[0] = MergeSource{O->d, O->n, Cx{1.0, 0.0}};
-    sp.src[1] = MergeSource{k->d, k->n, Cx{a, 0.0}};
+    sp.src[0] = source(O, Cx{1.0, 0.0});
+    sp.src[1] = source(k, Cx{a, 0.0});
     sp.nsrc = 2;
     return merge_run(sp, O->stream, &X.s);
   };
@@ -99,13 +108,14 @@ int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trun
   PS_TRY(L(&X.s, &k4.s));
   // S = ((k1 + 2 k2) + 2 k3) + k4;  O' = O + (dt/6) S
   MergeSpec sp;
-  sp.src[0] = MergeSource{k1.s.d, k1.s.n, Cx{1.0, 0.0}};
-  sp.src[1] = MergeSource{k2.s.d, k2.s.n, Cx{2.0, 0.0}};
-  sp.src[2] = MergeSource{k3.s.d, k3.s.n, Cx{2.0, 0.0}};
-  sp.src[3] = MergeSource{k4.s.d, k4.s.n, Cx{1.0, 0.0}};
+  sp.src[0] = source(&k1.s, Cx{1.0, 0.0});
+  sp.src[1] = source(&k2.s, Cx{2.0, 0.0});
+  sp.src[2] = source(&k3.s, Cx{2.0, 0.0});
+  sp.src[3] = source(&k4.s, Cx{1.0, 0.0});
   sp.nsrc = 4;
   sp.pre = O->d;
   sp.npre = O->n;
+  sp.clsPre = O->cls;
   sp.has_post = true;
   sp.post = Cx{h6, 0.0};
   PS_TRY(merge_run(sp, O->stream, &X.s));
@@ -127,8 +137,10 @@ int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, 
   sp.nH = (int)H->n;
   sp.X = O_cur->d;
   sp.nX = O_cur->n;
+  sp.clsH = H->cls;
+  sp.clsX = O_cur->cls;
   if (O_prev->n > 0) {
-    sp.src[0] = MergeSource{O_prev->d, O_prev->n, Cx{-b_prev, 0.0}};
+    sp.src[0] = source(O_prev, Cx{-b_prev, 0.0});
     sp.nsrc = 1;
   }
   PS_TRY(merge_run(sp, O_cur->stream, &A.s));

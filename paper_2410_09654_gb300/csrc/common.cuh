@@ -78,9 +78,25 @@ struct pauli_sum {
   ps::Rec* d;
   int64_t cap;
   int64_t n;
+  int cls;  // coefficient class: bit 0 = real parts may be non-zero, bit 1 = imaginary parts may be
 };
 
 namespace ps {
+
+// ----------------------------------------------------------------------------- coefficient classes
+// A class is the set of components that may be non-zero: 0 (no terms), 1 (real),
+// 2 (imaginary), 3 (complex).  Hermitian strings with real coefficients stay real or
+// imaginary through the whole commutator path, which lets the merge use one real
+// product per contribution.
+constexpr int kClsReal = 1, kClsImag = 2, kClsComplex = 3;
+inline int cls_swap(int c) { return ((c & 1) << 1) | ((c >> 1) & 1); }        // times i
+inline int cls_mul(int a, int b) {                                               // product of values
+  if (!a || !b) return 0;
+  if (a == kClsComplex || b == kClsComplex) return kClsComplex;
+  return a == b ? kClsReal : kClsImag;
+}
+inline int cls_of(double re, double im) { return (re != 0.0 ? 1 : 0) | (im != 0.0 ? 2 : 0); }
+int compute_cls(const Rec* d, int64_t n, cudaStream_t s, int* cls);  // reduction over a sum
 
 int sum_reserve(pauli_sum* s, int64_t cap, bool keep_contents);
 int sum_adopt(pauli_sum* s, Rec* d, int64_t cap, int64_t n);  // take ownership of a buffer
@@ -196,6 +212,7 @@ struct MergeSource {
   const Rec* rec;
   int64_t n;
   Cx alpha;
+  int cls = kClsComplex;  // coefficient class of rec
 };
 struct MergeSpec {
   const Rec* H = nullptr;
@@ -209,6 +226,7 @@ struct MergeSpec {
   int64_t npre = 0;
   bool has_post = false;
   Cx post{1.0, 0.0};
+  int clsH = kClsComplex, clsX = kClsComplex, clsPre = kClsComplex;  // coefficient classes of the operands
 };
 int merge_run(const MergeSpec& spec, cudaStream_t s, pauli_sum* out);
 void record_merge_stats(const pauli_merge_stats& st);

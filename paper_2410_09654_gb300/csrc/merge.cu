@@ -17,6 +17,7 @@
 //      then the sources in order).  That is exactly the order in which Alg. 1 with H
 //      in the outer loop adds them, so the result is independent of scheduling.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -65,8 +66,10 @@ constexpr int kMaxH = 0xEFFF;
 constexpr int kHChunk = 2048;    // H terms per emission launch (shared memory)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint16_t kNone16 = 0xFFFFu;
+constexpr int kNoPow2 = 0x7FFF;
 constexpr int kMaxGroupBins = 512;  // bins per group (a group also starts every kMaxGroupBins bins)
 constexpr int kBatch = 4;           // entries per thread with loads in flight together
+static_assert(kCap <= 2048, "order key packs the entry index in 11 bits");
 
 __device__ __forceinline__ uint32_t table_hash(uint64_t v, uint64_t w) {
   uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w * 0xC2B2AE3D27D4EB4Full + 0x165667B19E3779F9ull);
@@ -215,77 +218,44 @@ struct MergeArgs {
   int* err;               // bit 0: capacity, bit 1: unresolved table overflow
   unsigned* split_groups;
   ulonglong2 sent_lo, sent_hi;  // empty-slot keys for groups in the lower / upper half
+  // structured (single-component) mode: every coefficient is s * i^u with s real
+  const double2* hscal;   // per H term: (s, pow2 exponent of |s| or kNoPow2)
+  int uH, uX;             // u of the H and X coefficients (0 real, 1 imaginary)
+  double src_s[4];        // alpha_s = src_s * i^(src_u)
+  int src_e[4];           // pow2 exponent of |src_s| or kNoPow2
+  int src_q[4];           // u(alpha_s) + u(Y_s)
+  int src_uy[4];          // u(Y_s): the component of Y_s that holds its values
+  int pre_u;              // u of the pre operand
+  double post_s;          // post = post_s * i^(post_q - u(acc))
+  int post_q;             // u(post) + u(acc)
+  int out_imag;           // the output's non-zero component: 0 real, 1 imaginary
 };
 
+// Shared memory of one merge block.  S: single-component mode (no imaginary array).
+template <bool S>
 struct MergeSmem {
   // hash table over the group's output strings
   ulonglong2 key[kTable];
-  uint32_t cnt[kTable];      // contributions per slot (the pre operand not counted)
+  uint32_t head[kTable];     // first entry of the slot's contribution list, or kNone
   uint16_t pre[kTable];      // entry holding the pre operand of the slot, or kNone16
-  uint16_t upos[kTable];     // position of the slot in the key list
-  // the occupied slots as a list of keys (insertion order); phases 2-5 run over it
-  uint16_t ulist[kTable];
-  uint32_t uoff[kTable];     // per key: start of its entry run, then its output rank
-  uint32_t ucur[kTable];     // per key: scatter cursor, then its output flag
-  uint16_t ures[kTable];     // per key: entry that holds its result
+  uint16_t ulist[kTable];    // occupied slots (one per distinct output string)
   // the entries of the current pass
   double ere[kCap];
-  double eim[kCap];
-  uint16_t eslot[kCap];
-  uint16_t eord[kCap];
-  uint16_t perm[kCap];
+  double eim[S ? 1 : kCap];
+  uint16_t eord[kCap];       // order code: H index, or kCodeSrc + s
+  uint16_t enext[kCap];      // next entry of the same slot, or kNone16
   // the group's bins
   unsigned long long gbase[kMaxGroupBins];
   uint32_t gpre[kMaxGroupBins + 1];
-  uint32_t wsum[kMergeThreads / 32];
   uint32_t n_e, n_u;
   int flags;
   unsigned group;
-  unsigned long long out_base;
   ulonglong2 cur_sent;
 };
 
-// Exclusive block scan of arr[0..n) into out[0..n) (n <= kTable); returns the total.
-__device__ __forceinline__ uint32_t block_scan(MergeSmem& s, const uint32_t* arr, uint32_t* out, uint32_t n) {
-  constexpr int per = kTable / kMergeThreads;
-  const int t = threadIdx.x;
-  uint32_t local[per];
-  uint32_t sum = 0;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    uint32_t i = t * per + k;
-    local[k] = i < n ? arr[i] : 0u;
-    sum += local[k];
-  }
-  int lane = t & 31, warp = t >> 5;
-  uint32_t incl = sum;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += u;
-  }
-  if (lane == 31) s.wsum[warp] = incl;
-  __syncthreads();
-  uint32_t wpre = 0, total = 0;
-#pragma unroll
-  for (int k = 0; k < kMergeThreads / 32; ++k) {
-    uint32_t x = s.wsum[k];
-    if (k < warp) wpre += x;
-    total += x;
-  }
-  uint32_t run = wpre + incl - sum;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    uint32_t i = t * per + k;
-    if (i < n) out[i] = run;
-    run += local[k];
-  }
-  __syncthreads();
-  return total;
-}
-
 // Insert key c (or find it).  fresh = this thread claimed the empty slot.
-__device__ __forceinline__ int table_insert(MergeSmem& s, ulonglong2 c, ulonglong2 sent, bool& fresh) {
+template <bool S>
+__device__ __forceinline__ int table_insert(MergeSmem<S>& s, ulonglong2 c, ulonglong2 sent, bool& fresh) {
   fresh = false;
   uint32_t slot = table_hash(c.x, c.y) & (kTable - 1);
   for (int probe = 0; probe < kMaxProbe; ++probe) {
@@ -324,15 +294,65 @@ __device__ __forceinline__ void build_contribution(const MergeArgs& a, uint32_t 
   }
 }
 
+// y * 2^e when y is normal and the result stays normal (exact); ok = false otherwise.
+__device__ __forceinline__ double scale_pow2(double y, int e, bool& ok) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  int E = (int)((b >> 52) & 0x7FF);
+  int E2 = E + e;
+  ok = (E != 0 && E != 0x7FF && E2 >= 1 && E2 <= 2046);
+  return ok ? __longlong_as_double((long long)(b + ((unsigned long long)(long long)e << 52))) : 0.0;
+}
+
+__device__ __forceinline__ double neg_if(double x, bool c) {  // sign flip on the integer pipe
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
+}
+__device__ __forceinline__ bool sign_bit(double x) { return __double_as_longlong(x) < 0; }
+
+// round(s * y) for a real constant s with pow2 exponent e (kNoPow2: general), times 2^extra.
+// For a power of two the product is an exponent shift on the integer pipe; otherwise one
+// rounded FP64 product (then an exact doubling when extra == 1).
+__device__ __forceinline__ double scaled(double s, int e, double y, int extra) {
+  if (e != kNoPow2) {
+    bool ok;
+    double r = scale_pow2(y, e + extra, ok);
+    if (ok) return neg_if(r, sign_bit(s));
+  }
+  double p = __dmul_rn(s, y);
+  return extra ? twice(p) : p;
+}
+
+// Structured mode: the signed real value of the entry's single non-zero component.
+// Product: 2 i^(k+rot) (h y) with h = s_h i^uH, y = s_y i^uX gives 2 round(s_h s_y) i^q,
+// q = k + rot + uH + uX; the value is the real factor times i^(q mod 2), the sign from q & 2.
+__device__ __forceinline__ void build_scalar(const MergeArgs& a, uint32_t code, const Rec& y, ulonglong2& key,
+                                             double& t) {
+  if (code < kCodeSrc) {
+    const Rec h = a.H[code];
+    const double2 hs = a.hscal[code];
+    key = make_ulonglong2(h.v ^ y.v, h.w ^ y.w);
+    int q = (product_phase(h.v, h.w, y.v, y.w) + a.rot + a.uH + a.uX) & 3;
+    double sy = a.uX ? y.im : y.re;
+    t = neg_if(scaled(hs.x, (int)hs.y, sy, 1), (q & 2) != 0);
+  } else if (code == kCodePre) {
+    key = make_ulonglong2(y.v, y.w);
+    t = a.pre_u ? y.im : y.re;
+  } else {
+    const uint32_t si = code - kCodeSrc;
+    key = make_ulonglong2(y.v, y.w);
+    double sy = a.src_uy[si] ? y.im : y.re;
+    t = neg_if(scaled(a.src_s[si], a.src_e[si], sy, 0), (a.src_q[si] & 2) != 0);
+  }
+}
+
 // Return the table to empty after a pass (only the slots the pass used).
-__device__ __forceinline__ void release_keys(MergeSmem& s, ulonglong2 sent) {
+template <bool S>
+__device__ __forceinline__ void release_keys(MergeSmem<S>& s, ulonglong2 sent) {
   const uint32_t n_u = s.n_u;
   for (uint32_t u = threadIdx.x; u < n_u; u += kMergeThreads) {
     uint32_t slot = s.ulist[u];
     s.key[slot] = sent;
-    s.cnt[slot] = 0;
+    s.head[slot] = kNone;
     s.pre[slot] = kNone16;
-    s.ucur[u] = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -343,17 +363,20 @@ __device__ __forceinline__ void release_keys(MergeSmem& s, ulonglong2 sent) {
   __syncthreads();
 }
 
+constexpr int kSortMax = 8;  // contributions of one string sorted in registers up to this count
+
+template <bool S>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  MergeSmem& s = *reinterpret_cast<MergeSmem*>(smem_raw);
+  MergeSmem<S>& s = *reinterpret_cast<MergeSmem<S>*>(smem_raw);
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const uint32_t ngroups = *a.ngroups;
   // full initialisation once; afterwards each pass releases only what it used
   for (int i = tid; i < kTable; i += kMergeThreads) {
     s.key[i] = a.sent_lo;
-    s.cnt[i] = 0;
+    s.head[i] = kNone;
     s.pre[i] = kNone16;
-    s.ucur[i] = 0;
   }
   if (tid == 0) {
     s.n_u = 0;
@@ -408,8 +431,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
       --sp;
       const int level = stk_level[sp];
       const uint32_t sub = stk_sub[sp];
-      // ---- phase 1: rebuild entries, insert keys, count per key.  Each thread keeps
-      // kBatch entry loads and then kBatch operand gathers in flight together.
+      // ---- phase 1: rebuild entries, insert keys, chain each key's entries.  Each thread
+      // keeps kBatch entry loads and then kBatch operand gathers in flight together.
       for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)kBatch * kMergeThreads) {
         uint64_t ent[kBatch];
         Rec rec[kBatch];
@@ -442,13 +465,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
           uint32_t code = 0;
           if (keep) {
             code = (uint32_t)(ent[k] & 0xFFFFu);
-            build_contribution(a, code, rec[k], key, t);
+            if constexpr (S) build_scalar(a, code, rec[k], key, t.re);
+            else build_contribution(a, code, rec[k], key, t);
             if (level > 0) keep = dev_hash(key.x, key.y, a.bits, level) == sub;
           }
           // warp-aggregated entry index for the kept entries
           unsigned m = __ballot_sync(0xffffffffu, keep);
           if (!m) continue;
-          const int lane = tid & 31, leader = __ffs(m) - 1;
+          const int leader = __ffs(m) - 1;
           uint32_t eb = 0;
           if (lane == leader) eb = atomicAdd(&s.n_e, (uint32_t)__popc(m));
           eb = __shfl_sync(0xffffffffu, eb, leader);
@@ -464,20 +488,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
             atomicOr(&s.flags, 1);
             continue;
           }
-          if (fresh) {
-            uint32_t u = atomicAdd(&s.n_u, 1u);
-            s.ulist[u] = (uint16_t)slot;
-            s.upos[slot] = (uint16_t)u;
-          }
-          s.eslot[e] = (uint16_t)slot;
+          if (fresh) s.ulist[atomicAdd(&s.n_u, 1u)] = (uint16_t)slot;
           s.ere[e] = t.re;
-          s.eim[e] = t.im;
+          if constexpr (!S) s.eim[e] = t.im;
           if (code == kCodePre) {
-            s.eord[e] = 0xFFFF;
             s.pre[slot] = (uint16_t)e;
           } else {
             s.eord[e] = (uint16_t)code;
-            atomicAdd(&s.cnt[slot], 1u);
+            s.enext[e] = (uint16_t)atomicExch(&s.head[slot], e);
           }
         }
       }
@@ -496,87 +514,119 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
         sp += 2;
         continue;
       }
-      const uint32_t n_e = s.n_e, n_u = s.n_u;
-      // ---- phase 2: start of each key's entry run
-      {
-        // gather per-key counts in list order into ucur (still zero), scan into uoff
-        for (uint32_t u = tid; u < n_u; u += kMergeThreads) s.ucur[u] = s.cnt[s.ulist[u]];
-        __syncthreads();
-        block_scan(s, s.ucur, s.uoff, n_u);
-        for (uint32_t u = tid; u < n_u; u += kMergeThreads) s.ucur[u] = 0;
-        __syncthreads();
-      }
-      // ---- phase 3: scatter entry indices per key
-      for (uint32_t e = tid; e < n_e; e += kMergeThreads) {
-        if (s.eord[e] == 0xFFFF) continue;
-        uint32_t u = s.upos[s.eslot[e]];
-        uint32_t pos = s.uoff[u] + atomicAdd(&s.ucur[u], 1u);
-        s.perm[pos] = (uint16_t)e;
-      }
-      __syncthreads();
-      // ---- phase 4: per key, sum its contributions in increasing order code
-      for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
-        const uint32_t slot = s.ulist[u];
-        const uint32_t n = s.cnt[slot];
-        const uint32_t pe = s.pre[slot];
-        const uint32_t o = s.uoff[u];
-        Cx acc{0.0, 0.0};
-        int last = -1;
-        for (uint32_t m = 0; m < n; ++m) {  // selection in (order code, entry) order
-          int best = 0x7FFFFFFF, bi = -1;
-          for (uint32_t q = 0; q < n; ++q) {
-            int e = (int)s.perm[o + q];
-            int key = ((int)s.eord[e] << 11) | e;
-            if (key > last && key < best) {
-              best = key;
-              bi = e;
+      const uint32_t n_u = s.n_u;
+      // ---- phase 2: per string, sum its contributions in increasing order code (H order,
+      // then the sources), apply the combination, and write the non-zero results
+      for (uint32_t u0 = 0; u0 < n_u; u0 += kMergeThreads) {
+        const uint32_t u = u0 + tid;
+        Cx r{0.0, 0.0};
+        bool flag = false;
+        ulonglong2 kout = make_ulonglong2(0, 0);
+        if (u < n_u) {
+          const uint32_t slot = s.ulist[u];
+          kout = s.key[slot];
+          const uint32_t pe = s.pre[slot];
+          // collect the chain
+          int ord[kSortMax];
+          uint32_t idx[kSortMax];
+          uint32_t n = 0;
+          for (uint32_t e = s.head[slot]; e != kNone; e = (s.enext[e] == kNone16) ? kNone : s.enext[e]) {
+            if (n < kSortMax) {
+              ord[n] = ((int)s.eord[e] << 11) | (int)e;
+              idx[n] = e;
+            }
+            ++n;
+          }
+          Cx acc{0.0, 0.0};
+          if (n <= kSortMax) {
+            // insertion sort by (order code, entry); orders are distinct for distinct inputs
+            for (uint32_t i = 1; i < n; ++i) {
+              int ko = ord[i];
+              uint32_t ki = idx[i];
+              int j = (int)i - 1;
+              while (j >= 0 && ord[j] > ko) {
+                ord[j + 1] = ord[j];
+                idx[j + 1] = idx[j];
+                --j;
+              }
+              ord[j + 1] = ko;
+              idx[j + 1] = ki;
+            }
+            for (uint32_t i = 0; i < n; ++i) {
+              const uint32_t e = idx[i];
+              if constexpr (S) {
+                acc.re = (i == 0) ? s.ere[e] : add_rn(acc.re, s.ere[e]);
+              } else {
+                if (i == 0) acc = Cx{s.ere[e], s.eim[e]};
+                else {
+                  acc.re = add_rn(acc.re, s.ere[e]);
+                  acc.im = add_rn(acc.im, s.eim[e]);
+                }
+              }
+            }
+          } else {
+            // long chains: repeated selection of the next order code
+            int last = -1;
+            for (uint32_t m = 0; m < n; ++m) {
+              int best = 0x7FFFFFFF;
+              uint32_t bi = kNone;
+              for (uint32_t e = s.head[slot]; e != kNone; e = (s.enext[e] == kNone16) ? kNone : s.enext[e]) {
+                int key = ((int)s.eord[e] << 11) | (int)e;
+                if (key > last && key < best) {
+                  best = key;
+                  bi = e;
+                }
+              }
+              if (bi == kNone) break;
+              last = best;
+              if constexpr (S) {
+                acc.re = (m == 0) ? s.ere[bi] : add_rn(acc.re, s.ere[bi]);
+              } else {
+                if (m == 0) acc = Cx{s.ere[bi], s.eim[bi]};
+                else {
+                  acc.re = add_rn(acc.re, s.ere[bi]);
+                  acc.im = add_rn(acc.im, s.eim[bi]);
+                }
+              }
             }
           }
-          if (bi < 0) break;
-          last = best;
-          Cx t{s.ere[bi], s.eim[bi]};
-          if (m == 0) acc = t;
-          else {
-            acc.re = add_rn(acc.re, t.re);
-            acc.im = add_rn(acc.im, t.im);
-          }
-        }
-        Cx r;
-        if (a.has_post) {
-          Cx sc = (n > 0) ? cmul(a.post, acc) : Cx{0.0, 0.0};
-          if (pe != kNone16) {
-            Cx pv{s.ere[pe], s.eim[pe]};
-            r = (n > 0) ? Cx{add_rn(pv.re, sc.re), add_rn(pv.im, sc.im)} : pv;
+          if constexpr (S) {
+            if (a.has_post) {
+              double sc = (n > 0) ? neg_if(__dmul_rn(a.post_s, acc.re), (a.post_q & 2) != 0) : 0.0;
+              if (pe != kNone16) r.re = (n > 0) ? add_rn(s.ere[pe], sc) : s.ere[pe];
+              else r.re = sc;
+            } else {
+              r.re = acc.re;
+            }
           } else {
-            r = sc;
+            if (a.has_post) {
+              Cx sc = (n > 0) ? cmul(a.post, acc) : Cx{0.0, 0.0};
+              if (pe != kNone16) {
+                Cx pv{s.ere[pe], s.eim[pe]};
+                r = (n > 0) ? Cx{add_rn(pv.re, sc.re), add_rn(pv.im, sc.im)} : pv;
+              } else {
+                r = sc;
+              }
+            } else {
+              r = acc;
+            }
           }
-        } else {
-          r = acc;
+          flag = !(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16);
         }
-        uint32_t flag = 0;
-        if (!(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16)) {
-          flag = 1;
-          uint32_t res = (n > 0) ? (uint32_t)s.perm[o] : pe;
-          s.ere[res] = r.re;
-          s.eim[res] = r.im;
-          s.ures[u] = (uint16_t)res;
-        }
-        s.ucur[u] = flag;
-      }
-      __syncthreads();
-      // ---- phase 5: compact and write
-      uint32_t U = block_scan(s, s.ucur, s.uoff, n_u);
-      if (tid == 0) s.out_base = U ? atomicAdd(a.out_n, (unsigned long long)U) : 0ull;
-      __syncthreads();
-      const unsigned long long ob = s.out_base;
-      if (ob + U > a.out_cap) {
-        if (tid == 0) atomicOr(a.err, 1);
-      } else {
-        for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
-          if (!s.ucur[u]) continue;
-          ulonglong2 k = s.key[s.ulist[u]];
-          uint32_t res = s.ures[u];
-          a.out[ob + s.uoff[u]] = Rec{k.x, k.y, s.ere[res], s.eim[res]};
+        // warp-aggregated output slots
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          unsigned long long ob = 0;
+          if (lane == leader) ob = atomicAdd(a.out_n, (unsigned long long)__popc(m));
+          ob = __shfl_sync(0xffffffffu, ob, leader);
+          if (ob + __popc(m) > a.out_cap) {
+            if (lane == leader) atomicOr(a.err, 1);
+          } else if (flag) {
+            const unsigned long long o = ob + __popc(m & ((1u << lane) - 1));
+            if constexpr (S) a.out[o] = a.out_imag ? Rec{kout.x, kout.y, 0.0, r.re} : Rec{kout.x, kout.y, r.re, 0.0};
+            else a.out[o] = Rec{kout.x, kout.y, r.re, r.im};
+          }
         }
       }
       __syncthreads();
@@ -614,6 +664,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   st.pair_tests = pairs;
   if (bound_total == 0) {
     out->n = 0;
+    out->cls = 0;
     record_merge_stats(st);
     return PS_OK;
   }
@@ -640,6 +691,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   PS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
 
   auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
+  std::vector<Rec> hh_host;
 
   // 1. hashes, histograms and bin bounds
   if (nX > 0) {
@@ -649,10 +701,10 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
     PS_CUDA(cudaGetLastError());
     std::vector<uint32_t> hf(sp.nH);
-    std::vector<Rec> hh(sp.nH);
-    PS_CUDA(cudaMemcpyAsync(hh.data(), sp.H, sp.nH * sizeof(Rec), cudaMemcpyDeviceToHost, s));
+    hh_host.resize(sp.nH);
+    PS_CUDA(cudaMemcpyAsync(hh_host.data(), sp.H, sp.nH * sizeof(Rec), cudaMemcpyDeviceToHost, s));
     PS_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < sp.nH; ++i) hf[i] = host_hash(hh[i].v, hh[i].w, bits);
+    for (int i = 0; i < sp.nH; ++i) hf[i] = host_hash(hh_host[i].v, hh_host[i].w, bits);
     PS_TRY(fH.alloc(sp.nH, s));
     PS_CUDA(cudaMemcpyAsync(fH.p, hf.data(), sp.nH * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
   }
@@ -716,6 +768,24 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_CUDA(cudaGetLastError());
   }
 
+  // coefficient classes: the merge runs in single-component mode when every term of every
+  // output string lies in the same component (real or imaginary)
+  auto cls_scalar = [](Cx c) { return cls_of(c.re, c.im); };
+  int prod_cls = 0;
+  if (nX > 0) {
+    prod_cls = cls_mul(sp.clsH, sp.clsX);  // then times i^(k + rot) with k odd
+    if (!(sp.rot & 1)) prod_cls = cls_swap(prod_cls);
+  }
+  int acc_cls = prod_cls;
+  int src_cls[4] = {0, 0, 0, 0};
+  for (int i = 0; i < sp.nsrc; ++i) {
+    src_cls[i] = sp.src[i].n > 0 ? cls_mul(cls_scalar(sp.src[i].alpha), sp.src[i].cls) : 0;
+    acc_cls |= src_cls[i];
+  }
+  int out_cls = acc_cls;
+  if (sp.has_post) out_cls = (sp.npre > 0 ? sp.clsPre : 0) | cls_mul(cls_scalar(sp.post), acc_cls);
+  const bool structured = acc_cls != kClsComplex && out_cls != kClsComplex;
+
   // 4. merge into a fresh output buffer
   int64_t out_cap = std::max<int64_t>(total_entries, 1);
   Rec* outbuf = nullptr;
@@ -750,12 +820,47 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   host_key_with_hash(nbins / 2, bits, &kv, &kw);  // hash in the upper half: empty key for lower-half groups
   a.sent_lo = make_ulonglong2(kv, kw);
   a.sent_hi = make_ulonglong2(0ull, 0ull);        // hash 0: empty key for upper-half groups
-  size_t sm = sizeof(MergeSmem);
-  PS_CUDA(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  Buf<double2> hscal;
+  if (structured) {
+    auto pow2_exp = [](double x) -> int {
+      uint64_t b;
+      memcpy(&b, &x, 8);
+      int E = (int)((b >> 52) & 0x7FF);
+      return ((b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046) ? E - 1023 : kNoPow2;
+    };
+    a.uH = sp.clsH == kClsImag;
+    a.uX = sp.clsX == kClsImag;
+    if (nX > 0) {
+      std::vector<double2> hs(sp.nH);
+      for (int i = 0; i < sp.nH; ++i) {
+        double v = a.uH ? hh_host[i].im : hh_host[i].re;
+        hs[i] = make_double2(v, (double)pow2_exp(v));
+      }
+      PS_TRY(hscal.alloc(sp.nH, s));
+      PS_CUDA(cudaMemcpyAsync(hscal.p, hs.data(), sp.nH * sizeof(double2), cudaMemcpyHostToDevice, s));
+      a.hscal = hscal.p;
+    }
+    for (int i = 0; i < sp.nsrc; ++i) {
+      int ua = cls_scalar(sp.src[i].alpha) == kClsImag;
+      int uy = sp.src[i].cls == kClsImag;
+      a.src_s[i] = ua ? sp.src[i].alpha.im : sp.src[i].alpha.re;
+      a.src_e[i] = pow2_exp(a.src_s[i]);
+      a.src_q[i] = ua + uy;
+      a.src_uy[i] = uy;
+    }
+    a.pre_u = sp.clsPre == kClsImag;
+    int up = cls_scalar(sp.post) == kClsImag;
+    a.post_s = up ? sp.post.im : sp.post.re;
+    a.post_q = up + (acc_cls == kClsImag);
+    a.out_imag = out_cls == kClsImag;
+  }
+  size_t sm = structured ? sizeof(MergeSmem<true>) : sizeof(MergeSmem<false>);
+  auto kern = structured ? k_merge<true> : k_merge<false>;
+  PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int per_sm = 0;
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge, kMergeThreads, sm));
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMergeThreads, sm));
   int grid = std::max(1, per_sm) * nsm;
-  PS_LAUNCH("k_merge", s, k_merge<<<grid, kMergeThreads, sm, s>>>(a));
+  PS_LAUNCH(structured ? "k_merge_s" : "k_merge", s, kern<<<grid, kMergeThreads, sm, s>>>(a));
   PS_CUDA(cudaGetLastError());
   unsigned long long hres[2];
   unsigned hmisc[3];
@@ -769,6 +874,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     return (herr & 2) ? PS_ERR_TABLE_FULL : PS_ERR_CAPACITY;
   }
   PS_TRY(sum_adopt(out, outbuf, out_cap, (int64_t)hres[1]));
+  out->cls = out_cls;
   st.merged = (int64_t)hres[1];
   st.groups = hmisc[1];
   st.split_groups = hmisc[2];

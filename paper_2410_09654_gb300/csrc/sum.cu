@@ -158,6 +158,31 @@ void host_key_with_hash(uint32_t target, int bits, uint64_t* v, uint64_t* w) {
   *w = kw;
 }
 
+// ----------------------------------------------------------------------------- coefficient class
+__global__ void k_cls(const Rec* __restrict__ d, int64_t n, int* cls) {
+  int c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Rec r = d[i];
+    c |= (((__double_as_longlong(r.re) << 1) != 0) ? 1 : 0) | (((__double_as_longlong(r.im) << 1) != 0) ? 2 : 0);
+  }
+  for (int o = 16; o > 0; o >>= 1) c |= __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicOr(cls, c);
+}
+
+int compute_cls(const Rec* d, int64_t n, cudaStream_t s, int* cls) {
+  *cls = 0;
+  if (n == 0) return PS_OK;
+  Buf<int> c;
+  PS_TRY(c.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(c.p, 0, sizeof(int), s));
+  int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 4 * num_sms());
+  PS_LAUNCH("k_cls", s, k_cls<<<blocks, 256, 0, s>>>(d, n, c.p));
+  PS_CUDA(cudaGetLastError());
+  PS_CUDA(cudaMemcpyAsync(cls, c.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  return PS_OK;
+}
+
 // ----------------------------------------------------------------------------- validation kernels
 __global__ void k_check_bits(const Rec* __restrict__ d, int64_t n, uint64_t inv_mask, int* bad) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -280,7 +305,7 @@ int pauli_sum_create(int n_sites, int64_t capacity, void* cuda_stream, pauli_sum
   if (!out || n_sites < 1 || n_sites > 64 || capacity < 0) return PS_ERR_INVALID;
   *out = nullptr;
   PS_TRY(upload_hash_tables());
-  pauli_sum* s = new pauli_sum{n_sites, (cudaStream_t)cuda_stream, nullptr, 0, 0};
+  pauli_sum* s = new pauli_sum{n_sites, (cudaStream_t)cuda_stream, nullptr, 0, 0, 0};
   int st = sum_reserve(s, std::max<int64_t>(capacity, 64), false);
   if (st != PS_OK) {
     delete s;
@@ -344,6 +369,7 @@ int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const d
   if (ok) PS_TRY(check_distinct_device(s->d, n, s->stream, &ok));
   PS_CUDA(cudaStreamSynchronize(s->stream));  // the caller's host arrays may be released on return
   if (!ok) return PS_ERR_INVALID;
+  PS_TRY(compute_cls(s->d, n, s->stream, &s->cls));
   s->n = n;
   return PS_OK;
 }
@@ -377,6 +403,7 @@ int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, 
     s->n = 0;
     return PS_ERR_INVALID;
   }
+  PS_TRY(compute_cls(s->d, n, s->stream, &s->cls));
   return PS_OK;
 }
 
@@ -423,6 +450,7 @@ int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst) {
     PS_CUDA(cudaMemcpyAsync(dst->d, src->d, (size_t)src->n * sizeof(Rec), cudaMemcpyDeviceToDevice, dst->stream));
   }
   dst->n = src->n;
+  dst->cls = src->cls;
   return PS_OK;
 }
 

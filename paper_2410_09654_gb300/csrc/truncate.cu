@@ -30,12 +30,20 @@ struct TruncArgs {
   int use_div;
   double divisor;
   const double* factor;  // exp(-(gamma*dt) w), w = 0..64
+  int cls;               // coefficient class of the input: components that may be non-zero
 };
 
 __device__ __forceinline__ double sq_sum(double re, double im) {
   double a = is_zero(re) ? 0.0 : __dmul_rn(re, re);
   double b = is_zero(im) ? 0.0 : __dmul_rn(im, im);
   return add_rn(a, b);
+}
+
+// re*re + im*im when only the components in `cls` can be non-zero (identical value).
+__device__ __forceinline__ double sq_sum_cls(double re, double im, int cls) {
+  if (cls == 1) return __dmul_rn(re, re);
+  if (cls == 2) return __dmul_rn(im, im);
+  return sq_sum(re, im);
 }
 
 // Steps 1-3 with compaction (order of survivors is unspecified).  For a later top-k
@@ -57,19 +65,19 @@ __global__ void k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a, Rec
     uint64_t a2 = 0;
     if (i < n) {
       r = in[i];
-      if (a.use_div) {
-        r.re = is_zero(r.re) ? r.re : __ddiv_rn(r.re, a.divisor);
-        r.im = is_zero(r.im) ? r.im : __ddiv_rn(r.im, a.divisor);
+      if (a.use_div) {  // components outside the class are zero and stay zero
+        if (a.cls & 1) r.re = __ddiv_rn(r.re, a.divisor);
+        if (a.cls & 2) r.im = __ddiv_rn(r.im, a.divisor);
       }
       int wt = __popcll(r.v | r.w);
       if (a.use_gamma) {
         double f = a.factor[wt];
-        r.re = is_zero(r.re) ? r.re : __dmul_rn(r.re, f);
-        r.im = is_zero(r.im) ? r.im : __dmul_rn(r.im, f);
+        if (a.cls & 1) r.re = __dmul_rn(r.re, f);
+        if (a.cls & 2) r.im = __dmul_rn(r.im, f);
       }
       keep = !(a.max_weight >= 0 && wt > a.max_weight) && !(is_zero(r.re) && is_zero(r.im));
       if (keep && (a.use_cut || ab)) {
-        double q = sq_sum(r.re, r.im);
+        double q = sq_sum_cls(r.re, r.im, a.cls);
         a2 = (uint64_t)__double_as_longlong(q);
         if (a.use_cut) keep = !(q < a.cut2);
       }
@@ -286,6 +294,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   a.use_gamma = use_gamma;
   a.use_div = divisor != nullptr;
   a.divisor = divisor ? *divisor : 1.0;
+  a.cls = O->cls ? O->cls : kClsComplex;
   if (use_gamma) {
     double h[65];
     double x = P->gamma * dt;

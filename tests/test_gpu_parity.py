@@ -121,6 +121,18 @@ def test_add():
         assert_match(out.download(), orc.axpy(ref(n, A), alpha, ref(n, B)), what=f"add {alpha}")
 
 
+@pytest.mark.parametrize("ka,kb,alpha", [("real", "real", 1.0), ("real", "real", -0.75), ("imag", "imag", 0.3),
+                                         ("imag", "real", 2j), ("real", "imag", -1.5j), ("real", "real", 0.5j),
+                                         ("complex", "real", 1.0)])
+def test_add_classes(ka, kb, alpha):
+    # single-component (structured) and general merges, alpha real, imaginary or mixed class
+    n = 24
+    A = I.random_sum(41, n, 3000, ka, max_support=5)
+    B = I.random_sum(42, n, 3000, kb, max_support=5)
+    out = ps.pauli_add(dev(n, A), alpha, dev(n, B))
+    assert_match(out.download(), orc.axpy(ref(n, A), alpha, ref(n, B)), what=f"add {ka} {kb} {alpha}")
+
+
 @pytest.mark.parametrize("case", range(6))
 def test_truncate(case):
     rng = np.random.default_rng(500 + case)
