@@ -152,6 +152,27 @@ int pauli_trace_product(const pauli_sum* A, const pauli_sum* B, double* re, doub
  * read with the square root), from the exactly rounded sum of squares. */
 int pauli_norm(const pauli_sum* O, double* out);
 
+/* Allocation-free variant of pauli_trace_product, for callers that cannot allocate
+ * device memory (code running under another framework's allocator or memory budget,
+ * plug-ins handed only pre-allocated buffers, code that must not call cudaMalloc while
+ * a CUDA graph is being captured elsewhere in the process).  The paper has no
+ * counterpart; it computes the same exactly rounded Tr(AB)/2^N.
+ *   av, aw, are, aim: DEVICE arrays of A's na strings (masks and coefficients);
+ *   bv, bw, bre, bim: DEVICE arrays of B's nb strings; both caller-owned, read only;
+ *     strings within each operand must be distinct;
+ *   cuda_stream: the cudaStream_t the work is ordered on (NULL: legacy default stream);
+ *   re, im: HOST doubles receiving the result; the call synchronises the stream.
+ * Scratch lives in one fixed device array of about 6 MiB inside the library (held by
+ * every GPU that loads it, until exit): no cudaMalloc, cudaFree or allocating library
+ * routine is called.  The smaller of na, nb may be at most 131072 strings; larger
+ * inputs return PS_ERR_CAPACITY without launching anything.  The first call on a device
+ * looks up the scratch address on that device (make that first call before any stream
+ * capture).  Every call reuses the same scratch, so calls that overlap on the GPU (on
+ * different streams, or from different host threads) race: serialise them. */
+int pauli_trace_product_noalloc(const uint64_t* av, const uint64_t* aw, const double* are, const double* aim,
+                                int64_t na, const uint64_t* bv, const uint64_t* bw, const double* bre,
+                                const double* bim, int64_t nb, void* cuda_stream, double* re, double* im);
+
 /* ------------------------------------------------------------------ statistics */
 /* Counters of the last pauli_commutator / merge on this sum's stream: pair tests
  * (|H|*|O|), anticommuting contributions, merged output strings. */

@@ -99,6 +99,7 @@ def load(build_if_missing: bool = False):
         "pauli_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "pauli_profile_report": ([ctypes.c_char_p, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_launch_count": ([], I64),
+        "pauli_trace_product_noalloc": ([P, P, P, P, I64, P, P, P, P, I64, P, F64P, F64P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +256,19 @@ def pauli_lanczos_step(H: PauliSum, O_prev: PauliSum, O_cur: PauliSum, b_prev: f
 def pauli_trace_product(A: PauliSum, B: PauliSum) -> complex:
     re, im = ctypes.c_double(), ctypes.c_double()
     _check(load().pauli_trace_product(A.handle, B.handle, ctypes.byref(re), ctypes.byref(im)), "pauli_trace_product")
+    return complex(re.value, im.value)
+
+
+def pauli_trace_product_noalloc(a_arrays, b_arrays, stream=None) -> complex:
+    """Allocation-free Tr(AB)/2^N from device arrays: a_arrays/b_arrays are (v, w, re, im)
+    torch CUDA tensors (64-bit masks, float64 coefficients)."""
+    lib = load()
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(lib.pauli_trace_product_noalloc(*[ptr(t) for t in a_arrays], int(a_arrays[0].numel()),
+                                           *[ptr(t) for t in b_arrays], int(b_arrays[0].numel()), st,
+                                           ctypes.byref(re), ctypes.byref(im)), "pauli_trace_product_noalloc")
     return complex(re.value, im.value)
 
 
