@@ -343,6 +343,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
+            "launches_before_timed": launches0,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -244,18 +244,25 @@ struct MergeSmem {
   double eim[S ? 1 : kCap];
   uint16_t eord[kCap];       // order code: H index, or kCodeSrc + s
   uint16_t enext[kCap];      // next entry of the same slot, or kNone16
+  // results of the current pass, staged for one contiguous output reservation
+  double ore[kTable];
+  double oim[S ? 1 : kTable];
+  uint16_t oslot[kTable];
   // the group's bins
   unsigned long long gbase[kMaxGroupBins];
   uint32_t gpre[kMaxGroupBins + 1];
-  uint32_t n_e, n_u;
+  uint16_t longq[kTable];    // slots whose chains are longer than 4
+  uint32_t n_e, n_u, n_out, n_long;
   int flags;
   unsigned group;
+  unsigned long long out_base;
   ulonglong2 cur_sent;
 };
 
-// Insert key c (or find it).  fresh = this thread claimed the empty slot.
-template <bool S>
-__device__ __forceinline__ int table_insert(MergeSmem<S>& s, ulonglong2 c, ulonglong2 sent, bool& fresh) {
+// Insert key c (or find it) in a shared-memory table of kTable slots (any layout with a
+// `key` array).  fresh = this thread claimed the empty slot.
+template <class SM>
+__device__ __forceinline__ int table_insert(SM& s, ulonglong2 c, ulonglong2 sent, bool& fresh) {
   fresh = false;
   uint32_t slot = table_hash(c.x, c.y) & (kTable - 1);
   for (int probe = 0; probe < kMaxProbe; ++probe) {
@@ -358,12 +365,170 @@ __device__ __forceinline__ void release_keys(MergeSmem<S>& s, ulonglong2 sent) {
   if (threadIdx.x == 0) {
     s.n_u = 0;
     s.n_e = 0;
+    s.n_out = 0;
+    s.n_long = 0;
     s.flags = 0;
   }
   __syncthreads();
 }
 
-constexpr int kSortMax = 8;  // contributions of one string sorted in registers up to this count
+constexpr int kNet = 16;         // chains up to this length are sorted in registers
+constexpr int kLongChain = 64;   // longer chains: local-array insertion sort; beyond it, selection
+
+// Bitonic sorting network on (k, e) pairs, ascending in k, fully unrolled (registers only).
+template <int N>
+__device__ __forceinline__ void sort_net(int (&k)[N], uint32_t (&e)[N]) {
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ stride;
+        if (l > i) {
+          const bool up = (i & size) == 0;
+          if ((k[i] > k[l]) == up) {
+            int t = k[i]; k[i] = k[l]; k[l] = t;
+            uint32_t u = e[i]; e[i] = e[l]; e[l] = u;
+          }
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t chain_next(const uint16_t* enext, uint32_t e) {
+  return enext[e] == kNone16 ? kNone : (uint32_t)enext[e];
+}
+
+template <bool S>
+__device__ __forceinline__ void acc_add(MergeSmem<S>& s, Cx& acc, uint32_t e, bool first) {
+  if constexpr (S) {
+    acc.re = first ? s.ere[e] : add_rn(acc.re, s.ere[e]);
+  } else {
+    if (first) acc = Cx{s.ere[e], s.eim[e]};
+    else {
+      acc.re = add_rn(acc.re, s.ere[e]);
+      acc.im = add_rn(acc.im, s.eim[e]);
+    }
+  }
+}
+
+// Sum a slot's chain in (order code, entry) order when it holds at most W entries (sorted
+// in registers); returns false, summing nothing, when the chain is longer.
+template <bool S, int W>
+__device__ __forceinline__ bool chain_sum_regs(MergeSmem<S>& s, uint32_t slot, Cx& acc, uint32_t& n) {
+  int ko[W];
+  uint32_t ke[W];
+  uint32_t e = s.head[slot];
+  n = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    if (e != kNone) {
+      ko[i] = ((int)s.eord[e] << 11) | (int)e;
+      ke[i] = e;
+      e = chain_next(s.enext, e);
+      ++n;
+    } else {
+      ko[i] = 0x7FFFFFFF;
+      ke[i] = 0;
+    }
+  }
+  if (e != kNone) return false;
+  sort_net<W>(ko, ke);
+#pragma unroll
+  for (int i = 0; i < W; ++i)
+    if ((uint32_t)i < n) acc_add(s, acc, ke[i], i == 0);
+  return true;
+}
+
+// Any chain length: a local-array insertion sort up to kLongChain, else repeated selection.
+template <bool S>
+__device__ __forceinline__ void chain_sum_long(MergeSmem<S>& s, uint32_t slot, Cx& acc, uint32_t& n) {
+  int lo_[kLongChain];
+  uint32_t le_[kLongChain];
+  uint32_t m = 0;
+  uint32_t x = s.head[slot];
+  for (; x != kNone && m < (uint32_t)kLongChain; x = chain_next(s.enext, x)) {
+    int key = ((int)s.eord[x] << 11) | (int)x;
+    int j = (int)m - 1;
+    while (j >= 0 && lo_[j] > key) {
+      lo_[j + 1] = lo_[j];
+      le_[j + 1] = le_[j];
+      --j;
+    }
+    lo_[j + 1] = key;
+    le_[j + 1] = x;
+    ++m;
+  }
+  if (x == kNone) {
+    n = m;
+    for (uint32_t i = 0; i < m; ++i) acc_add(s, acc, le_[i], i == 0);
+    return;
+  }
+  n = 0;
+  int last = -1;
+  for (;;) {
+    int best = 0x7FFFFFFF;
+    uint32_t bi = kNone;
+    for (uint32_t y = s.head[slot]; y != kNone; y = chain_next(s.enext, y)) {
+      int key = ((int)s.eord[y] << 11) | (int)y;
+      if (key > last && key < best) {
+        best = key;
+        bi = y;
+      }
+    }
+    if (bi == kNone) break;
+    last = best;
+    acc_add(s, acc, bi, n == 0);
+    ++n;
+  }
+}
+
+// The output value of a string: acc alone, or pre + post * acc (absent terms are zero).
+template <bool S>
+__device__ __forceinline__ Cx finish(const MergeArgs& a, MergeSmem<S>& s, Cx acc, uint32_t n, uint32_t pe) {
+  Cx r{0.0, 0.0};
+  if constexpr (S) {
+    if (a.has_post) {
+      double sc = (n > 0) ? neg_if(__dmul_rn(a.post_s, acc.re), (a.post_q & 2) != 0) : 0.0;
+      if (pe != kNone16) r.re = (n > 0) ? add_rn(s.ere[pe], sc) : s.ere[pe];
+      else r.re = sc;
+    } else {
+      r.re = acc.re;
+    }
+  } else {
+    if (a.has_post) {
+      Cx sc = (n > 0) ? cmul(a.post, acc) : Cx{0.0, 0.0};
+      if (pe != kNone16) {
+        Cx pv{s.ere[pe], s.eim[pe]};
+        r = (n > 0) ? Cx{add_rn(pv.re, sc.re), add_rn(pv.im, sc.im)} : pv;
+      } else {
+        r = sc;
+      }
+    } else {
+      r = acc;
+    }
+  }
+  return r;
+}
+
+// Stage a non-zero result of the pass (warp-aggregated slots in shared memory).
+template <bool S>
+__device__ __forceinline__ void stage_result(MergeSmem<S>& s, bool flag, Cx r, uint32_t slot, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  uint32_t ob = 0;
+  if (lane == leader) ob = atomicAdd(&s.n_out, (uint32_t)__popc(m));
+  ob = __shfl_sync(0xffffffffu, ob, leader);
+  if (flag) {
+    const uint32_t o = ob + __popc(m & ((1u << lane) - 1));
+    s.ore[o] = r.re;
+    if constexpr (!S) s.oim[o] = r.im;
+    s.oslot[o] = (uint16_t)slot;
+  }
+}
 
 template <bool S>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
@@ -381,6 +546,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
   if (tid == 0) {
     s.n_u = 0;
     s.n_e = 0;
+    s.n_out = 0;
+    s.n_long = 0;
     s.flags = 0;
     s.cur_sent = a.sent_lo;
   }
@@ -476,26 +643,35 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
           uint32_t eb = 0;
           if (lane == leader) eb = atomicAdd(&s.n_e, (uint32_t)__popc(m));
           eb = __shfl_sync(0xffffffffu, eb, leader);
-          if (!keep) continue;
-          uint32_t e = eb + __popc(m & ((1u << lane) - 1));
-          if (e >= (uint32_t)kCap) {
-            atomicOr(&s.flags, 1);
-            continue;
+          const uint32_t e = eb + __popc(m & ((1u << lane) - 1));
+          bool fresh = false;
+          int slot = -1;
+          if (keep) {
+            if (e >= (uint32_t)kCap) {
+              atomicOr(&s.flags, 1);
+            } else {
+              slot = table_insert(s, key, sent, fresh);
+              if (slot < 0) atomicOr(&s.flags, 1);
+            }
           }
-          bool fresh;
-          int slot = table_insert(s, key, sent, fresh);
-          if (slot < 0) {
-            atomicOr(&s.flags, 1);
-            continue;
+          // warp-aggregated key list positions for the strings this warp inserted first
+          const unsigned mf = __ballot_sync(0xffffffffu, fresh);
+          if (mf) {
+            const int lf = __ffs(mf) - 1;
+            uint32_t ub = 0;
+            if (lane == lf) ub = atomicAdd(&s.n_u, (uint32_t)__popc(mf));
+            ub = __shfl_sync(0xffffffffu, ub, lf);
+            if (fresh) s.ulist[ub + __popc(mf & ((1u << lane) - 1))] = (uint16_t)slot;
           }
-          if (fresh) s.ulist[atomicAdd(&s.n_u, 1u)] = (uint16_t)slot;
-          s.ere[e] = t.re;
-          if constexpr (!S) s.eim[e] = t.im;
-          if (code == kCodePre) {
-            s.pre[slot] = (uint16_t)e;
-          } else {
-            s.eord[e] = (uint16_t)code;
-            s.enext[e] = (uint16_t)atomicExch(&s.head[slot], e);
+          if (slot >= 0) {
+            s.ere[e] = t.re;
+            if constexpr (!S) s.eim[e] = t.im;
+            if (code == kCodePre) {
+              s.pre[slot] = (uint16_t)e;
+            } else {
+              s.eord[e] = (uint16_t)code;
+              s.enext[e] = (uint16_t)atomicExch(&s.head[slot], e);
+            }
           }
         }
       }
@@ -516,80 +692,361 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
       }
       const uint32_t n_u = s.n_u;
       // ---- phase 2: per string, sum its contributions in increasing order code (H order,
-      // then the sources), apply the combination, and write the non-zero results
+      // then the sources), apply the combination, stage the non-zero results.  Chains of at
+      // most 4 entries first; longer chains are queued and done densely afterwards.
+      for (uint32_t u0 = 0; u0 < n_u; u0 += kMergeThreads) {
+        const uint32_t u = u0 + tid;
+        Cx r{0.0, 0.0};
+        bool flag = false, deferred = false;
+        uint32_t slot = 0;
+        if (u < n_u) {
+          slot = s.ulist[u];
+          const uint32_t pe = s.pre[slot];
+          Cx acc{0.0, 0.0};
+          uint32_t n = 0;
+          if (chain_sum_regs<S, 4>(s, slot, acc, n)) {
+            r = finish(a, s, acc, n, pe);
+            flag = !(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16);
+          } else {
+            deferred = true;
+          }
+        }
+        const unsigned md = __ballot_sync(0xffffffffu, deferred);
+        if (md) {
+          const int leader = __ffs(md) - 1;
+          uint32_t qb = 0;
+          if (lane == leader) qb = atomicAdd(&s.n_long, (uint32_t)__popc(md));
+          qb = __shfl_sync(0xffffffffu, qb, leader);
+          if (deferred) s.longq[qb + __popc(md & ((1u << lane) - 1))] = (uint16_t)slot;
+        }
+        stage_result(s, flag, r, slot, lane);
+      }
+      __syncthreads();
+      const uint32_t n_long = s.n_long;
+      for (uint32_t q0 = 0; q0 < n_long; q0 += kMergeThreads) {
+        const uint32_t q = q0 + tid;
+        Cx r{0.0, 0.0};
+        bool flag = false;
+        uint32_t slot = 0;
+        if (q < n_long) {
+          slot = s.longq[q];
+          const uint32_t pe = s.pre[slot];
+          Cx acc{0.0, 0.0};
+          uint32_t n = 0;
+          if (!chain_sum_regs<S, kNet>(s, slot, acc, n)) {
+            acc = Cx{0.0, 0.0};
+            chain_sum_long(s, slot, acc, n);
+          }
+          r = finish(a, s, acc, n, pe);
+          flag = !(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16);
+        }
+        stage_result(s, flag, r, slot, lane);
+      }
+      __syncthreads();
+      // ---- phase 3: one output reservation per pass, coalesced writes
+      const uint32_t n_out = s.n_out;
+      if (tid == 0) s.out_base = n_out ? atomicAdd(a.out_n, (unsigned long long)n_out) : 0ull;
+      __syncthreads();
+      const unsigned long long ob = s.out_base;
+      if (ob + n_out > a.out_cap) {
+        if (tid == 0 && n_out) atomicOr(a.err, 1);
+      } else {
+        for (uint32_t i = tid; i < n_out; i += kMergeThreads) {
+          const ulonglong2 k = s.key[s.oslot[i]];
+          if constexpr (S) {
+            const double x = s.ore[i];
+            a.out[ob + i] = a.out_imag ? Rec{k.x, k.y, 0.0, x} : Rec{k.x, k.y, x, 0.0};
+          } else {
+            a.out[ob + i] = Rec{k.x, k.y, s.ore[i], s.oim[i]};
+          }
+        }
+      }
+      __syncthreads();
+      release_keys(s, sent);
+     }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- ranked merge
+// The merge used when the order codes fit a kMaskBits-bit mask (|H| + sources <= 256).  Each
+// slot records which order codes contributed; once all entries of a pass are in, the rank of
+// a contribution among its string's contributions is the popcount of the lower mask bits, so
+// it is written straight to its ordered position in a per-string run, and each string is
+// summed over its contiguous run in increasing order code.  Valid inputs (distinct strings in
+// every operand) give distinct order codes per string.
+constexpr int kMaskWords = 4;
+constexpr int kMaskBits = 64 * kMaskWords;
+
+template <bool S>
+struct RankSmem {
+  ulonglong2 key[kTable];
+  unsigned long long mask[kTable][kMaskWords];  // order codes present per slot
+  uint16_t pre[kTable];
+  uint16_t ulist[kTable];
+  uint16_t run[kTable];        // start of the slot's run in seg[]
+  double ere[kCap];
+  double eim[S ? 1 : kCap];
+  uint16_t ebit[kCap];         // order bit of the entry (kNone16: pre operand)
+  uint16_t eslot[kCap];
+  double seg[kCap];            // contributions ordered by (string, order code)
+  double segim[S ? 1 : kCap];
+  double ore[kTable];
+  double oim[S ? 1 : kTable];
+  uint16_t oslot[kTable];
+  unsigned long long gbase[kMaxGroupBins];
+  uint32_t gpre[kMaxGroupBins + 1];
+  uint32_t n_e, n_u, n_out, n_seg;
+  int flags;
+  unsigned group;
+  unsigned long long out_base;
+  ulonglong2 cur_sent;
+};
+
+template <bool S>
+__device__ __forceinline__ void rank_release(RankSmem<S>& s, ulonglong2 sent) {
+  const uint32_t n_u = s.n_u;
+  for (uint32_t u = threadIdx.x; u < n_u; u += kMergeThreads) {
+    const uint32_t slot = s.ulist[u];
+    s.key[slot] = sent;
+#pragma unroll
+    for (int w = 0; w < kMaskWords; ++w) s.mask[slot][w] = 0ull;
+    s.pre[slot] = kNone16;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s.n_u = 0;
+    s.n_e = 0;
+    s.n_out = 0;
+    s.n_seg = 0;
+    s.flags = 0;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t code_bit(uint32_t code, int nH) {
+  return code < kCodeSrc ? code : (uint32_t)nH + (code - kCodeSrc);
+}
+
+template <bool S>
+__global__ void __launch_bounds__(kMergeThreads) k_merge_rank(MergeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RankSmem<S>& s = *reinterpret_cast<RankSmem<S>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const uint32_t ngroups = *a.ngroups;
+  for (int i = tid; i < kTable; i += kMergeThreads) {
+    s.key[i] = a.sent_lo;
+#pragma unroll
+    for (int w = 0; w < kMaskWords; ++w) s.mask[i][w] = 0ull;
+    s.pre[i] = kNone16;
+  }
+  if (tid == 0) {
+    s.n_u = s.n_e = s.n_out = s.n_seg = 0;
+    s.flags = 0;
+    s.cur_sent = a.sent_lo;
+  }
+  __syncthreads();
+
+  for (;;) {
+    if (tid == 0) s.group = atomicAdd(a.next_group, 1u);
+    __syncthreads();
+    const uint32_t g = s.group;
+    __syncthreads();
+    if (g >= ngroups) break;
+    const uint32_t lo = a.gstart[g], hi = a.gstart[g + 1];
+    const uint64_t e0 = a.cpre[lo];
+    const uint64_t E = a.cpre[hi] - e0;
+    if (E == 0) continue;
+    const uint32_t nb = hi - lo;
+    if (nb > (uint32_t)kMaxGroupBins) {
+      if (tid == 0) atomicOr(a.err, 2);
+      continue;
+    }
+    const ulonglong2 sent = (lo >= a.nbins / 2) ? a.sent_hi : a.sent_lo;
+    if (sent.x != s.cur_sent.x || sent.y != s.cur_sent.y) {
+      __syncthreads();
+      for (int i = tid; i < kTable; i += kMergeThreads) s.key[i] = sent;
+      __syncthreads();
+      if (tid == 0) s.cur_sent = sent;
+    }
+    for (uint32_t i = tid; i <= nb; i += kMergeThreads) s.gpre[i] = (uint32_t)(a.cpre[lo + i] - e0);
+    for (uint32_t i = tid; i < nb; i += kMergeThreads) s.gbase[i] = a.base[lo + i];
+    __syncthreads();
+
+    int level0 = 0;
+    while (((uint64_t)kCap << level0) < E + E / 4 && level0 < 16) ++level0;
+    if (a.bits + level0 > kHashRows) {
+      if (tid == 0) atomicOr(a.err, 2);
+      continue;
+    }
+    if (level0 > 0 && tid == 0) atomicAdd(a.split_groups, 1u);
+
+    for (uint32_t sub0 = 0; sub0 < (1u << level0); ++sub0) {
+     int stk_level[2 * kHashRows + 2];
+     uint32_t stk_sub[2 * kHashRows + 2];
+     int sp = 1;
+     stk_level[0] = level0;
+     stk_sub[0] = sub0;
+     while (sp > 0) {
+      --sp;
+      const int level = stk_level[sp];
+      const uint32_t sub = stk_sub[sp];
+      // ---- phase 1: rebuild entries, insert keys, mark order codes per key
+      for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)kBatch * kMergeThreads) {
+        uint64_t ent[kBatch];
+        Rec rec[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          uint64_t j = j0 + (uint64_t)k * kMergeThreads + tid;
+          ent[k] = ~0ull;
+          if (j < E) {
+            uint32_t l = 0, r = nb;
+            while (r - l > 1) {
+              uint32_t m = (l + r) >> 1;
+              if (s.gpre[m] <= j) l = m; else r = m;
+            }
+            ent[k] = a.entries[s.gbase[l] + (j - s.gpre[l])];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          if (ent[k] == ~0ull) continue;
+          uint32_t code = (uint32_t)(ent[k] & 0xFFFFu);
+          uint64_t idx = ent[k] >> 16;
+          const Rec* base = code < kCodeSrc ? a.X : (code == kCodePre ? a.pre : a.src[code - kCodeSrc]);
+          rec[k] = base[idx];
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          bool keep = ent[k] != ~0ull;
+          ulonglong2 key = make_ulonglong2(0, 0);
+          Cx t{0.0, 0.0};
+          uint32_t code = 0;
+          if (keep) {
+            code = (uint32_t)(ent[k] & 0xFFFFu);
+            if constexpr (S) build_scalar(a, code, rec[k], key, t.re);
+            else build_contribution(a, code, rec[k], key, t);
+            if (level > 0) keep = dev_hash(key.x, key.y, a.bits, level) == sub;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (!m) continue;
+          const int leader = __ffs(m) - 1;
+          uint32_t eb = 0;
+          if (lane == leader) eb = atomicAdd(&s.n_e, (uint32_t)__popc(m));
+          eb = __shfl_sync(0xffffffffu, eb, leader);
+          const uint32_t e = eb + __popc(m & ((1u << lane) - 1));
+          bool fresh = false;
+          int slot = -1;
+          if (keep) {
+            if (e >= (uint32_t)kCap) {
+              atomicOr(&s.flags, 1);
+            } else {
+              slot = table_insert(s, key, sent, fresh);
+              if (slot < 0) atomicOr(&s.flags, 1);
+            }
+          }
+          const unsigned mf = __ballot_sync(0xffffffffu, fresh);
+          if (mf) {
+            const int lf = __ffs(mf) - 1;
+            uint32_t ub = 0;
+            if (lane == lf) ub = atomicAdd(&s.n_u, (uint32_t)__popc(mf));
+            ub = __shfl_sync(0xffffffffu, ub, lf);
+            if (fresh) s.ulist[ub + __popc(mf & ((1u << lane) - 1))] = (uint16_t)slot;
+          }
+          if (slot >= 0) {
+            s.ere[e] = t.re;
+            if constexpr (!S) s.eim[e] = t.im;
+            s.eslot[e] = (uint16_t)slot;
+            if (code == kCodePre) {
+              s.pre[slot] = (uint16_t)e;
+              s.ebit[e] = kNone16;
+            } else {
+              const uint32_t bit = code_bit(code, a.nH);
+              s.ebit[e] = (uint16_t)bit;
+              atomicOr(&s.mask[slot][bit >> 6], 1ull << (bit & 63));
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (s.flags) {
+        rank_release(s, sent);
+        if (level >= 16 || a.bits + level + 1 > kHashRows || sp + 2 > 2 * kHashRows + 2) {
+          if (tid == 0) atomicOr(a.err, 2);
+          continue;
+        }
+        if (level == 0 && tid == 0) atomicAdd(a.split_groups, 1u);
+        stk_level[sp] = level + 1;
+        stk_sub[sp] = sub + (1u << level);
+        stk_level[sp + 1] = level + 1;
+        stk_sub[sp + 1] = sub;
+        sp += 2;
+        continue;
+      }
+      const uint32_t n_u = s.n_u, n_e = s.n_e;
+      // ---- phase 2: a run per string (its length is the popcount of its mask)
+      for (uint32_t u0 = 0; u0 < n_u; u0 += kMergeThreads) {
+        const uint32_t u = u0 + tid;
+        uint32_t c = 0, slot = 0;
+        if (u < n_u) {
+          slot = s.ulist[u];
+#pragma unroll
+          for (int w = 0; w < kMaskWords; ++w) c += __popcll(s.mask[slot][w]);
+        }
+        // warp-inclusive scan of c, one shared-memory reservation per warp
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        uint32_t wb = 0;
+        if (lane == 31) wb = atomicAdd(&s.n_seg, incl);
+        wb = __shfl_sync(0xffffffffu, wb, 31);
+        if (u < n_u) s.run[slot] = (uint16_t)(wb + incl - c);
+      }
+      __syncthreads();
+      // ---- phase 3: every contribution to its ordered position in its string's run
+      for (uint32_t e = tid; e < n_e; e += kMergeThreads) {
+        const uint32_t bit = s.ebit[e];
+        if (bit == kNone16) continue;
+        const uint32_t slot = s.eslot[e];
+        const uint32_t wi = bit >> 6;
+        uint32_t rank = __popcll(s.mask[slot][wi] & ((1ull << (bit & 63)) - 1ull));
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w)
+          if ((uint32_t)w < wi) rank += __popcll(s.mask[slot][w]);
+        const uint32_t pos = s.run[slot] + rank;
+        s.seg[pos] = s.ere[e];
+        if constexpr (!S) s.segim[pos] = s.eim[e];
+      }
+      __syncthreads();
+      // ---- phase 4: per string, add its run in order, apply the combination, stage
       for (uint32_t u0 = 0; u0 < n_u; u0 += kMergeThreads) {
         const uint32_t u = u0 + tid;
         Cx r{0.0, 0.0};
         bool flag = false;
-        ulonglong2 kout = make_ulonglong2(0, 0);
+        uint32_t slot = 0;
         if (u < n_u) {
-          const uint32_t slot = s.ulist[u];
-          kout = s.key[slot];
-          const uint32_t pe = s.pre[slot];
-          // collect the chain
-          int ord[kSortMax];
-          uint32_t idx[kSortMax];
+          slot = s.ulist[u];
           uint32_t n = 0;
-          for (uint32_t e = s.head[slot]; e != kNone; e = (s.enext[e] == kNone16) ? kNone : s.enext[e]) {
-            if (n < kSortMax) {
-              ord[n] = ((int)s.eord[e] << 11) | (int)e;
-              idx[n] = e;
-            }
-            ++n;
-          }
+#pragma unroll
+          for (int w = 0; w < kMaskWords; ++w) n += __popcll(s.mask[slot][w]);
+          const uint32_t b0 = s.run[slot];
           Cx acc{0.0, 0.0};
-          if (n <= kSortMax) {
-            // insertion sort by (order code, entry); orders are distinct for distinct inputs
-            for (uint32_t i = 1; i < n; ++i) {
-              int ko = ord[i];
-              uint32_t ki = idx[i];
-              int j = (int)i - 1;
-              while (j >= 0 && ord[j] > ko) {
-                ord[j + 1] = ord[j];
-                idx[j + 1] = idx[j];
-                --j;
-              }
-              ord[j + 1] = ko;
-              idx[j + 1] = ki;
-            }
-            for (uint32_t i = 0; i < n; ++i) {
-              const uint32_t e = idx[i];
-              if constexpr (S) {
-                acc.re = (i == 0) ? s.ere[e] : add_rn(acc.re, s.ere[e]);
-              } else {
-                if (i == 0) acc = Cx{s.ere[e], s.eim[e]};
-                else {
-                  acc.re = add_rn(acc.re, s.ere[e]);
-                  acc.im = add_rn(acc.im, s.eim[e]);
-                }
-              }
-            }
-          } else {
-            // long chains: repeated selection of the next order code
-            int last = -1;
-            for (uint32_t m = 0; m < n; ++m) {
-              int best = 0x7FFFFFFF;
-              uint32_t bi = kNone;
-              for (uint32_t e = s.head[slot]; e != kNone; e = (s.enext[e] == kNone16) ? kNone : s.enext[e]) {
-                int key = ((int)s.eord[e] << 11) | (int)e;
-                if (key > last && key < best) {
-                  best = key;
-                  bi = e;
-                }
-              }
-              if (bi == kNone) break;
-              last = best;
-              if constexpr (S) {
-                acc.re = (m == 0) ? s.ere[bi] : add_rn(acc.re, s.ere[bi]);
-              } else {
-                if (m == 0) acc = Cx{s.ere[bi], s.eim[bi]};
-                else {
-                  acc.re = add_rn(acc.re, s.ere[bi]);
-                  acc.im = add_rn(acc.im, s.eim[bi]);
-                }
+          for (uint32_t i = 0; i < n; ++i) {
+            if constexpr (S) {
+              acc.re = (i == 0) ? s.seg[b0] : add_rn(acc.re, s.seg[b0 + i]);
+            } else {
+              if (i == 0) acc = Cx{s.seg[b0], s.segim[b0]};
+              else {
+                acc.re = add_rn(acc.re, s.seg[b0 + i]);
+                acc.im = add_rn(acc.im, s.segim[b0 + i]);
               }
             }
           }
+          const uint32_t pe = s.pre[slot];
           if constexpr (S) {
             if (a.has_post) {
               double sc = (n > 0) ? neg_if(__dmul_rn(a.post_s, acc.re), (a.post_q & 2) != 0) : 0.0;
@@ -613,24 +1070,41 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
           }
           flag = !(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16);
         }
-        // warp-aggregated output slots
         const unsigned m = __ballot_sync(0xffffffffu, flag);
         if (m) {
           const int leader = __ffs(m) - 1;
-          unsigned long long ob = 0;
-          if (lane == leader) ob = atomicAdd(a.out_n, (unsigned long long)__popc(m));
+          uint32_t ob = 0;
+          if (lane == leader) ob = atomicAdd(&s.n_out, (uint32_t)__popc(m));
           ob = __shfl_sync(0xffffffffu, ob, leader);
-          if (ob + __popc(m) > a.out_cap) {
-            if (lane == leader) atomicOr(a.err, 1);
-          } else if (flag) {
-            const unsigned long long o = ob + __popc(m & ((1u << lane) - 1));
-            if constexpr (S) a.out[o] = a.out_imag ? Rec{kout.x, kout.y, 0.0, r.re} : Rec{kout.x, kout.y, r.re, 0.0};
-            else a.out[o] = Rec{kout.x, kout.y, r.re, r.im};
+          if (flag) {
+            const uint32_t o = ob + __popc(m & ((1u << lane) - 1));
+            s.ore[o] = r.re;
+            if constexpr (!S) s.oim[o] = r.im;
+            s.oslot[o] = (uint16_t)slot;
           }
         }
       }
       __syncthreads();
-      release_keys(s, sent);
+      // ---- phase 5: one output reservation per pass, coalesced writes
+      const uint32_t n_out = s.n_out;
+      if (tid == 0) s.out_base = n_out ? atomicAdd(a.out_n, (unsigned long long)n_out) : 0ull;
+      __syncthreads();
+      const unsigned long long ob = s.out_base;
+      if (ob + n_out > a.out_cap) {
+        if (tid == 0 && n_out) atomicOr(a.err, 1);
+      } else {
+        for (uint32_t i = tid; i < n_out; i += kMergeThreads) {
+          const ulonglong2 k = s.key[s.oslot[i]];
+          if constexpr (S) {
+            const double x = s.ore[i];
+            a.out[ob + i] = a.out_imag ? Rec{k.x, k.y, 0.0, x} : Rec{k.x, k.y, x, 0.0};
+          } else {
+            a.out[ob + i] = Rec{k.x, k.y, s.ore[i], s.oim[i]};
+          }
+        }
+      }
+      __syncthreads();
+      rank_release(s, sent);
      }
     }
   }
@@ -854,13 +1328,25 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     a.post_q = up + (acc_cls == kClsImag);
     a.out_imag = out_cls == kClsImag;
   }
-  size_t sm = structured ? sizeof(MergeSmem<true>) : sizeof(MergeSmem<false>);
-  auto kern = structured ? k_merge<true> : k_merge<false>;
+  // ranked merge when the order codes fit the slot masks, chained merge otherwise
+  const bool ranked = sp.nH + sp.nsrc <= kMaskBits;
+  size_t sm;
+  void (*kern)(MergeArgs);
+  const char* kname;
+  if (ranked) {
+    sm = structured ? sizeof(RankSmem<true>) : sizeof(RankSmem<false>);
+    kern = structured ? k_merge_rank<true> : k_merge_rank<false>;
+    kname = structured ? "k_merge_rank_s" : "k_merge_rank";
+  } else {
+    sm = structured ? sizeof(MergeSmem<true>) : sizeof(MergeSmem<false>);
+    kern = structured ? k_merge<true> : k_merge<false>;
+    kname = structured ? "k_merge_s" : "k_merge";
+  }
   PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int per_sm = 0;
   PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMergeThreads, sm));
   int grid = std::max(1, per_sm) * nsm;
-  PS_LAUNCH(structured ? "k_merge_s" : "k_merge", s, kern<<<grid, kMergeThreads, sm, s>>>(a));
+  PS_LAUNCH(kname, s, kern<<<grid, kMergeThreads, sm, s>>>(a));
   PS_CUDA(cudaGetLastError());
   unsigned long long hres[2];
   unsigned hmisc[3];

@@ -78,6 +78,16 @@ def test_commutator_dense_anticommuting_forces_split():
     assert_match(out.download(), orc.commutator(ref(n, Ha), ref(n, Oa)), what="dense")
 
 
+@pytest.mark.parametrize("n,mh,mo", [(7, 300, 2500), (6, 600, 4000)])
+def test_commutator_long_chains(n, mh, mo):
+    # few sites, many terms: output strings collect tens to hundreds of contributions,
+    # which exercises the register, local-array and selection orderings of a key's chain
+    Ha = I.random_sum(90 + n, n, mh, "real")
+    Oa = I.random_sum(91 + n, n, mo, "imag")
+    out = ps.pauli_commutator(dev(n, Ha), dev(n, Oa))
+    assert_match(out.download(), orc.commutator(ref(n, Ha), ref(n, Oa)), what="long chains")
+
+
 def test_commutator_edges():
     n = 64
     top = np.uint64(1 << 63)
