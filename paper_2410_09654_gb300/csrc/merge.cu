@@ -58,7 +58,7 @@ namespace {
 
 constexpr int kCap = 2048;       // entries per merge pass
 constexpr int kTable = 1024;     // shared-memory hash slots (power of two)
-constexpr int kMergeThreads = 256;
+constexpr int kMergeThreads = 512;
 constexpr int kMaxProbe = 128;
 constexpr uint32_t kCodeSrc = 0xF000u;  // entry code of extra source s: kCodeSrc + s
 constexpr uint32_t kCodePre = 0xFFFFu;  // entry code of the `pre` operand
@@ -68,7 +68,8 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint16_t kNone16 = 0xFFFFu;
 constexpr int kNoPow2 = 0x7FFF;
 constexpr int kMaxGroupBins = 512;  // bins per group (a group also starts every kMaxGroupBins bins)
-constexpr int kBatch = 4;           // entries per thread with loads in flight together
+constexpr int kGroupQuota = 1536;   // a new group starts when the running entry count crosses a multiple
+constexpr int kBatch = 2;           // entries per thread with loads in flight together
 static_assert(kCap <= 2048, "order key packs the entry index in 11 bits");
 
 __device__ __forceinline__ uint32_t table_hash(uint64_t v, uint64_t w) {
@@ -531,7 +532,7 @@ __device__ __forceinline__ void stage_result(MergeSmem<S>& s, bool flag, Cx r, u
 }
 
 template <bool S>
-__global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
+__global__ void __launch_bounds__(kMergeThreads, 2) k_merge(MergeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MergeSmem<S>& s = *reinterpret_cast<MergeSmem<S>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs a) {
     __syncthreads();
 
     int level0 = 0;  // split level: a pass (level, sub) keeps keys whose next `level` hash bits equal sub
-    while (((uint64_t)kCap << level0) < E + E / 4 && level0 < 16) ++level0;
+    while (((uint64_t)kCap << level0) < E && level0 < 16) ++level0;
     if (a.bits + level0 > kHashRows) {  // cannot split this far: report, skip the group
       if (tid == 0) atomicOr(a.err, 2);
       continue;
@@ -829,7 +830,7 @@ __device__ __forceinline__ uint32_t code_bit(uint32_t code, int nH) {
 }
 
 template <bool S>
-__global__ void __launch_bounds__(kMergeThreads) k_merge_rank(MergeArgs a) {
+__global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RankSmem<S>& s = *reinterpret_cast<RankSmem<S>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -875,7 +876,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_rank(MergeArgs a) {
     __syncthreads();
 
     int level0 = 0;
-    while (((uint64_t)kCap << level0) < E + E / 4 && level0 < 16) ++level0;
+    while (((uint64_t)kCap << level0) < E && level0 < 16) ++level0;
     if (a.bits + level0 > kHashRows) {
       if (tid == 0) atomicOr(a.err, 2);
       continue;
@@ -1235,7 +1236,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   PS_TRY(gstart.alloc(nbins + 1, s));
   {
     int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
-    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)kCap / 2, flag.p));
+    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)kGroupQuota, flag.p));
     PS_CUDA(cudaGetLastError());
     PS_TRY(scan_u32_to_u64(flag.p, fpre.p, nbins, s));
     PS_LAUNCH("k_group_scatter", s, k_group_scatter<<<blocks, 256, 0, s>>>(flag.p, fpre.p, nbins, gstart.p, misc.p + 1));
