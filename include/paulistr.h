@@ -200,6 +200,10 @@ int64_t pauli_launch_count(void);
 /* Make the next n-th device allocation of the library fail (n >= 1; 0 disables).
  * Host-side fault injection for tests; it never touches the GPU. */
 int pauli_debug_fail_alloc_after(int64_t n);
+/* Divide n DEVICE doubles in place by b with the division used by the Lanczos
+ * normalisation (correctly rounded, equal to the IEEE quotient); synchronises the stream.
+ * For tests of that arithmetic. */
+int pauli_debug_divide(double* x, int64_t n, double b, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -162,6 +162,69 @@ __device__ __forceinline__ Cx rot(Cx a, int k) {  // multiply by i^k (exact)
   }
 }
 
+// ----------------------------------------------------------------------------- division by a constant
+// a / b correctly rounded (round to nearest even) for a fixed b, with one FP64 multiply and
+// one FMA instead of a full division: Q = RN(|a| * RN(1/|b|)) is within 1.5 ulp of
+// t = |a|/|b|; the remainder rho = |a| - Q|b| is exact (one FMA); comparing rho with the exact
+// products |b| * (half gaps to Q's neighbours), powers of two times |b|, decides RN(t) among
+// Q and its two neighbours.  Whenever an operand or result leaves the normal range, or Q is
+// more than one ulp away, it falls back to the IEEE division.
+struct DivConst {
+  double b;       // divisor
+  double rabs;    // RN(1 / |b|)
+  double babs;    // |b|
+  int ok;         // |b| normal and RN(1/|b|) normal
+};
+
+__host__ inline DivConst make_divconst(double b) {
+  DivConst d;
+  d.b = b;
+  d.babs = b < 0 ? -b : b;
+  d.rabs = 1.0 / d.babs;
+  d.ok = (d.babs >= 2.2250738585072014e-308 && d.babs <= 8.98846567431158e307 && d.rabs >= 2.2250738585072014e-308) ? 1 : 0;
+  return d;
+}
+
+// x * 2^k for a normal x when the result stays normal; ok = false otherwise.
+__device__ __forceinline__ double ldexp_exact(double x, int k, bool& ok) {
+  unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+  int E = (int)((bx >> 52) & 0x7FF);
+  int E2 = E + k;
+  ok = (E != 0 && E != 0x7FF && E2 >= 1 && E2 <= 2046);
+  return ok ? __longlong_as_double((long long)(bx + ((unsigned long long)(long long)k << 52))) : 0.0;
+}
+
+__device__ __forceinline__ double div_const(double a, const DivConst& d) {
+  if (!d.ok) return __ddiv_rn(a, d.b);
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long sign = (ua ^ (unsigned long long)__double_as_longlong(d.b)) & (1ull << 63);
+  const int Ea = (int)((ua >> 52) & 0x7FF);
+  if (Ea < 128 || Ea > 1900) return __ddiv_rn(a, d.b);  // zeros, tiny, huge, non-finite
+  const double A = __longlong_as_double((long long)(ua & ~(1ull << 63)));
+  const double Q = __dmul_rn(A, d.rabs);
+  const unsigned long long uq = (unsigned long long)__double_as_longlong(Q);
+  const int Eq = (int)((uq >> 52) & 0x7FF);
+  if (Eq < 64 || Eq > 2000) return __ddiv_rn(a, d.b);
+  const double rho = __fma_rn(-Q, d.babs, A);  // A - Q |b|, exact
+  const bool pow2 = (uq & ((1ull << 52) - 1)) == 0;
+  bool ok1, ok2;
+  const double eu = ldexp_exact(d.babs, Eq - 1076, ok1);                 // |b| * ulp(Q)/2
+  const double el = pow2 ? ldexp_exact(d.babs, Eq - 1077, ok2) : eu;     // |b| * (gap below Q)/2
+  if (!ok1 || (pow2 && !ok2)) return __ddiv_rn(a, d.b);
+  const long long ir = __double_as_longlong(rho);
+  const long long ieu = __double_as_longlong(eu), iel = __double_as_longlong(el);
+  unsigned long long r = uq;
+  if (ir > 0) {  // t above Q: compare rho with |b| ulp/2 (positive doubles order like their bits)
+    if (ir >= ieu + (1ll << 52)) return __ddiv_rn(a, d.b);  // rho >= 2 eu: more than one ulp away
+    if (ir > ieu || (ir == ieu && (uq & 1))) r = uq + 1;
+  } else if (ir < 0) {
+    const long long mr = ir & 0x7FFFFFFFFFFFFFFFll;  // |rho|
+    if (mr >= iel + (1ll << 52)) return __ddiv_rn(a, d.b);
+    if (mr > iel || (mr == iel && (uq & 1))) r = uq - 1;
+  }
+  return __longlong_as_double((long long)(r | sign));
+}
+
 __device__ __forceinline__ double add_rn(double a, double b) {
   if (is_zero(b)) return a;
   if (is_zero(a)) return b;

@@ -62,7 +62,7 @@ KTimer::~KTimer() {
   if (!b) return;
   cudaEventRecord(b, s_);
   g_pending.push_back({name_, (cudaEvent_t)a_, b});
-  if (g_pending.size() > 4096) drain_locked();
+  if (g_pending.size() > 3800) drain_locked();
 }
 
 }  // namespace ps
@@ -73,7 +73,15 @@ int pauli_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(ps::g_mu);
   ps::drain_locked();
   ps::g_enabled = on != 0;
-  if (on) ps::g_totals.clear();
+  if (on) {
+    ps::g_totals.clear();
+    // pre-create events so that timing does not create them inside the measured region
+    while (ps::g_pool.size() < 8192) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      ps::g_pool.push_back(e);
+    }
+  }
   return PS_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -22,6 +23,28 @@ void set_cuda_error(cudaError_t e, const char* where) {
 // ----------------------------------------------------------------------------- memory
 static std::atomic<int64_t> g_fail_after{0};
 
+// Freed blocks are kept in size classes (8 per power of two) per stream and handed back
+// to later requests of the same class on the same stream, so steady-state iterations do
+// not make the stream-ordered pool map new memory when their sizes drift slightly.
+namespace {
+struct CachedBlock {
+  void* p;
+  size_t bytes;
+};
+std::mutex g_cache_mu;
+std::map<std::pair<cudaStream_t, size_t>, std::vector<CachedBlock>> g_cache;  // (stream, class) -> blocks
+std::map<void*, size_t> g_live;                                               // pointer -> class bytes
+size_t g_cached_bytes = 0;
+constexpr size_t kCacheLimit = (size_t)96 << 30;  // keep at most this much in the cache
+
+size_t size_class(size_t bytes) {
+  if (bytes <= 4096) return 4096;
+  int lg = 63 - __builtin_clzll((unsigned long long)(bytes - 1));  // 2^lg < bytes <= 2^(lg+1)
+  size_t step = (size_t)1 << (lg - 3);                             // 8 classes per octave
+  return ((bytes + step - 1) / step) * step;
+}
+}  // namespace
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   int64_t f = g_fail_after.load();
@@ -39,22 +62,62 @@ int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
   });
-  cudaError_t e = cudaMallocAsync(p, bytes, s);
-  if (e == cudaErrorMemoryAllocation) {
+  const size_t cls = size_class(bytes);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find({s, cls});
+    if (it != g_cache.end() && !it->second.empty()) {
+      CachedBlock b = it->second.back();
+      it->second.pop_back();
+      g_cached_bytes -= b.bytes;
+      g_live[b.p] = b.bytes;
+      *p = b.p;
+      return PS_OK;
+    }
+  }
+  cudaError_t e = cudaMallocAsync(p, cls, s);
+  if (e == cudaErrorMemoryAllocation) {  // give the cache back to the pool and retry once
     cudaGetLastError();
-    *p = nullptr;
-    return PS_ERR_NOMEM;
+    {
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      for (auto& kv : g_cache)
+        for (auto& b : kv.second) cudaFreeAsync(b.p, kv.first.first);
+      g_cache.clear();
+      g_cached_bytes = 0;
+    }
+    e = cudaMallocAsync(p, cls, s);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      *p = nullptr;
+      return PS_ERR_NOMEM;
+    }
   }
   if (e != cudaSuccess) {
     set_cuda_error(e, "cudaMallocAsync");
     *p = nullptr;
     return PS_ERR_CUDA;
   }
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_live[*p] = cls;
   return PS_OK;
 }
 
 void dev_free(void* p, cudaStream_t s) {
-  if (p) cudaFreeAsync(p, s);
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_live.find(p);
+  if (it == g_live.end()) {  // not ours: hand straight back to the pool
+    cudaFreeAsync(p, s);
+    return;
+  }
+  const size_t cls = it->second;
+  g_live.erase(it);
+  if (g_cached_bytes + cls > kCacheLimit) {
+    cudaFreeAsync(p, s);
+    return;
+  }
+  g_cache[{s, cls}].push_back({p, cls});
+  g_cached_bytes += cls;
 }
 
 int num_sms() {

@@ -28,7 +28,7 @@ struct TruncArgs {
   int use_cut;
   int use_gamma;
   int use_div;
-  double divisor;
+  DivConst dc;
   const double* factor;  // exp(-(gamma*dt) w), w = 0..64
   int cls;               // coefficient class of the input: components that may be non-zero
 };
@@ -46,54 +46,94 @@ __device__ __forceinline__ double sq_sum_cls(double re, double im, int cls) {
   return sq_sum(re, im);
 }
 
+// Tile compaction: a block handles tiles of kTile elements (kTI per thread), counts the
+// kept ones per warp and item, and reserves their output range with one atomic per tile.
+constexpr int kTT = 256;
+constexpr int kTI = 4;
+constexpr int kTile = kTT * kTI;
+
+struct TileRes {
+  uint32_t wcnt[kTT / 32][kTI];
+  unsigned long long base;
+};
+
+__device__ __forceinline__ void tile_positions(const bool (&f)[kTI], TileRes& sm, unsigned long long* counter,
+                                               unsigned long long (&pos)[kTI]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned m[kTI];
+#pragma unroll
+  for (int k = 0; k < kTI; ++k) {
+    m[k] = __ballot_sync(0xffffffffu, f[k]);
+    if (lane == 0) sm.wcnt[warp][k] = __popc(m[k]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < kTI; ++k)
+      for (int w = 0; w < kTT / 32; ++w) {
+        uint32_t c = sm.wcnt[w][k];
+        sm.wcnt[w][k] = run;
+        run += c;
+      }
+    sm.base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kTI; ++k) pos[k] = sm.base + sm.wcnt[warp][k] + __popc(m[k] & ((1u << lane) - 1));
+  __syncthreads();
+}
+
 // Steps 1-3 with compaction (order of survivors is unspecified).  For a later top-k
 // select it also stores each survivor's |c|^2 bit pattern (non-negative doubles order
 // like their bit patterns) and histograms its top kDigitBits bits.
-__global__ void k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a, Rec* __restrict__ out,
-                         uint64_t* __restrict__ ab, unsigned* __restrict__ hist0, unsigned long long* __restrict__ n_out) {
+__global__ void __launch_bounds__(kTT) k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a,
+                                                Rec* __restrict__ out, uint64_t* __restrict__ ab,
+                                                unsigned* __restrict__ hist0, unsigned long long* __restrict__ n_out) {
   __shared__ unsigned s_hist[kBins];
+  __shared__ TileRes s_res;
   if (hist0) {
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
   }
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t iters = ceil_div_dev(n, stride);
-  for (int64_t it = 0; it < iters; ++it) {
-    int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool keep = false;
-    Rec r;
-    uint64_t a2 = 0;
-    if (i < n) {
-      r = in[i];
-      if (a.use_div) {  // components outside the class are zero and stay zero
-        if (a.cls & 1) r.re = __ddiv_rn(r.re, a.divisor);
-        if (a.cls & 2) r.im = __ddiv_rn(r.im, a.divisor);
-      }
-      int wt = __popcll(r.v | r.w);
-      if (a.use_gamma) {
-        double f = a.factor[wt];
-        if (a.cls & 1) r.re = __dmul_rn(r.re, f);
-        if (a.cls & 2) r.im = __dmul_rn(r.im, f);
-      }
-      keep = !(a.max_weight >= 0 && wt > a.max_weight) && !(is_zero(r.re) && is_zero(r.im));
-      if (keep && (a.use_cut || ab)) {
-        double q = sq_sum_cls(r.re, r.im, a.cls);
-        a2 = (uint64_t)__double_as_longlong(q);
-        if (a.use_cut) keep = !(q < a.cut2);
+  const int64_t tiles = ceil_div_dev(n, kTile);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    bool keep[kTI];
+    Rec r[kTI];
+    uint64_t a2[kTI];
+#pragma unroll
+    for (int k = 0; k < kTI; ++k) {
+      const int64_t i = tile * kTile + (int64_t)k * kTT + threadIdx.x;
+      keep[k] = false;
+      a2[k] = 0;
+      if (i < n) {
+        r[k] = in[i];
+        if (a.use_div) {  // components outside the class are zero and stay zero
+          if (a.cls & 1) r[k].re = div_const(r[k].re, a.dc);
+          if (a.cls & 2) r[k].im = div_const(r[k].im, a.dc);
+        }
+        const int wt = __popcll(r[k].v | r[k].w);
+        if (a.use_gamma) {
+          const double f = a.factor[wt];
+          if (a.cls & 1) r[k].re = __dmul_rn(r[k].re, f);
+          if (a.cls & 2) r[k].im = __dmul_rn(r[k].im, f);
+        }
+        keep[k] = !(a.max_weight >= 0 && wt > a.max_weight) && !(is_zero(r[k].re) && is_zero(r[k].im));
+        if (keep[k] && (a.use_cut || ab)) {
+          const double q = sq_sum_cls(r[k].re, r[k].im, a.cls);
+          a2[k] = (uint64_t)__double_as_longlong(q);
+          if (a.use_cut) keep[k] = !(q < a.cut2);
+        }
       }
     }
-    unsigned mask = __ballot_sync(0xffffffffu, keep);
-    if (!mask) continue;
-    int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    if (lane == __ffs(mask) - 1) base = atomicAdd(n_out, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
-    if (keep) {
-      unsigned long long o = base + __popc(mask & ((1u << lane) - 1));
-      out[o] = r;
+    unsigned long long pos[kTI];
+    tile_positions(keep, s_res, n_out, pos);
+#pragma unroll
+    for (int k = 0; k < kTI; ++k) {
+      if (!keep[k]) continue;
+      out[pos[k]] = r[k];
       if (ab) {
-        ab[o] = a2;
-        atomicAdd(&s_hist[a2 >> (64 - kDigitBits)], 1u);
+        ab[pos[k]] = a2[k];
+        atomicAdd(&s_hist[a2[k] >> (64 - kDigitBits)], 1u);
       }
     }
   }
@@ -142,15 +182,44 @@ __device__ __forceinline__ bool matches_prefix(const uint64_t k[3], const SelSta
   return true;
 }
 
-__global__ void k_sel_hist(const Rec* __restrict__ d, const uint64_t* __restrict__ ab, int64_t n,
+// After the first digit is fixed, only candidates with that top digit can decide the
+// threshold: collect their indices once.
+__global__ void __launch_bounds__(kTT) k_sel_narrow(const uint64_t* __restrict__ ab, int64_t n,
+                                                    const SelState* __restrict__ st_p, uint32_t* __restrict__ list,
+                                                    unsigned long long* __restrict__ n_list) {
+  __shared__ TileRes s_res;
+  const SelState st = *st_p;
+  if (st.done) return;
+  const uint64_t d0 = st.prefix[0] >> (64 - kDigitBits);
+  const int64_t tiles = ceil_div_dev(n, kTile);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    bool f[kTI];
+    int64_t idx[kTI];
+#pragma unroll
+    for (int k = 0; k < kTI; ++k) {
+      idx[k] = tile * kTile + (int64_t)k * kTT + threadIdx.x;
+      f[k] = idx[k] < n && (ab[idx[k]] >> (64 - kDigitBits)) == d0;
+    }
+    unsigned long long pos[kTI];
+    tile_positions(f, s_res, n_list, pos);
+#pragma unroll
+    for (int k = 0; k < kTI; ++k)
+      if (f[k]) list[pos[k]] = (uint32_t)idx[k];
+  }
+}
+
+__global__ void k_sel_hist(const Rec* __restrict__ d, const uint64_t* __restrict__ ab,
+                           const uint32_t* __restrict__ list, const unsigned long long* __restrict__ n_list,
                            const SelState* __restrict__ st_p, int pass, unsigned* __restrict__ hist) {
   __shared__ unsigned s_hist[kBins];
-  SelState st = *st_p;
+  const SelState st = *st_p;
   if (st.done) return;
+  const int64_t n = (int64_t)*n_list;
   const bool need_key = (pass + 1) * kDigitBits > 64;  // this pass reads bits of ~v / ~w
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = list[j];
     uint64_t k[3];
     Rec r;
     if (need_key) r = d[i];
@@ -233,40 +302,54 @@ __global__ void __launch_bounds__(256) k_sel_pick(SelState* st_p, int pass, unsi
 }
 
 // keep iff rank key >= threshold (prefix with zero low bits), or in the keep set (sorted keys)
-__global__ void k_sel_compact(const Rec* __restrict__ in, const uint64_t* __restrict__ ab, int64_t n,
-                              const SelState* __restrict__ st_p,
-                              const ulonglong2* __restrict__ keep, int64_t nkeep, Rec* __restrict__ out,
-                              unsigned long long* __restrict__ n_out) {
+__global__ void __launch_bounds__(kTT) k_sel_compact(const Rec* __restrict__ in, const uint64_t* __restrict__ ab,
+                                                     int64_t n, const SelState* __restrict__ st_p,
+                                                     const ulonglong2* __restrict__ keep, int64_t nkeep,
+                                                     Rec* __restrict__ out, unsigned long long* __restrict__ n_out) {
+  __shared__ TileRes s_res;
   const SelState st = *st_p;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t iters = ceil_div_dev(n, stride);
-  for (int64_t it = 0; it < iters; ++it) {
-    int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool kp = false;
-    Rec r;
-    if (i < n) {
-      r = in[i];
-      uint64_t k[3];
-      rank_key(ab[i], &r, k);
-      kp = (k[0] > st.prefix[0]) || (k[0] == st.prefix[0] && (k[1] > st.prefix[1] || (k[1] == st.prefix[1] && k[2] >= st.prefix[2])));
-      if (!kp && nkeep > 0) {
-        int64_t l = 0, h = nkeep;
-        while (l < h) {
-          int64_t m = (l + h) >> 1;
-          ulonglong2 c = keep[m];
-          if (c.x < r.v || (c.x == r.v && c.y < r.w)) l = m + 1; else h = m;
+  const int64_t tiles = ceil_div_dev(n, kTile);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    bool kp[kTI];
+    Rec r[kTI];
+#pragma unroll
+    for (int k = 0; k < kTI; ++k) {
+      const int64_t i = tile * kTile + (int64_t)k * kTT + threadIdx.x;
+      kp[k] = false;
+      if (i < n) {
+        const uint64_t a2 = ab[i];
+        if (a2 > st.prefix[0]) {
+          kp[k] = true;
+          r[k] = in[i];
+        } else if (a2 == st.prefix[0] || nkeep > 0) {
+          r[k] = in[i];
+          uint64_t key[3];
+          rank_key(a2, &r[k], key);
+          kp[k] = (key[0] > st.prefix[0]) ||
+                  (key[0] == st.prefix[0] && (key[1] > st.prefix[1] || (key[1] == st.prefix[1] && key[2] >= st.prefix[2])));
+          if (!kp[k] && nkeep > 0) {
+            int64_t l = 0, h = nkeep;
+            while (l < h) {
+              int64_t m = (l + h) >> 1;
+              ulonglong2 c = keep[m];
+              if (c.x < r[k].v || (c.x == r[k].v && c.y < r[k].w)) l = m + 1; else h = m;
+            }
+            kp[k] = (l < nkeep && keep[l].x == r[k].v && keep[l].y == r[k].w);
+          }
         }
-        kp = (l < nkeep && keep[l].x == r.v && keep[l].y == r.w);
       }
     }
-    unsigned mask = __ballot_sync(0xffffffffu, kp);
-    if (!mask) continue;
-    int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    if (lane == __ffs(mask) - 1) base = atomicAdd(n_out, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
-    if (kp) out[base + __popc(mask & ((1u << lane) - 1))] = r;
+    unsigned long long pos[kTI];
+    tile_positions(kp, s_res, n_out, pos);
+#pragma unroll
+    for (int k = 0; k < kTI; ++k)
+      if (kp[k]) out[pos[k]] = r[k];
   }
+}
+
+__global__ void k_debug_divide(double* __restrict__ x, int64_t n, DivConst dc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = div_const(x[i], dc);
 }
 
 }  // namespace
@@ -293,7 +376,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   a.cut2 = use_cut ? P->cutoff * P->cutoff : 0.0;
   a.use_gamma = use_gamma;
   a.use_div = divisor != nullptr;
-  a.divisor = divisor ? *divisor : 1.0;
+  a.dc = make_divconst(divisor ? *divisor : 1.0);
   a.cls = O->cls ? O->cls : kClsComplex;
   if (use_gamma) {
     double h[65];
@@ -313,7 +396,8 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
     PS_TRY(hist.alloc(kBins, s));
     PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
   }
-  PS_LAUNCH("k_filter", s, k_filter<<<grid_for(O->n), 256, 0, s>>>(O->d, O->n, a, cand, ab.p, hist.p, cnt.p));
+  auto tile_grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTile), 8 * nsm)); };
+  PS_LAUNCH("k_filter", s, k_filter<<<tile_grid(O->n), kTT, 0, s>>>(O->d, O->n, a, cand, ab.p, hist.p, cnt.p));
   cudaError_t e = cudaGetLastError();
   unsigned long long nc = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nc, cnt.p, sizeof(nc), cudaMemcpyDeviceToHost, s);
@@ -345,10 +429,17 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
     PS_CUDA(cudaMemcpyAsync(keepk.p, kk.data(), kk.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, s));
   }
   int hb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)nc, 256), 4 * nsm));
+  // first digit from the filter's histogram; then only candidates with that digit matter
+  Buf<uint32_t> list;
+  Buf<unsigned long long> n_list;
+  PS_TRY(list.alloc((size_t)nc, s));
+  PS_TRY(n_list.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(n_list.p, 0, sizeof(unsigned long long), s));
+  PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 0, hist.p));
+  PS_LAUNCH("k_sel_narrow", s, k_sel_narrow<<<tile_grid((int64_t)nc), kTT, 0, s>>>(ab.p, (int64_t)nc, st.p, list.p, n_list.p));
   // |c|^2 digits first (6 passes); the key digits only matter for exact ties
-  for (int pass = 0; pass < kPasses; ++pass) {
-    if (pass > 0)  // the first histogram came with the filter
-      PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(cand, ab.p, (int64_t)nc, st.p, pass, hist.p));
+  for (int pass = 1; pass < kPasses; ++pass) {
+    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(cand, ab.p, list.p, n_list.p, st.p, pass, hist.p));
     PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, pass, hist.p));
     if (pass == 5 || pass == kPasses - 1) {
       SelState hs;
@@ -361,7 +452,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   Rec* outb = nullptr;
   int64_t ocap = (int64_t)nc;  // kept <= top_k + |keep| <= nc
   PS_TRY(dev_alloc((void**)&outb, (size_t)std::max<int64_t>(ocap, 1) * sizeof(Rec), s));
-  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<grid_for((int64_t)nc), 256, 0, s>>>(cand, ab.p, (int64_t)nc, st.p, keepk.p, nkeep, outb, cnt.p + 1));
+  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<tile_grid((int64_t)nc), kTT, 0, s>>>(cand, ab.p, (int64_t)nc, st.p, keepk.p, nkeep, outb, cnt.p + 1));
   e = cudaGetLastError();
   unsigned long long nk = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nk, cnt.p + 1, sizeof(nk), cudaMemcpyDeviceToHost, s);
@@ -376,3 +467,14 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
 }
 
 }  // namespace ps
+
+extern "C" int pauli_debug_divide(double* x, int64_t n, double b, void* cuda_stream) {
+  if (n < 0 || (n > 0 && !x)) return PS_ERR_INVALID;
+  if (n == 0) return PS_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ps::ceil_div(n, 256), 4 * ps::num_sms()));
+  PS_LAUNCH("k_debug_divide", s, ps::k_debug_divide<<<blocks, 256, 0, s>>>(x, n, ps::make_divconst(b)));
+  PS_CUDA(cudaGetLastError());
+  PS_CUDA(cudaStreamSynchronize(s));
+  return PS_OK;
+}

@@ -99,6 +99,7 @@ def load(build_if_missing: bool = False):
         "pauli_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "pauli_profile_report": ([ctypes.c_char_p, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_launch_count": ([], I64),
+        "pauli_debug_divide": ([P, I64, ctypes.c_double, P], ctypes.c_int),
         "pauli_trace_product_noalloc": ([P, P, P, P, I64, P, P, P, P, I64, P, F64P, F64P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -301,6 +302,14 @@ def pauli_profile_report() -> dict:
 
 def pauli_launch_count() -> int:
     return int(load().pauli_launch_count())
+
+
+def pauli_debug_divide(x, b: float, stream=None):
+    """In-place division of a float64 CUDA tensor by b with the library's Lanczos division."""
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _check(load().pauli_debug_divide(ctypes.c_void_p(x.data_ptr()), int(x.numel()), float(b), st),
+           "pauli_debug_divide")
+    return x
 
 
 def pauli_debug_fail_alloc_after(n: int):

@@ -180,6 +180,25 @@ def test_truncate_all_ties():
     assert_match(O.download(), orc.truncate(ref(n, (v, w, re, im)), top_k=1234), what="ties")
 
 
+def test_division_matches_ieee():
+    # the Lanczos normalisation divides with one multiply, one FMA and an exact midpoint
+    # test; it must equal the IEEE quotient bit for bit (numpy's division is IEEE)
+    rng = np.random.default_rng(77)
+    m = 1 << 22
+    x = rng.standard_normal(m) * 2.0 ** rng.integers(-300, 300, m)
+    # near-ties: products of b with values that have short mantissas, powers of two, tiny/huge
+    x[:4096] = (rng.integers(1, 1 << 20, 4096) * 2.0 ** rng.integers(-40, 40, 4096))
+    x[4096:4200] = [5e-324, -5e-324, 1e-310, 0.0, -0.0, 1e308, -1e308, 2.0 ** -1022] * 13
+    for b in (3.0, 0.1, 12.847329889893492, 2.0 ** -30 * 1.9999999999999998, -7.5, 1.0, 2.0 ** 600, 1e-300):
+        xb = x.copy()
+        xb[4200:8296] = xb[:4096] * b  # exact multiples and their neighbourhoods
+        t = torch.from_numpy(xb).cuda()
+        got = ps.pauli_debug_divide(t, b).cpu().numpy()
+        want = xb / b
+        same = (got == want) | (np.isnan(got) & np.isnan(want))
+        assert same.all() and np.array_equal(np.signbit(got), np.signbit(want)), (b, int((~same).sum()))
+
+
 # ----------------------------------------------------------------------------- reductions
 def test_norm_and_trace_exact():
     rng = np.random.default_rng(21)
