@@ -67,6 +67,7 @@ constexpr int kHChunk = 2048;    // H terms per emission launch (shared memory)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint16_t kNone16 = 0xFFFFu;
 constexpr int kNoPow2 = 0x7FFF;
+constexpr uint64_t kFullBudget = (uint64_t)48 << 30;  // bytes of full contribution records per merge
 constexpr int kMaxGroupBins = 512;  // bins per group (a group also starts every kMaxGroupBins bins)
 constexpr int kGroupQuota = 1536;   // a new group starts when the running entry count crosses a multiple
 constexpr int kBatch = 2;           // entries per thread with loads in flight together
@@ -120,44 +121,182 @@ __global__ void k_bound(const uint32_t* __restrict__ histX, const uint32_t* __re
 }
 
 // --------------------------------------------------------------------------- emission
-// One thread per x; H terms [h0, h0+nh) in shared memory.
-__global__ void __launch_bounds__(256) k_emit_products(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
+constexpr int kEmitThreads = 256;
+constexpr int kQueue = 64;  // per-warp queue of (lane, h) codes
+
+// A finished contribution (single-component mode): output string, signed real value of its
+// non-zero component, and order code (H index, kCodeSrc + source, or kCodePre).
+struct __align__(16) Contrib {
+  uint64_t v, w;
+  double val;
+  uint32_t code;
+  uint32_t pad;
+};
+
+// Scalars of the single-component arithmetic (see build_scalar).
+struct EmitScalars {
+  int rot, uH, uX;
+  double src_s[4];
+  int src_e[4], src_q[4], src_uy[4];
+  int pre_u;
+};
+
+// y * 2^e when y is normal and the result stays normal (exact); ok = false otherwise.
+__device__ __forceinline__ double scale_pow2(double y, int e, bool& ok) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  int E = (int)((b >> 52) & 0x7FF);
+  int E2 = E + e;
+  ok = (E != 0 && E != 0x7FF && E2 >= 1 && E2 <= 2046);
+  return ok ? __longlong_as_double((long long)(b + ((unsigned long long)(long long)e << 52))) : 0.0;
+}
+
+__device__ __forceinline__ double neg_if(double x, bool c) {  // sign flip on the integer pipe
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
+}
+__device__ __forceinline__ bool sign_bit(double x) { return __double_as_longlong(x) < 0; }
+
+// round(s * y) for a real constant s with pow2 exponent e (kNoPow2: general), times 2^extra.
+// For a power of two the product is an exponent shift on the integer pipe; otherwise one
+// rounded FP64 product (then an exact doubling when extra == 1).
+__device__ __forceinline__ double scaled(double s, int e, double y, int extra) {
+  if (e != kNoPow2) {
+    bool ok;
+    double r = scale_pow2(y, e + extra, ok);
+    if (ok) return neg_if(r, sign_bit(s));
+  }
+  double p = __dmul_rn(s, y);
+  return extra ? twice(p) : p;
+}
+
+// Emission of the products.  A warp holds 32 x in registers and walks the H terms; the
+// anticommuting (h, lane) pairs are queued as 32-bit codes and, 32 at a time, turned into
+// entries with every lane active: the lane fetches its x by shuffle, then reserves a slot in
+// bin F(h) ^ F(x) and writes the entry there.  The queue is emptied before the warp moves on
+// to its next 32 x.  FULL: the entry is the finished contribution record (string, value,
+// H index); otherwise the 8-byte reference (x index << 16 | H index) that the merge resolves.
+template <bool FULL>
+__global__ void __launch_bounds__(kEmitThreads) k_emit_products(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
                                                        int64_t nX, const Rec* __restrict__ H,
-                                                       const uint32_t* __restrict__ fH, int h0, int nh,
-                                                       const uint64_t* __restrict__ base, uint32_t* __restrict__ cnt,
-                                                       uint64_t* __restrict__ entries,
+                                                       const uint32_t* __restrict__ fH,
+                                                       const double2* __restrict__ hscal, int h0, int nh,
+                                                       EmitScalars es, const uint64_t* __restrict__ base,
+                                                       uint32_t* __restrict__ cnt, uint64_t* __restrict__ entries,
+                                                       Contrib* __restrict__ fout,
                                                        unsigned long long* __restrict__ total) {
-  extern __shared__ unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   ulonglong2* s_hk = reinterpret_cast<ulonglong2*>(smem);
-  uint32_t* s_hf = reinterpret_cast<uint32_t*>(smem + sizeof(ulonglong2) * nh);
+  double2* s_hs = reinterpret_cast<double2*>(smem + sizeof(ulonglong2) * nh);  // FULL only
+  uint32_t* s_hf = reinterpret_cast<uint32_t*>(smem + (sizeof(ulonglong2) + (FULL ? sizeof(double2) : 0)) * nh);
+  __shared__ uint32_t s_q[kEmitThreads / 32][kQueue];
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     s_hk[i] = make_ulonglong2(H[h0 + i].v, H[h0 + i].w);
+    if constexpr (FULL) s_hs[i] = hscal[h0 + i];
     s_hf[i] = fH[h0 + i];
   }
   __syncthreads();
-  uint32_t mine = 0;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nX; i += stride) {
-    const ulonglong2 xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
-    const uint32_t fx = fX[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* q = s_q[warp];
+  uint32_t emitted = 0;  // warp-uniform
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t0 = wid * 32; t0 < nX; t0 += nwarps * 32) {
+    const int64_t i = t0 + lane;
+    const bool valid = i < nX;
+    ulonglong2 xk = make_ulonglong2(0, 0);
+    double sy = 0.0;
+    uint32_t fx = 0;
+    if (valid) {
+      xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
+      if constexpr (FULL) sy = es.uX ? X[i].im : X[i].re;
+      fx = fX[i];
+    }
+    // entries for queue codes q[0, n): lane l takes q[l]; all lanes take part in the shuffles
+    auto flush = [&](int n) {
+      const uint32_t c = lane < n ? q[lane] : 0u;
+      const int src = (int)(c >> 16);
+      const uint32_t h = c & 0xFFFFu;
+      const uint32_t pfx = __shfl_sync(0xffffffffu, fx, src);
+      if constexpr (FULL) {
+        const uint64_t xv = __shfl_sync(0xffffffffu, xk.x, src);
+        const uint64_t xw = __shfl_sync(0xffffffffu, xk.y, src);
+        const double xs = __shfl_sync(0xffffffffu, sy, src);
+        if (lane < n) {
+          const ulonglong2 hk = s_hk[h];
+          const double2 hs = s_hs[h];
+          const int ph = (product_phase(hk.x, hk.y, xv, xw) + es.rot + es.uH + es.uX) & 3;
+          Contrib r;
+          r.v = hk.x ^ xv;
+          r.w = hk.y ^ xw;
+          r.val = neg_if(scaled(hs.x, (int)hs.y, xs, 1), (ph & 2) != 0);
+          r.code = h0 + h;
+          r.pad = 0;
+          const uint32_t p = pfx ^ s_hf[h];
+          const uint32_t pos = atomicAdd(&cnt[p], 1u);
+          fout[base[p] + pos] = r;
+        }
+      } else {
+        if (lane < n) {
+          const uint32_t p = pfx ^ s_hf[h];
+          const uint32_t pos = atomicAdd(&cnt[p], 1u);
+          entries[base[p] + pos] = ((uint64_t)(t0 + src) << 16) | (uint64_t)(h0 + h);
+        }
+      }
+      emitted += n;
+    };
+    int qn = 0;  // queued codes of this warp (warp-uniform)
     for (int h = 0; h < nh; ++h) {
       const ulonglong2 hk = s_hk[h];
-      if (anticommute(hk.x, hk.y, xk.x, xk.y)) {
-        uint32_t p = fx ^ s_hf[h];
-        uint32_t pos = atomicAdd(&cnt[p], 1u);
-        entries[base[p] + pos] = ((uint64_t)i << 16) | (uint64_t)(h0 + h);
-        ++mine;
+      const bool anti = valid && anticommute(hk.x, hk.y, xk.x, xk.y);
+      const unsigned m = __ballot_sync(0xffffffffu, anti);
+      if (!m) continue;
+      if (anti) q[qn + __popc(m & ((1u << lane) - 1))] = ((uint32_t)lane << 16) | (uint32_t)h;
+      qn += __popc(m);
+      if (qn >= 32) {  // take the first 32, move the rest (fewer than 32) to the front
+        __syncwarp();
+        flush(32);
+        const int rest = qn - 32;
+        const uint32_t rc = lane < rest ? q[32 + lane] : 0u;
+        __syncwarp();
+        if (lane < rest) q[lane] = rc;
+        __syncwarp();
+        qn = rest;
       }
     }
+    __syncwarp();
+    if (qn > 0) flush(qn);
+    __syncwarp();
   }
-  // block total
   __shared__ unsigned long long s_tot;
   if (threadIdx.x == 0) s_tot = 0;
   __syncthreads();
-  for (int d = 16; d > 0; d >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, d);
-  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_tot, (unsigned long long)mine);
+  if (lane == 0 && emitted) atomicAdd(&s_tot, (unsigned long long)emitted);
   __syncthreads();
   if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
+}
+
+// Full-record emission of an extra source (code < kCodePre) or of the pre operand.
+__global__ void k_emit_source_full(const Rec* __restrict__ Y, int64_t n, int bits, uint32_t code, EmitScalars es,
+                                   const uint64_t* __restrict__ base, uint32_t* __restrict__ cnt,
+                                   Contrib* __restrict__ out) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const Rec y = Y[i];
+    const uint32_t p = dev_hash(y.v, y.w, 0, bits);
+    Contrib c;
+    c.v = y.v;
+    c.w = y.w;
+    c.code = code;
+    c.pad = 0;
+    if (code == kCodePre) {
+      c.val = es.pre_u ? y.im : y.re;
+    } else {
+      const uint32_t si = code - kCodeSrc;
+      const double sy = es.src_uy[si] ? y.im : y.re;
+      c.val = neg_if(scaled(es.src_s[si], es.src_e[si], sy, 0), (es.src_q[si] & 2) != 0);
+    }
+    const uint32_t pos = atomicAdd(&cnt[p], 1u);
+    out[base[p] + pos] = c;
+  }
 }
 
 __global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, uint32_t code,
@@ -210,6 +349,7 @@ struct MergeArgs {
   const uint32_t* cnt;    // bin fill counts
   const uint64_t* cpre;   // exclusive prefix of cnt
   const uint64_t* entries;
+  const Contrib* fent;    // full-record entries (single-component mode), or null
   const uint32_t* gstart;
   const uint32_t* ngroups;
   unsigned* next_group;
@@ -300,33 +440,6 @@ __device__ __forceinline__ void build_contribution(const MergeArgs& a, uint32_t 
     key = make_ulonglong2(y.v, y.w);
     t = cmul(a.alpha[code - kCodeSrc], Cx{y.re, y.im});
   }
-}
-
-// y * 2^e when y is normal and the result stays normal (exact); ok = false otherwise.
-__device__ __forceinline__ double scale_pow2(double y, int e, bool& ok) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(y);
-  int E = (int)((b >> 52) & 0x7FF);
-  int E2 = E + e;
-  ok = (E != 0 && E != 0x7FF && E2 >= 1 && E2 <= 2046);
-  return ok ? __longlong_as_double((long long)(b + ((unsigned long long)(long long)e << 52))) : 0.0;
-}
-
-__device__ __forceinline__ double neg_if(double x, bool c) {  // sign flip on the integer pipe
-  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
-}
-__device__ __forceinline__ bool sign_bit(double x) { return __double_as_longlong(x) < 0; }
-
-// round(s * y) for a real constant s with pow2 exponent e (kNoPow2: general), times 2^extra.
-// For a power of two the product is an exponent shift on the integer pipe; otherwise one
-// rounded FP64 product (then an exact doubling when extra == 1).
-__device__ __forceinline__ double scaled(double s, int e, double y, int extra) {
-  if (e != kNoPow2) {
-    bool ok;
-    double r = scale_pow2(y, e + extra, ok);
-    if (ok) return neg_if(r, sign_bit(s));
-  }
-  double p = __dmul_rn(s, y);
-  return extra ? twice(p) : p;
 }
 
 // Structured mode: the signed real value of the entry's single non-zero component.
@@ -829,7 +942,7 @@ __device__ __forceinline__ uint32_t code_bit(uint32_t code, int nH) {
   return code < kCodeSrc ? code : (uint32_t)nH + (code - kCodeSrc);
 }
 
-template <bool S>
+template <bool S, bool FULL>
 __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RankSmem<S>& s = *reinterpret_cast<RankSmem<S>*>(smem_raw);
@@ -897,37 +1010,49 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)kBatch * kMergeThreads) {
         uint64_t ent[kBatch];
         Rec rec[kBatch];
+        Contrib cf[kBatch];
+        bool has[kBatch];
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
           uint64_t j = j0 + (uint64_t)k * kMergeThreads + tid;
-          ent[k] = ~0ull;
-          if (j < E) {
+          has[k] = j < E;
+          ent[k] = 0;
+          if (has[k]) {
             uint32_t l = 0, r = nb;
             while (r - l > 1) {
               uint32_t m = (l + r) >> 1;
               if (s.gpre[m] <= j) l = m; else r = m;
             }
-            ent[k] = a.entries[s.gbase[l] + (j - s.gpre[l])];
+            if constexpr (FULL) cf[k] = a.fent[s.gbase[l] + (j - s.gpre[l])];
+            else ent[k] = a.entries[s.gbase[l] + (j - s.gpre[l])];
+          }
+        }
+        if constexpr (!FULL) {
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+            if (!has[k]) continue;
+            uint32_t code = (uint32_t)(ent[k] & 0xFFFFu);
+            uint64_t idx = ent[k] >> 16;
+            const Rec* base = code < kCodeSrc ? a.X : (code == kCodePre ? a.pre : a.src[code - kCodeSrc]);
+            rec[k] = base[idx];
           }
         }
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
-          if (ent[k] == ~0ull) continue;
-          uint32_t code = (uint32_t)(ent[k] & 0xFFFFu);
-          uint64_t idx = ent[k] >> 16;
-          const Rec* base = code < kCodeSrc ? a.X : (code == kCodePre ? a.pre : a.src[code - kCodeSrc]);
-          rec[k] = base[idx];
-        }
-#pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-          bool keep = ent[k] != ~0ull;
+          bool keep = has[k];
           ulonglong2 key = make_ulonglong2(0, 0);
           Cx t{0.0, 0.0};
           uint32_t code = 0;
           if (keep) {
-            code = (uint32_t)(ent[k] & 0xFFFFu);
-            if constexpr (S) build_scalar(a, code, rec[k], key, t.re);
-            else build_contribution(a, code, rec[k], key, t);
+            if constexpr (FULL) {
+              key = make_ulonglong2(cf[k].v, cf[k].w);
+              t.re = cf[k].val;
+              code = cf[k].code;
+            } else {
+              code = (uint32_t)(ent[k] & 0xFFFFu);
+              if constexpr (S) build_scalar(a, code, rec[k], key, t.re);
+              else build_contribution(a, code, rec[k], key, t);
+            }
             if (level > 0) keep = dev_hash(key.x, key.y, a.bits, level) == sub;
           }
           const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -1146,105 +1271,10 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   const int bits = choose_bits(bound_total);
   const uint32_t nbins = 1u << bits;
   const int nsm = num_sms();
-
-  Buf<uint32_t> fX, fH, histX, histY, cnt, flag, gstart;
-  Buf<uint64_t> bound, base, cpre, fpre, entries;
-  Buf<unsigned long long> counters;  // [0] product entries, [1] out_n
-  Buf<unsigned> misc;                // [0] next_group, [1] ngroups, [2] split groups
-  Buf<int> err;
-  PS_TRY(histY.alloc(nbins, s));
-  PS_TRY(cnt.alloc(nbins, s));
-  PS_TRY(bound.alloc(nbins, s));
-  PS_TRY(base.alloc(nbins + 1, s));
-  PS_TRY(counters.alloc(2, s));
-  PS_TRY(misc.alloc(3, s));
-  PS_TRY(err.alloc(1, s));
-  PS_CUDA(cudaMemsetAsync(histY.p, 0, nbins * sizeof(uint32_t), s));
-  PS_CUDA(cudaMemsetAsync(cnt.p, 0, nbins * sizeof(uint32_t), s));
-  PS_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), s));
-  PS_CUDA(cudaMemsetAsync(misc.p, 0, 3 * sizeof(unsigned), s));
-  PS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-
   auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
-  std::vector<Rec> hh_host;
 
-  // 1. hashes, histograms and bin bounds
-  if (nX > 0) {
-    PS_TRY(fX.alloc(nX, s));
-    PS_TRY(histX.alloc(nbins, s));
-    PS_CUDA(cudaMemsetAsync(histX.p, 0, nbins * sizeof(uint32_t), s));
-    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
-    PS_CUDA(cudaGetLastError());
-    std::vector<uint32_t> hf(sp.nH);
-    hh_host.resize(sp.nH);
-    PS_CUDA(cudaMemcpyAsync(hh_host.data(), sp.H, sp.nH * sizeof(Rec), cudaMemcpyDeviceToHost, s));
-    PS_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < sp.nH; ++i) hf[i] = host_hash(hh_host[i].v, hh_host[i].w, bits);
-    PS_TRY(fH.alloc(sp.nH, s));
-    PS_CUDA(cudaMemcpyAsync(fH.p, hf.data(), sp.nH * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
-  }
-  for (int i = 0; i < sp.nsrc; ++i)
-    if (sp.src[i].n > 0) {
-      PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
-      PS_CUDA(cudaGetLastError());
-    }
-  if (sp.npre > 0) {
-    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, nullptr, histY.p));
-    PS_CUDA(cudaGetLastError());
-  }
-  {
-    int nh = nX > 0 ? sp.nH : 0;
-    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
-    PS_LAUNCH("k_bound", s, k_bound<<<blocks, 256, 0, s>>>(nX > 0 ? histX.p : nullptr, histY.p, fH.p, nh, nbins, bound.p));
-    PS_CUDA(cudaGetLastError());
-  }
-  PS_TRY(scan_u64(bound.p, base.p, nbins, s));
-  PS_TRY(entries.alloc((size_t)bound_total, s));
-
-  // 2. emission
-  if (nX > 0) {
-    for (int h0 = 0; h0 < sp.nH; h0 += kHChunk) {
-      int nh = std::min(kHChunk, sp.nH - h0);
-      size_t sm = (size_t)nh * (sizeof(ulonglong2) + sizeof(uint32_t));
-      if (sm > 48 * 1024) PS_CUDA(cudaFuncSetAttribute(k_emit_products, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      PS_LAUNCH("k_emit_products", s, k_emit_products<<<grid_for(nX), 256, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, h0, nh, base.p, cnt.p, entries.p,
-                                                     counters.p));
-      PS_CUDA(cudaGetLastError());
-    }
-  }
-  for (int i = 0; i < sp.nsrc; ++i)
-    if (sp.src[i].n > 0) {
-      PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, kCodeSrc + i, base.p,
-                                                          cnt.p, entries.p));
-      PS_CUDA(cudaGetLastError());
-    }
-  if (sp.npre > 0) {
-    PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, kCodePre, base.p, cnt.p, entries.p));
-    PS_CUDA(cudaGetLastError());
-  }
-  unsigned long long n_prod = 0;
-  PS_CUDA(cudaMemcpyAsync(&n_prod, counters.p, sizeof(n_prod), cudaMemcpyDeviceToHost, s));
-  PS_CUDA(cudaStreamSynchronize(s));
-  const int64_t total_entries = (int64_t)n_prod + nsrc_total;
-  st.contributions = (int64_t)n_prod;
-
-  // 3. groups
-  PS_TRY(cpre.alloc(nbins + 1, s));
-  PS_TRY(scan_u32_to_u64(cnt.p, cpre.p, nbins, s));
-  PS_TRY(flag.alloc(nbins, s));
-  PS_TRY(fpre.alloc(nbins + 1, s));
-  PS_TRY(gstart.alloc(nbins + 1, s));
-  {
-    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
-    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)kGroupQuota, flag.p));
-    PS_CUDA(cudaGetLastError());
-    PS_TRY(scan_u32_to_u64(flag.p, fpre.p, nbins, s));
-    PS_LAUNCH("k_group_scatter", s, k_group_scatter<<<blocks, 256, 0, s>>>(flag.p, fpre.p, nbins, gstart.p, misc.p + 1));
-    PS_CUDA(cudaGetLastError());
-  }
-
-  // coefficient classes: the merge runs in single-component mode when every term of every
-  // output string lies in the same component (real or imaginary)
+  // ---- coefficient classes: the merge runs in single-component mode when every term of
+  // every output string lies in the same component (real or imaginary)
   auto cls_scalar = [](Cx c) { return cls_of(c.re, c.im); };
   int prod_cls = 0;
   if (nX > 0) {
@@ -1252,57 +1282,32 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     if (!(sp.rot & 1)) prod_cls = cls_swap(prod_cls);
   }
   int acc_cls = prod_cls;
-  int src_cls[4] = {0, 0, 0, 0};
-  for (int i = 0; i < sp.nsrc; ++i) {
-    src_cls[i] = sp.src[i].n > 0 ? cls_mul(cls_scalar(sp.src[i].alpha), sp.src[i].cls) : 0;
-    acc_cls |= src_cls[i];
-  }
+  for (int i = 0; i < sp.nsrc; ++i)
+    acc_cls |= sp.src[i].n > 0 ? cls_mul(cls_scalar(sp.src[i].alpha), sp.src[i].cls) : 0;
   int out_cls = acc_cls;
   if (sp.has_post) out_cls = (sp.npre > 0 ? sp.clsPre : 0) | cls_mul(cls_scalar(sp.post), acc_cls);
   const bool structured = acc_cls != kClsComplex && out_cls != kClsComplex;
+  // ranked merge when the order codes fit the slot masks, chained merge otherwise; full
+  // contribution records (no gather in the merge) when single-component and they fit
+  const bool ranked = sp.nH + sp.nsrc <= kMaskBits;
+  const bool full = structured && ranked && (uint64_t)bound_total * sizeof(Contrib) <= kFullBudget;
 
-  // 4. merge into a fresh output buffer
-  int64_t out_cap = std::max<int64_t>(total_entries, 1);
-  Rec* outbuf = nullptr;
-  PS_TRY(dev_alloc((void**)&outbuf, (size_t)out_cap * sizeof(Rec), s));
-  MergeArgs a{};
-  a.H = sp.H;
-  a.nH = sp.nH;
-  a.X = sp.X;
-  a.rot = sp.rot;
-  for (int i = 0; i < sp.nsrc; ++i) {
-    a.src[i] = sp.src[i].rec;
-    a.alpha[i] = sp.src[i].alpha;
+  std::vector<Rec> hh_host;
+  if (nX > 0) {
+    hh_host.resize(sp.nH);
+    PS_CUDA(cudaMemcpyAsync(hh_host.data(), sp.H, sp.nH * sizeof(Rec), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
   }
-  a.pre = sp.pre;
-  a.has_post = sp.has_post ? 1 : 0;
-  a.post = sp.post;
-  a.bits = bits;
-  a.nbins = nbins;
-  a.base = base.p;
-  a.cnt = cnt.p;
-  a.cpre = cpre.p;
-  a.entries = entries.p;
-  a.gstart = gstart.p;
-  a.ngroups = misc.p + 1;
-  a.next_group = misc.p;
-  a.out = outbuf;
-  a.out_n = counters.p + 1;
-  a.out_cap = (unsigned long long)out_cap;
-  a.err = err.p;
-  a.split_groups = misc.p + 2;
-  uint64_t kv, kw;
-  host_key_with_hash(nbins / 2, bits, &kv, &kw);  // hash in the upper half: empty key for lower-half groups
-  a.sent_lo = make_ulonglong2(kv, kw);
-  a.sent_hi = make_ulonglong2(0ull, 0ull);        // hash 0: empty key for upper-half groups
+  auto pow2_exp = [](double x) -> int {
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    int E = (int)((b >> 52) & 0x7FF);
+    return ((b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046) ? E - 1023 : kNoPow2;
+  };
+  MergeArgs a{};
+  EmitScalars es{};
   Buf<double2> hscal;
   if (structured) {
-    auto pow2_exp = [](double x) -> int {
-      uint64_t b;
-      memcpy(&b, &x, 8);
-      int E = (int)((b >> 52) & 0x7FF);
-      return ((b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046) ? E - 1023 : kNoPow2;
-    };
     a.uH = sp.clsH == kClsImag;
     a.uX = sp.clsX == kClsImag;
     if (nX > 0) {
@@ -1328,16 +1333,161 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     a.post_s = up ? sp.post.im : sp.post.re;
     a.post_q = up + (acc_cls == kClsImag);
     a.out_imag = out_cls == kClsImag;
+    es.rot = sp.rot;
+    es.uH = a.uH;
+    es.uX = a.uX;
+    for (int i = 0; i < 4; ++i) {
+      es.src_s[i] = a.src_s[i];
+      es.src_e[i] = a.src_e[i];
+      es.src_q[i] = a.src_q[i];
+      es.src_uy[i] = a.src_uy[i];
+    }
+    es.pre_u = a.pre_u;
   }
-  // ranked merge when the order codes fit the slot masks, chained merge otherwise
-  const bool ranked = sp.nH + sp.nsrc <= kMaskBits;
+
+  Buf<uint32_t> fX, fH, histX, histY, cnt, flag, gstart;
+  Buf<uint64_t> bound, base, cpre, fpre, entries;
+  Buf<Contrib> fent;
+  Buf<unsigned long long> counters;  // [0] product entries, [1] out_n
+  Buf<unsigned> misc;                // [0] next_group, [1] ngroups, [2] split groups
+  Buf<int> err;
+  PS_TRY(histY.alloc(nbins, s));
+  PS_TRY(cnt.alloc(nbins, s));
+  PS_TRY(bound.alloc(nbins, s));
+  PS_TRY(base.alloc(nbins + 1, s));
+  PS_TRY(counters.alloc(2, s));
+  PS_TRY(misc.alloc(3, s));
+  PS_TRY(err.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(histY.p, 0, nbins * sizeof(uint32_t), s));
+  PS_CUDA(cudaMemsetAsync(cnt.p, 0, nbins * sizeof(uint32_t), s));
+  PS_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), s));
+  PS_CUDA(cudaMemsetAsync(misc.p, 0, 3 * sizeof(unsigned), s));
+  PS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+
+  // ---- 1. hashes, histograms and bin bounds
+  if (nX > 0) {
+    PS_TRY(fX.alloc(nX, s));
+    PS_TRY(histX.alloc(nbins, s));
+    PS_CUDA(cudaMemsetAsync(histX.p, 0, nbins * sizeof(uint32_t), s));
+    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
+    PS_CUDA(cudaGetLastError());
+    std::vector<uint32_t> hf(sp.nH);
+    for (int i = 0; i < sp.nH; ++i) hf[i] = host_hash(hh_host[i].v, hh_host[i].w, bits);
+    PS_TRY(fH.alloc(sp.nH, s));
+    PS_CUDA(cudaMemcpyAsync(fH.p, hf.data(), sp.nH * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  }
+  for (int i = 0; i < sp.nsrc; ++i)
+    if (sp.src[i].n > 0) {
+      PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
+      PS_CUDA(cudaGetLastError());
+    }
+  if (sp.npre > 0) {
+    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, nullptr, histY.p));
+    PS_CUDA(cudaGetLastError());
+  }
+  {
+    int nh = nX > 0 ? sp.nH : 0;
+    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
+    PS_LAUNCH("k_bound", s, k_bound<<<blocks, 256, 0, s>>>(nX > 0 ? histX.p : nullptr, histY.p, fH.p, nh, nbins, bound.p));
+    PS_CUDA(cudaGetLastError());
+  }
+  PS_TRY(scan_u64(bound.p, base.p, nbins, s));
+  if (full) PS_TRY(fent.alloc((size_t)bound_total, s));
+  else PS_TRY(entries.alloc((size_t)bound_total, s));
+
+  // ---- 2. emission
+  if (nX > 0) {
+    if (full) {
+      size_t sm = (size_t)sp.nH * (sizeof(ulonglong2) + sizeof(double2) + sizeof(uint32_t));
+      PS_LAUNCH("k_emit_products", s, k_emit_products<true><<<grid_for(nX), kEmitThreads, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, hscal.p, 0, sp.nH, es, base.p, cnt.p, nullptr, fent.p, counters.p));
+      PS_CUDA(cudaGetLastError());
+    } else {
+      for (int h0 = 0; h0 < sp.nH; h0 += kHChunk) {
+        int nh = std::min(kHChunk, sp.nH - h0);
+        size_t sm = (size_t)nh * (sizeof(ulonglong2) + sizeof(uint32_t));
+        if (sm > 48 * 1024) PS_CUDA(cudaFuncSetAttribute(k_emit_products<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        PS_LAUNCH("k_emit_products", s, k_emit_products<false><<<grid_for(nX), kEmitThreads, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, nullptr, h0, nh, es, base.p, cnt.p, entries.p, nullptr, counters.p));
+        PS_CUDA(cudaGetLastError());
+      }
+    }
+  }
+  for (int i = 0; i < sp.nsrc; ++i)
+    if (sp.src[i].n > 0) {
+      if (full)
+        PS_LAUNCH("k_emit_source", s, k_emit_source_full<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, kCodeSrc + i, es, base.p, cnt.p, fent.p));
+      else
+        PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, kCodeSrc + i, base.p, cnt.p, entries.p));
+      PS_CUDA(cudaGetLastError());
+    }
+  if (sp.npre > 0) {
+    if (full)
+      PS_LAUNCH("k_emit_source", s, k_emit_source_full<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, kCodePre, es, base.p, cnt.p, fent.p));
+    else
+      PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, kCodePre, base.p, cnt.p, entries.p));
+    PS_CUDA(cudaGetLastError());
+  }
+  unsigned long long n_prod = 0;
+  PS_CUDA(cudaMemcpyAsync(&n_prod, counters.p, sizeof(n_prod), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  const int64_t total_entries = (int64_t)n_prod + nsrc_total;
+  st.contributions = (int64_t)n_prod;
+
+  // ---- 3. groups
+  PS_TRY(cpre.alloc(nbins + 1, s));
+  PS_TRY(scan_u32_to_u64(cnt.p, cpre.p, nbins, s));
+  PS_TRY(flag.alloc(nbins, s));
+  PS_TRY(fpre.alloc(nbins + 1, s));
+  PS_TRY(gstart.alloc(nbins + 1, s));
+  {
+    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
+    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)kGroupQuota, flag.p));
+    PS_CUDA(cudaGetLastError());
+    PS_TRY(scan_u32_to_u64(flag.p, fpre.p, nbins, s));
+    PS_LAUNCH("k_group_scatter", s, k_group_scatter<<<blocks, 256, 0, s>>>(flag.p, fpre.p, nbins, gstart.p, misc.p + 1));
+    PS_CUDA(cudaGetLastError());
+  }
+
+  // ---- 4. merge into a fresh output buffer
+  int64_t out_cap = std::max<int64_t>(total_entries, 1);
+  Rec* outbuf = nullptr;
+  PS_TRY(dev_alloc((void**)&outbuf, (size_t)out_cap * sizeof(Rec), s));
+  a.H = sp.H;
+  a.nH = sp.nH;
+  a.X = sp.X;
+  a.rot = sp.rot;
+  for (int i = 0; i < sp.nsrc; ++i) {
+    a.src[i] = sp.src[i].rec;
+    a.alpha[i] = sp.src[i].alpha;
+  }
+  a.pre = sp.pre;
+  a.has_post = sp.has_post ? 1 : 0;
+  a.post = sp.post;
+  a.bits = bits;
+  a.nbins = nbins;
+  a.base = base.p;
+  a.cnt = cnt.p;
+  a.cpre = cpre.p;
+  a.entries = entries.p;
+  a.fent = fent.p;
+  a.gstart = gstart.p;
+  a.ngroups = misc.p + 1;
+  a.next_group = misc.p;
+  a.out = outbuf;
+  a.out_n = counters.p + 1;
+  a.out_cap = (unsigned long long)out_cap;
+  a.err = err.p;
+  a.split_groups = misc.p + 2;
+  uint64_t kv, kw;
+  host_key_with_hash(nbins / 2, bits, &kv, &kw);  // hash in the upper half: empty key for lower-half groups
+  a.sent_lo = make_ulonglong2(kv, kw);
+  a.sent_hi = make_ulonglong2(0ull, 0ull);        // hash 0: empty key for upper-half groups
   size_t sm;
   void (*kern)(MergeArgs);
   const char* kname;
   if (ranked) {
     sm = structured ? sizeof(RankSmem<true>) : sizeof(RankSmem<false>);
-    kern = structured ? k_merge_rank<true> : k_merge_rank<false>;
-    kname = structured ? "k_merge_rank_s" : "k_merge_rank";
+    kern = full ? k_merge_rank<true, true> : (structured ? k_merge_rank<true, false> : k_merge_rank<false, false>);
+    kname = full ? "k_merge_rank_f" : (structured ? "k_merge_rank_s" : "k_merge_rank");
   } else {
     sm = structured ? sizeof(MergeSmem<true>) : sizeof(MergeSmem<false>);
     kern = structured ? k_merge<true> : k_merge<false>;

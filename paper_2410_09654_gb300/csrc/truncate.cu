@@ -364,7 +364,6 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   if (!use_gamma && !use_w && !use_cut && !use_top && !divisor) return PS_OK;
   if (O->n == 0) return PS_OK;
   const int nsm = num_sms();
-  auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
 
   Buf<double> factor;
   Buf<unsigned long long> cnt;
