@@ -33,8 +33,12 @@ sys.path.insert(0, ROOT)
 METRIC = "[H,O] Pauli products/s + RK4 steps/s at ≤1e-6 rel error vs FP64 oracle"
 N_SITES = 64
 TOP_K = 1 << 22
-WORKLOAD = ("Lanczos on the open XXZ chain N=64 (H = sum XX+YY+0.5ZZ, 189 strings), O_0 = sum X_i/8, "
-            "top 2^22 strings kept after each step; timed steps start once |O| has reached 2^22")
+
+
+def workload(top_k: int) -> str:
+    cap = f"2^{top_k.bit_length() - 1}" if top_k & (top_k - 1) == 0 else str(top_k)
+    return ("Lanczos on the open XXZ chain N=64 (H = sum XX+YY+0.5ZZ, 189 strings), O_0 = sum X_i/8, "
+            f"top {cap} strings kept after each step; timed steps start once |O| has reached {cap}")
 RK4_WORKLOAD = "RK4 on the open N=10 chain sum ZZ + 1.05 sum X + 0.5 sum Z, O(0)=Z_1, dt=0.05, 40 steps, weight<=6 then |c|<1e-10"
 
 
@@ -149,7 +153,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Pauli products/s", "n_gpus": args.gpus,
         "steps": len(rec), "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(rec), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"same recursion with the cap lowered to 2^16 strings"},
+        "config": {"workload": workload(args.top_k), "sample": f"same recursion with the cap lowered to 2^16 strings"},
         "cpu_baseline": {"value": value, "unit": "Pauli products/s", "cores": 1, "kind": "oracle",
                          "sample": f"{len(rec)} oracle Lanczos steps at |O| = 2^16 (single-threaded C++ oracle)"},
         "e2e": {"value": value, "unit": "Pauli products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -352,9 +356,11 @@ def main():
             "metric": METRIC, "value": value, "unit": "Pauli products/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_sites": N_SITES, "H_strings": nH, "top_k": args.top_k,
-                       "ramp_steps": ramp_steps, "l2": "inputs larger than L2 (|O| = 2^22 strings x 32 B = 134 MB; "
-                       "the merge bins are several GB)", "parallelism": "replicas" if world > 1 else "single"},
+            "config": {"workload": workload(args.top_k), "n_sites": N_SITES, "H_strings": nH, "top_k": args.top_k,
+                       "ramp_steps": ramp_steps,
+                       "l2": f"inputs larger than L2: |O| = {args.top_k} strings x 32 B = {args.top_k * 32 / 1e6:.0f} MB per operand; the merge "
+                       f"bins hold {contributions / args.steps * 32 / 1e9:.1f} GB of contribution records per step "
+                       "(L2 is 129 MB)", "parallelism": "replicas" if world > 1 else "single"},
             "merged_strings_per_s": merged_rate,
             "contributions_per_step": contributions / args.steps,
             "b_n_timed": bs,

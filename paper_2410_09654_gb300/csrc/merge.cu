@@ -133,6 +133,14 @@ struct __align__(16) Contrib {
   uint32_t pad;
 };
 
+// Real factor of an H term in single-component mode and the exponent of |s| when s is a
+// power of two (kNoPow2 otherwise).
+struct __align__(16) HScal {
+  double s;
+  int e;
+  int pad;
+};
+
 // Scalars of the single-component arithmetic (see build_scalar).
 struct EmitScalars {
   int rot, uH, uX;
@@ -168,29 +176,35 @@ __device__ __forceinline__ double scaled(double s, int e, double y, int extra) {
   return extra ? twice(p) : p;
 }
 
-// Emission of the products.  A warp holds 32 x in registers and walks the H terms; the
-// anticommuting (h, lane) pairs are queued as 32-bit codes and, 32 at a time, turned into
-// entries with every lane active: the lane fetches its x by shuffle, then reserves a slot in
-// bin F(h) ^ F(x) and writes the entry there.  The queue is emptied before the warp moves on
-// to its next 32 x.  FULL: the entry is the finished contribution record (string, value,
-// H index); otherwise the 8-byte reference (x index << 16 | H index) that the merge resolves.
-template <bool FULL>
+// Bin cursors: cur[p] starts at the bin's first slot (base[p]) and one 64-bit atomic add
+// reserves slots and returns their absolute position.  A warp reserves once per distinct bin
+// among its 32 entries (the entries of one h over neighbouring x often share bins).
+__device__ __forceinline__ uint64_t reserve_slot(unsigned long long* __restrict__ cur, uint32_t p, bool act, int lane) {
+  const unsigned mm = __match_any_sync(0xffffffffu, act ? p : 0xFFFFFFFFu);
+  const int leader = __ffs(mm) - 1;
+  unsigned long long b = 0;
+  if (act && lane == leader) b = atomicAdd(&cur[p], (unsigned long long)__popc(mm));
+  b = __shfl_sync(0xffffffffu, b, leader);
+  return b + (uint32_t)__popc(mm & ((1u << lane) - 1u));
+}
+
+// Emission of the products for |H| > 256 (8-byte entries, H in chunks [h0, h0 + nh)).  A warp
+// holds 32 x in registers and walks the H terms; the anticommuting (h, lane) pairs are
+// queued as 32-bit codes and, 32 at a time, turned into entries (x index << 16 | H index)
+// with every lane active: the lane fetches its x's hash by shuffle and reserves a slot in
+// bin F(h) ^ F(x).  The queue is emptied before the warp moves on to its next 32 x.
 __global__ void __launch_bounds__(kEmitThreads) k_emit_products(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
                                                        int64_t nX, const Rec* __restrict__ H,
-                                                       const uint32_t* __restrict__ fH,
-                                                       const double2* __restrict__ hscal, int h0, int nh,
-                                                       EmitScalars es, const uint64_t* __restrict__ base,
-                                                       uint32_t* __restrict__ cnt, uint64_t* __restrict__ entries,
-                                                       Contrib* __restrict__ fout,
+                                                       const uint32_t* __restrict__ fH, int h0, int nh,
+                                                       unsigned long long* __restrict__ cur,
+                                                       uint64_t* __restrict__ entries,
                                                        unsigned long long* __restrict__ total) {
   extern __shared__ __align__(16) unsigned char smem[];
   ulonglong2* s_hk = reinterpret_cast<ulonglong2*>(smem);
-  double2* s_hs = reinterpret_cast<double2*>(smem + sizeof(ulonglong2) * nh);  // FULL only
-  uint32_t* s_hf = reinterpret_cast<uint32_t*>(smem + (sizeof(ulonglong2) + (FULL ? sizeof(double2) : 0)) * nh);
+  uint32_t* s_hf = reinterpret_cast<uint32_t*>(smem + sizeof(ulonglong2) * nh);
   __shared__ uint32_t s_q[kEmitThreads / 32][kQueue];
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     s_hk[i] = make_ulonglong2(H[h0 + i].v, H[h0 + i].w);
-    if constexpr (FULL) s_hs[i] = hscal[h0 + i];
     s_hf[i] = fH[h0 + i];
   }
   __syncthreads();
@@ -203,44 +217,20 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_products(const Rec* __res
     const int64_t i = t0 + lane;
     const bool valid = i < nX;
     ulonglong2 xk = make_ulonglong2(0, 0);
-    double sy = 0.0;
     uint32_t fx = 0;
     if (valid) {
       xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
-      if constexpr (FULL) sy = es.uX ? X[i].im : X[i].re;
       fx = fX[i];
     }
     // entries for queue codes q[0, n): lane l takes q[l]; all lanes take part in the shuffles
     auto flush = [&](int n) {
-      const uint32_t c = lane < n ? q[lane] : 0u;
+      const bool act = lane < n;
+      const uint32_t c = act ? q[lane] : 0u;
       const int src = (int)(c >> 16);
       const uint32_t h = c & 0xFFFFu;
-      const uint32_t pfx = __shfl_sync(0xffffffffu, fx, src);
-      if constexpr (FULL) {
-        const uint64_t xv = __shfl_sync(0xffffffffu, xk.x, src);
-        const uint64_t xw = __shfl_sync(0xffffffffu, xk.y, src);
-        const double xs = __shfl_sync(0xffffffffu, sy, src);
-        if (lane < n) {
-          const ulonglong2 hk = s_hk[h];
-          const double2 hs = s_hs[h];
-          const int ph = (product_phase(hk.x, hk.y, xv, xw) + es.rot + es.uH + es.uX) & 3;
-          Contrib r;
-          r.v = hk.x ^ xv;
-          r.w = hk.y ^ xw;
-          r.val = neg_if(scaled(hs.x, (int)hs.y, xs, 1), (ph & 2) != 0);
-          r.code = h0 + h;
-          r.pad = 0;
-          const uint32_t p = pfx ^ s_hf[h];
-          const uint32_t pos = atomicAdd(&cnt[p], 1u);
-          fout[base[p] + pos] = r;
-        }
-      } else {
-        if (lane < n) {
-          const uint32_t p = pfx ^ s_hf[h];
-          const uint32_t pos = atomicAdd(&cnt[p], 1u);
-          entries[base[p] + pos] = ((uint64_t)(t0 + src) << 16) | (uint64_t)(h0 + h);
-        }
-      }
+      const uint32_t p = __shfl_sync(0xffffffffu, fx, src) ^ s_hf[h];
+      const uint64_t at = reserve_slot(cur, p, act, lane);
+      if (act) entries[at] = ((uint64_t)(t0 + src) << 16) | (uint64_t)(h0 + h);
       emitted += n;
     };
     int qn = 0;  // queued codes of this warp (warp-uniform)
@@ -274,40 +264,241 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_products(const Rec* __res
   if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
 }
 
-// Full-record emission of an extra source (code < kCodePre) or of the pre operand.
-__global__ void k_emit_source_full(const Rec* __restrict__ Y, int64_t n, int bits, uint32_t code, EmitScalars es,
-                                   const uint64_t* __restrict__ base, uint32_t* __restrict__ cnt,
-                                   Contrib* __restrict__ out) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    const Rec y = Y[i];
-    const uint32_t p = dev_hash(y.v, y.w, 0, bits);
-    Contrib c;
-    c.v = y.v;
-    c.w = y.w;
-    c.code = code;
-    c.pad = 0;
-    if (code == kCodePre) {
-      c.val = es.pre_u ? y.im : y.re;
-    } else {
-      const uint32_t si = code - kCodeSrc;
-      const double sy = es.src_uy[si] ? y.im : y.re;
-      c.val = neg_if(scaled(es.src_s[si], es.src_e[si], sy, 0), (es.src_q[si] & 2) != 0);
+// ---- table-driven emission (|H| <= 256)
+// Whether h and x anticommute is the parity of popcount((h.w & x.v) ^ (h.v & x.w)), a
+// GF(2)-linear function of the 128 bits of x.  So the bitmap A(x) (bit h set iff h and x
+// anticommute) is the XOR, over the 32 nibbles of x, of a table row indexed by (nibble
+// position, nibble value): A(x) = XOR_p T[p][nibble_p(x)].  Positions 0..15 are the nibbles
+// of x.v (paired with h.w), 16..31 those of x.w (paired with h.v).  A row holds NW 32-bit
+// words and is padded to a stride of kTabStride(NW) words (2 mod 4), so that 16 lanes
+// reading 64-bit words of 16 different rows of one position hit 16 distinct bank pairs.
+constexpr int kTabPos = 32, kTabVals = 16;
+
+__host__ __device__ constexpr int tab_stride(int nw) { return nw <= 2 ? 2 : (nw <= 6 ? 6 : 10); }
+
+// T[p][val][k]: bit b of word k is the parity of popcount(val & nibble_p(h = 32k + b)).
+__global__ void k_anti_table(const Rec* __restrict__ H, int nH, int stride, uint32_t* __restrict__ T) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kTabPos * kTabVals) return;
+  const int p = t / kTabVals, val = t % kTabVals;
+  for (int k = 0; k < stride; ++k) {
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int h = 32 * k + b;
+      if (h >= nH) break;
+      const uint64_t m = p < 16 ? H[h].w : H[h].v;
+      const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
+      word |= (uint32_t)(__popc(nib & (uint32_t)val) & 1) << b;
     }
-    const uint32_t pos = atomicAdd(&cnt[p], 1u);
-    out[base[p] + pos] = c;
+    T[t * stride + k] = word;
   }
 }
 
-__global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, uint32_t code,
-                              const uint64_t* __restrict__ base, uint32_t* __restrict__ cnt,
-                              uint64_t* __restrict__ entries) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    uint32_t p = dev_hash(Y[i].v, Y[i].w, 0, bits);
-    uint32_t pos = atomicAdd(&cnt[p], 1u);
-    entries[base[p] + pos] = ((uint64_t)i << 16) | code;
+constexpr int kRing = 64;  // per-warp ring of queued (lane, h) codes
+constexpr int kRingMask = kRing - 1;
+
+template <bool FULL, int NW>
+__global__ void __launch_bounds__(kEmitThreads, 5) k_emit_tab(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
+                                                  int64_t nX, const Rec* __restrict__ H,
+                                                  const uint32_t* __restrict__ fH,
+                                                  const HScal* __restrict__ hscal, int nh,
+                                                  const uint32_t* __restrict__ T, EmitScalars es,
+                                                  unsigned long long* __restrict__ cur,
+                                                  uint64_t* __restrict__ entries, Contrib* __restrict__ fout,
+                                                  unsigned long long* __restrict__ total,
+                                                  unsigned long long* __restrict__ next_tile) {
+  constexpr int S = tab_stride(NW);
+  constexpr int kTabWords = kTabPos * kTabVals * S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_ring = s_tab + kTabWords;
+  ulonglong2* s_hk = reinterpret_cast<ulonglong2*>(s_ring + (kEmitThreads / 32) * kRing);
+  HScal* s_hs = reinterpret_cast<HScal*>(s_hk + nh);  // FULL only
+  uint32_t* s_hf = reinterpret_cast<uint32_t*>(s_hs + (FULL ? nh : 0));
+  for (int i = threadIdx.x; i < kTabWords; i += blockDim.x) s_tab[i] = T[i];
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+    s_hk[i] = make_ulonglong2(H[i].v, H[i].w);
+    if constexpr (FULL) s_hs[i] = hscal[i];
+    s_hf[i] = fH[i];
   }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* q = s_ring + warp * kRing;
+  uint32_t emitted = 0;  // warp-uniform
+  for (;;) {  // tiles of 32 x, handed out one at a time
+    unsigned long long tile = 0;
+    if (lane == 0) tile = atomicAdd(next_tile, 1ull);
+    const int64_t t0 = (int64_t)__shfl_sync(0xffffffffu, tile, 0) * 32;
+    if (t0 >= nX) break;
+    const int64_t i = t0 + lane;
+    const bool valid = i < nX;
+    ulonglong2 xk = make_ulonglong2(0, 0);
+    double sy = 0.0;
+    uint32_t fx = 0;
+    if (valid) {
+      xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
+      if constexpr (FULL) sy = es.uX ? X[i].im : X[i].re;
+      fx = fX[i];
+    }
+    // anticommutation bitmap of this lane's x
+    uint32_t A[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) A[k] = 0u;
+    if (valid) {
+#pragma unroll
+      for (int p = 0; p < kTabPos; ++p) {
+        const uint64_t m = p < 16 ? xk.x : xk.y;
+        const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
+        const uint32_t* row = s_tab + (p * kTabVals + nib) * S;
+#pragma unroll
+        for (int k = 0; k < NW; k += 2) {
+          const uint2 t = *reinterpret_cast<const uint2*>(row + k);
+          A[k] ^= t.x;
+          A[k + 1] ^= t.y;
+        }
+      }
+    }
+    uint32_t head = 0, tail = 0;  // ring positions (warp-uniform), taken mod kRing
+    // entries for the codes at ring positions [head, head + n): lane l takes head + l
+    auto flush = [&](int n) {
+      const bool act = lane < n;
+      const uint32_t c = act ? q[(head + lane) & kRingMask] : 0u;
+      const int src = (int)(c >> 16);
+      const uint32_t h = c & 0xFFFFu;
+      const uint32_t pfx = __shfl_sync(0xffffffffu, fx, src);
+      Contrib r;
+      if constexpr (FULL) {
+        const uint64_t xv = __shfl_sync(0xffffffffu, xk.x, src);
+        const uint64_t xw = __shfl_sync(0xffffffffu, xk.y, src);
+        const double xs = __shfl_sync(0xffffffffu, sy, src);
+        const ulonglong2 hk = s_hk[h];
+        const HScal hs = s_hs[h];
+        const int ph = (product_phase(hk.x, hk.y, xv, xw) + es.rot + es.uH + es.uX) & 3;
+        r.v = hk.x ^ xv;
+        r.w = hk.y ^ xw;
+        r.val = neg_if(scaled(hs.s, hs.e, xs, 1), (ph & 2) != 0);
+        r.code = h;
+        r.pad = 0;
+      }
+      const uint64_t at = reserve_slot(cur, pfx ^ s_hf[h], act, lane);
+      if (act) {
+        if constexpr (FULL) fout[at] = r;
+        else entries[at] = ((uint64_t)(t0 + src) << 16) | (uint64_t)h;
+      }
+      __syncwarp();
+      head += n;
+      emitted += n;
+    };
+    // h-major queue order (the x of a tile are neighbours in hash order, so the entries of
+    // one h land in few bins): per h, a ballot of the lanes whose bitmap has bit h
+#pragma unroll 1
+    for (uint32_t hb = 0; hb < 32u * NW; hb += 32u) {
+      uint32_t a = A[0];
+#pragma unroll
+      for (int k = 0; k + 1 < NW; ++k) A[k] = A[k + 1];
+      A[NW - 1] = 0u;
+      uint32_t any = __ballot_sync(0xffffffffu, a != 0u) ? 1u : 0u;
+      if (!any) continue;
+      // h offsets of this word that some lane has (OR over the warp)
+      uint32_t word_or = a;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) word_or |= __shfl_xor_sync(0xffffffffu, word_or, d);
+      while (word_or) {
+        const int b = __ffs(word_or) - 1;
+        word_or &= word_or - 1u;
+        const bool anti = (a >> b) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, anti);
+        if (anti) q[(tail + __popc(m & ((1u << lane) - 1u))) & kRingMask] = ((uint32_t)lane << 16) | (hb + (uint32_t)b);
+        tail += __popc(m);
+        if (tail - head >= 32u) {
+          __syncwarp();
+          flush(32);
+        }
+      }
+    }
+    __syncwarp();
+    if (tail != head) flush((int)(tail - head));
+  }
+  __shared__ unsigned long long s_tot;
+  if (threadIdx.x == 0) s_tot = 0;
+  __syncthreads();
+  if (lane == 0 && emitted) atomicAdd(&s_tot, (unsigned long long)emitted);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
+}
+
+template <bool FULL, int NW>
+int launch_emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, const uint32_t* fH,
+                    const HScal* hscal, int nh, const uint32_t* T, const EmitScalars& es,
+                    unsigned long long* cur, uint64_t* entries, Contrib* fout, unsigned long long* total, int nsm,
+                    cudaStream_t s) {
+  Buf<unsigned long long> next_tile;
+  PS_TRY(next_tile.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(next_tile.p, 0, sizeof(unsigned long long), s));
+  const size_t sm = (size_t)kTabPos * kTabVals * tab_stride(NW) * sizeof(uint32_t) +
+                    (size_t)(kEmitThreads / 32) * kRing * sizeof(uint32_t) + (size_t)nh * (sizeof(ulonglong2) + (FULL ? sizeof(HScal) : 0) + sizeof(uint32_t));
+  PS_CUDA(cudaFuncSetAttribute(k_emit_tab<FULL, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int per_sm = 0;
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit_tab<FULL, NW>, kEmitThreads, sm));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * nsm, ceil_div(nX, kEmitThreads)));
+  PS_LAUNCH("k_emit_products", s, k_emit_tab<FULL, NW><<<grid, kEmitThreads, sm, s>>>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, next_tile.p));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+template <bool FULL>
+int emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, const uint32_t* fH, const HScal* hscal,
+             int nh, const uint32_t* T, const EmitScalars& es, unsigned long long* cur,
+             uint64_t* entries, Contrib* fout, unsigned long long* total, int nsm, cudaStream_t s) {
+  const int nw = (nh + 31) / 32;
+  if (nw <= 2) return launch_emit_tab<FULL, 2>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
+  if (nw <= 4) return launch_emit_tab<FULL, 4>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
+  if (nw <= 6) return launch_emit_tab<FULL, 6>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
+  return launch_emit_tab<FULL, 8>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
+}
+
+// Emission of an extra source (code kCodeSrc + i) or of the pre operand (kCodePre): FULL, the
+// contribution record; otherwise the 8-byte reference (index << 16 | code).  Warp-strided so
+// that all 32 lanes take part in every slot reservation.
+template <bool FULL>
+__global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, uint32_t code, EmitScalars es,
+                              unsigned long long* __restrict__ cur, uint64_t* __restrict__ entries,
+                              Contrib* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    const bool act = i < n;
+    Rec y = Rec{0, 0, 0.0, 0.0};
+    if (act) y = Y[i];
+    const uint32_t p = dev_hash(y.v, y.w, 0, bits);
+    const uint64_t at = reserve_slot(cur, p, act, lane);
+    if (!act) continue;
+    if constexpr (FULL) {
+      Contrib c;
+      c.v = y.v;
+      c.w = y.w;
+      c.code = code;
+      c.pad = 0;
+      if (code == kCodePre) {
+        c.val = es.pre_u ? y.im : y.re;
+      } else {
+        const uint32_t si = code - kCodeSrc;
+        const double sy = es.src_uy[si] ? y.im : y.re;
+        c.val = neg_if(scaled(es.src_s[si], es.src_e[si], sy, 0), (es.src_q[si] & 2) != 0);
+      }
+      out[at] = c;
+    } else {
+      entries[at] = ((uint64_t)i << 16) | code;
+    }
+  }
+}
+
+// Slots used per bin: cnt[p] = cur[p] - base[p].
+__global__ void k_bin_counts(const unsigned long long* __restrict__ cur, const uint64_t* __restrict__ base,
+                             uint32_t nbins, uint32_t* __restrict__ cnt) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nbins; p += gridDim.x * blockDim.x)
+    cnt[p] = (uint32_t)(cur[p] - base[p]);
 }
 
 // --------------------------------------------------------------------------- grouping
@@ -346,7 +537,6 @@ struct MergeArgs {
   int bits;
   uint32_t nbins;
   const uint64_t* base;   // bin region starts
-  const uint32_t* cnt;    // bin fill counts
   const uint64_t* cpre;   // exclusive prefix of cnt
   const uint64_t* entries;
   const Contrib* fent;    // full-record entries (single-component mode), or null
@@ -360,7 +550,7 @@ struct MergeArgs {
   unsigned* split_groups;
   ulonglong2 sent_lo, sent_hi;  // empty-slot keys for groups in the lower / upper half
   // structured (single-component) mode: every coefficient is s * i^u with s real
-  const double2* hscal;   // per H term: (s, pow2 exponent of |s| or kNoPow2)
+  const HScal* hscal;     // per H term: real factor and its pow2 exponent
   int uH, uX;             // u of the H and X coefficients (0 real, 1 imaginary)
   double src_s[4];        // alpha_s = src_s * i^(src_u)
   int src_e[4];           // pow2 exponent of |src_s| or kNoPow2
@@ -449,11 +639,11 @@ __device__ __forceinline__ void build_scalar(const MergeArgs& a, uint32_t code, 
                                              double& t) {
   if (code < kCodeSrc) {
     const Rec h = a.H[code];
-    const double2 hs = a.hscal[code];
+    const HScal hs = a.hscal[code];
     key = make_ulonglong2(h.v ^ y.v, h.w ^ y.w);
     int q = (product_phase(h.v, h.w, y.v, y.w) + a.rot + a.uH + a.uX) & 3;
     double sy = a.uX ? y.im : y.re;
-    t = neg_if(scaled(hs.x, (int)hs.y, sy, 1), (q & 2) != 0);
+    t = neg_if(scaled(hs.s, hs.e, sy, 1), (q & 2) != 0);
   } else if (code == kCodePre) {
     key = make_ulonglong2(y.v, y.w);
     t = a.pre_u ? y.im : y.re;
@@ -1306,18 +1496,18 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   };
   MergeArgs a{};
   EmitScalars es{};
-  Buf<double2> hscal;
+  Buf<HScal> hscal;
   if (structured) {
     a.uH = sp.clsH == kClsImag;
     a.uX = sp.clsX == kClsImag;
     if (nX > 0) {
-      std::vector<double2> hs(sp.nH);
+      std::vector<HScal> hs(sp.nH);
       for (int i = 0; i < sp.nH; ++i) {
         double v = a.uH ? hh_host[i].im : hh_host[i].re;
-        hs[i] = make_double2(v, (double)pow2_exp(v));
+        hs[i] = HScal{v, pow2_exp(v), 0};
       }
       PS_TRY(hscal.alloc(sp.nH, s));
-      PS_CUDA(cudaMemcpyAsync(hscal.p, hs.data(), sp.nH * sizeof(double2), cudaMemcpyHostToDevice, s));
+      PS_CUDA(cudaMemcpyAsync(hscal.p, hs.data(), sp.nH * sizeof(HScal), cudaMemcpyHostToDevice, s));
       a.hscal = hscal.p;
     }
     for (int i = 0; i < sp.nsrc; ++i) {
@@ -1359,7 +1549,6 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   PS_TRY(misc.alloc(3, s));
   PS_TRY(err.alloc(1, s));
   PS_CUDA(cudaMemsetAsync(histY.p, 0, nbins * sizeof(uint32_t), s));
-  PS_CUDA(cudaMemsetAsync(cnt.p, 0, nbins * sizeof(uint32_t), s));
   PS_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned long long), s));
   PS_CUDA(cudaMemsetAsync(misc.p, 0, 3 * sizeof(unsigned), s));
   PS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
@@ -1395,35 +1584,42 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   if (full) PS_TRY(fent.alloc((size_t)bound_total, s));
   else PS_TRY(entries.alloc((size_t)bound_total, s));
 
-  // ---- 2. emission
-  if (nX > 0) {
-    if (full) {
-      size_t sm = (size_t)sp.nH * (sizeof(ulonglong2) + sizeof(double2) + sizeof(uint32_t));
-      PS_LAUNCH("k_emit_products", s, k_emit_products<true><<<grid_for(nX), kEmitThreads, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, hscal.p, 0, sp.nH, es, base.p, cnt.p, nullptr, fent.p, counters.p));
+  // ---- 2. emission (bin cursors start at the bins' first slots)
+  Buf<unsigned long long> cur;
+  PS_TRY(cur.alloc(nbins, s));
+  PS_CUDA(cudaMemcpyAsync(cur.p, base.p, nbins * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  Buf<uint32_t> tab;
+  if (nX > 0 && sp.nH <= kMaskBits) {
+    // |H| <= 256: anticommutation bitmaps from the nibble table
+    const int stride = tab_stride((sp.nH + 31) / 32);
+    PS_TRY(tab.alloc((size_t)kTabPos * kTabVals * stride, s));
+    PS_LAUNCH("k_anti_table", s, k_anti_table<<<(kTabPos * kTabVals + 255) / 256, 256, 0, s>>>(sp.H, sp.nH, stride, tab.p));
+    PS_CUDA(cudaGetLastError());
+    if (full) PS_TRY(emit_tab<true>(sp.X, fX.p, nX, sp.H, fH.p, hscal.p, sp.nH, tab.p, es, cur.p, nullptr, fent.p, counters.p, nsm, s));
+    else PS_TRY(emit_tab<false>(sp.X, fX.p, nX, sp.H, fH.p, nullptr, sp.nH, tab.p, es, cur.p, entries.p, nullptr, counters.p, nsm, s));
+  } else if (nX > 0) {
+    for (int h0 = 0; h0 < sp.nH; h0 += kHChunk) {
+      int nh = std::min(kHChunk, sp.nH - h0);
+      size_t sm = (size_t)nh * (sizeof(ulonglong2) + sizeof(uint32_t));
+      if (sm > 48 * 1024) PS_CUDA(cudaFuncSetAttribute(k_emit_products, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      PS_LAUNCH("k_emit_products", s, k_emit_products<<<grid_for(nX), kEmitThreads, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, h0, nh, cur.p, entries.p, counters.p));
       PS_CUDA(cudaGetLastError());
-    } else {
-      for (int h0 = 0; h0 < sp.nH; h0 += kHChunk) {
-        int nh = std::min(kHChunk, sp.nH - h0);
-        size_t sm = (size_t)nh * (sizeof(ulonglong2) + sizeof(uint32_t));
-        if (sm > 48 * 1024) PS_CUDA(cudaFuncSetAttribute(k_emit_products<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        PS_LAUNCH("k_emit_products", s, k_emit_products<false><<<grid_for(nX), kEmitThreads, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, nullptr, h0, nh, es, base.p, cnt.p, entries.p, nullptr, counters.p));
-        PS_CUDA(cudaGetLastError());
-      }
     }
   }
-  for (int i = 0; i < sp.nsrc; ++i)
-    if (sp.src[i].n > 0) {
-      if (full)
-        PS_LAUNCH("k_emit_source", s, k_emit_source_full<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, kCodeSrc + i, es, base.p, cnt.p, fent.p));
-      else
-        PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, kCodeSrc + i, base.p, cnt.p, entries.p));
-      PS_CUDA(cudaGetLastError());
-    }
-  if (sp.npre > 0) {
+  auto emit_source = [&](const Rec* y, int64_t n, uint32_t code) -> int {
     if (full)
-      PS_LAUNCH("k_emit_source", s, k_emit_source_full<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, kCodePre, es, base.p, cnt.p, fent.p));
+      PS_LAUNCH("k_emit_source", s, k_emit_source<true><<<grid_for(n), 256, 0, s>>>(y, n, bits, code, es, cur.p, nullptr, fent.p));
     else
-      PS_LAUNCH("k_emit_source", s, k_emit_source<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, kCodePre, base.p, cnt.p, entries.p));
+      PS_LAUNCH("k_emit_source", s, k_emit_source<false><<<grid_for(n), 256, 0, s>>>(y, n, bits, code, es, cur.p, entries.p, nullptr));
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+  };
+  for (int i = 0; i < sp.nsrc; ++i)
+    if (sp.src[i].n > 0) PS_TRY(emit_source(sp.src[i].rec, sp.src[i].n, kCodeSrc + i));
+  if (sp.npre > 0) PS_TRY(emit_source(sp.pre, sp.npre, kCodePre));
+  {
+    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
+    PS_LAUNCH("k_bin_counts", s, k_bin_counts<<<blocks, 256, 0, s>>>(cur.p, base.p, nbins, cnt.p));
     PS_CUDA(cudaGetLastError());
   }
   unsigned long long n_prod = 0;
@@ -1465,7 +1661,6 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   a.bits = bits;
   a.nbins = nbins;
   a.base = base.p;
-  a.cnt = cnt.p;
   a.cpre = cpre.p;
   a.entries = entries.p;
   a.fent = fent.p;

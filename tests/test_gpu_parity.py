@@ -39,7 +39,11 @@ def ref(n, arrays):
 # ----------------------------------------------------------------------------- commutator
 @pytest.mark.parametrize("kind", ["real", "imag", "complex"])
 @pytest.mark.parametrize("n,mh,mo,sup", [(3, 9, 17, None), (10, 29, 500, 5), (32, 60, 3000, 8), (64, 120, 5000, 10),
-                                         (64, 40, 20000, None)])
+                                         (64, 40, 20000, None),
+                                         # |H| at the bitmap-width and order-mask boundaries:
+                                         # 250 (8-word bitmaps), 256 (largest ranked merge),
+                                         # 257 (per-term ballot emission, chained merge)
+                                         (20, 250, 4000, 6), (16, 256, 3000, 6), (16, 257, 3000, 6)])
 def test_commutator_random(kind, n, mh, mo, sup):
     Ha = I.random_sum(1000 + n, n, mh, "real" if kind != "complex" else "complex", max_support=min(3, n))
     Oa = I.random_sum(2000 + n + mo, n, mo, kind, max_support=sup)
