@@ -1338,29 +1338,75 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         if constexpr (!S) s.segim[pos] = s.eim[e];
       }
       __syncthreads();
-      // ---- phase 4: per string, add its run in order, apply the combination, stage
+      // ---- phase 3b: strings ordered by run length, longest first, so that the lanes of a
+      // warp add runs of nearly equal length in phase 4 (the adds of a warp cost as much as
+      // its longest run).  A counting sort; ebit/eslot are free once phase 3 is done.
+      uint32_t* s_hist = reinterpret_cast<uint32_t*>(s.ebit);  // kMaskBits + 1 counters
+      uint16_t* s_order = s.eslot;
+      for (uint32_t i = tid; i <= (uint32_t)kMaskBits; i += kMergeThreads) s_hist[i] = 0;
+      __syncthreads();
+      for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
+        const uint32_t slot = s.ulist[u];
+        uint32_t n = 0;
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w) n += __popcll(s.mask[slot][w]);
+        atomicAdd(&s_hist[kMaskBits - n], 1u);
+      }
+      __syncthreads();
+      if (tid < 32) {  // exclusive scan of the kMaskBits + 1 counters, 9 per lane
+        constexpr int kPer = (kMaskBits + 1 + 31) / 32;
+        uint32_t v[kPer], t = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const int i = tid * kPer + k;
+          v[k] = i <= kMaskBits ? s_hist[i] : 0u;
+          t += v[k];
+        }
+        uint32_t incl = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (tid >= d) incl += y;
+        }
+        uint32_t run = incl - t;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const int i = tid * kPer + k;
+          if (i <= kMaskBits) s_hist[i] = run;
+          run += v[k];
+        }
+      }
+      __syncthreads();
+      for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
+        const uint32_t slot = s.ulist[u];
+        uint32_t n = 0;
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w) n += __popcll(s.mask[slot][w]);
+        s_order[atomicAdd(&s_hist[kMaskBits - n], 1u)] = (uint16_t)slot;
+      }
+      __syncthreads();
+      // ---- phase 4: per string, add its run in order, apply the combination, stage.  The
+      // fold uses plain IEEE adds: they differ from skipping zero terms only in the sign of
+      // a zero sum, and strings whose value is zero are dropped.
       for (uint32_t u0 = 0; u0 < n_u; u0 += kMergeThreads) {
         const uint32_t u = u0 + tid;
         Cx r{0.0, 0.0};
         bool flag = false;
         uint32_t slot = 0;
         if (u < n_u) {
-          slot = s.ulist[u];
+          slot = s_order[u];
           uint32_t n = 0;
 #pragma unroll
           for (int w = 0; w < kMaskWords; ++w) n += __popcll(s.mask[slot][w]);
           const uint32_t b0 = s.run[slot];
           Cx acc{0.0, 0.0};
-          for (uint32_t i = 0; i < n; ++i) {
-            if constexpr (S) {
-              acc.re = (i == 0) ? s.seg[b0] : add_rn(acc.re, s.seg[b0 + i]);
-            } else {
-              if (i == 0) acc = Cx{s.seg[b0], s.segim[b0]};
-              else {
-                acc.re = add_rn(acc.re, s.seg[b0 + i]);
-                acc.im = add_rn(acc.im, s.segim[b0 + i]);
-              }
-            }
+          if (n > 0) {
+            acc.re = s.seg[b0];
+            if constexpr (!S) acc.im = s.segim[b0];
+          }
+          for (uint32_t i = 1; i < n; ++i) {
+            acc.re = __dadd_rn(acc.re, s.seg[b0 + i]);
+            if constexpr (!S) acc.im = __dadd_rn(acc.im, s.segim[b0 + i]);
           }
           const uint32_t pe = s.pre[slot];
           if constexpr (S) {
