@@ -261,8 +261,10 @@ def main():
     evp0 = torch.cuda.Event(enable_timing=True)
     evp1 = torch.cuda.Event(enable_timing=True)
     evp0.record(stream)
+    prof_src = 0
     for _ in range(args.steps):
         prof_products += nH * len(cur)
+        prof_src += len(prev)  # O_{n-1} enters the merge as a source term
         b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
         st = ps.pauli_last_merge_stats()
         prof_contrib += st["contributions"]
@@ -282,22 +284,34 @@ def main():
     avg_s = kms / 1e3 / max(klaunch, 1)
     roof = {"kernel": kname, "share": kms / max(sum(v[1] for v in prof.values()), 1e-9)}
     per_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in prof.items()}
+    entries = (prof_contrib + prof_src) / args.steps  # merge entries per launch
     if kname.startswith("k_merge"):
-        # algorithmic bytes per launch: each entry (8 B) read once, its product operand (32 B)
-        # gathered once, each merged output string (32 B) written once
-        alg = (prof_contrib / args.steps) * (8 + 32) + (prof_merged / args.steps) * 32
+        if kname.endswith("_f"):
+            # full contribution records: each entry (32 B) read once, each merged string written once
+            alg = entries * 32 + (prof_merged / args.steps) * 32
+        else:
+            # 8-byte references read once, each referenced operand record (32 B) gathered once
+            alg = entries * (8 + 32) + (prof_merged / args.steps) * 32
         roof.update({"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                     "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"})
+                     "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), kernel timed inside the step",
+                     "algorithmic_bytes_per_launch": alg, "entries_per_launch": entries})
+        tr = dram_traffic(kname)
+        if tr is not None:
+            roof["traffic"] = tr["bytes_per_entry"] * entries
+            roof["traffic_source"] = tr["source"]
     elif kname == "k_emit_products":
-        alg = (prof_products / args.steps) / max(klaunch / args.steps, 1)
-        pair_peak = POPC_PEAK_PAIRS_PER_S
-        roof.update({"bound": "alu", "achieved": alg / avg_s / 1e9, "peak": pair_peak / 1e9, "unit": "Gpairtests/s",
-                     "peak_kind": "integer popcount issue rate (see DESIGN.md)"})
+        # each operand string (32 B record + 4 B hash) read once, each contribution record
+        # (32 B) written once; the pair tests are table lookups, not the bound
+        alg = (prof_products / args.steps / nH) * 36 + (prof_contrib / args.steps) * 32
+        alg /= max(klaunch / args.steps, 1)
+        roof.update({"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), kernel timed inside the step",
+                     "algorithmic_bytes_per_launch": alg})
     else:
         roof.update({"bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s"})
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof.setdefault("traffic", None)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -379,9 +393,25 @@ def main():
         dist.destroy_process_group()
 
 
-# Pair-test peak used for an ALU-bound emission kernel: one 64-bit popcount (two 32-bit
-# POPC) per pair; 152 SMs x 16 POPC/clk/SM x 2.07 GHz / 2.
-POPC_PEAK_PAIRS_PER_S = 152 * 16 * 2.07e9 / 2
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2410_09654_gb300", "csrc", "merge.cu")
+
+
+def dram_traffic(kname: str):
+    """DRAM bytes per merge entry measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
+    over entries of the captured launch), from the committed capture summary; None when the
+    kernel source has changed since the capture (sha1 of merge.cu recorded beside it)."""
+    import hashlib
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    sha = hashlib.sha1(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    for line in open(TRAFFIC_FILE):
+        if line.startswith("#"):
+            continue
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kname and f.get("merge_cu_sha1") == sha:
+            return {"bytes_per_entry": float(f["dram_bytes_per_entry"]), "source": f.get("capture", "")}
+    return None
 
 if __name__ == "__main__":
     main()
