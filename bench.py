@@ -184,19 +184,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2410_09654_gb300 import replicas as R
+
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return R.reduce_scalar(x, "max")
 
     def sum_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return R.reduce_scalar(x, "sum")
 
     Ha, O0a = workload_arrays()
     H = ps.PauliSum.from_arrays(N_SITES, *Ha)
@@ -247,9 +241,7 @@ def main():
     launches = ps.pauli_launch_count() - launches0
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    ms_max = max_over_ranks(ms)
-    products_all = sum_over_ranks(products)
-    value = products_all / (ms_max / 1e3)
+    value, ms_max, products_all = R.job_rate(products, ms)
     merged_rate = sum_over_ranks(merged) / (ms_max / 1e3)
 
     # per-kernel durations over a second timed region (same K steps, events on)

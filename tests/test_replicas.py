@@ -1,0 +1,66 @@
+"""Replica runs on more than one GPU: the path does not shard, so N ranks run independent
+instances and only the benchmark's bookkeeping crosses ranks (max time, summed work).
+Checked here with two gloo ranks on CPU, and the reference arm's rank handling under a
+two-rank environment."""
+from __future__ import annotations
+
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2410_09654_gb300 import replicas as R
+        # rank r did (r + 1) * 1000 units in (r + 1) * 10 ms
+        value, ms_max, units = R.job_rate((rank + 1) * 1000.0, (rank + 1) * 10.0, device="cpu")
+        out[rank] = (value, ms_max, units, R.reduce_scalar(rank + 0.5, "max", device="cpu"))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_job_rate_two_gloo_ranks():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    for rank in range(world):
+        value, ms_max, units, mx = res[rank]
+        assert ms_max == 20.0                 # the slowest rank's time
+        assert units == 3000.0                # work of both ranks
+        assert value == pytest.approx(3000.0 / 0.020)
+        assert mx == 1.5
+
+
+def test_job_rate_single_process_is_identity():
+    from paper_2410_09654_gb300 import replicas as R
+    assert R.job_rate(500.0, 4.0, device="cpu") == (500.0 / 0.004, 4.0, 500.0)
+
+
+def test_reference_arm_runs_on_rank0_only():
+    # under a two-rank launch the non-zero rank exits at once without output
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
