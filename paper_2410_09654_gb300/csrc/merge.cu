@@ -71,6 +71,7 @@ constexpr uint64_t kFullBudget = (uint64_t)48 << 30;  // bytes of full contribut
 constexpr int kMaxGroupBins = 512;  // bins per group (a group also starts every kMaxGroupBins bins)
 constexpr int kGroupQuota = 1536;   // a new group starts when the running entry count crosses a multiple
 constexpr int kBatch = 2;           // entries per thread with loads in flight together
+constexpr int kBatchFull = 4;       // the same for full records (one load round per pass of 2048)
 static_assert(kCap <= 2048, "order key packs the entry index in 11 bits");
 
 __device__ __forceinline__ uint32_t table_hash(uint64_t v, uint64_t w) {
@@ -1079,13 +1080,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(MergeArgs a) {
 // it is written straight to its ordered position in a per-string run, and each string is
 // summed over its contiguous run in increasing order code.  Valid inputs (distinct strings in
 // every operand) give distinct order codes per string.
-constexpr int kMaskWords = 4;
-constexpr int kMaskBits = 64 * kMaskWords;
+constexpr int kMaskWords = 8;  // 32-bit words: shared-memory OR on 32 bits is one native atomic
+constexpr int kMaskBits = 32 * kMaskWords;
 
 template <bool S>
 struct RankSmem {
   ulonglong2 key[kTable];
-  unsigned long long mask[kTable][kMaskWords];  // order codes present per slot
+  uint32_t mask[kTable][kMaskWords];  // order codes present per slot
   uint16_t pre[kTable];
   uint16_t ulist[kTable];
   uint16_t run[kTable];        // start of the slot's run in seg[]
@@ -1114,7 +1115,7 @@ __device__ __forceinline__ void rank_release(RankSmem<S>& s, ulonglong2 sent) {
     const uint32_t slot = s.ulist[u];
     s.key[slot] = sent;
 #pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) s.mask[slot][w] = 0ull;
+    for (int w = 0; w < kMaskWords; ++w) s.mask[slot][w] = 0u;
     s.pre[slot] = kNone16;
   }
   __syncthreads();
@@ -1134,6 +1135,7 @@ __device__ __forceinline__ uint32_t code_bit(uint32_t code, int nH) {
 
 template <bool S, bool FULL>
 __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
+  constexpr int B = FULL ? kBatchFull : kBatch;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RankSmem<S>& s = *reinterpret_cast<RankSmem<S>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -1142,7 +1144,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
   for (int i = tid; i < kTable; i += kMergeThreads) {
     s.key[i] = a.sent_lo;
 #pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) s.mask[i][w] = 0ull;
+    for (int w = 0; w < kMaskWords; ++w) s.mask[i][w] = 0u;
     s.pre[i] = kNone16;
   }
   if (tid == 0) {
@@ -1197,13 +1199,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       const int level = stk_level[sp];
       const uint32_t sub = stk_sub[sp];
       // ---- phase 1: rebuild entries, insert keys, mark order codes per key
-      for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)kBatch * kMergeThreads) {
-        uint64_t ent[kBatch];
-        Rec rec[kBatch];
-        Contrib cf[kBatch];
-        bool has[kBatch];
+      for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)B * kMergeThreads) {
+        uint64_t ent[B];
+        Rec rec[B];
+        Contrib cf[B];
+        bool has[B];
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
+        for (int k = 0; k < B; ++k) {
           uint64_t j = j0 + (uint64_t)k * kMergeThreads + tid;
           has[k] = j < E;
           ent[k] = 0;
@@ -1219,7 +1221,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         }
         if constexpr (!FULL) {
 #pragma unroll
-          for (int k = 0; k < kBatch; ++k) {
+          for (int k = 0; k < B; ++k) {
             if (!has[k]) continue;
             uint32_t code = (uint32_t)(ent[k] & 0xFFFFu);
             uint64_t idx = ent[k] >> 16;
@@ -1228,7 +1230,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           }
         }
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
+        for (int k = 0; k < B; ++k) {
           bool keep = has[k];
           ulonglong2 key = make_ulonglong2(0, 0);
           Cx t{0.0, 0.0};
@@ -1247,11 +1249,16 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           }
           const unsigned m = __ballot_sync(0xffffffffu, keep);
           if (!m) continue;
-          const int leader = __ffs(m) - 1;
-          uint32_t eb = 0;
-          if (lane == leader) eb = atomicAdd(&s.n_e, (uint32_t)__popc(m));
-          eb = __shfl_sync(0xffffffffu, eb, leader);
-          const uint32_t e = eb + __popc(m & ((1u << lane) - 1));
+          uint32_t e;
+          if (level == 0) {
+            e = (uint32_t)(j0 + (uint64_t)k * kMergeThreads + tid);  // every entry kept, E <= kCap
+          } else {
+            const int leader = __ffs(m) - 1;
+            uint32_t eb = 0;
+            if (lane == leader) eb = atomicAdd(&s.n_e, (uint32_t)__popc(m));
+            eb = __shfl_sync(0xffffffffu, eb, leader);
+            e = eb + __popc(m & ((1u << lane) - 1));
+          }
           bool fresh = false;
           int slot = -1;
           if (keep) {
@@ -1280,7 +1287,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
             } else {
               const uint32_t bit = code_bit(code, a.nH);
               s.ebit[e] = (uint16_t)bit;
-              atomicOr(&s.mask[slot][bit >> 6], 1ull << (bit & 63));
+              atomicOr(&s.mask[slot][bit >> 5], 1u << (bit & 31));
             }
           }
         }
@@ -1300,7 +1307,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         sp += 2;
         continue;
       }
-      const uint32_t n_u = s.n_u, n_e = s.n_e;
+      const uint32_t n_u = s.n_u, n_e = level == 0 ? (uint32_t)E : s.n_e;
       // ---- phase 2: a run per string (its length is the popcount of its mask)
       for (uint32_t u0 = 0; u0 < n_u; u0 += kMergeThreads) {
         const uint32_t u = u0 + tid;
@@ -1308,7 +1315,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         if (u < n_u) {
           slot = s.ulist[u];
 #pragma unroll
-          for (int w = 0; w < kMaskWords; ++w) c += __popcll(s.mask[slot][w]);
+          for (int w = 0; w < kMaskWords; ++w) c += __popc(s.mask[slot][w]);
         }
         // warp-inclusive scan of c, one shared-memory reservation per warp
         uint32_t incl = c;
@@ -1328,11 +1335,11 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         const uint32_t bit = s.ebit[e];
         if (bit == kNone16) continue;
         const uint32_t slot = s.eslot[e];
-        const uint32_t wi = bit >> 6;
-        uint32_t rank = __popcll(s.mask[slot][wi] & ((1ull << (bit & 63)) - 1ull));
+        const uint32_t wi = bit >> 5;
+        uint32_t rank = __popc(s.mask[slot][wi] & ((1u << (bit & 31)) - 1u));
 #pragma unroll
         for (int w = 0; w < kMaskWords; ++w)
-          if ((uint32_t)w < wi) rank += __popcll(s.mask[slot][w]);
+          if ((uint32_t)w < wi) rank += __popc(s.mask[slot][w]);
         const uint32_t pos = s.run[slot] + rank;
         s.seg[pos] = s.ere[e];
         if constexpr (!S) s.segim[pos] = s.eim[e];
@@ -1349,7 +1356,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         const uint32_t slot = s.ulist[u];
         uint32_t n = 0;
 #pragma unroll
-        for (int w = 0; w < kMaskWords; ++w) n += __popcll(s.mask[slot][w]);
+        for (int w = 0; w < kMaskWords; ++w) n += __popc(s.mask[slot][w]);
         atomicAdd(&s_hist[kMaskBits - n], 1u);
       }
       __syncthreads();
@@ -1381,7 +1388,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         const uint32_t slot = s.ulist[u];
         uint32_t n = 0;
 #pragma unroll
-        for (int w = 0; w < kMaskWords; ++w) n += __popcll(s.mask[slot][w]);
+        for (int w = 0; w < kMaskWords; ++w) n += __popc(s.mask[slot][w]);
         s_order[atomicAdd(&s_hist[kMaskBits - n], 1u)] = (uint16_t)slot;
       }
       __syncthreads();
@@ -1397,7 +1404,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           slot = s_order[u];
           uint32_t n = 0;
 #pragma unroll
-          for (int w = 0; w < kMaskWords; ++w) n += __popcll(s.mask[slot][w]);
+          for (int w = 0; w < kMaskWords; ++w) n += __popc(s.mask[slot][w]);
           const uint32_t b0 = s.run[slot];
           Cx acc{0.0, 0.0};
           if (n > 0) {
