@@ -524,6 +524,24 @@ __global__ void k_group_scatter(const uint32_t* __restrict__ flag, const uint64_
   }
 }
 
+// Per group: its bin range and entry range, so that a block reads one record per group.
+struct __align__(16) GroupHead {
+  uint32_t lo, hi;  // bins [lo, hi)
+  uint64_t e0;      // entries before the group (prefix of the bin fill counts)
+  uint64_t E;       // entries in the group
+  uint64_t pad;
+};
+
+__global__ void k_group_heads(const uint32_t* __restrict__ gstart, const uint64_t* __restrict__ cpre,
+                              const uint32_t* __restrict__ ngroups, GroupHead* __restrict__ heads) {
+  const uint32_t n = *ngroups;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    const uint32_t lo = gstart[g], hi = gstart[g + 1];
+    const uint64_t e0 = cpre[lo];
+    heads[g] = GroupHead{lo, hi, e0, cpre[hi] - e0, 0};
+  }
+}
+
 // --------------------------------------------------------------------------- merge
 struct MergeArgs {
   const Rec* H;
@@ -542,6 +560,7 @@ struct MergeArgs {
   const uint64_t* entries;
   const Contrib* fent;    // full-record entries (single-component mode), or null
   const uint32_t* gstart;
+  const GroupHead* heads;
   const uint32_t* ngroups;
   unsigned* next_group;
   Rec* out;
@@ -1106,6 +1125,7 @@ struct RankSmem {
   unsigned group;
   unsigned long long out_base;
   ulonglong2 cur_sent;
+  uint32_t h_g;  // the block's next group, claimed while the current one is set up
 };
 
 template <bool S>
@@ -1152,23 +1172,27 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
     s.flags = 0;
     s.cur_sent = a.sent_lo;
   }
-  __syncthreads();
-
+  // Groups are claimed from a shared counter.  The next group is claimed while the current
+  // one's setup runs, by the last warp's lane 0 (no bin-table work: a group has fewer bins
+  // than the first 480 threads), so the claim's round trip overlaps the header and table
+  // reads of the other threads.
+  constexpr int kClaimTid = kMergeThreads - 32;
+  if (tid == kClaimTid) s.h_g = atomicAdd(a.next_group, 1u);
   for (;;) {
-    if (tid == 0) s.group = atomicAdd(a.next_group, 1u);
     __syncthreads();
-    const uint32_t g = s.group;
-    __syncthreads();
+    const uint32_t g = s.h_g;
+    __syncthreads();  // g read by all before the next claim overwrites it
     if (g >= ngroups) break;
-    const uint32_t lo = a.gstart[g], hi = a.gstart[g + 1];
-    const uint64_t e0 = a.cpre[lo];
-    const uint64_t E = a.cpre[hi] - e0;
-    if (E == 0) continue;
-    const uint32_t nb = hi - lo;
-    if (nb > (uint32_t)kMaxGroupBins) {
-      if (tid == 0) atomicOr(a.err, 2);
+    if (tid == kClaimTid) s.h_g = atomicAdd(a.next_group, 1u);
+    const GroupHead gh = a.heads[g];
+    const uint32_t lo = gh.lo, hi = gh.hi;
+    const uint64_t e0 = gh.e0;
+    const uint64_t E = gh.E;
+    if (E == 0 || hi - lo > (uint32_t)kMaxGroupBins) {
+      if (E != 0 && tid == 0) atomicOr(a.err, 2);
       continue;
     }
+    const uint32_t nb = hi - lo;
     const ulonglong2 sent = (lo >= a.nbins / 2) ? a.sent_hi : a.sent_lo;
     if (sent.x != s.cur_sent.x || sent.y != s.cur_sent.y) {
       __syncthreads();
@@ -1198,6 +1222,9 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       --sp;
       const int level = stk_level[sp];
       const uint32_t sub = stk_sub[sp];
+      // run-length histogram for phase 3b, in oslot (free until phase 4 stages outputs)
+      uint32_t* s_hist = reinterpret_cast<uint32_t*>(s.oslot);  // kMaskBits + 1 counters
+      for (uint32_t i = tid; i <= (uint32_t)kMaskBits; i += kMergeThreads) s_hist[i] = 0;
       // ---- phase 1: rebuild entries, insert keys, mark order codes per key
       for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)B * kMergeThreads) {
         uint64_t ent[B];
@@ -1327,40 +1354,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         uint32_t wb = 0;
         if (lane == 31) wb = atomicAdd(&s.n_seg, incl);
         wb = __shfl_sync(0xffffffffu, wb, 31);
-        if (u < n_u) s.run[slot] = (uint16_t)(wb + incl - c);
+        if (u < n_u) {
+          s.run[slot] = (uint16_t)(wb + incl - c);
+          atomicAdd(&s_hist[kMaskBits - c], 1u);  // longest runs first
+        }
       }
       __syncthreads();
-      // ---- phase 3: every contribution to its ordered position in its string's run
-      for (uint32_t e = tid; e < n_e; e += kMergeThreads) {
-        const uint32_t bit = s.ebit[e];
-        if (bit == kNone16) continue;
-        const uint32_t slot = s.eslot[e];
-        const uint32_t wi = bit >> 5;
-        uint32_t rank = __popc(s.mask[slot][wi] & ((1u << (bit & 31)) - 1u));
-#pragma unroll
-        for (int w = 0; w < kMaskWords; ++w)
-          if ((uint32_t)w < wi) rank += __popc(s.mask[slot][w]);
-        const uint32_t pos = s.run[slot] + rank;
-        s.seg[pos] = s.ere[e];
-        if constexpr (!S) s.segim[pos] = s.eim[e];
-      }
-      __syncthreads();
-      // ---- phase 3b: strings ordered by run length, longest first, so that the lanes of a
-      // warp add runs of nearly equal length in phase 4 (the adds of a warp cost as much as
-      // its longest run).  A counting sort; ebit/eslot are free once phase 3 is done.
-      uint32_t* s_hist = reinterpret_cast<uint32_t*>(s.ebit);  // kMaskBits + 1 counters
-      uint16_t* s_order = s.eslot;
-      for (uint32_t i = tid; i <= (uint32_t)kMaskBits; i += kMergeThreads) s_hist[i] = 0;
-      __syncthreads();
-      for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
-        const uint32_t slot = s.ulist[u];
-        uint32_t n = 0;
-#pragma unroll
-        for (int w = 0; w < kMaskWords; ++w) n += __popc(s.mask[slot][w]);
-        atomicAdd(&s_hist[kMaskBits - n], 1u);
-      }
-      __syncthreads();
-      if (tid < 32) {  // exclusive scan of the kMaskBits + 1 counters, 9 per lane
+      if (tid < 32) {  // exclusive scan of the run-length counters, 9 per lane, before phase 3
         constexpr int kPer = (kMaskBits + 1 + 31) / 32;
         uint32_t v[kPer], t = 0;
 #pragma unroll
@@ -1383,7 +1383,26 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           run += v[k];
         }
       }
+      // ---- phase 3: every contribution to its ordered position in its string's run
+      for (uint32_t e = tid; e < n_e; e += kMergeThreads) {
+        const uint32_t bit = s.ebit[e];
+        if (bit == kNone16) continue;
+        const uint32_t slot = s.eslot[e];
+        const uint32_t wi = bit >> 5;
+        uint32_t rank = __popc(s.mask[slot][wi] & ((1u << (bit & 31)) - 1u));
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w)
+          if ((uint32_t)w < wi) rank += __popc(s.mask[slot][w]);
+        const uint32_t pos = s.run[slot] + rank;
+        s.seg[pos] = s.ere[e];
+        if constexpr (!S) s.segim[pos] = s.eim[e];
+      }
       __syncthreads();
+      // ---- phase 3b: strings ordered by run length, longest first, so that the lanes of a
+      // warp add runs of nearly equal length in phase 4 (the adds of a warp cost as much as
+      // its longest run): the scatter of a counting sort whose counts phase 2 took; eslot
+      // is free once phase 3 is done.
+      uint16_t* s_order = s.eslot;
       for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
         const uint32_t slot = s.ulist[u];
         uint32_t n = 0;
@@ -1589,6 +1608,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   }
 
   Buf<uint32_t> fX, fH, histX, histY, cnt, flag, gstart;
+  Buf<GroupHead> heads;
   Buf<uint64_t> bound, base, cpre, fpre, entries;
   Buf<Contrib> fent;
   Buf<unsigned long long> counters;  // [0] product entries, [1] out_n
@@ -1694,6 +1714,9 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_TRY(scan_u32_to_u64(flag.p, fpre.p, nbins, s));
     PS_LAUNCH("k_group_scatter", s, k_group_scatter<<<blocks, 256, 0, s>>>(flag.p, fpre.p, nbins, gstart.p, misc.p + 1));
     PS_CUDA(cudaGetLastError());
+    PS_TRY(heads.alloc(nbins, s));  // at most one group per bin
+    PS_LAUNCH("k_group_heads", s, k_group_heads<<<blocks, 256, 0, s>>>(gstart.p, cpre.p, misc.p + 1, heads.p));
+    PS_CUDA(cudaGetLastError());
   }
 
   // ---- 4. merge into a fresh output buffer
@@ -1718,6 +1741,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   a.entries = entries.p;
   a.fent = fent.p;
   a.gstart = gstart.p;
+  a.heads = heads.p;
   a.ngroups = misc.p + 1;
   a.next_group = misc.p;
   a.out = outbuf;
