@@ -69,6 +69,8 @@ def _load():
         lib.or_anticommute.restype = ctypes.c_int
         lib.or_commutator.argtypes = _OP + _OP
         lib.or_commutator.restype = vp
+        lib.or_product.argtypes = _OP + _OP
+        lib.or_product.restype = vp
         lib.or_axpy.argtypes = _OP + [ctypes.c_double, ctypes.c_double] + _OP
         lib.or_axpy.restype = vp
         lib.or_scale.argtypes = _OP + [ctypes.c_double]
@@ -168,6 +170,12 @@ def commutator(H: Op, O: Op) -> Op:
     """[H, O] by Alg. 1 adapted with eq. eps_com (H outer loop in the given order)."""
     lib = _load()
     return _take(lib, lib.or_commutator(*H._args(), *O._args()), O.n_sites)[0]
+
+
+def product(A: Op, B: Op) -> Op:
+    """A B by Alg. 1 proper: every pair, P_a P_b = i^k P_{a^b} (A outer loop in the given order)."""
+    lib = _load()
+    return _take(lib, lib.or_product(*A._args(), *B._args()), A.n_sites)[0]
 
 
 def axpy(A: Op, alpha: complex, B: Op) -> Op:

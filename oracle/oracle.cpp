@@ -107,6 +107,29 @@ std::vector<Term> from_arrays(const uint64_t* v, const uint64_t* w, const double
   return t;
 }
 
+// Alg. 1 proper, the operator product: C = A B = sum_{a in A} sum_{b in B} A_a B_b P_a P_b
+// with P_a P_b = i^k P_{a^b} (eqs. v12, w12, eps12 in the Hermitian basis).  Same visiting
+// order as the commutator below: A outer, B inner, contributions added in that order.
+std::vector<Term> product(const std::vector<Term>& A, const std::vector<Term>& B) {
+  Dict C;
+  C.reserve(A.size() * B.size() + 16);
+  for (const Term& a : A) {
+    for (const Term& b : B) {
+      int k = product_phase(a.k.v, a.k.w, b.k.v, b.k.w);
+      Cx t = rot(cmul(a.c, b.c), k);
+      Key c{a.k.v ^ b.k.v, a.k.w ^ b.k.w};
+      auto it = C.find(c);
+      if (it == C.end()) {
+        C.emplace(c, t);
+      } else {
+        it->second.re += t.re;
+        it->second.im += t.im;
+      }
+    }
+  }
+  return canonical(C);
+}
+
 // Alg. 1 adapted with eq. eps_com: C = [A, B] = sum_{a in A} sum_{b in B} A_a B_b [P_a, P_b].
 // A's terms are visited in the order given (outer loop), B's in the order given (inner
 // loop); every contribution is added to the dictionary entry in that visiting order.
@@ -409,6 +432,14 @@ or_result* or_commutator(const uint64_t* av, const uint64_t* aw, const double* a
                          int64_t na, const uint64_t* bv, const uint64_t* bw, const double* bre,
                          const double* bim, int64_t nb) {
   return new or_result{commutator(from_arrays(av, aw, are, aim, na), from_arrays(bv, bw, bre, bim, nb)), {}};
+}
+
+// A B by Alg. 1 (A outer in the given order).  Parity: pinned by dense matrix products,
+// the single-site Pauli table, AB - BA = [A, B] and exact associativity on dyadic sums.
+or_result* or_product(const uint64_t* av, const uint64_t* aw, const double* are, const double* aim,
+                      int64_t na, const uint64_t* bv, const uint64_t* bw, const double* bre,
+                      const double* bim, int64_t nb) {
+  return new or_result{product(from_arrays(av, aw, are, aim, na), from_arrays(bv, bw, bre, bim, nb)), {}};
 }
 
 // A + alpha B.  Parity: pinned by dense matrices and by brute force on small inputs.

@@ -74,12 +74,17 @@ constexpr int kBatch = 2;           // entries per thread with loads in flight t
 constexpr int kBatchFull = 4;       // the same for full records (one load round per pass of 2048)
 static_assert(kCap <= 2048, "order key packs the entry index in 11 bits");
 
+// Shared-table slot hash of a string: the four 32-bit words folded with odd multipliers,
+// then a multiply-xorshift finaliser (32-bit multiplies only).
 __device__ __forceinline__ uint32_t table_hash(uint64_t v, uint64_t w) {
-  uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w * 0xC2B2AE3D27D4EB4Full + 0x165667B19E3779F9ull);
-  h ^= h >> 29;
-  h *= 0xBF58476D1CE4E5B9ull;
-  h ^= h >> 32;
-  return (uint32_t)h;
+  uint32_t h = (uint32_t)v * 0x9E3779B1u ^ (uint32_t)(v >> 32) * 0x85EBCA77u ^ (uint32_t)w * 0xC2B2AE3Du ^
+               (uint32_t)(w >> 32) * 0x27D4EB2Fu;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return h;
 }
 
 __device__ __forceinline__ ulonglong2 cas128_shared(ulonglong2* p, ulonglong2 expect, ulonglong2 desired) {

@@ -108,6 +108,65 @@ def test_commutator_dyadic_exact_vs_dense():
         assert got[k] == want[k]
 
 
+# ----------------------------------------------------------------------------- operator product
+def test_product_vs_dense_all_pairs_n2():
+    # single strings: A B equals the dense matrix product, for every pair of two-site strings
+    n = 2
+    for va, wa, vb, wb in itertools.product(range(4), repeat=4):
+        A = orc.Op(n, [va], [wa], [1.0], [0.0])
+        B = orc.Op(n, [vb], [wb], [1.0], [0.0])
+        got = as_dict(orc.product(A, B))
+        want = dense.decompose(dense.op_matrix(A, n) @ dense.op_matrix(B, n), n)
+        close_dicts(got, want, 0.0)
+
+
+@pytest.mark.parametrize("pair", sorted(PAULI_TABLE))
+def test_product_single_site_table(pair):
+    a, b = pair
+    A = orc.Op(1, [LET[a][0]], [LET[a][1]], [1.0], [0.0])
+    B = orc.Op(1, [LET[b][0]], [LET[b][1]], [1.0], [0.0])
+    got = as_dict(orc.product(A, B))
+    letter, phase = PAULI_TABLE[pair]
+    assert got == {LET[letter]: complex(phase)}
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_product_random_sums_vs_dense(n):
+    A = op(n, I.random_sum(31 + n, n, 11, "complex"))
+    B = op(n, I.random_sum(37 + n, n, 19, "complex"))
+    got = as_dict(orc.product(A, B))
+    want = dense.decompose(dense.op_matrix(A, n) @ dense.op_matrix(B, n), n)
+    close_dicts(got, want, 1e-13)
+
+
+def test_product_minus_reverse_is_commutator_dyadic():
+    # AB - BA = [A, B]; with dyadic coefficients every sum is exact, so bit for bit
+    n = 5
+    A = op(n, I.random_sum(41, n, 14, "real", dyadic=True))
+    B = op(n, I.random_sum(42, n, 23, "imag", dyadic=True))
+    ab_ba = orc.axpy(orc.product(A, B), -1.0, orc.product(B, A))
+    assert as_dict(ab_ba) == as_dict(orc.commutator(A, B))
+
+
+def test_product_associative_dyadic():
+    n = 4
+    A = op(n, I.random_sum(51, n, 6, "real", dyadic=True))
+    B = op(n, I.random_sum(52, n, 7, "real", dyadic=True))
+    C = op(n, I.random_sum(53, n, 5, "imag", dyadic=True))
+    assert as_dict(orc.product(orc.product(A, B), C)) == as_dict(orc.product(A, orc.product(B, C)))
+
+
+def test_product_identity_coefficient_is_trace_product_dyadic():
+    # the identity coefficient of A B is Tr(AB)/2^N
+    n = 6
+    A = op(n, I.random_sum(61, n, 40, "complex", dyadic=True))
+    B = op(n, I.random_sum(62, n, 30, "complex", dyadic=True, max_support=3))
+    B = orc.axpy(B, 1.0, orc.Op(n, A.v[:10], A.w[:10], A.re[:10], A.im[:10]))  # shared strings
+    got = as_dict(orc.product(A, B)).get((0, 0), 0j)
+    assert got == orc.trace_product(A, B)
+    assert got != 0
+
+
 def test_axpy_vs_dense():
     n = 3
     A = op(n, I.random_sum(1, n, 20, "complex"))
