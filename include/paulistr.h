@@ -108,6 +108,16 @@ int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst);
  * exact zeros dropped.  out must be distinct from H and O. */
 int pauli_commutator(const pauli_sum* H, const pauli_sum* O, pauli_sum* out);
 
+/* out = A B, the operator product (Alg. 1 proper): every pair of strings a in A,
+ * b in B contributes i^k a b to the string with masks (va ^ vb, wa ^ wb), k the
+ * popcount phase of eq. eps12 in the Hermitian basis; duplicates are merged with the
+ * contributions to each output string added in A's order, exact zeros dropped.
+ * A is the outer operand and may hold at most 61439 strings (PS_ERR_INVALID beyond);
+ * B any number.  The identity coefficient of A B is Tr(AB)/2^N (pauli_trace_product
+ * gives it exactly rounded without forming the product).  out must be distinct from A
+ * and B; all three must have the same number of sites. */
+int pauli_multiply(const pauli_sum* A, const pauli_sum* B, pauli_sum* out);
+
 /* out = A + alpha * B over the union of supports (absent strings are zero),
  * exact zeros dropped.  out must be distinct from A and B. */
 int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_sum* B, pauli_sum* out);
@@ -151,6 +161,16 @@ int pauli_trace_product(const pauli_sum* A, const pauli_sum* B, double* re, doub
 /* ||O|| = sqrt(sum |c|^2) = sqrt(Tr(O^dag O) / 2^N) (the norm of the Krylov section,
  * read with the square root), from the exactly rounded sum of squares. */
 int pauli_norm(const pauli_sum* O, double* out);
+
+/* Coefficients of given strings in O, for two-point correlators such as
+ * Tr(O(t) Z_j)/2^N over all sites j (section "Heisenberg time evolution"; the
+ * Hermitian strings are trace-orthonormal, so Tr(O P_q)/2^N is O's coefficient of q).
+ *   qv, qw: HOST arrays of nq query strings (caller-owned; duplicates allowed; bits at
+ *     or above n_sites give PS_ERR_INVALID);
+ *   re, im: HOST arrays of nq doubles receiving each coefficient (0 for strings absent
+ *     from O).  O is read once on the device; the call synchronises O's stream. */
+int pauli_coefficients(const pauli_sum* O, const uint64_t* qv, const uint64_t* qw, int64_t nq, double* re,
+                       double* im);
 
 /* Allocation-free variant of pauli_trace_product, for callers that cannot allocate
  * device memory (code running under another framework's allocator or memory budget,

@@ -64,6 +64,23 @@ int pauli_commutator(const pauli_sum* H, const pauli_sum* O, pauli_sum* out) {
   return commutator_into(H, O, 0, out);
 }
 
+int pauli_multiply(const pauli_sum* A, const pauli_sum* B, pauli_sum* out) {
+  if (!A || !B || !out || out == A || out == B) return PS_ERR_INVALID;
+  if (!same_sites(A, B) || !same_sites(B, out)) return PS_ERR_INVALID;
+  if (A->n > 0xEFFF) return PS_ERR_INVALID;
+  if (A->stream != out->stream) PS_CUDA(cudaStreamSynchronize(A->stream));
+  if (B->stream != out->stream) PS_CUDA(cudaStreamSynchronize(B->stream));
+  MergeSpec sp;
+  sp.H = A->d;
+  sp.nH = (int)A->n;
+  sp.X = B->d;
+  sp.nX = B->n;
+  sp.product = true;
+  sp.clsH = A->cls;
+  sp.clsX = B->cls;
+  return merge_run(sp, out->stream, out);
+}
+
 int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_sum* B, pauli_sum* out) {
   if (!A || !B || !out || out == A || out == B) return PS_ERR_INVALID;
   if (!same_sites(A, B) || !same_sites(A, out)) return PS_ERR_INVALID;
@@ -166,6 +183,15 @@ int pauli_trace_product(const pauli_sum* A, const pauli_sum* B, double* re, doub
   if (!A || !B || !re || !im || !same_sites(A, B)) return PS_ERR_INVALID;
   if (A->stream != B->stream) PS_CUDA(cudaStreamSynchronize(B->stream));
   return exact_trace_product(A->d, A->n, B->d, B->n, A->stream, re, im);
+}
+
+int pauli_coefficients(const pauli_sum* O, const uint64_t* qv, const uint64_t* qw, int64_t nq, double* re,
+                       double* im) {
+  if (!O || nq < 0 || (nq > 0 && (!qv || !qw || !re || !im))) return PS_ERR_INVALID;
+  const uint64_t inv = O->n_sites >= 64 ? 0ull : ~((1ull << O->n_sites) - 1ull);
+  for (int64_t j = 0; j < nq; ++j)
+    if ((qv[j] | qw[j]) & inv) return PS_ERR_INVALID;
+  return coefficients(O->d, O->n, qv, qw, nq, O->stream, re, im);
 }
 
 int pauli_norm(const pauli_sum* O, double* out) {

@@ -283,6 +283,8 @@ struct MergeSpec {
   const Rec* X = nullptr;
   int64_t nX = 0;
   int rot = 0;
+  bool product = false;  // X pairs: every (h, x) with i^k h x (operator product); else the commutator's
+                         // anticommuting pairs with 2 i^(k + rot) h x
   MergeSource src[4];
   int nsrc = 0;
   const Rec* pre = nullptr;
@@ -298,5 +300,7 @@ void record_merge_stats(const pauli_merge_stats& st);
 int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor);
 int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out);
 int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cudaStream_t s, double* re, double* im);
+int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw, int64_t nq, cudaStream_t s,
+                 double* re, double* im);
 
 }  // namespace ps

@@ -194,11 +194,13 @@ __device__ __forceinline__ uint64_t reserve_slot(unsigned long long* __restrict_
   return b + (uint32_t)__popc(mm & ((1u << lane) - 1u));
 }
 
-// Emission of the products for |H| > 256 (8-byte entries, H in chunks [h0, h0 + nh)).  A warp
+// Emission of the products for |H| > 256 and of operator products (ALL: every pair, not only
+// the anticommuting ones) as 8-byte entries, H in chunks [h0, h0 + nh).  A warp
 // holds 32 x in registers and walks the H terms; the anticommuting (h, lane) pairs are
 // queued as 32-bit codes and, 32 at a time, turned into entries (x index << 16 | H index)
 // with every lane active: the lane fetches its x's hash by shuffle and reserves a slot in
 // bin F(h) ^ F(x).  The queue is emptied before the warp moves on to its next 32 x.
+template <bool ALL>
 __global__ void __launch_bounds__(kEmitThreads) k_emit_products(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
                                                        int64_t nX, const Rec* __restrict__ H,
                                                        const uint32_t* __restrict__ fH, int h0, int nh,
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_products(const Rec* __res
     int qn = 0;  // queued codes of this warp (warp-uniform)
     for (int h = 0; h < nh; ++h) {
       const ulonglong2 hk = s_hk[h];
-      const bool anti = valid && anticommute(hk.x, hk.y, xk.x, xk.y);
+      const bool anti = valid && (ALL || anticommute(hk.x, hk.y, xk.x, xk.y));
       const unsigned m = __ballot_sync(0xffffffffu, anti);
       if (!m) continue;
       if (anti) q[qn + __popc(m & ((1u << lane) - 1))] = ((uint32_t)lane << 16) | (uint32_t)h;
@@ -553,6 +555,7 @@ struct MergeArgs {
   int nH;
   const Rec* X;
   int rot;
+  int twice;  // 1: commutator contributions 2 i^(k + rot) h x; 0: operator product i^k h x
   const Rec* src[4];
   Cx alpha[4];
   const Rec* pre;
@@ -647,7 +650,7 @@ __device__ __forceinline__ void build_contribution(const MergeArgs& a, uint32_t 
     key = make_ulonglong2(h.v ^ y.v, h.w ^ y.w);
     int k = product_phase(h.v, h.w, y.v, y.w) + a.rot;
     Cx p = cmul(Cx{h.re, h.im}, Cx{y.re, y.im});
-    t = rot(Cx{twice(p.re), twice(p.im)}, k);
+    t = a.twice ? rot(Cx{twice(p.re), twice(p.im)}, k) : rot(p, k);
   } else if (code == kCodePre) {
     key = make_ulonglong2(y.v, y.w);
     t = Cx{y.re, y.im};
@@ -1545,8 +1548,12 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   auto cls_scalar = [](Cx c) { return cls_of(c.re, c.im); };
   int prod_cls = 0;
   if (nX > 0) {
-    prod_cls = cls_mul(sp.clsH, sp.clsX);  // then times i^(k + rot) with k odd
-    if (!(sp.rot & 1)) prod_cls = cls_swap(prod_cls);
+    if (sp.product) {
+      prod_cls = kClsComplex;  // i^k with k of either parity
+    } else {
+      prod_cls = cls_mul(sp.clsH, sp.clsX);  // then times i^(k + rot) with k odd
+      if (!(sp.rot & 1)) prod_cls = cls_swap(prod_cls);
+    }
   }
   int acc_cls = prod_cls;
   for (int i = 0; i < sp.nsrc; ++i)
@@ -1667,7 +1674,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   PS_TRY(cur.alloc(nbins, s));
   PS_CUDA(cudaMemcpyAsync(cur.p, base.p, nbins * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
   Buf<uint32_t> tab;
-  if (nX > 0 && sp.nH <= kMaskBits) {
+  if (nX > 0 && sp.nH <= kMaskBits && !sp.product) {
     // |H| <= 256: anticommutation bitmaps from the nibble table
     const int stride = tab_stride((sp.nH + 31) / 32);
     PS_TRY(tab.alloc((size_t)kTabPos * kTabVals * stride, s));
@@ -1679,8 +1686,9 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     for (int h0 = 0; h0 < sp.nH; h0 += kHChunk) {
       int nh = std::min(kHChunk, sp.nH - h0);
       size_t sm = (size_t)nh * (sizeof(ulonglong2) + sizeof(uint32_t));
-      if (sm > 48 * 1024) PS_CUDA(cudaFuncSetAttribute(k_emit_products, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      PS_LAUNCH("k_emit_products", s, k_emit_products<<<grid_for(nX), kEmitThreads, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, h0, nh, cur.p, entries.p, counters.p));
+      auto kern = sp.product ? k_emit_products<true> : k_emit_products<false>;
+      if (sm > 48 * 1024) PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      PS_LAUNCH("k_emit_products", s, kern<<<grid_for(nX), kEmitThreads, sm, s>>>(sp.X, fX.p, nX, sp.H, fH.p, h0, nh, cur.p, entries.p, counters.p));
       PS_CUDA(cudaGetLastError());
     }
   }
@@ -1732,6 +1740,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   a.nH = sp.nH;
   a.X = sp.X;
   a.rot = sp.rot;
+  a.twice = sp.product ? 0 : 1;
   for (int i = 0; i < sp.nsrc; ++i) {
     a.src[i] = sp.src[i].rec;
     a.alpha[i] = sp.src[i].alpha;

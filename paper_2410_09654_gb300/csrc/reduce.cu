@@ -72,6 +72,19 @@ __global__ void k_tp_build(const Rec* __restrict__ B, int64_t n, ulonglong2* tke
   }
 }
 
+// ---------------------------------------------------------------- coefficient lookup
+// out[j] = (re, im) of the O string equal to table key j (the table holds distinct keys;
+// entries with no match keep their zero).
+__global__ void k_coef_probe(const Rec* __restrict__ O, int64_t n, const ulonglong2* tkey, const int64_t* tidx,
+                             uint64_t tmask, const long long* ones_idx, double2* __restrict__ out) {
+  const long long oi = *ones_idx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Rec r = O[i];
+    const int64_t j = tp_find(tkey, tidx, tmask, oi, r.v, r.w);
+    if (j >= 0) out[j] = make_double2(r.re, r.im);
+  }
+}
+
 __global__ void k_tp_top(const Rec* __restrict__ A, int64_t n, const Rec* __restrict__ B, const ulonglong2* tkey,
                          const int64_t* tidx, uint64_t tmask, const long long* ones_idx, int* top) {
   int m = -100000;
@@ -187,6 +200,63 @@ int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cuda
   std::vector<long long> fim(h.begin() + span + kWinDigits, h.end());
   *re = round_exact(fre, h.data(), hi[1]);
   *im = round_exact(fim, h.data() + span, hi[1]);
+  return PS_OK;
+}
+
+}  // namespace ps
+
+namespace ps {
+
+// Coefficients of nq query strings (host arrays) in the device sum O.  Queries are
+// deduplicated on the host, their table built on the device, O streamed once.
+int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw, int64_t nq, cudaStream_t s,
+                 double* re, double* im) {
+  for (int64_t j = 0; j < nq; ++j) re[j] = im[j] = 0.0;
+  if (nq == 0 || n == 0) return PS_OK;
+  std::vector<int64_t> ord((size_t)nq);
+  for (int64_t j = 0; j < nq; ++j) ord[(size_t)j] = j;
+  std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+    return qv[a] < qv[b] || (qv[a] == qv[b] && qw[a] < qw[b]);
+  });
+  std::vector<Rec> uq;
+  std::vector<int64_t> slot_of((size_t)nq);
+  for (int64_t r = 0; r < nq; ++r) {
+    const int64_t j = ord[(size_t)r];
+    if (uq.empty() || uq.back().v != qv[j] || uq.back().w != qw[j]) uq.push_back(Rec{qv[j], qw[j], 0.0, 0.0});
+    slot_of[(size_t)j] = (int64_t)uq.size() - 1;
+  }
+  const int64_t nu = (int64_t)uq.size();
+  uint64_t slots = 1;
+  while (slots < (uint64_t)(2 * nu)) slots <<= 1;
+  Buf<Rec> dq;
+  Buf<ulonglong2> tkey;
+  Buf<int64_t> tidx;
+  Buf<long long> ones;
+  Buf<double2> out;
+  PS_TRY(dq.alloc(nu, s));
+  PS_TRY(tkey.alloc(slots, s));
+  PS_TRY(tidx.alloc(slots, s));
+  PS_TRY(ones.alloc(1, s));
+  PS_TRY(out.alloc(nu, s));
+  PS_CUDA(cudaMemcpyAsync(dq.p, uq.data(), nu * sizeof(Rec), cudaMemcpyHostToDevice, s));
+  PS_CUDA(cudaMemsetAsync(tkey.p, 0xFF, slots * sizeof(ulonglong2), s));
+  PS_CUDA(cudaMemsetAsync(out.p, 0, nu * sizeof(double2), s));
+  long long neg1 = -1;
+  PS_CUDA(cudaMemcpyAsync(ones.p, &neg1, sizeof(neg1), cudaMemcpyHostToDevice, s));
+  const int nsm = num_sms();
+  int bt = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nu, 256), 4 * nsm));
+  PS_LAUNCH("k_tp_build", s, k_tp_build<<<bt, 256, 0, s>>>(dq.p, nu, tkey.p, tidx.p, slots - 1, ones.p));
+  PS_CUDA(cudaGetLastError());
+  int bp = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * nsm));
+  PS_LAUNCH("k_coef_probe", s, k_coef_probe<<<bp, 256, 0, s>>>(O, n, tkey.p, tidx.p, slots - 1, ones.p, out.p));
+  PS_CUDA(cudaGetLastError());
+  std::vector<double2> h((size_t)nu);
+  PS_CUDA(cudaMemcpyAsync(h.data(), out.p, nu * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  for (int64_t j = 0; j < nq; ++j) {
+    re[j] = h[(size_t)slot_of[(size_t)j]].x;
+    im[j] = h[(size_t)slot_of[(size_t)j]].y;
+  }
   return PS_OK;
 }
 

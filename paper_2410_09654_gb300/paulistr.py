@@ -88,11 +88,13 @@ def load(build_if_missing: bool = False):
         "pauli_sum_download_device": ([P, P, P, P, P, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_sum_copy": ([P, P], ctypes.c_int),
         "pauli_commutator": ([P, P, P], ctypes.c_int),
+        "pauli_multiply": ([P, P, P], ctypes.c_int),
         "pauli_add": ([P, ctypes.c_double, ctypes.c_double, P, P], ctypes.c_int),
         "pauli_truncate": ([P, ctypes.POINTER(pauli_trunc_policy), P, ctypes.c_double], ctypes.c_int),
         "pauli_rk4_step": ([P, P, ctypes.c_double, ctypes.POINTER(pauli_trunc_policy), P], ctypes.c_int),
         "pauli_lanczos_step": ([P, P, P, ctypes.c_double, ctypes.POINTER(pauli_trunc_policy), F64P], ctypes.c_int),
         "pauli_trace_product": ([P, P, F64P, F64P], ctypes.c_int),
+        "pauli_coefficients": ([P, P, P, I64, P, P], ctypes.c_int),
         "pauli_norm": ([P, F64P], ctypes.c_int),
         "pauli_last_merge_stats": ([ctypes.POINTER(pauli_merge_stats)], ctypes.c_int),
         "pauli_debug_fail_alloc_after": ([I64], ctypes.c_int),
@@ -222,6 +224,13 @@ def pauli_commutator(H: PauliSum, O: PauliSum, out: PauliSum | None = None) -> P
     return out
 
 
+def pauli_multiply(A: PauliSum, B: PauliSum, out: PauliSum | None = None) -> PauliSum:
+    """A B (operator product; A is the outer operand, at most 61439 strings)."""
+    out = out or PauliSum(B.n_sites, 0, B.stream.value)
+    _check(load().pauli_multiply(A.handle, B.handle, out.handle), "pauli_multiply")
+    return out
+
+
 def pauli_add(A: PauliSum, alpha: complex, B: PauliSum, out: PauliSum | None = None) -> PauliSum:
     out = out or PauliSum(A.n_sites, 0, A.stream.value)
     alpha = complex(alpha)
@@ -258,6 +267,18 @@ def pauli_trace_product(A: PauliSum, B: PauliSum) -> complex:
     re, im = ctypes.c_double(), ctypes.c_double()
     _check(load().pauli_trace_product(A.handle, B.handle, ctypes.byref(re), ctypes.byref(im)), "pauli_trace_product")
     return complex(re.value, im.value)
+
+
+def pauli_coefficients(O: PauliSum, v, w) -> np.ndarray:
+    """Coefficients of the query strings (v[j], w[j]) in O (0 where absent): Tr(O P_q)/2^N,
+    e.g. the two-point correlators Tr(O(t) Z_j)/2^N for all sites j."""
+    v = np.ascontiguousarray(v, dtype=np.uint64)
+    w = np.ascontiguousarray(w, dtype=np.uint64)
+    n = len(v)
+    re, im = np.zeros(n), np.zeros(n)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(load().pauli_coefficients(O.handle, ptr(v), ptr(w), n, ptr(re), ptr(im)), "pauli_coefficients")
+    return re + 1j * im
 
 
 def pauli_trace_product_noalloc(a_arrays, b_arrays, stream=None) -> complex:

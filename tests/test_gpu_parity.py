@@ -117,6 +117,102 @@ def test_commutator_n1():
 
 
 # ----------------------------------------------------------------------------- add / truncate
+# ----------------------------------------------------------------------------- operator product
+@pytest.mark.parametrize("n,ma,mb,sup", [(3, 9, 17, None), (10, 29, 500, 5), (64, 120, 5000, 10),
+                                         (16, 256, 3000, 6), (12, 300, 2000, 6)])
+def test_multiply_random(n, ma, mb, sup):
+    # ranked merge (|A| <= 256) and chained merge (|A| = 300); complex coefficients
+    Aa = I.random_sum(3000 + n, n, ma, "complex", max_support=min(3, n))
+    Ba = I.random_sum(4000 + n + mb, n, mb, "complex", max_support=sup)
+    out = ps.pauli_multiply(dev(n, Aa), dev(n, Ba))
+    assert_match(out.download(), orc.product(ref(n, Aa), ref(n, Ba)), what="product")
+
+
+@pytest.mark.parametrize("ka,kb", [("real", "real"), ("real", "imag"), ("imag", "complex")])
+def test_multiply_classes(ka, kb):
+    n = 24
+    Aa = I.random_sum(71, n, 60, ka, max_support=4)
+    Ba = I.random_sum(72, n, 4000, kb, max_support=8)
+    out = ps.pauli_multiply(dev(n, Aa), dev(n, Ba))
+    assert_match(out.download(), orc.product(ref(n, Aa), ref(n, Ba)), what=f"product {ka}x{kb}")
+
+
+def test_multiply_identity_coefficient_is_trace_product():
+    n = 20
+    Aa = I.random_sum(81, n, 50, "complex", dyadic=True, max_support=4)
+    Ba = I.random_sum(82, n, 3000, "complex", dyadic=True, max_support=4)
+    have = set(zip(Ba[0].tolist(), Ba[1].tolist()))
+    add = [i for i in range(len(Aa[0])) if (int(Aa[0][i]), int(Aa[1][i])) not in have][:20]
+    Ba = tuple(np.concatenate([x, y[add]]) for x, y in zip(Ba, Aa))  # 20 strings shared with A
+    A, B = dev(n, Aa), dev(n, Ba)
+    got = ps.pauli_multiply(A, B).download()
+    ident = [complex(re, im) for v, w, re, im in zip(*got) if v == 0 and w == 0]
+    assert ident and ident[0] == ps.pauli_trace_product(A, B) != 0
+
+
+def test_multiply_edges():
+    n = 8
+    empty = ps.PauliSum(n)
+    B = dev(n, I.random_sum(91, n, 50, "real"))
+    assert len(ps.pauli_multiply(empty, B)) == 0
+    assert len(ps.pauli_multiply(B, empty)) == 0
+    ident = dev(n, (np.array([0], np.uint64), np.array([0], np.uint64), np.array([1.0]), np.array([0.0])))
+    assert_match(ps.pauli_multiply(ident, B).download(), ref(n, B.download()), what="1 B")
+    with pytest.raises(ps.PauliError):
+        ps.pauli_multiply(B, B, B)  # out aliases an operand
+
+
+# ----------------------------------------------------------------------------- coefficients / correlators
+def _single(n, v, w):
+    return orc.Op(n, [v], [w], [1.0], [0.0])
+
+
+def test_coefficients_random_queries():
+    n = 64
+    Oa = I.random_sum(111, n, 20000, "complex", max_support=8)
+    O = dev(n, Oa)
+    rng = np.random.default_rng(5)
+    pick = rng.integers(0, 20000, 300)
+    qv = np.concatenate([Oa[0][pick], rng.integers(0, 2**63, 100, dtype=np.uint64),
+                         Oa[0][pick[:50]], [0, np.uint64(2**64 - 1)]]).astype(np.uint64)
+    qw = np.concatenate([Oa[1][pick], rng.integers(0, 2**63, 100, dtype=np.uint64),
+                         Oa[1][pick[:50]], [0, np.uint64(2**64 - 1)]]).astype(np.uint64)
+    got = ps.pauli_coefficients(O, qv, qw)
+    Or = ref(n, Oa)
+    for j in range(len(qv)):  # Tr(O P_q)/2^N from the oracle's exactly rounded trace product
+        assert got[j] == orc.trace_product(Or, _single(n, int(qv[j]), int(qw[j]))), j
+
+
+def test_coefficients_all_ones_key_and_edges():
+    n = 64
+    ones = np.uint64(2**64 - 1)
+    O = dev(n, (np.array([ones, 3], np.uint64), np.array([ones, 5], np.uint64), np.array([0.25, 1.0]),
+                np.array([-1.0, 0.0])))
+    got = ps.pauli_coefficients(O, [ones, 3, 3, 7], [ones, 5, 5, 7])
+    assert list(got) == [0.25 - 1j, 1.0, 1.0, 0.0]
+    assert len(ps.pauli_coefficients(O, [], [])) == 0
+    with pytest.raises(ps.PauliError):
+        ps.pauli_coefficients(dev(8, I.random_sum(1, 8, 5, "real")), [1 << 9], [0])
+
+
+def test_two_point_correlators_after_rk4():
+    # Tr(O(t) Z_j)/2^N for every site j on the N=10 chain after a few RK4 steps
+    n = 10
+    Ha = I.chaotic_ising_chain(n).arrays()
+    O0 = I.single(n, "Z", 1).arrays()
+    H, O = dev(n, Ha), dev(n, O0)
+    Hr, Or = ref(n, Ha), ref(n, O0)
+    pol = ps.policy(max_weight=6, cutoff=1e-10)
+    for _ in range(5):
+        ps.pauli_rk4_step(H, O, 0.05, pol)
+        Or = orc.rk4_step(Hr, Or, 0.05, max_weight=6, cutoff=1e-10)
+    qv = np.array([1 << j for j in range(n)], np.uint64)
+    got = ps.pauli_coefficients(O, qv, np.zeros(n, np.uint64))
+    want = [orc.trace_product(Or, _single(n, 1 << j, 0)) for j in range(n)]
+    assert list(got) == want
+    assert got[0] != 0 and got[1] != 0
+
+
 def test_add():
     n = 20
     A = I.random_sum(31, n, 4000, "complex", max_support=6)
