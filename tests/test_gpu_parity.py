@@ -173,10 +173,10 @@ def test_coefficients_random_queries():
     O = dev(n, Oa)
     rng = np.random.default_rng(5)
     pick = rng.integers(0, 20000, 300)
-    qv = np.concatenate([Oa[0][pick], rng.integers(0, 2**63, 100, dtype=np.uint64),
-                         Oa[0][pick[:50]], [0, np.uint64(2**64 - 1)]]).astype(np.uint64)
-    qw = np.concatenate([Oa[1][pick], rng.integers(0, 2**63, 100, dtype=np.uint64),
-                         Oa[1][pick[:50]], [0, np.uint64(2**64 - 1)]]).astype(np.uint64)
+    corner = np.array([0, 2**64 - 1], dtype=np.uint64)  # identity and the all-ones key
+    qv = np.concatenate([Oa[0][pick], rng.integers(0, 2**63, 100, dtype=np.uint64), Oa[0][pick[:50]], corner])
+    qw = np.concatenate([Oa[1][pick], rng.integers(0, 2**63, 100, dtype=np.uint64), Oa[1][pick[:50]], corner])
+    assert qv.dtype == np.uint64 and qv[-1] == np.uint64(2**64 - 1)
     got = ps.pauli_coefficients(O, qv, qw)
     Or = ref(n, Oa)
     for j in range(len(qv)):  # Tr(O P_q)/2^N from the oracle's exactly rounded trace product
