@@ -71,6 +71,21 @@ def _load():
         lib.or_commutator.restype = vp
         lib.or_product.argtypes = _OP + _OP
         lib.or_product.restype = vp
+        lib.or_ts_expand.argtypes = _OP + [ctypes.c_int]
+        lib.or_ts_expand.restype = vp
+        lib.or_ts_canonical_merge.argtypes = _OP + [ctypes.c_int]
+        lib.or_ts_canonical_merge.restype = vp
+        lib.or_ts_canonical.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _U64P, _U64P]
+        lib.or_ts_canonical.restype = ctypes.c_int
+        lib.or_ts_period.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
+        lib.or_ts_period.restype = ctypes.c_int
+        lib.or_ts_commutator.argtypes = _OP + _OP + [ctypes.c_int]
+        lib.or_ts_commutator.restype = vp
+        lib.or_ts_norm2.argtypes = _OP + [ctypes.c_int]
+        lib.or_ts_norm2.restype = ctypes.c_double
+        lib.or_ts_lanczos_step.argtypes = _OP + _OP + _OP + [ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                                             ctypes.c_int64, ctypes.c_int]
+        lib.or_ts_lanczos_step.restype = vp
         lib.or_axpy.argtypes = _OP + [ctypes.c_double, ctypes.c_double] + _OP
         lib.or_axpy.restype = vp
         lib.or_scale.argtypes = _OP + [ctypes.c_double]
@@ -176,6 +191,53 @@ def product(A: Op, B: Op) -> Op:
     """A B by Alg. 1 proper: every pair, P_a P_b = i^k P_{a^b} (A outer loop in the given order)."""
     lib = _load()
     return _take(lib, lib.or_product(*A._args(), *B._args()), A.n_sites)[0]
+
+
+# ------------------------------------------------------------------ translation symmetry
+# A translation-symmetric operator on a periodic chain of n = n_sites sites is stored as its
+# generator O_0 (one representative string per translation orbit): O = sum_{i<n} T_i(O_0).
+
+def ts_canonical(s: tuple[int, int], n: int) -> tuple[tuple[int, int], int]:
+    """Orbit representative of s (smallest translate, v then w) and the smallest shift to it."""
+    cv, cw = ctypes.c_uint64(), ctypes.c_uint64()
+    r = _load().or_ts_canonical(s[0], s[1], n, ctypes.byref(cv), ctypes.byref(cw))
+    return (cv.value, cw.value), r
+
+
+def ts_period(s: tuple[int, int], n: int) -> int:
+    return int(_load().or_ts_period(s[0], s[1], n))
+
+
+def ts_expand(G: Op) -> Op:
+    """sum_{k<n} T_k(G) as a plain sum."""
+    lib = _load()
+    return _take(lib, lib.or_ts_expand(*G._args(), G.n_sites), G.n_sites)[0]
+
+
+def ts_canonical_merge(X: Op) -> Op:
+    """Every string moved to its orbit representative, contributions added by increasing shift."""
+    lib = _load()
+    return _take(lib, lib.or_ts_canonical_merge(*X._args(), X.n_sites), X.n_sites)[0]
+
+
+def ts_commutator(H0: Op, O0: Op) -> Op:
+    """Generator of [H, O] for translation-symmetric H, O (Alg. 2's sums, representative order)."""
+    lib = _load()
+    return _take(lib, lib.or_ts_commutator(*H0._args(), *O0._args(), O0.n_sites), O0.n_sites)[0]
+
+
+def ts_norm2(O0: Op) -> float:
+    """||O||^2 / n, exact then rounded once."""
+    return float(_load().or_ts_norm2(*O0._args(), O0.n_sites))
+
+
+def ts_lanczos_step(H0: Op, O_prev: Op, O_cur: Op, b_prev: float, max_weight: int = -1, cutoff: float = 0.0,
+                    top_k: int = 0) -> tuple[float, Op]:
+    lib = _load()
+    h = lib.or_ts_lanczos_step(*H0._args(), *O_prev._args(), *O_cur._args(), float(b_prev), max_weight,
+                               float(cutoff), int(top_k), O_cur.n_sites)
+    out, sc = _take(lib, h, O_cur.n_sites)
+    return float(sc[0]), out
 
 
 def axpy(A: Op, alpha: complex, B: Op) -> Op:

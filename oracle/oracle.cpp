@@ -383,6 +383,117 @@ std::vector<Term> rk4_step(const std::vector<Term>& H, const std::vector<Term>& 
   return truncate(On, P, keep, dt);
 }
 
+// ---------------------------------------------------------------------------
+// Translation-symmetric operators on a periodic chain of n sites (Methods, the
+// translation-symmetric encoding and Alg. 2).  Such an operator is O = sum_{i<n} T_i(O_0),
+// T_i the translation by i sites (site j -> j + i mod n, a rotation of both masks), and is
+// stored as its generator O_0: one representative string per translation orbit.
+// ---------------------------------------------------------------------------
+inline uint64_t rotl_n(uint64_t x, int k, int n) {
+  const uint64_t mask = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+  k %= n;
+  if (k == 0) return x & mask;
+  return ((x << k) | (x >> (n - k))) & mask;
+}
+
+inline Key translate(Key s, int k, int n) { return {rotl_n(s.v, k, n), rotl_n(s.w, k, n)}; }
+
+// Representative of the orbit of s: its smallest translate in (v, then w) unsigned order;
+// *r receives the smallest shift with T_r(s) equal to it.  (The paper's Shiftleft moves a
+// string to start on the first site; any fixed choice of one string per orbit serves, and
+// this one is also defined for strings that wrap around the ring.)
+inline Key ts_canonical(Key s, int n, int* r) {
+  Key best = s;
+  int br = 0;
+  for (int k = 1; k < n; ++k) {
+    Key t = translate(s, k, n);
+    if (t < best) {
+      best = t;
+      br = k;
+    }
+  }
+  if (r) *r = br;
+  return best;
+}
+
+// Smallest d > 0 with T_d(s) = s (a divisor of n).
+inline int ts_period(Key s, int n) {
+  for (int d = 1; d < n; ++d)
+    if (translate(s, d, n) == s) return d;
+  return n;
+}
+
+// sum_{k<n} T_k(G) as a plain sum; G outer, then k, contributions added in that order.
+std::vector<Term> ts_expand(const std::vector<Term>& G, int n) {
+  Dict C;
+  for (const Term& g : G)
+    for (int k = 0; k < n; ++k) {
+      Key s = translate(g.k, k, n);
+      auto it = C.find(s);
+      if (it == C.end()) {
+        C.emplace(s, g.c);
+      } else {
+        it->second.re += g.c.re;
+        it->second.im += g.c.im;
+      }
+    }
+  return canonical(C);
+}
+
+// Every string of X moved to its orbit's representative; the contributions to one
+// representative are added in increasing shift r (distinct strings of one orbit need
+// distinct smallest shifts, so the order is total).  Exact zeros dropped.
+std::vector<Term> ts_canonical_merge(const std::vector<Term>& X, int n) {
+  struct E {
+    Key k;
+    int r;
+    Cx c;
+  };
+  std::vector<E> e;
+  e.reserve(X.size());
+  for (const Term& x : X) {
+    int r = 0;
+    Key k = ts_canonical(x.k, n, &r);
+    e.push_back({k, r, x.c});
+  }
+  std::sort(e.begin(), e.end(), [](const E& a, const E& b) { return a.k < b.k || (a.k == b.k && a.r < b.r); });
+  std::vector<Term> out;
+  for (size_t i = 0; i < e.size();) {
+    Cx acc = e[i].c;
+    size_t j = i + 1;
+    for (; j < e.size() && e[j].k == e[i].k; ++j) {
+      acc.re += e[j].c.re;
+      acc.im += e[j].c.im;
+    }
+    if (acc.re != 0.0 || acc.im != 0.0) out.push_back({e[i].k, acc});
+    i = j;
+  }
+  return out;
+}
+
+// [H, O] of translation-symmetric operators: H = sum_i T_i(H_0) is translation invariant,
+// so [H, O] = sum_j T_j([H, O_0]) and its generator is [H, O_0] with H expanded in full,
+// moved to representatives.  (Alg. 2 forms the same sums, A_0 against every translate of
+// B_0; summing per representative in the order above fixes the rounding.)
+std::vector<Term> ts_commutator(const std::vector<Term>& H0, const std::vector<Term>& O0, int n) {
+  return ts_canonical_merge(commutator(ts_expand(H0, n), O0), n);
+}
+
+// ||O||^2 / n for O = sum_i T_i(O_0): a representative of period d stands for n/d copies of
+// each of its d distinct translates, so ||O||^2 = n sum_r (n/d_r) |c_r|^2.  The sum is exact,
+// rounded once.
+double ts_norm2_exact(const std::vector<Term>& O0, int n) {
+  ExactSum s;
+  for (const Term& t : O0) {
+    const int m = n / ts_period(t.k, n);
+    for (int j = 0; j < m; ++j) {
+      s.add_product(t.c.re, t.c.re);
+      s.add_product(t.c.im, t.c.im);
+    }
+  }
+  return s.value();
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -440,6 +551,61 @@ or_result* or_product(const uint64_t* av, const uint64_t* aw, const double* are,
                       int64_t na, const uint64_t* bv, const uint64_t* bw, const double* bre,
                       const double* bim, int64_t nb) {
   return new or_result{product(from_arrays(av, aw, are, aim, na), from_arrays(bv, bw, bre, bim, nb)), {}};
+}
+
+// Translation-symmetric operators (n = ring length).  Parity: pinned by brute-force orbit
+// checks, dense matrices of the expanded operators, expand(C_0) = [expand(H_0), expand(O_0)]
+// bit for bit on dyadic sums, and b_n equal to the plain Lanczos of the expanded chain.
+or_result* or_ts_expand(const uint64_t* gv, const uint64_t* gw, const double* gre, const double* gim, int64_t ng,
+                        int n) {
+  return new or_result{ts_expand(from_arrays(gv, gw, gre, gim, ng), n), {}};
+}
+
+or_result* or_ts_canonical_merge(const uint64_t* xv, const uint64_t* xw, const double* xre, const double* xim,
+                                 int64_t nx, int n) {
+  return new or_result{ts_canonical_merge(from_arrays(xv, xw, xre, xim, nx), n), {}};
+}
+
+int or_ts_canonical(uint64_t v, uint64_t w, int n, uint64_t* cv, uint64_t* cw) {
+  int r = 0;
+  Key k = ts_canonical({v, w}, n, &r);
+  *cv = k.v;
+  *cw = k.w;
+  return r;
+}
+
+int or_ts_period(uint64_t v, uint64_t w, int n) { return ts_period({v, w}, n); }
+
+or_result* or_ts_commutator(const uint64_t* hv, const uint64_t* hw, const double* hre, const double* him,
+                            int64_t nh, const uint64_t* ov, const uint64_t* ow, const double* ore,
+                            const double* oim, int64_t no, int n) {
+  return new or_result{ts_commutator(from_arrays(hv, hw, hre, him, nh), from_arrays(ov, ow, ore, oim, no), n), {}};
+}
+
+double or_ts_norm2(const uint64_t* ov, const uint64_t* ow, const double* ore, const double* oim, int64_t no, int n) {
+  return ts_norm2_exact(from_arrays(ov, ow, ore, oim, no), n);
+}
+
+// One Lanczos step of translation-symmetric operators, as the plain step with the TS
+// commutator and norm: A_0 = C_0 - b_prev O_prev,0, b = ||A||, O_0 = trunc(A_0 / b).
+or_result* or_ts_lanczos_step(const uint64_t* hv, const uint64_t* hw, const double* hre, const double* him,
+                              int64_t nh, const uint64_t* pv, const uint64_t* pw, const double* pre,
+                              const double* pim, int64_t np, const uint64_t* cv, const uint64_t* cw,
+                              const double* cre, const double* cim, int64_t nc, double b_prev, int max_weight,
+                              double cutoff, int64_t top_k, int n) {
+  std::vector<Term> H0 = from_arrays(hv, hw, hre, him, nh);
+  std::vector<Term> Op = from_arrays(pv, pw, pre, pim, np);
+  std::vector<Term> Oc = from_arrays(cv, cw, cre, cim, nc);
+  std::vector<Term> A = ts_commutator(H0, Oc, n);
+  if (!Op.empty()) A = axpy(A, {-b_prev, 0.0}, Op);
+  const double b = std::sqrt(ts_norm2_exact(A, n));
+  or_result* r = new or_result;
+  r->scalars.push_back(b);
+  if (b == 0.0) return r;
+  Policy P{max_weight, cutoff, top_k, 0.0};
+  std::vector<Term> none;
+  r->t = truncate(divide(A, b), P, none, 0.0);
+  return r;
 }
 
 // A + alpha B.  Parity: pinned by dense matrices and by brute force on small inputs.

@@ -76,6 +76,25 @@ def xxz_chain(n: int, delta: float = 0.5):
     return b
 
 
+def xxz_generator(n: int, delta: float = 0.5):
+    """Translation generator H_0 of the periodic XXZ chain: X_1X_2 + Y_1Y_2 + delta Z_1Z_2
+    (H = sum_i T_i(H_0) on a ring of n sites)."""
+    b = SumBuilder(n)
+    b.add(1.0, "X", 1, "X", 2)
+    b.add(1.0, "Y", 1, "Y", 2)
+    b.add(delta, "Z", 1, "Z", 2)
+    return b
+
+
+def tilted_ising_generator(n: int, jz: float = 1.0, hx: float = 1.05, hz: float = 0.5):
+    """Translation generator of the periodic chain sum Z_iZ_{i+1} + hx X_i + hz Z_i."""
+    b = SumBuilder(n)
+    b.add(jz, "Z", 1, "Z", 2)
+    b.add(hx, "X", 1)
+    b.add(hz, "Z", 1)
+    return b
+
+
 def xxx_chain(n: int):
     """Open XXX chain, eq. XXXmodel."""
     return xxz_chain(n, 1.0)

@@ -167,6 +167,95 @@ def test_product_identity_coefficient_is_trace_product_dyadic():
     assert got != 0
 
 
+# ----------------------------------------------------------------------------- translation symmetry
+def _rot(x: int, k: int, n: int) -> int:
+    k %= n
+    m = (1 << n) - 1
+    return ((x << k) | (x >> (n - k))) & m if k else x
+
+
+def test_ts_canonical_and_period_brute_force():
+    rng = np.random.default_rng(3)
+    for n in (3, 8, 13, 64):
+        for _ in range(200):
+            v = int(rng.integers(0, 2**min(n, 62))) & ((1 << n) - 1)
+            w = int(rng.integers(0, 2**min(n, 62))) & ((1 << n) - 1)
+            if rng.random() < 0.2:  # periodic strings
+                d = [x for x in range(1, n + 1) if n % x == 0][int(rng.integers(0, 2))]
+                v = sum(((v >> 0) & ((1 << d) - 1)) << (d * j) for j in range(n // d))
+                w = sum(((w >> 0) & ((1 << d) - 1)) << (d * j) for j in range(n // d))
+            trans = [(_rot(v, k, n), _rot(w, k, n)) for k in range(n)]
+            best = min(trans)
+            (cv, cw), r = orc.ts_canonical((v, w), n)
+            assert (cv, cw) == best and r == trans.index(best)
+            assert orc.ts_period((v, w), n) == next(d for d in range(1, n + 1) if trans[d % n] == (v, w))
+
+
+def _translation_matrix(n: int) -> np.ndarray:
+    # U |s_1 ... s_n> = |s_n s_1 ... s_{n-1}>: the value at site j moves to site j + 1 (site 1 is
+    # the most significant bit of the basis index, matching dense.string_matrix)
+    d = 2 ** n
+    U = np.zeros((d, d))
+    for b in range(d):
+        bits = [(b >> (n - 1 - j)) & 1 for j in range(n)]
+        nb = [bits[-1]] + bits[:-1]
+        U[sum(x << (n - 1 - j) for j, x in enumerate(nb)), b] = 1.0
+    return U
+
+
+def test_ts_expand_is_sum_of_translates_dense():
+    n = 4
+    U = _translation_matrix(n)
+    G = op(n, I.random_sum(71, n, 6, "complex", max_support=2))
+    got = dense.op_matrix(orc.ts_expand(G), n)
+    g = dense.op_matrix(G, n)
+    want = sum(np.linalg.matrix_power(U, k) @ g @ np.linalg.matrix_power(U, k).T for k in range(n))
+    assert np.abs(got - want).max() < 1e-13
+
+
+def test_ts_commutator_expands_to_full_commutator_dyadic():
+    for n in (6, 9):
+        H0 = orc.ts_canonical_merge(op(n, I.xxz_generator(n, 0.5).arrays()))
+        O0 = orc.ts_canonical_merge(op(n, I.random_sum(80 + n, n, 25, "imag", max_support=4, dyadic=True)))
+        lhs = orc.ts_expand(orc.ts_commutator(H0, O0))
+        rhs = orc.commutator(orc.ts_expand(H0), orc.ts_expand(O0))
+        assert as_dict(lhs) == as_dict(rhs)
+        assert len(lhs) > 0
+
+
+def test_ts_norm_is_full_norm_over_n_dyadic():
+    n = 8
+    X = I.random_sum(90, n, 30, "complex", max_support=5, dyadic=True)
+    # add strings of period 1, 2 and 4
+    per = [(0xFF, 0x00), (0x55, 0xAA), (0x11, 0x33)]
+    X = tuple(np.concatenate([x, np.array(y)]) for x, y in zip(X, ([p[0] for p in per], [p[1] for p in per],
+                                                                    [0.5, -1.0, 2.0], [0.25, 0.0, -0.5])))
+    O0 = orc.ts_canonical_merge(op(n, X))
+    assert orc.ts_norm2(O0) * n == orc.norm2(orc.ts_expand(O0))
+
+
+@pytest.mark.parametrize("gen", ["xxz", "ising"])
+def test_ts_lanczos_matches_plain_lanczos_of_expanded_chain(gen):
+    n = 8
+    H0a = (I.xxz_generator(n, 0.5) if gen == "xxz" else I.tilted_ising_generator(n)).arrays()
+    H0 = orc.ts_canonical_merge(op(n, H0a))
+    O00 = orc.ts_canonical_merge(op(n, I.single(n, "X" if gen == "xxz" else "Z", 1).arrays()))
+    # the TS recursion, starting from O_0 normalised in the TS norm
+    b0 = math.sqrt(orc.ts_norm2(O00))
+    prev, cur, b = orc.Op.empty(n), orc.divide(O00, b0), 0.0
+    bs = []
+    for _ in range(8):
+        b, nxt = orc.ts_lanczos_step(H0, prev, cur, b)
+        bs.append(b)
+        prev, cur = cur, nxt
+    # the plain recursion on the expanded chain, from O_0 normalised in its own norm (the two
+    # norms differ by the constant factor n, to which b_n are blind)
+    full = orc.ts_expand(O00)
+    b_plain, _ = orc.lanczos(orc.ts_expand(H0), orc.divide(full, math.sqrt(orc.norm2(full))), 8)
+    assert np.allclose(bs, b_plain, rtol=1e-12, atol=0)
+    assert len(set(np.round(bs, 6))) > 2  # a non-trivial sequence
+
+
 def test_axpy_vs_dense():
     n = 3
     A = op(n, I.random_sum(1, n, 20, "complex"))
