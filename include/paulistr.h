@@ -162,6 +162,38 @@ int pauli_trace_product(const pauli_sum* A, const pauli_sum* B, double* re, doub
  * read with the square root), from the exactly rounded sum of squares. */
 int pauli_norm(const pauli_sum* O, double* out);
 
+/* ------------------------------------------------------- translation symmetry
+ * A translation-symmetric operator on a periodic chain of n = n_sites sites (2..64),
+ * O = sum_{i<n} T_i(O_0) with T_i the translation by i sites (site j -> j + i mod n),
+ * is stored as its generator O_0: one representative string per translation orbit, the
+ * orbit's smallest translate in (v, then w) unsigned order (the Methods' translation-
+ * symmetric encoding and Alg. 2, whose Shiftleft picks a representative per orbit).
+ * These calls need single-component coefficients (all real or all imaginary; the
+ * Lanczos recursion of a real H keeps them so) and return PS_ERR_INVALID otherwise. */
+
+/* out = sum_{k<n} T_k(G) as a plain sum (G any strings). */
+int pauli_ts_expand(const pauli_sum* G, pauli_sum* out);
+
+/* out = X with every string moved to its orbit representative; the contributions to one
+ * representative are added in increasing shift (the smallest k with T_k(x) = rep). */
+int pauli_ts_canonicalize(const pauli_sum* X, pauli_sum* out);
+
+/* out = generator of [H, O] for generators H0, O0: [sum_k T_k(H0), O0] moved to
+ * representatives (H is translation invariant, so [H, O] = sum_j T_j([H, O0])).  H0
+ * expanded may hold at most 61439 strings. */
+int pauli_ts_commutator(const pauli_sum* H0, const pauli_sum* O0, pauli_sum* out);
+
+/* *out = ||O|| / sqrt(n) for O = sum_i T_i(O0): sqrt(sum_r (n/d_r) |c_r|^2), d_r the period
+ * of representative r; the sum exact, rounded once. */
+int pauli_ts_norm(const pauli_sum* O0, double* out);
+
+/* One Lanczos step on generators, as pauli_lanczos_step with the calls above:
+ * A_0 = TS commutator(H0, O_cur) - b_prev O_prev, b = pauli_ts_norm(A_0),
+ * O_cur <- trunc(A_0 / b) (policy as in pauli_lanczos_step), O_prev <- old O_cur.
+ * b_n equal those of the expanded periodic chain (the norm's constant factor cancels). */
+int pauli_ts_lanczos_step(const pauli_sum* H0, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev,
+                          const pauli_trunc_policy* policy, double* b_out);
+
 /* Coefficients of given strings in O, for two-point correlators such as
  * Tr(O(t) Z_j)/2^N over all sites j (section "Heisenberg time evolution"; the
  * Hermitian strings are trace-orthonormal, so Tr(O P_q)/2^N is O's coefficient of q).

@@ -423,11 +423,13 @@ inline int ts_period(Key s, int n) {
   return n;
 }
 
-// sum_{k<n} T_k(G) as a plain sum; G outer, then k, contributions added in that order.
+// sum_{k<n} T_k(G) as a plain sum: the translates T_0(G), T_1(G), ... added in turn (k outer,
+// then G), so the contributions to one string arrive in increasing shift (one string of G
+// per shift reaches a given string).
 std::vector<Term> ts_expand(const std::vector<Term>& G, int n) {
   Dict C;
-  for (const Term& g : G)
-    for (int k = 0; k < n; ++k) {
+  for (int k = 0; k < n; ++k)
+    for (const Term& g : G) {
       Key s = translate(g.k, k, n);
       auto it = C.find(s);
       if (it == C.end()) {

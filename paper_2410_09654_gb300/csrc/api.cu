@@ -51,6 +51,28 @@ bool policy_valid(const pauli_trunc_policy* p) {
   return std::isfinite(p->cutoff) && std::isfinite(p->gamma) && p->max_weight <= 64;
 }
 
+// translation symmetry
+
+int ts_merge(const pauli_sum* X, int mode, pauli_sum* out) {
+  MergeSpec sp;
+  sp.src[0] = source(X, Cx{1.0, 0.0});
+  sp.src[0].ts = mode;
+  sp.nsrc = 1;
+  sp.ring = X->n_sites;
+  return merge_run(sp, out->stream, out);
+}
+
+// Generator of [H, O] (ts_commutator of the oracle): [H_full, O_0] moved to representatives.
+int ts_commutator_into(const pauli_sum* H0, const pauli_sum* O0, pauli_sum* out) {
+  Tmp Hf(O0), C(O0);
+  PS_TRY(ts_merge(H0, kTsExpand, &Hf.s));
+  if (Hf.s.n > 0xEFFF) return PS_ERR_INVALID;
+  PS_TRY(commutator_into(&Hf.s, O0, 0, &C.s));
+  return ts_merge(&C.s, kTsCanon, out);
+}
+
+bool ts_ok(const pauli_sum* s) { return s && s->n_sites >= 2; }
+
 }  // namespace
 
 extern "C" {
@@ -79,6 +101,74 @@ int pauli_multiply(const pauli_sum* A, const pauli_sum* B, pauli_sum* out) {
   sp.clsH = A->cls;
   sp.clsX = B->cls;
   return merge_run(sp, out->stream, out);
+}
+
+
+int pauli_ts_expand(const pauli_sum* G, pauli_sum* out) {
+  if (!ts_ok(G) || !out || out == G || !same_sites(G, out)) return PS_ERR_INVALID;
+  if (G->stream != out->stream) PS_CUDA(cudaStreamSynchronize(G->stream));
+  return ts_merge(G, kTsExpand, out);
+}
+
+int pauli_ts_canonicalize(const pauli_sum* X, pauli_sum* out) {
+  if (!ts_ok(X) || !out || out == X || !same_sites(X, out)) return PS_ERR_INVALID;
+  if (X->stream != out->stream) PS_CUDA(cudaStreamSynchronize(X->stream));
+  return ts_merge(X, kTsCanon, out);
+}
+
+int pauli_ts_commutator(const pauli_sum* H0, const pauli_sum* O0, pauli_sum* out) {
+  if (!ts_ok(H0) || !ts_ok(O0) || !out || out == H0 || out == O0) return PS_ERR_INVALID;
+  if (!same_sites(H0, O0) || !same_sites(O0, out)) return PS_ERR_INVALID;
+  if (H0->stream != out->stream) PS_CUDA(cudaStreamSynchronize(H0->stream));
+  if (O0->stream != out->stream) PS_CUDA(cudaStreamSynchronize(O0->stream));
+  return ts_commutator_into(H0, O0, out);
+}
+
+int pauli_ts_norm(const pauli_sum* O0, double* out) {
+  if (!ts_ok(O0) || !out) return PS_ERR_INVALID;
+  double n2 = 0.0;
+  PS_TRY(exact_norm2(O0->d, O0->n, O0->stream, &n2, O0->n_sites));
+  *out = std::sqrt(n2);
+  return PS_OK;
+}
+
+int pauli_ts_lanczos_step(const pauli_sum* H0, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev,
+                          const pauli_trunc_policy* policy, double* b_out) {
+  if (!ts_ok(H0) || !O_prev || !O_cur || !b_out || O_prev == O_cur || H0 == O_prev || H0 == O_cur)
+    return PS_ERR_INVALID;
+  if (!same_sites(H0, O_cur) || !same_sites(O_prev, O_cur) || !policy_valid(policy) || !std::isfinite(b_prev))
+    return PS_ERR_INVALID;
+  *b_out = 0.0;
+  Tmp Hf(O_cur), C(O_cur), A(O_cur);
+  PS_TRY(ts_merge(H0, kTsExpand, &Hf.s));
+  if (Hf.s.n > 0xEFFF) return PS_ERR_INVALID;
+  PS_TRY(commutator_into(&Hf.s, O_cur, 0, &C.s));
+  // A_0 = C_0 - b_prev O_prev (representatives in shift order, then the O_prev term)
+  MergeSpec sp;
+  sp.src[0] = source(&C.s, Cx{1.0, 0.0});
+  sp.src[0].ts = kTsCanon;
+  sp.nsrc = 1;
+  if (O_prev->n > 0) {
+    sp.src[1] = source(O_prev, Cx{-b_prev, 0.0});
+    sp.nsrc = 2;
+  }
+  sp.ring = O_cur->n_sites;
+  PS_TRY(merge_run(sp, O_cur->stream, &A.s));
+  double n2 = 0.0;
+  PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2, O_cur->n_sites));
+  const double b = std::sqrt(n2);
+  *b_out = b;
+  if (b == 0.0) return PS_ERR_KRYLOV_EXHAUSTED;
+  pauli_trunc_policy p{-1, 0.0, 0, 0.0, 0};
+  if (policy) {
+    p.max_weight = policy->max_weight;
+    p.cutoff = policy->cutoff;
+    p.top_k = policy->top_k;
+  }
+  PS_TRY(truncate_run(&A.s, &p, nullptr, 0.0, &b));
+  swap_contents(O_prev, O_cur);
+  swap_contents(O_cur, &A.s);
+  return PS_OK;
 }
 
 int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_sum* B, pauli_sum* out) {

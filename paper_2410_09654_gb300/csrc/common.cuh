@@ -128,6 +128,47 @@ __device__ __forceinline__ int product_phase(uint64_t va, uint64_t wa, uint64_t 
   return k & 3;
 }
 
+// Translation on a ring of n sites (site j -> j + k mod n): a rotation of both masks by k
+// within their low n bits.
+__host__ __device__ __forceinline__ uint64_t rotl_ring(uint64_t x, int k, int n) {
+  const uint64_t mask = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+  return k == 0 ? (x & mask) : (((x << k) | (x >> (n - k))) & mask);
+}
+
+// Representative of the translation orbit of (v, w) on a ring of n sites: the smallest
+// translate in (v, then w) unsigned order, and the smallest shift r reaching it.
+__device__ __forceinline__ void ts_canonical(uint64_t v, uint64_t w, int n, uint64_t& cv, uint64_t& cw, int& r) {
+  cv = v;
+  cw = w;
+  r = 0;
+  for (int k = 1; k < n; ++k) {
+    const uint64_t tv = rotl_ring(v, k, n), tw = rotl_ring(w, k, n);
+    if (tv < cv || (tv == cv && tw < cw)) {
+      cv = tv;
+      cw = tw;
+      r = k;
+    }
+  }
+}
+
+// Smallest period d of (v, w) on a ring of n sites; divmask has bit d set for each proper
+// divisor d of n (the only candidates).
+__device__ __forceinline__ int ts_period(uint64_t v, uint64_t w, int n, uint64_t divmask) {
+  while (divmask) {
+    const int d = __ffsll((long long)divmask) - 1;
+    divmask &= divmask - 1;
+    if (rotl_ring(v, d, n) == v && rotl_ring(w, d, n) == w) return d;
+  }
+  return n;
+}
+
+inline uint64_t proper_divisor_mask(int n) {
+  uint64_t m = 0;
+  for (int d = 1; d < n; ++d)
+    if (n % d == 0) m |= 1ull << d;
+  return m;
+}
+
 // Exactly-rounded FP64 operations without contraction into FMA.
 __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
 
@@ -276,14 +317,19 @@ struct MergeSource {
   int64_t n;
   Cx alpha;
   int cls = kClsComplex;  // coefficient class of rec
+  int ts = 0;             // translation symmetry: 0 none; kTsCanon each string to its orbit
+                          // representative (order code = shift); kTsExpand each string to all
+                          // ring translates (order code = shift)
 };
+constexpr int kTsCanon = 1, kTsExpand = 2;
 struct MergeSpec {
   const Rec* H = nullptr;
   int nH = 0;
   const Rec* X = nullptr;
   int64_t nX = 0;
   int rot = 0;
-  bool product = false;  // X pairs: every (h, x) with i^k h x (operator product); else the commutator's
+  bool product = false;
+  int ring = 0;  // ring length of translation-symmetric sources (their order codes are 0..ring-1)  // X pairs: every (h, x) with i^k h x (operator product); else the commutator's
                          // anticommuting pairs with 2 i^(k + rot) h x
   MergeSource src[4];
   int nsrc = 0;
@@ -298,7 +344,7 @@ void record_merge_stats(const pauli_merge_stats& st);
 
 // truncate.cu / reduce.cu
 int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor);
-int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out);
+int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring = 0);
 int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cudaStream_t s, double* re, double* im);
 int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw, int64_t nq, cudaStream_t s,
                  double* re, double* im);

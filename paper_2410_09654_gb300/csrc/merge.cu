@@ -114,6 +114,23 @@ __global__ void k_hash_hist(const Rec* __restrict__ r, int64_t n, int bits, uint
   }
 }
 
+// Histogram of the bins of a translation-symmetric source: each string's representative
+// (kTsCanon) or each of its ring translates (kTsExpand).
+__global__ void k_hash_hist_ts(const Rec* __restrict__ r, int64_t n, int bits, int mode, int ring,
+                               uint32_t* __restrict__ hist) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = r[i].v, w = r[i].w;
+    if (mode == kTsCanon) {
+      uint64_t cv, cw;
+      int sh;
+      ts_canonical(v, w, ring, cv, cw, sh);
+      atomicAdd(&hist[dev_hash(cv, cw, 0, bits)], 1u);
+    } else {
+      for (int k = 0; k < ring; ++k) atomicAdd(&hist[dev_hash(rotl_ring(v, k, ring), rotl_ring(w, k, ring), 0, bits)], 1u);
+    }
+  }
+}
+
 // bound[p] = histY[p] + sum_h histX[p ^ F(h)]: the number of (h, x) pairs routed to bin p,
 // plus the source entries of bin p.
 __global__ void k_bound(const uint32_t* __restrict__ histX, const uint32_t* __restrict__ histY,
@@ -468,10 +485,15 @@ int emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, const u
 // Emission of an extra source (code kCodeSrc + i) or of the pre operand (kCodePre): FULL, the
 // contribution record; otherwise the 8-byte reference (index << 16 | code).  Warp-strided so
 // that all 32 lanes take part in every slot reservation.
+// Emission of an extra source (code kCodeSrc + i) or of the pre operand (kCodePre): FULL, the
+// contribution record; otherwise the 8-byte reference (index << 16 | code).  Warp-strided so
+// that all 32 lanes take part in every slot reservation.  A translation-symmetric source
+// (ts, full records only) emits each string at its orbit representative with the shift as
+// order code (kTsCanon), or at each of its ring translates with code k (kTsExpand).
 template <bool FULL>
 __global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, uint32_t code, EmitScalars es,
                               unsigned long long* __restrict__ cur, uint64_t* __restrict__ entries,
-                              Contrib* __restrict__ out) {
+                              Contrib* __restrict__ out, int ts, int ring) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; i0 < n; i0 += stride) {
@@ -479,25 +501,34 @@ __global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, ui
     const bool act = i < n;
     Rec y = Rec{0, 0, 0.0, 0.0};
     if (act) y = Y[i];
-    const uint32_t p = dev_hash(y.v, y.w, 0, bits);
-    const uint64_t at = reserve_slot(cur, p, act, lane);
-    if (!act) continue;
     if constexpr (FULL) {
-      Contrib c;
-      c.v = y.v;
-      c.w = y.w;
-      c.code = code;
-      c.pad = 0;
+      double val;
       if (code == kCodePre) {
-        c.val = es.pre_u ? y.im : y.re;
+        val = es.pre_u ? y.im : y.re;
       } else {
         const uint32_t si = code - kCodeSrc;
         const double sy = es.src_uy[si] ? y.im : y.re;
-        c.val = neg_if(scaled(es.src_s[si], es.src_e[si], sy, 0), (es.src_q[si] & 2) != 0);
+        val = neg_if(scaled(es.src_s[si], es.src_e[si], sy, 0), (es.src_q[si] & 2) != 0);
       }
-      out[at] = c;
+      if (ts == kTsExpand) {
+        for (int k = 0; k < ring; ++k) {
+          const uint64_t tv = rotl_ring(y.v, k, ring), tw = rotl_ring(y.w, k, ring);
+          const uint64_t at = reserve_slot(cur, dev_hash(tv, tw, 0, bits), act, lane);
+          if (act) out[at] = Contrib{tv, tw, val, (uint32_t)k, 0};
+        }
+        continue;
+      }
+      Contrib c{y.v, y.w, val, code, 0};
+      if (ts == kTsCanon) {
+        int sh = 0;
+        ts_canonical(y.v, y.w, ring, c.v, c.w, sh);
+        c.code = (uint32_t)sh;
+      }
+      const uint64_t at = reserve_slot(cur, dev_hash(c.v, c.w, 0, bits), act, lane);
+      if (act) out[at] = c;
     } else {
-      entries[at] = ((uint64_t)i << 16) | code;
+      const uint64_t at = reserve_slot(cur, dev_hash(y.v, y.w, 0, bits), act, lane);
+      if (act) entries[at] = ((uint64_t)i << 16) | code;
     }
   }
 }
@@ -1527,7 +1558,14 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   if (sp.nH > kMaxH || sp.nsrc > 4) return PS_ERR_INVALID;
   const int64_t nX = (sp.X && sp.nH > 0) ? sp.nX : 0;
   int64_t nsrc_total = sp.npre;
-  for (int i = 0; i < sp.nsrc; ++i) nsrc_total += sp.src[i].n;
+  bool has_ts = false;
+  for (int i = 0; i < sp.nsrc; ++i) {
+    nsrc_total += sp.src[i].n * (sp.src[i].ts == kTsExpand ? sp.ring : 1);
+    has_ts |= sp.src[i].ts != 0;
+  }
+  // translation-symmetric sources: no product operand, their shifts are the first order codes
+  if (has_ts && (nX > 0 || sp.ring < 2 || sp.ring > 64)) return PS_ERR_INVALID;
+  const int ncode_h = nX > 0 ? sp.nH : (has_ts ? sp.ring : 0);
   const int64_t pairs = (int64_t)sp.nH * nX;
   const int64_t bound_total = pairs + nsrc_total;
   pauli_merge_stats st{};
@@ -1563,8 +1601,9 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   const bool structured = acc_cls != kClsComplex && out_cls != kClsComplex;
   // ranked merge when the order codes fit the slot masks, chained merge otherwise; full
   // contribution records (no gather in the merge) when single-component and they fit
-  const bool ranked = sp.nH + sp.nsrc <= kMaskBits;
+  const bool ranked = ncode_h + sp.nsrc <= kMaskBits;
   const bool full = structured && ranked && (uint64_t)bound_total * sizeof(Contrib) <= kFullBudget;
+  if (has_ts && !full) return PS_ERR_INVALID;  // representatives need full records: one component
 
   std::vector<Rec> hh_host;
   if (nX > 0) {
@@ -1652,7 +1691,10 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   }
   for (int i = 0; i < sp.nsrc; ++i)
     if (sp.src[i].n > 0) {
-      PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
+      if (sp.src[i].ts)
+        PS_LAUNCH("k_hash_hist", s, k_hash_hist_ts<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, sp.src[i].ts, sp.ring, histY.p));
+      else
+        PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
       PS_CUDA(cudaGetLastError());
     }
   if (sp.npre > 0) {
@@ -1692,17 +1734,17 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
       PS_CUDA(cudaGetLastError());
     }
   }
-  auto emit_source = [&](const Rec* y, int64_t n, uint32_t code) -> int {
+  auto emit_source = [&](const Rec* y, int64_t n, uint32_t code, int ts) -> int {
     if (full)
-      PS_LAUNCH("k_emit_source", s, k_emit_source<true><<<grid_for(n), 256, 0, s>>>(y, n, bits, code, es, cur.p, nullptr, fent.p));
+      PS_LAUNCH("k_emit_source", s, k_emit_source<true><<<grid_for(n), 256, 0, s>>>(y, n, bits, code, es, cur.p, nullptr, fent.p, ts, sp.ring));
     else
-      PS_LAUNCH("k_emit_source", s, k_emit_source<false><<<grid_for(n), 256, 0, s>>>(y, n, bits, code, es, cur.p, entries.p, nullptr));
+      PS_LAUNCH("k_emit_source", s, k_emit_source<false><<<grid_for(n), 256, 0, s>>>(y, n, bits, code, es, cur.p, entries.p, nullptr, 0, 0));
     PS_CUDA(cudaGetLastError());
     return PS_OK;
   };
   for (int i = 0; i < sp.nsrc; ++i)
-    if (sp.src[i].n > 0) PS_TRY(emit_source(sp.src[i].rec, sp.src[i].n, kCodeSrc + i));
-  if (sp.npre > 0) PS_TRY(emit_source(sp.pre, sp.npre, kCodePre));
+    if (sp.src[i].n > 0) PS_TRY(emit_source(sp.src[i].rec, sp.src[i].n, kCodeSrc + i, sp.src[i].ts));
+  if (sp.npre > 0) PS_TRY(emit_source(sp.pre, sp.npre, kCodePre, 0));
   {
     int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
     PS_LAUNCH("k_bin_counts", s, k_bin_counts<<<blocks, 256, 0, s>>>(cur.p, base.p, nbins, cnt.p));
@@ -1737,7 +1779,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   Rec* outbuf = nullptr;
   PS_TRY(dev_alloc((void**)&outbuf, (size_t)out_cap * sizeof(Rec), s));
   a.H = sp.H;
-  a.nH = sp.nH;
+  a.nH = ncode_h;
   a.X = sp.X;
   a.rot = sp.rot;
   a.twice = sp.product ? 0 : 1;

@@ -95,6 +95,11 @@ def load(build_if_missing: bool = False):
         "pauli_lanczos_step": ([P, P, P, ctypes.c_double, ctypes.POINTER(pauli_trunc_policy), F64P], ctypes.c_int),
         "pauli_trace_product": ([P, P, F64P, F64P], ctypes.c_int),
         "pauli_coefficients": ([P, P, P, I64, P, P], ctypes.c_int),
+        "pauli_ts_expand": ([P, P], ctypes.c_int),
+        "pauli_ts_canonicalize": ([P, P], ctypes.c_int),
+        "pauli_ts_commutator": ([P, P, P], ctypes.c_int),
+        "pauli_ts_norm": ([P, F64P], ctypes.c_int),
+        "pauli_ts_lanczos_step": ([P, P, P, ctypes.c_double, ctypes.POINTER(pauli_trunc_policy), F64P], ctypes.c_int),
         "pauli_norm": ([P, F64P], ctypes.c_int),
         "pauli_last_merge_stats": ([ctypes.POINTER(pauli_merge_stats)], ctypes.c_int),
         "pauli_debug_fail_alloc_after": ([I64], ctypes.c_int),
@@ -260,6 +265,42 @@ def pauli_lanczos_step(H: PauliSum, O_prev: PauliSum, O_cur: PauliSum, b_prev: f
     if st == PS_ERR_KRYLOV_EXHAUSTED:
         return 0.0
     _check(st, "pauli_lanczos_step")
+    return float(b.value)
+
+
+# translation-symmetric generators (periodic chain of n_sites sites)
+def pauli_ts_expand(G: PauliSum, out: PauliSum | None = None) -> PauliSum:
+    out = out or PauliSum(G.n_sites, 0, G.stream.value)
+    _check(load().pauli_ts_expand(G.handle, out.handle), "pauli_ts_expand")
+    return out
+
+
+def pauli_ts_canonicalize(X: PauliSum, out: PauliSum | None = None) -> PauliSum:
+    out = out or PauliSum(X.n_sites, 0, X.stream.value)
+    _check(load().pauli_ts_canonicalize(X.handle, out.handle), "pauli_ts_canonicalize")
+    return out
+
+
+def pauli_ts_commutator(H0: PauliSum, O0: PauliSum, out: PauliSum | None = None) -> PauliSum:
+    out = out or PauliSum(O0.n_sites, 0, O0.stream.value)
+    _check(load().pauli_ts_commutator(H0.handle, O0.handle, out.handle), "pauli_ts_commutator")
+    return out
+
+
+def pauli_ts_norm(O0: PauliSum) -> float:
+    r = ctypes.c_double()
+    _check(load().pauli_ts_norm(O0.handle, ctypes.byref(r)), "pauli_ts_norm")
+    return float(r.value)
+
+
+def pauli_ts_lanczos_step(H0: PauliSum, O_prev: PauliSum, O_cur: PauliSum, b_prev: float,
+                          pol: pauli_trunc_policy | None = None) -> float:
+    b = ctypes.c_double()
+    st = load().pauli_ts_lanczos_step(H0.handle, O_prev.handle, O_cur.handle, float(b_prev),
+                                      None if pol is None else ctypes.byref(pol), ctypes.byref(b))
+    if st == PS_ERR_KRYLOV_EXHAUSTED:
+        return 0.0
+    _check(st, "pauli_ts_lanczos_step")
     return float(b.value)
 
 

@@ -213,6 +213,87 @@ def test_two_point_correlators_after_rk4():
     assert got[0] != 0 and got[1] != 0
 
 
+# ----------------------------------------------------------------------------- translation symmetry
+def _with_periodic(n, arrays):
+    # add strings of short period (period 1, 2 and n/2 when n is even) to a real sum
+    v, w, re, im = arrays
+    have = set(zip(v.tolist(), w.tolist()))
+    m = (1 << n) - 1 if n < 64 else 2**64 - 1
+    extra = [(m, 0), (0x5555555555555555 & m, 0xAAAAAAAAAAAAAAAA & m)]
+    if n % 2 == 0:
+        half = (1 << (n // 2)) - 1
+        extra.append((0x3 | (0x3 << (n // 2)), 0x1 | (0x1 << (n // 2))))
+    extra = [e for e in extra if e not in have and e != (0, 0)]
+    ev = np.array([e[0] for e in extra], np.uint64)
+    ew = np.array([e[1] for e in extra], np.uint64)
+    return (np.concatenate([v, ev]), np.concatenate([w, ew]), np.concatenate([re, np.linspace(0.5, 1.5, len(extra))]),
+            np.concatenate([im, np.zeros(len(extra))]))
+
+
+@pytest.mark.parametrize("n", [8, 13, 64])
+def test_ts_canonicalize_and_expand(n):
+    Xa = _with_periodic(n, I.random_sum(700 + n, n, 3000, "real", max_support=5))
+    assert_match(ps.pauli_ts_canonicalize(dev(n, Xa)).download(), orc.ts_canonical_merge(ref(n, Xa)),
+                 what="canonicalize")
+    Ga = _with_periodic(n, I.random_sum(710 + n, n, 200, "real", max_support=4))
+    assert_match(ps.pauli_ts_expand(dev(n, Ga)).download(), orc.ts_expand(ref(n, Ga)), what="expand")
+
+
+@pytest.mark.parametrize("gen,n", [("xxz", 16), ("ising", 24), ("xxz", 64)])
+def test_ts_commutator_and_norm(gen, n):
+    H0a = (I.xxz_generator(n, 0.5) if gen == "xxz" else I.tilted_ising_generator(n)).arrays()
+    O0r = orc.ts_canonical_merge(ref(n, I.random_sum(720 + n, n, 2000, "real", max_support=6)))
+    O0a = (O0r.v, O0r.w, O0r.re, O0r.im)
+    H0 = dev(n, H0a)
+    out = ps.pauli_ts_commutator(H0, dev(n, O0a))
+    want = orc.ts_commutator(orc.ts_canonical_merge(ref(n, H0a)), O0r)
+    # H0 as given (not canonical) and canonicalised expand to the same H
+    assert_match(out.download(), want, what="ts commutator")
+    assert ps.pauli_ts_norm(out) == math.sqrt(orc.ts_norm2(want))
+
+
+def test_ts_lanczos_matches_oracle_steps():
+    n = 24
+    H0a = I.xxz_generator(n, 0.5).arrays()
+    H0, H0r = dev(n, H0a), orc.ts_canonical_merge(ref(n, H0a))
+    x1 = I.single(n, "X", 1).arrays()
+    prev, cur = ps.PauliSum(n), dev(n, x1)
+    rprev, rcur = orc.Op.empty(n), ref(n, x1)
+    b = rb = 0.0
+    pol = ps.policy(top_k=3000)
+    for step in range(10):
+        b = ps.pauli_ts_lanczos_step(H0, prev, cur, b, pol)
+        rb, nxt = orc.ts_lanczos_step(H0r, rprev, rcur, rb, top_k=3000)
+        rprev, rcur = rcur, nxt
+        assert b == rb, (step, b, rb)
+        assert_match(cur.download(), rcur, what=f"ts lanczos {step}")
+
+
+def test_ts_lanczos_b_equal_expanded_chain():
+    n = 10
+    H0 = dev(n, I.xxz_generator(n, 0.5).arrays())
+    O0 = dev(n, I.single(n, "X", 1).arrays())
+    Hf, Of = ps.pauli_ts_expand(H0), ps.pauli_ts_expand(O0)
+    # normalise both starts in their own norms (b_n are blind to the constant factor)
+    b0, bf0 = ps.pauli_ts_norm(O0), math.sqrt(orc.norm2(ref(n, Of.download())))
+    arr = lambda r: (r.v, r.w, r.re, r.im)
+    O0 = dev(n, arr(orc.divide(ref(n, O0.download()), b0)))
+    Of = dev(n, arr(orc.divide(ref(n, Of.download()), bf0)))
+    pt, ct, pf, cf = ps.PauliSum(n), O0, ps.PauliSum(n), Of
+    bt = bf = 0.0
+    for _ in range(8):
+        bt = ps.pauli_ts_lanczos_step(H0, pt, ct, bt)
+        bf = ps.pauli_lanczos_step(Hf, pf, cf, bf)
+        assert abs(bt - bf) <= 1e-12 * bf, (bt, bf)
+
+
+def test_ts_rejects_complex():
+    n = 8
+    Xa = I.random_sum(730, n, 50, "complex", max_support=3)
+    with pytest.raises(ps.PauliError):
+        ps.pauli_ts_canonicalize(dev(n, Xa))
+
+
 def test_add():
     n = 20
     A = I.random_sum(31, n, 4000, "complex", max_support=6)
