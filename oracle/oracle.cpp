@@ -473,12 +473,22 @@ std::vector<Term> ts_canonical_merge(const std::vector<Term>& X, int n) {
   return out;
 }
 
+// The translates of G as a list, not merged: T_0(G), T_1(G), ..., T_{n-1}(G) in turn.
+std::vector<Term> ts_translates(const std::vector<Term>& G, int n) {
+  std::vector<Term> out;
+  out.reserve(G.size() * (size_t)n);
+  for (int k = 0; k < n; ++k)
+    for (const Term& g : G) out.push_back({translate(g.k, k, n), g.c});
+  return out;
+}
+
 // [H, O] of translation-symmetric operators: H = sum_i T_i(H_0) is translation invariant,
-// so [H, O] = sum_j T_j([H, O_0]) and its generator is [H, O_0] with H expanded in full,
-// moved to representatives.  (Alg. 2 forms the same sums, A_0 against every translate of
-// B_0; summing per representative in the order above fixes the rounding.)
+// so [H, O] = sum_j T_j([H, O_0]) and its generator is [H, O_0] with H written out as the
+// list of H_0's translates (Alg. 1's outer loop over that list), moved to representatives.
+// Alg. 2 forms the same sums, A_0 against every translate of B_0; the loop order and the
+// representative order above fix the rounding.
 std::vector<Term> ts_commutator(const std::vector<Term>& H0, const std::vector<Term>& O0, int n) {
-  return ts_canonical_merge(commutator(ts_expand(H0, n), O0), n);
+  return ts_canonical_merge(commutator(ts_translates(H0, n), O0), n);
 }
 
 // ||O||^2 / n for O = sum_i T_i(O_0): a representative of period d stands for n/d copies of

@@ -62,11 +62,22 @@ int ts_merge(const pauli_sum* X, int mode, pauli_sum* out) {
   return merge_run(sp, out->stream, out);
 }
 
-// Generator of [H, O] (ts_commutator of the oracle): [H_full, O_0] moved to representatives.
+// H written out as the list of H0's translates T_0(H0), T_1(H0), ... (not merged).
+int ts_translates_into(const pauli_sum* H0, pauli_sum* out) {
+  const int64_t n = H0->n * H0->n_sites;
+  if (n > 0xEFFF) return PS_ERR_INVALID;
+  PS_TRY(sum_reserve(out, n, false));
+  PS_TRY(ts_translates(H0->d, H0->n, H0->n_sites, out->stream, out->d));
+  out->n = n;
+  out->cls = H0->cls;
+  return PS_OK;
+}
+
+// Generator of [H, O] (ts_commutator of the oracle): [translates of H0, O_0] moved to
+// representatives.
 int ts_commutator_into(const pauli_sum* H0, const pauli_sum* O0, pauli_sum* out) {
   Tmp Hf(O0), C(O0);
-  PS_TRY(ts_merge(H0, kTsExpand, &Hf.s));
-  if (Hf.s.n > 0xEFFF) return PS_ERR_INVALID;
+  PS_TRY(ts_translates_into(H0, &Hf.s));
   PS_TRY(commutator_into(&Hf.s, O0, 0, &C.s));
   return ts_merge(&C.s, kTsCanon, out);
 }
@@ -140,8 +151,7 @@ int pauli_ts_lanczos_step(const pauli_sum* H0, pauli_sum* O_prev, pauli_sum* O_c
     return PS_ERR_INVALID;
   *b_out = 0.0;
   Tmp Hf(O_cur), C(O_cur), A(O_cur);
-  PS_TRY(ts_merge(H0, kTsExpand, &Hf.s));
-  if (Hf.s.n > 0xEFFF) return PS_ERR_INVALID;
+  PS_TRY(ts_translates_into(H0, &Hf.s));
   PS_TRY(commutator_into(&Hf.s, O_cur, 0, &C.s));
   // A_0 = C_0 - b_prev O_prev (representatives in shift order, then the O_prev term)
   MergeSpec sp;

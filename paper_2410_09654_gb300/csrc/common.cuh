@@ -340,6 +340,7 @@ struct MergeSpec {
   int clsH = kClsComplex, clsX = kClsComplex, clsPre = kClsComplex;  // coefficient classes of the operands
 };
 int merge_run(const MergeSpec& spec, cudaStream_t s, pauli_sum* out);
+int ts_translates(const Rec* G, int64_t n, int ring, cudaStream_t s, Rec* out);
 void record_merge_stats(const pauli_merge_stats& st);
 
 // truncate.cu / reduce.cu

@@ -114,6 +114,16 @@ __global__ void k_hash_hist(const Rec* __restrict__ r, int64_t n, int bits, uint
   }
 }
 
+// out[k * n + i] = T_k(G[i]) for k < ring: the translates of G as a list, not merged.
+__global__ void k_ts_translates(const Rec* __restrict__ G, int64_t n, int ring, Rec* __restrict__ out) {
+  const int64_t total = n * ring;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(j / n);
+    const Rec g = G[j - (int64_t)k * n];
+    out[j] = Rec{rotl_ring(g.v, k, ring), rotl_ring(g.w, k, ring), g.re, g.im};
+  }
+}
+
 // Histogram of the bins of a translation-symmetric source: each string's representative
 // (kTsCanon) or each of its ring translates (kTsExpand).
 __global__ void k_hash_hist_ts(const Rec* __restrict__ r, int64_t n, int bits, int mode, int ring,
@@ -1855,3 +1865,16 @@ extern "C" int pauli_last_merge_stats(pauli_merge_stats* out) {
   *out = ps::g_stats;
   return PS_OK;
 }
+
+namespace ps {
+
+int ts_translates(const Rec* G, int64_t n, int ring, cudaStream_t s, Rec* out) {
+  if (n == 0) return PS_OK;
+  const int64_t total = n * ring;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 4 * num_sms()));
+  PS_LAUNCH("k_ts_translates", s, k_ts_translates<<<blocks, 256, 0, s>>>(G, n, ring, out));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+}  // namespace ps
