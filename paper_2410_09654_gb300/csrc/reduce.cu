@@ -34,8 +34,9 @@ __global__ void k_norm_top(const Rec* __restrict__ d, int64_t n, int* top) {
   if ((threadIdx.x & 31) == 0) atomicMax(top, m);
 }
 
-// ring > 0: a translation-symmetric generator on a ring of that many sites; a string of
-// period p stands for ring/p copies of each translate, so its |c|^2 is added ring/p times.
+// TS: a translation-symmetric generator on a ring of `ring` sites; a string of period p
+// stands for ring/p copies of each translate, so its |c|^2 is added ring/p times.
+template <bool TS>
 __global__ void __launch_bounds__(kRedThreads) k_norm_acc(const Rec* __restrict__ d, int64_t n, const int* top,
                                                           long long* gwin, long long* full, int* wlo_out, int ring,
                                                           uint64_t divmask) {
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_acc(const Rec* __restrict_
   Win acc{{0, 0, 0, 0}};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     Rec r = d[i];
-    const int m = ring > 0 ? ring / ts_period(r.v, r.w, ring, divmask) : 1;
+    const int m = TS ? ring / ts_period(r.v, r.w, ring, divmask) : 1;
     for (int j = 0; j < m; ++j) {
       add_product(acc, r.re, r.re, wlo, full);
       add_product(acc, r.im, r.im, wlo, full);
@@ -147,8 +148,12 @@ int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) 
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kRedThreads), 4 * num_sms()));
   PS_LAUNCH("k_norm_top", s, k_norm_top<<<blocks, kRedThreads, 0, s>>>(d, n, ints.p));
   PS_CUDA(cudaGetLastError());
-  PS_LAUNCH("k_norm_acc", s, k_norm_acc<<<blocks, kRedThreads, 0, s>>>(d, n, ints.p, acc.p, acc.p + kWinDigits, ints.p + 1,
-                                                                      ring, ring > 0 ? proper_divisor_mask(ring) : 0ull));
+  if (ring > 0)
+    PS_LAUNCH("k_norm_acc", s, k_norm_acc<true><<<blocks, kRedThreads, 0, s>>>(d, n, ints.p, acc.p, acc.p + kWinDigits,
+                                                                              ints.p + 1, ring, proper_divisor_mask(ring)));
+  else
+    PS_LAUNCH("k_norm_acc", s, k_norm_acc<false><<<blocks, kRedThreads, 0, s>>>(d, n, ints.p, acc.p, acc.p + kWinDigits,
+                                                                               ints.p + 1, 0, 0ull));
   PS_CUDA(cudaGetLastError());
   std::vector<long long> h(kWinDigits + kFullDigits);
   int hi[2];
