@@ -115,7 +115,8 @@ def workload_arrays():
 
 def oracle_rate(top_k: int, steps: int, warmup: int, budget_s: float = 25.0):
     """The CPU oracle on a bounded sample of the same workload: the same Lanczos recursion
-    with the cap lowered so that one step takes about a second; returns per-step timings."""
+    with the cap lowered (2^18 strings: about a second per step on one core); returns the
+    per-step (products, seconds) of the timed steps, stopping once budget_s has passed."""
     import oracle as orc
     Ha, O0a = workload_arrays()
     H = orc.Op(N_SITES, *Ha)
@@ -144,7 +145,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sample_k = 1 << 16
+    sample_k = 1 << 18
     rec = oracle_rate(sample_k, args.steps, args.warmup, budget_s=150.0)
     prods = sum(p for p, _ in rec)
     secs = sum(t for _, t in rec)
@@ -153,9 +154,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Pauli products/s", "n_gpus": args.gpus,
         "steps": len(rec), "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(rec), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload(args.top_k), "sample": f"same recursion with the cap lowered to 2^16 strings"},
+        "config": {"workload": workload(args.top_k), "sample": f"same recursion with the cap lowered to 2^18 strings"},
         "cpu_baseline": {"value": value, "unit": "Pauli products/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{len(rec)} oracle Lanczos steps at |O| = 2^16 (single-threaded C++ oracle)"},
+                         "sample": f"{len(rec)} oracle Lanczos steps at |O| = 2^18 (single-threaded C++ oracle)"},
         "e2e": {"value": value, "unit": "Pauli products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -351,10 +352,10 @@ def main():
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rec = oracle_rate(1 << 16, 4, 1, budget_s=20.0)
+        rec = oracle_rate(1 << 18, 16, 1, budget_s=15.0)
         cp = sum(p for p, _ in rec) / sum(t for _, t in rec)
         cpu = {"value": cp, "unit": "Pauli products/s", "cores": 1, "kind": "oracle",
-               "sample": f"{len(rec)} Lanczos steps of the same recursion with the cap lowered to 2^16 strings "
+               "sample": f"{len(rec)} Lanczos steps of the same recursion with the cap lowered to 2^18 strings "
                          f"(single-threaded C++ oracle)"}
 
     if rank == 0:
