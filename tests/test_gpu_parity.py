@@ -293,6 +293,41 @@ def test_ts_rejects_complex():
         ps.pauli_ts_canonicalize(dev(n, Xa))
 
 
+# ----------------------------------------------------------------------------- |H| beyond 256 (chunked H)
+def test_lanczos_lattice_8x8_chunked_h():
+    # the 8x8 Heisenberg lattice has 336 strings: H goes through the merge in chunks, the
+    # partial sums carried between them, and the Lanczos source joins the last chunk
+    n = 64
+    Ha = I.heisenberg_2d(8, 8).arrays()
+    O0 = I.single(n, "Z", 28).arrays()
+    H, Hr = dev(n, Ha), ref(n, Ha)
+    prev, cur = ps.PauliSum(n), dev(n, O0)
+    rprev, rcur = orc.Op.empty(n), ref(n, O0)
+    b = rb = 0.0
+    pol = ps.policy(top_k=6000)
+    for step in range(6):
+        b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
+        rb, nxt = orc.lanczos_step(Hr, rprev, rcur, rb, top_k=6000)
+        rprev, rcur = rcur, nxt
+        assert b == rb, (step, b, rb)
+        assert_match(cur.download(), rcur, what=f"8x8 lanczos {step}")
+
+
+def test_rk4_lattice_8x8_dissipation_trimmed():
+    # the 2D RK4 workload's shape: 8x8 Heisenberg, O = Z at (4,4), dt = 0.02, gamma = 0.1,
+    # top-k with trimmed stages
+    n = 64
+    Ha = I.heisenberg_2d(8, 8).arrays()
+    O0 = I.single(n, "Z", 28).arrays()
+    H, O = dev(n, Ha), dev(n, O0)
+    Hr, Or = ref(n, Ha), ref(n, O0)
+    pol = ps.policy(top_k=4000, gamma=0.1, trim_stages=1)
+    for step in range(4):
+        ps.pauli_rk4_step(H, O, 0.02, pol)
+        Or = orc.rk4_step(Hr, Or, 0.02, top_k=4000, gamma=0.1, trim_stages=1)
+        assert_match(O.download(), Or, what=f"8x8 rk4 {step}")
+
+
 def test_add():
     n = 20
     A = I.random_sum(31, n, 4000, "complex", max_support=6)
