@@ -661,10 +661,10 @@ struct MergeSmem {
 
 // Insert key c (or find it) in a shared-memory table of kTable slots (any layout with a
 // `key` array).  fresh = this thread claimed the empty slot.
-template <class SM>
+template <int TAB = kTable, class SM>
 __device__ __forceinline__ int table_insert(SM& s, ulonglong2 c, ulonglong2 sent, bool& fresh) {
   fresh = false;
-  uint32_t slot = table_hash(c.x, c.y) & (kTable - 1);
+  uint32_t slot = table_hash(c.x, c.y) & (TAB - 1);
   for (int probe = 0; probe < kMaxProbe; ++probe) {
     ulonglong2 k = s.key[slot];
     if (k.x == c.x && k.y == c.y) return (int)slot;
@@ -676,7 +676,7 @@ __device__ __forceinline__ int table_insert(SM& s, ulonglong2 c, ulonglong2 sent
       }
       if (old.x == c.x && old.y == c.y) return (int)slot;
     }
-    slot = (slot + 1) & (kTable - 1);
+    slot = (slot + 1) & (TAB - 1);
   }
   return -1;
 }
@@ -1151,22 +1151,35 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(MergeArgs a) {
 constexpr int kMaskWords = 8;  // 32-bit words: shared-memory OR on 32 bits is one native atomic
 constexpr int kMaskBits = 32 * kMaskWords;
 
-template <bool S>
+// Geometry of a ranked merge with W mask words: W = 8 (256 order codes) keeps 1024 slots and
+// passes of up to kCap entries; W = 16 (512 codes, for larger H) halves both so that two
+// blocks still fit an SM.
+template <int W>
+struct RankGeom {
+  static constexpr int kWords = W;
+  static constexpr int kBits = 32 * W;
+  static constexpr int kTab = W <= 8 ? kTable : kTable / 2;
+  static constexpr int kEnt = W <= 8 ? kCap : kCap / 2;
+};
+
+template <bool S, int W>
 struct RankSmem {
-  ulonglong2 key[kTable];
-  uint32_t mask[kTable][kMaskWords];  // order codes present per slot
-  uint16_t pre[kTable];
-  uint16_t ulist[kTable];
-  uint16_t run[kTable];        // start of the slot's run in seg[]
-  double ere[kCap];
-  double eim[S ? 1 : kCap];
-  uint16_t ebit[kCap];         // order bit of the entry (kNone16: pre operand)
-  uint16_t eslot[kCap];
-  double seg[kCap];            // contributions ordered by (string, order code)
-  double segim[S ? 1 : kCap];
-  double ore[kTable];
-  double oim[S ? 1 : kTable];
-  uint16_t oslot[kTable];
+  using G = RankGeom<W>;
+  ulonglong2 key[G::kTab];
+  uint32_t mask[G::kTab][G::kWords];  // order codes present per slot
+  uint16_t pre[G::kTab];
+  uint16_t ulist[G::kTab];
+  uint16_t run[G::kTab];        // start of the slot's run in seg[]
+  double ere[G::kEnt];
+  double eim[S ? 1 : G::kEnt];
+  uint16_t ebit[G::kEnt];         // order bit of the entry (kNone16: pre operand)
+  uint16_t eslot[G::kEnt];
+  double seg[G::kEnt];            // contributions ordered by (string, order code)
+  double segim[S ? 1 : G::kEnt];
+  double ore[G::kTab];
+  double oim[S ? 1 : G::kTab];
+  uint16_t oslot[G::kTab];
+  uint32_t hist[W > 8 ? G::kBits + 1 : 1];  // run-length counters when they outgrow oslot
   unsigned long long gbase[kMaxGroupBins];
   uint32_t gpre[kMaxGroupBins + 1];
   uint32_t n_e, n_u, n_out, n_seg;
@@ -1177,14 +1190,15 @@ struct RankSmem {
   uint32_t h_g;  // the block's next group, claimed while the current one is set up
 };
 
-template <bool S>
-__device__ __forceinline__ void rank_release(RankSmem<S>& s, ulonglong2 sent) {
+template <bool S, int W>
+__device__ __forceinline__ void rank_release(RankSmem<S, W>& s, ulonglong2 sent) {
+  using G = RankGeom<W>;
   const uint32_t n_u = s.n_u;
   for (uint32_t u = threadIdx.x; u < n_u; u += kMergeThreads) {
     const uint32_t slot = s.ulist[u];
     s.key[slot] = sent;
 #pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) s.mask[slot][w] = 0u;
+    for (int w = 0; w < G::kWords; ++w) s.mask[slot][w] = 0u;
     s.pre[slot] = kNone16;
   }
   __syncthreads();
@@ -1202,18 +1216,19 @@ __device__ __forceinline__ uint32_t code_bit(uint32_t code, int nH) {
   return code < kCodeSrc ? code : (uint32_t)nH + (code - kCodeSrc);
 }
 
-template <bool S, bool FULL>
+template <bool S, bool FULL, int W>
 __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
+  using G = RankGeom<W>;
   constexpr int B = FULL ? kBatchFull : kBatch;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  RankSmem<S>& s = *reinterpret_cast<RankSmem<S>*>(smem_raw);
+  RankSmem<S, W>& s = *reinterpret_cast<RankSmem<S, W>*>(smem_raw);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const uint32_t ngroups = *a.ngroups;
-  for (int i = tid; i < kTable; i += kMergeThreads) {
+  for (int i = tid; i < G::kTab; i += kMergeThreads) {
     s.key[i] = a.sent_lo;
 #pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) s.mask[i][w] = 0u;
+    for (int w = 0; w < G::kWords; ++w) s.mask[i][w] = 0u;
     s.pre[i] = kNone16;
   }
   if (tid == 0) {
@@ -1245,7 +1260,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
     const ulonglong2 sent = (lo >= a.nbins / 2) ? a.sent_hi : a.sent_lo;
     if (sent.x != s.cur_sent.x || sent.y != s.cur_sent.y) {
       __syncthreads();
-      for (int i = tid; i < kTable; i += kMergeThreads) s.key[i] = sent;
+      for (int i = tid; i < G::kTab; i += kMergeThreads) s.key[i] = sent;
       __syncthreads();
       if (tid == 0) s.cur_sent = sent;
     }
@@ -1254,7 +1269,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
     __syncthreads();
 
     int level0 = 0;
-    while (((uint64_t)kCap << level0) < E && level0 < 16) ++level0;
+    while (((uint64_t)G::kEnt << level0) < E && level0 < 16) ++level0;
     if (a.bits + level0 > kHashRows) {
       if (tid == 0) atomicOr(a.err, 2);
       continue;
@@ -1272,8 +1287,8 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       const int level = stk_level[sp];
       const uint32_t sub = stk_sub[sp];
       // run-length histogram for phase 3b, in oslot (free until phase 4 stages outputs)
-      uint32_t* s_hist = reinterpret_cast<uint32_t*>(s.oslot);  // kMaskBits + 1 counters
-      for (uint32_t i = tid; i <= (uint32_t)kMaskBits; i += kMergeThreads) s_hist[i] = 0;
+      uint32_t* s_hist = W > 8 ? s.hist : reinterpret_cast<uint32_t*>(s.oslot);  // G::kBits + 1 counters
+      for (uint32_t i = tid; i <= (uint32_t)G::kBits; i += kMergeThreads) s_hist[i] = 0;
       // ---- phase 1: rebuild entries, insert keys, mark order codes per key
       for (uint64_t j0 = 0; j0 < E; j0 += (uint64_t)B * kMergeThreads) {
         uint64_t ent[B];
@@ -1327,7 +1342,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           if (!m) continue;
           uint32_t e;
           if (level == 0) {
-            e = (uint32_t)(j0 + (uint64_t)k * kMergeThreads + tid);  // every entry kept, E <= kCap
+            e = (uint32_t)(j0 + (uint64_t)k * kMergeThreads + tid);  // every entry kept, E <= G::kEnt
           } else {
             const int leader = __ffs(m) - 1;
             uint32_t eb = 0;
@@ -1338,10 +1353,10 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           bool fresh = false;
           int slot = -1;
           if (keep) {
-            if (e >= (uint32_t)kCap) {
+            if (e >= (uint32_t)G::kEnt) {
               atomicOr(&s.flags, 1);
             } else {
-              slot = table_insert(s, key, sent, fresh);
+              slot = table_insert<G::kTab>(s, key, sent, fresh);
               if (slot < 0) atomicOr(&s.flags, 1);
             }
           }
@@ -1391,7 +1406,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         if (u < n_u) {
           slot = s.ulist[u];
 #pragma unroll
-          for (int w = 0; w < kMaskWords; ++w) c += __popc(s.mask[slot][w]);
+          for (int w = 0; w < G::kWords; ++w) c += __popc(s.mask[slot][w]);
         }
         // warp-inclusive scan of c, one shared-memory reservation per warp
         uint32_t incl = c;
@@ -1405,17 +1420,17 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         wb = __shfl_sync(0xffffffffu, wb, 31);
         if (u < n_u) {
           s.run[slot] = (uint16_t)(wb + incl - c);
-          atomicAdd(&s_hist[kMaskBits - c], 1u);  // longest runs first
+          atomicAdd(&s_hist[G::kBits - c], 1u);  // longest runs first
         }
       }
       __syncthreads();
       if (tid < 32) {  // exclusive scan of the run-length counters, 9 per lane, before phase 3
-        constexpr int kPer = (kMaskBits + 1 + 31) / 32;
+        constexpr int kPer = (G::kBits + 1 + 31) / 32;
         uint32_t v[kPer], t = 0;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
           const int i = tid * kPer + k;
-          v[k] = i <= kMaskBits ? s_hist[i] : 0u;
+          v[k] = i <= G::kBits ? s_hist[i] : 0u;
           t += v[k];
         }
         uint32_t incl = t;
@@ -1428,7 +1443,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
           const int i = tid * kPer + k;
-          if (i <= kMaskBits) s_hist[i] = run;
+          if (i <= G::kBits) s_hist[i] = run;
           run += v[k];
         }
       }
@@ -1440,7 +1455,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         const uint32_t wi = bit >> 5;
         uint32_t rank = __popc(s.mask[slot][wi] & ((1u << (bit & 31)) - 1u));
 #pragma unroll
-        for (int w = 0; w < kMaskWords; ++w)
+        for (int w = 0; w < G::kWords; ++w)
           if ((uint32_t)w < wi) rank += __popc(s.mask[slot][w]);
         const uint32_t pos = s.run[slot] + rank;
         s.seg[pos] = s.ere[e];
@@ -1456,8 +1471,8 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         const uint32_t slot = s.ulist[u];
         uint32_t n = 0;
 #pragma unroll
-        for (int w = 0; w < kMaskWords; ++w) n += __popc(s.mask[slot][w]);
-        s_order[atomicAdd(&s_hist[kMaskBits - n], 1u)] = (uint16_t)slot;
+        for (int w = 0; w < G::kWords; ++w) n += __popc(s.mask[slot][w]);
+        s_order[atomicAdd(&s_hist[G::kBits - n], 1u)] = (uint16_t)slot;
       }
       __syncthreads();
       // ---- phase 4: per string, add its run in order, apply the combination, stage.  The
@@ -1472,7 +1487,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           slot = s_order[u];
           uint32_t n = 0;
 #pragma unroll
-          for (int w = 0; w < kMaskWords; ++w) n += __popc(s.mask[slot][w]);
+          for (int w = 0; w < G::kWords; ++w) n += __popc(s.mask[slot][w]);
           const uint32_t b0 = s.run[slot];
           Cx acc{0.0, 0.0};
           if (n > 0) {
@@ -1611,7 +1626,10 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   const bool structured = acc_cls != kClsComplex && out_cls != kClsComplex;
   // ranked merge when the order codes fit the slot masks, chained merge otherwise; full
   // contribution records (no gather in the merge) when single-component and they fit
+  // ranked merge when the order codes fit the slot masks (256 codes; 512 with the wide
+  // geometry), chained merge otherwise
   const bool ranked = ncode_h + sp.nsrc <= kMaskBits;
+  const bool ranked_wide = !ranked && !has_ts && ncode_h + sp.nsrc <= RankGeom<16>::kBits;
   const bool full = structured && ranked && (uint64_t)bound_total * sizeof(Contrib) <= kFullBudget;
   if (has_ts && !full) return PS_ERR_INVALID;  // representatives need full records: one component
 
@@ -1774,7 +1792,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   PS_TRY(gstart.alloc(nbins + 1, s));
   {
     int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
-    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)kGroupQuota, flag.p));
+    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)(ranked_wide ? kGroupQuota / 2 : kGroupQuota), flag.p));
     PS_CUDA(cudaGetLastError());
     PS_TRY(scan_u32_to_u64(flag.p, fpre.p, nbins, s));
     PS_LAUNCH("k_group_scatter", s, k_group_scatter<<<blocks, 256, 0, s>>>(flag.p, fpre.p, nbins, gstart.p, misc.p + 1));
@@ -1823,9 +1841,13 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   void (*kern)(MergeArgs);
   const char* kname;
   if (ranked) {
-    sm = structured ? sizeof(RankSmem<true>) : sizeof(RankSmem<false>);
-    kern = full ? k_merge_rank<true, true> : (structured ? k_merge_rank<true, false> : k_merge_rank<false, false>);
+    sm = structured ? sizeof(RankSmem<true, 8>) : sizeof(RankSmem<false, 8>);
+    kern = full ? k_merge_rank<true, true, 8> : (structured ? k_merge_rank<true, false, 8> : k_merge_rank<false, false, 8>);
     kname = full ? "k_merge_rank_f" : (structured ? "k_merge_rank_s" : "k_merge_rank");
+  } else if (ranked_wide) {
+    sm = structured ? sizeof(RankSmem<true, 16>) : sizeof(RankSmem<false, 16>);
+    kern = structured ? k_merge_rank<true, false, 16> : k_merge_rank<false, false, 16>;
+    kname = structured ? "k_merge_rank_ws" : "k_merge_rank_w";
   } else {
     sm = structured ? sizeof(MergeSmem<true>) : sizeof(MergeSmem<false>);
     kern = structured ? k_merge<true> : k_merge<false>;
