@@ -39,6 +39,8 @@ def workload(top_k: int) -> str:
     cap = f"2^{top_k.bit_length() - 1}" if top_k & (top_k - 1) == 0 else str(top_k)
     return ("Lanczos on the open XXZ chain N=64 (H = sum XX+YY+0.5ZZ, 189 strings), O_0 = sum X_i/8, "
             f"top {cap} strings kept after each step; timed steps start once |O| has reached {cap}")
+LATTICE_WORKLOAD = ("RK4 on the open 8x8 Heisenberg lattice (336 strings), O(0) = Z at (4,4), dt=0.02, dissipation "
+                    "gamma=0.1, top 2^20 strings (cap lowered from 2^23) with trimmed stages, timed once at the cap")
 RK4_WORKLOAD = "RK4 on the open N=10 chain sum ZZ + 1.05 sum X + 0.5 sum Z, O(0)=Z_1, dt=0.05, 40 steps, weight<=6 then |c|<1e-10"
 
 
@@ -349,6 +351,31 @@ def main():
     rk4 = {"steps_per_s": sum_over_ranks(40) / t_rk, "workload": RK4_WORKLOAD, "final_size": len(Or),
            "observable_t2": obs[-1]}
 
+    # ---------------------------------------------------------------- RK4 on the 8x8 lattice
+    # the 2D workload's shape (336-string H, beyond 256 order codes) at a lowered cap
+    lat_cap = 1 << 20
+    Hl = ps.PauliSum.from_arrays(N_SITES, *I.heisenberg_2d(8, 8).arrays())
+    Ol = ps.PauliSum.from_arrays(N_SITES, *I.single(N_SITES, "Z", 28).arrays())
+    lat_pol = ps.policy(top_k=lat_cap, gamma=0.1, trim_stages=1)
+    for i in range(40):  # ramp (untimed) until the cap holds
+        ps.pauli_rk4_step(Hl, Ol, 0.02, lat_pol)
+        if len(Ol) >= lat_cap and i >= 24:
+            break
+    lat_prod = 0
+    barrier()
+    evl0 = torch.cuda.Event(enable_timing=True)
+    evl1 = torch.cuda.Event(enable_timing=True)
+    evl0.record(stream)
+    for _ in range(4):
+        lat_prod += 4 * len(Hl) * len(Ol)  # four commutators per step
+        ps.pauli_rk4_step(Hl, Ol, 0.02, lat_pol)
+    evl1.record(stream)
+    barrier()
+    t_lat = max_over_ranks(evl0.elapsed_time(evl1)) / 1e3
+    rk4_lattice = {"workload": LATTICE_WORKLOAD, "ms_per_step": 1e3 * t_lat / 4,
+                   "steps_per_s": sum_over_ranks(4) / t_lat, "products_per_s": sum_over_ranks(lat_prod) / t_lat,
+                   "size": len(Ol)}
+
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -372,6 +399,7 @@ def main():
             "contributions_per_step": contributions / args.steps,
             "b_n_timed": bs,
             "rk4": rk4,
+            "rk4_lattice": rk4_lattice,
             "roofline": roof,
             "kernels_per_step_ms": {k: round(v[1], 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1][1])},
             "profiled_region_ms_per_step": prof_ms / args.steps,
