@@ -103,14 +103,30 @@ __device__ __forceinline__ ulonglong2 cas128_shared(ulonglong2* p, ulonglong2 ex
 }
 
 // --------------------------------------------------------------------------- hashing
+// With few bins (small sums: every block would hit the same global counters) the counts go
+// to a shared-memory histogram first, flushed once per block.
+constexpr int kHistSmemBits = 13;
+
 __global__ void k_hash_hist(const Rec* __restrict__ r, int64_t n, int bits, uint32_t* __restrict__ f,
                             uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[1 << kHistSmemBits];
+  const bool local = bits <= kHistSmemBits;
+  const uint32_t nb = 1u << bits;
+  if (local) {
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+  }
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < n; i += stride) {
     uint32_t h = dev_hash(r[i].v, r[i].w, 0, bits);
     if (f) f[i] = h;
-    atomicAdd(&hist[h], 1u);
+    atomicAdd(local ? &sh[h] : &hist[h], 1u);
+  }
+  if (local) {
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+      if (sh[b]) atomicAdd(&hist[b], sh[b]);
   }
 }
 
@@ -1605,6 +1621,8 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   const uint32_t nbins = 1u << bits;
   const int nsm = num_sms();
   auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
+  // shared-memory histograms: fewer, fuller blocks (one flush of the bins per block)
+  auto hist_grid = [&](int64_t n) { return bits <= kHistSmemBits ? std::min(grid_for(n), 2 * nsm) : grid_for(n); };
 
   // ---- coefficient classes: the merge runs in single-component mode when every term of
   // every output string lies in the same component (real or imaginary)
@@ -1710,7 +1728,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_TRY(fX.alloc(nX, s));
     PS_TRY(histX.alloc(nbins, s));
     PS_CUDA(cudaMemsetAsync(histX.p, 0, nbins * sizeof(uint32_t), s));
-    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
+    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
     PS_CUDA(cudaGetLastError());
     std::vector<uint32_t> hf(sp.nH);
     for (int i = 0; i < sp.nH; ++i) hf[i] = host_hash(hh_host[i].v, hh_host[i].w, bits);
@@ -1722,11 +1740,11 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
       if (sp.src[i].ts)
         PS_LAUNCH("k_hash_hist", s, k_hash_hist_ts<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, sp.src[i].ts, sp.ring, histY.p));
       else
-        PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
+        PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
       PS_CUDA(cudaGetLastError());
     }
   if (sp.npre > 0) {
-    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<grid_for(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, nullptr, histY.p));
+    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, nullptr, histY.p));
     PS_CUDA(cudaGetLastError());
   }
   {

@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
       if (lane >= d) ti += u;
     }
     if (lane < kScanThreads / 32) warp_tot[lane] = ti - t;  // exclusive warp offsets
-    if (lane == kScanThreads / 32 - 1) tile_sums[blockIdx.x] = ti;
+    if (lane == kScanThreads / 32 - 1) {
+      tile_sums[blockIdx.x] = ti;
+      if (gridDim.x == 1) out[n] = ti;  // a single tile: its sum is the total
+    }
   }
   __syncthreads();
   uint64_t run = warp_tot[warp] + incl - sum;
@@ -54,16 +57,14 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
   }
 }
 
-__global__ void k_add_offsets(uint64_t* __restrict__ out, int64_t n, const uint64_t* __restrict__ offs) {
+// Adds each tile's offset; the last tile also writes the total, out[n].
+__global__ void k_add_offsets(uint64_t* __restrict__ out, int64_t n, const uint64_t* __restrict__ offs,
+                              const uint64_t* __restrict__ tile_sums) {
   int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
   uint64_t o = offs[blockIdx.x];
   for (int k = 0; k < kScanItems; ++k, i += kScanThreads)
     if (i < n) out[i] += o;
-}
-
-template <class T>
-__global__ void k_write_total(const T* __restrict__ in, uint64_t* __restrict__ out, int64_t n) {
-  out[n] = (n > 0) ? out[n - 1] + (uint64_t)in[n - 1] : 0;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = o + tile_sums[blockIdx.x];
 }
 
 template <class T>
@@ -81,11 +82,9 @@ int scan_impl(const T* in, uint64_t* out, int64_t n, cudaStream_t s) {
     Buf<uint64_t> offs;
     PS_TRY(offs.alloc((size_t)tiles + 1, s));
     PS_TRY(scan_impl<uint64_t>(sums.p, offs.p, tiles, s));
-    PS_LAUNCH("k_add_offsets", s, k_add_offsets<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, offs.p));
+    PS_LAUNCH("k_add_offsets", s, k_add_offsets<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, offs.p, sums.p));
     PS_CUDA(cudaGetLastError());
   }
-  PS_LAUNCH("k_write_total", s, k_write_total<T><<<1, 1, 0, s>>>(in, out, n));
-  PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 
