@@ -198,6 +198,23 @@ struct EmitScalars {
   int pre_u;
 };
 
+// Per H term: its output-hash bits and (single-component mode, hscal non-null) its real factor
+// with the exponent of |s| when s is a power of two (kNoPow2 otherwise).
+__global__ void k_h_prep(const Rec* __restrict__ H, int nh, int bits, int uH, uint32_t* __restrict__ fH,
+                         HScal* __restrict__ hscal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nh) return;
+  const Rec h = H[i];
+  fH[i] = dev_hash(h.v, h.w, 0, bits);
+  if (hscal) {
+    const double v = uH ? h.im : h.re;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const bool p2 = (b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046;
+    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, 0};
+  }
+}
+
 // y * 2^e when y is normal and the result stays normal (exact); ok = false otherwise.
 __device__ __forceinline__ double scale_pow2(double y, int e, bool& ok) {
   unsigned long long b = (unsigned long long)__double_as_longlong(y);
@@ -1651,12 +1668,6 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   const bool full = structured && ranked && (uint64_t)bound_total * sizeof(Contrib) <= kFullBudget;
   if (has_ts && !full) return PS_ERR_INVALID;  // representatives need full records: one component
 
-  std::vector<Rec> hh_host;
-  if (nX > 0) {
-    hh_host.resize(sp.nH);
-    PS_CUDA(cudaMemcpyAsync(hh_host.data(), sp.H, sp.nH * sizeof(Rec), cudaMemcpyDeviceToHost, s));
-    PS_CUDA(cudaStreamSynchronize(s));
-  }
   auto pow2_exp = [](double x) -> int {
     uint64_t b;
     memcpy(&b, &x, 8);
@@ -1670,13 +1681,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     a.uH = sp.clsH == kClsImag;
     a.uX = sp.clsX == kClsImag;
     if (nX > 0) {
-      std::vector<HScal> hs(sp.nH);
-      for (int i = 0; i < sp.nH; ++i) {
-        double v = a.uH ? hh_host[i].im : hh_host[i].re;
-        hs[i] = HScal{v, pow2_exp(v), 0};
-      }
       PS_TRY(hscal.alloc(sp.nH, s));
-      PS_CUDA(cudaMemcpyAsync(hscal.p, hs.data(), sp.nH * sizeof(HScal), cudaMemcpyHostToDevice, s));
       a.hscal = hscal.p;
     }
     for (int i = 0; i < sp.nsrc; ++i) {
@@ -1730,10 +1735,9 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_CUDA(cudaMemsetAsync(histX.p, 0, nbins * sizeof(uint32_t), s));
     PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
     PS_CUDA(cudaGetLastError());
-    std::vector<uint32_t> hf(sp.nH);
-    for (int i = 0; i < sp.nH; ++i) hf[i] = host_hash(hh_host[i].v, hh_host[i].w, bits);
     PS_TRY(fH.alloc(sp.nH, s));
-    PS_CUDA(cudaMemcpyAsync(fH.p, hf.data(), sp.nH * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    PS_LAUNCH("k_h_prep", s, k_h_prep<<<(int)ceil_div(sp.nH, 256), 256, 0, s>>>(sp.H, sp.nH, bits, a.uH, fH.p, hscal.p));
+    PS_CUDA(cudaGetLastError());
   }
   for (int i = 0; i < sp.nsrc; ++i)
     if (sp.src[i].n > 0) {

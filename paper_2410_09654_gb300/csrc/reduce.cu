@@ -143,8 +143,9 @@ int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) 
   PS_TRY(acc.alloc(kWinDigits + kFullDigits, s));
   PS_TRY(ints.alloc(2, s));
   PS_CUDA(cudaMemsetAsync(acc.p, 0, (kWinDigits + kFullDigits) * sizeof(long long), s));
-  int init[2] = {-100000, 0};
-  PS_CUDA(cudaMemcpyAsync(ints.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  // top starts at 0x80808080 (far below any exponent; a memset, not a host copy, which would
+  // synchronise the stream)
+  PS_CUDA(cudaMemsetAsync(ints.p, 0x80, 2 * sizeof(int), s));
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kRedThreads), 4 * num_sms()));
   PS_LAUNCH("k_norm_top", s, k_norm_top<<<blocks, kRedThreads, 0, s>>>(d, n, ints.p));
   PS_CUDA(cudaGetLastError());
@@ -188,10 +189,8 @@ int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cuda
   PS_TRY(ints.alloc(2, s));
   PS_CUDA(cudaMemsetAsync(tkey.p, 0xFF, slots * sizeof(ulonglong2), s));
   PS_CUDA(cudaMemsetAsync(acc.p, 0, 2 * span * sizeof(long long), s));
-  long long neg1 = -1;
-  PS_CUDA(cudaMemcpyAsync(acc.p + 2 * span, &neg1, sizeof(neg1), cudaMemcpyHostToDevice, s));
-  int init[2] = {-100000, 0};
-  PS_CUDA(cudaMemcpyAsync(ints.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  PS_CUDA(cudaMemsetAsync(acc.p + 2 * span, 0xFF, sizeof(long long), s));  // ones_idx = -1
+  PS_CUDA(cudaMemsetAsync(ints.p, 0x80, 2 * sizeof(int), s));              // top far below any exponent
   int bt = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nt, 256), 4 * num_sms()));
   PS_LAUNCH("k_tp_build", s, k_tp_build<<<bt, 256, 0, s>>>(T, nt, tkey.p, tidx.p, slots - 1, acc.p + 2 * span));
   PS_CUDA(cudaGetLastError());
@@ -253,8 +252,7 @@ int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw
   PS_CUDA(cudaMemcpyAsync(dq.p, uq.data(), nu * sizeof(Rec), cudaMemcpyHostToDevice, s));
   PS_CUDA(cudaMemsetAsync(tkey.p, 0xFF, slots * sizeof(ulonglong2), s));
   PS_CUDA(cudaMemsetAsync(out.p, 0, nu * sizeof(double2), s));
-  long long neg1 = -1;
-  PS_CUDA(cudaMemcpyAsync(ones.p, &neg1, sizeof(neg1), cudaMemcpyHostToDevice, s));
+  PS_CUDA(cudaMemsetAsync(ones.p, 0xFF, sizeof(long long), s));  // -1: no all-ones query
   const int nsm = num_sms();
   int bt = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nu, 256), 4 * nsm));
   PS_LAUNCH("k_tp_build", s, k_tp_build<<<bt, 256, 0, s>>>(dq.p, nu, tkey.p, tidx.p, slots - 1, ones.p));

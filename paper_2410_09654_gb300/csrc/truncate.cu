@@ -29,7 +29,7 @@ struct TruncArgs {
   int use_gamma;
   int use_div;
   DivConst dc;
-  const double* factor;  // exp(-(gamma*dt) w), w = 0..64
+  double factor[65];     // exp(-(gamma*dt) w), w = 0..64 (passed by value: no host copy)
   int cls;               // coefficient class of the input: components that may be non-zero
 };
 
@@ -170,6 +170,12 @@ struct SelState {
   int done;
   int pass;
 };
+
+__global__ void k_sel_init(SelState* st, unsigned long long need) {
+  SelState z{};
+  z.need = need;
+  *st = z;
+}
 
 __device__ __forceinline__ bool matches_prefix(const uint64_t k[3], const SelState& st, int pass) {
   int nbits = min(pass * kDigitBits, 192);  // high bits already fixed
@@ -365,7 +371,6 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   if (O->n == 0) return PS_OK;
   const int nsm = num_sms();
 
-  Buf<double> factor;
   Buf<unsigned long long> cnt;
   PS_TRY(cnt.alloc(2, s));
   PS_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), s));
@@ -378,13 +383,8 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   a.dc = make_divconst(divisor ? *divisor : 1.0);
   a.cls = O->cls ? O->cls : kClsComplex;
   if (use_gamma) {
-    double h[65];
-    double x = P->gamma * dt;
-    for (int wt = 0; wt <= 64; ++wt) h[wt] = std::exp(-(x * (double)wt));
-    PS_TRY(factor.alloc(65, s));
-    PS_CUDA(cudaMemcpyAsync(factor.p, h, sizeof(h), cudaMemcpyHostToDevice, s));
-    PS_CUDA(cudaStreamSynchronize(s));
-    a.factor = factor.p;
+    const double x = P->gamma * dt;
+    for (int wt = 0; wt <= 64; ++wt) a.factor[wt] = std::exp(-(x * (double)wt));
   }
   Rec* cand = nullptr;
   PS_TRY(dev_alloc((void**)&cand, (size_t)O->n * sizeof(Rec), s));
@@ -412,9 +412,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   Buf<SelState> st;
   Buf<ulonglong2> keepk;
   PS_TRY(st.alloc(1, s));
-  SelState h0{};
-  h0.need = (unsigned long long)P->top_k;
-  PS_CUDA(cudaMemcpyAsync(st.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
+  PS_LAUNCH("k_sel_init", s, k_sel_init<<<1, 1, 0, s>>>(st.p, (unsigned long long)P->top_k));
   int64_t nkeep = 0;
   if (keep && keep->n > 0) {
     std::vector<Rec> hk((size_t)keep->n);
