@@ -292,7 +292,7 @@ def main():
                      "algorithmic_bytes_per_launch": alg, "entries_per_launch": entries})
         tr = dram_traffic(kname)
         if tr is not None:
-            roof["traffic"] = tr["bytes_per_entry"] * entries
+            roof["traffic"] = tr["bytes_per_unit"] * entries
             roof["traffic_source"] = tr["source"]
     elif kname == "k_emit_products":
         # each operand string (32 B record + 4 B hash) read once, each contribution record
@@ -302,6 +302,10 @@ def main():
         roof.update({"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), kernel timed inside the step",
                      "algorithmic_bytes_per_launch": alg})
+        tr = dram_traffic(kname)
+        if tr is not None:
+            roof["traffic"] = tr["bytes_per_unit"] * prof_contrib / max(klaunch, 1)
+            roof["traffic_source"] = tr["source"]
     else:
         roof.update({"bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s"})
     if roof.get("achieved") is not None:
@@ -419,9 +423,10 @@ KERNEL_SOURCE = os.path.join(ROOT, "paper_2410_09654_gb300", "csrc", "merge.cu")
 
 
 def dram_traffic(kname: str):
-    """DRAM bytes per merge entry measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
-    over entries of the captured launch), from the committed capture summary; None when the
-    kernel source has changed since the capture (sha1 of merge.cu recorded beside it)."""
+    """DRAM bytes per unit of work measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
+    of the captured launch over its units: merge entries for the merge, contribution records
+    for the emission), from the committed capture summary; None when the kernel source has
+    changed since the capture (sha1 of merge.cu recorded beside it)."""
     import hashlib
     if not os.path.exists(TRAFFIC_FILE):
         return None
@@ -431,7 +436,7 @@ def dram_traffic(kname: str):
             continue
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") == kname and f.get("merge_cu_sha1") == sha:
-            return {"bytes_per_entry": float(f["dram_bytes_per_entry"]), "source": f.get("capture", "")}
+            return {"bytes_per_unit": float(f["dram_bytes_per_unit"]), "source": f.get("capture", "")}
     return None
 
 if __name__ == "__main__":
