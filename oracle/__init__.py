@@ -12,7 +12,8 @@ holds an independent dense-matrix checker for tiny systems.
 
 Every function cites the passage of the paper it follows; see ``oracle.cpp``
 for the arithmetic.  Parity status: all entry points are pinned by the
-``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
+``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``; ``mlp.py`` (the learned
+truncation scorer and truncation by an arbitrary score) by ``tests/test_mlp_oracle.py``.
 """
 from __future__ import annotations
 
