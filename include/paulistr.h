@@ -237,6 +237,71 @@ typedef struct {
 } pauli_merge_stats;
 int pauli_last_merge_stats(pauli_merge_stats* out);
 
+/* ------------------------------------------------------------------ learned truncation
+ * The paper's conclusion proposes predicting the importance of strings with machine
+ * learning instead of ranking them by |c| alone.  This library's scorer is a small
+ * network on string features, trained and run with BF16 tensor-core kernels (FP32
+ * accumulation, FP32 master weights, Adam):
+ *   features x (80): x0 = wt/N (wt = popcount(v|w)); x1 = extent/N (last - first + 1 over
+ *     the non-identity sites; 0 for the identity); x2 = ln(max(|c|, 1e-300))/16; for each
+ *     of 16 site bins (site j, 0-based, in bin floor(16 j / N)) the fractions of the bin's
+ *     sites holding I, X, Y, Z at x[3 + 4b + 0..3] (zeros for an empty bin); x[67..79] = 0;
+ *   z = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 (W1 128x80, W2 128x128, rows = outputs);
+ *   truncation score = ln|c| - gamma dt wt + z (ln|c| after the dissipation factor), so a
+ *     network that outputs 0 ranks exactly as |c| does.
+ * Flat FP32 parameter layout (pauli_mlp_param_count() = 27009 floats): W1 (row-major),
+ * b1 (128), W2 (row-major), b2 (128), w3 (128), b3 (1).
+ * All calls are ordered on the model's stream; sums on another stream are synchronised
+ * first.  Record order ("storage order") is that of pauli_sum_download_device. */
+typedef struct pauli_mlp pauli_mlp; /* opaque: device-resident parameters and Adam state */
+
+int64_t pauli_mlp_param_count(void);
+/* New model on n_sites sites (features depend on N): weights drawn from N(0, 2/fan_in)
+ * (w3: N(0, 1/128)) with a splitmix64 stream seeded by seed, biases 0, Adam state 0. */
+int pauli_mlp_create(int n_sites, uint64_t seed, void* cuda_stream, pauli_mlp** out);
+int pauli_mlp_destroy(pauli_mlp* m);
+/* FP32 parameters to / from HOST arrays of exactly pauli_mlp_param_count() floats
+ * (PS_ERR_INVALID otherwise); set_params also clears the Adam state. */
+int pauli_mlp_get_params(const pauli_mlp* m, float* params, int64_t n);
+int pauli_mlp_set_params(pauli_mlp* m, const float* params, int64_t n);
+/* Per string of O in storage order, into DEVICE arrays (caller-owned):
+ *   features: x[80 * i + k] as BF16 bit patterns (round to nearest even);
+ *   logits:   z[i] (FP32);
+ *   scores:   score[i] = ln|c_i| - gamma_dt wt_i + z_i (FP64; -inf for c = 0).
+ * O must have the model's n_sites.  Each call synchronises the model's stream. */
+int pauli_mlp_features(const pauli_mlp* m, const pauli_sum* O, uint16_t* x);
+int pauli_mlp_logits(const pauli_mlp* m, const pauli_sum* O, float* z);
+int pauli_mlp_scores(const pauli_mlp* m, const pauli_sum* O, double gamma_dt, double* score);
+/* Gradient (HOST array of pauli_mlp_param_count() floats) and *loss (may be NULL) of the
+ * mean binary cross-entropy of z over records [i0, i0 + nb) of X against DEVICE labels
+ * (labels[i] in [0, 1], indexed like X's storage order).  The parameters are unchanged. */
+int pauli_mlp_gradient(pauli_mlp* m, const pauli_sum* X, const float* labels, int64_t i0, int64_t nb, float* grad,
+                       double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on that batch's
+ * gradient, nb >= 1.  *loss (if loss is not NULL; this synchronises) receives the batch
+ * loss before the update. */
+int pauli_mlp_train_step(pauli_mlp* m, const pauli_sum* X, const float* labels, int64_t i0, int64_t nb, float lr,
+                         double* loss);
+/* labels[i] = 1 if the i-th string of X (storage order) is present in target, else 0
+ * (DEVICE array of X's size).  The training label of a candidate string is whether a
+ * run at a larger cap keeps it. */
+int pauli_mlp_labels(const pauli_sum* X, const pauli_sum* target, float* labels);
+
+/* pauli_truncate with the top-k ranked by score[i] (DEVICE array, one FP64 value per
+ * string of O in storage order, read during the call) instead of |c|^2: higher scores
+ * are kept first, exact ties keep the smaller key (v, then w), a NaN score ranks below
+ * every number, -0 equals +0.  Dissipation, the weight filter, exact-zero removal, the
+ * cutoff (on |c|) and the keep set are as in pauli_truncate. */
+int pauli_truncate_scored(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt,
+                          const double* score);
+
+/* pauli_rk4_step whose final truncation ranks the top_k by the learned score of model
+ * (model NULL: by |c|, as pauli_rk4_step).  Stage trims (trim_stages) stay by |c|.
+ * cand_out (may be NULL; distinct from H and O) receives the step's result before that
+ * final truncation: the candidates the truncation chose from. */
+int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
+                       const pauli_sum* keep, const pauli_mlp* model, pauli_sum* cand_out);
+
 /* ------------------------------------------------------------------ profiling */
 /* Enable (1) or disable (0) per-kernel timing: every kernel launch of the library is
  * bracketed by CUDA events recorded on its launching stream.  Enabling clears the totals. */

@@ -137,7 +137,8 @@ def scores(p: np.ndarray, v, w, re, im, n_sites: int, gamma_dt: float = 0.0) -> 
     z, _ = forward(p, X)
     wt = np.array([bin(int(a) | int(b)).count("1") for a, b in zip(v, w)], np.float64)
     a2 = np.asarray(re, np.float64) ** 2 + np.asarray(im, np.float64) ** 2
-    return 0.5 * np.log(np.maximum(a2, LOG_FLOOR ** 2)) - gamma_dt * wt + z
+    with np.errstate(divide="ignore"):
+        return 0.5 * np.log(a2) - gamma_dt * wt + z  # -inf for c = 0
 
 
 def truncate_scored(v, w, re, im, score, max_weight: int = -1, cutoff: float = 0.0, top_k: int = 0,

@@ -196,10 +196,21 @@ int pauli_truncate(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_s
   return truncate_run(O, policy, keep, dt, nullptr);
 }
 
-int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
-                   const pauli_sum* keep) {
-  if (!H || !O || H == O || !same_sites(H, O) || !same_sites(O, keep)) return PS_ERR_INVALID;
-  if (!policy_valid(policy) || !std::isfinite(dt) || H->n > 0xEFFF) return PS_ERR_INVALID;
+int pauli_truncate_scored(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt,
+                          const double* score) {
+  if (!O || !same_sites(O, keep) || !policy_valid(policy) || !std::isfinite(dt)) return PS_ERR_INVALID;
+  if (O->n > 0 && !score) return PS_ERR_INVALID;
+  return truncate_run(O, policy, keep, dt, nullptr, score);
+}
+
+}  // extern "C"
+
+namespace {
+
+// One RK4 step; the final truncation ranks by the learned score when a model is given;
+// cand (optional) receives the step's result before that truncation.
+int rk4_impl(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy, const pauli_sum* keep,
+             const pauli_mlp* model, pauli_sum* cand) {
   const double h2 = dt / 2.0, h6 = dt / 6.0;
   const bool trim = policy && policy->trim_stages && policy->top_k > 0;
   pauli_trunc_policy stage{-1, 0.0, policy ? policy->top_k : 0, 0.0, 0};
@@ -236,9 +247,46 @@ int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trun
   sp.has_post = true;
   sp.post = Cx{h6, 0.0};
   PS_TRY(merge_run(sp, O->stream, &X.s));
-  PS_TRY(truncate_run(&X.s, policy, keep, dt, nullptr));
+  if (cand) {
+    PS_TRY(sum_reserve(cand, X.s.n, false));
+    if (X.s.n > 0)
+      PS_CUDA(cudaMemcpyAsync(cand->d, X.s.d, (size_t)X.s.n * sizeof(Rec), cudaMemcpyDeviceToDevice, O->stream));
+    cand->n = X.s.n;
+    cand->cls = X.s.cls;
+    if (cand->stream != O->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
+  }
+  if (model && policy && policy->top_k > 0 && X.s.n > policy->top_k) {
+    Buf<double> score;
+    PS_TRY(score.alloc((size_t)X.s.n, O->stream));
+    const double gdt = policy->gamma != 0.0 ? policy->gamma * dt : 0.0;
+    PS_TRY(mlp_scores(model, X.s.d, X.s.n, gdt, O->stream, score.p));
+    PS_TRY(truncate_run(&X.s, policy, keep, dt, nullptr, score.p));
+  } else {
+    PS_TRY(truncate_run(&X.s, policy, keep, dt, nullptr));
+  }
   swap_contents(O, &X.s);
   return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
+                   const pauli_sum* keep) {
+  if (!H || !O || H == O || !same_sites(H, O) || !same_sites(O, keep)) return PS_ERR_INVALID;
+  if (!policy_valid(policy) || !std::isfinite(dt) || H->n > 0xEFFF) return PS_ERR_INVALID;
+  return rk4_impl(H, O, dt, policy, keep, nullptr, nullptr);
+}
+
+int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
+                       const pauli_sum* keep, const pauli_mlp* model, pauli_sum* cand_out) {
+  if (!H || !O || H == O || !same_sites(H, O) || !same_sites(O, keep) || !same_sites(O, cand_out)) return PS_ERR_INVALID;
+  if (cand_out == O || cand_out == H) return PS_ERR_INVALID;
+  if (!policy_valid(policy) || !std::isfinite(dt) || H->n > 0xEFFF) return PS_ERR_INVALID;
+  if (model && mlp_n_sites(model) != O->n_sites) return PS_ERR_INVALID;
+  if (model && mlp_stream(model) != O->stream) PS_CUDA(cudaStreamSynchronize(mlp_stream(model)));
+  return rk4_impl(H, O, dt, policy, keep, model, cand_out);
 }
 
 int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev,

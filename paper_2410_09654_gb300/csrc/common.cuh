@@ -344,10 +344,19 @@ int ts_translates(const Rec* G, int64_t n, int ring, cudaStream_t s, Rec* out);
 void record_merge_stats(const pauli_merge_stats& st);
 
 // truncate.cu / reduce.cu
-int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor);
+// score (optional): a ranking value per record of O (storage order) that replaces |c|^2 in
+// the top-k select (higher kept first, exact ties to the smaller key, NaN lowest).
+int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor,
+                 const double* score = nullptr);
 int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring = 0);
 int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cudaStream_t s, double* re, double* im);
 int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw, int64_t nq, cudaStream_t s,
                  double* re, double* im);
+int membership(const Rec* X, int64_t nx, const Rec* T, int64_t nt, cudaStream_t s, float* label);
+
+// mlp.cu: learned truncation score ln|c| - gamma_dt wt + z of every record (storage order)
+int mlp_scores(const pauli_mlp* m, const Rec* d, int64_t n, double gamma_dt, cudaStream_t s, double* score);
+int mlp_n_sites(const pauli_mlp* m);
+cudaStream_t mlp_stream(const pauli_mlp* m);
 
 }  // namespace ps

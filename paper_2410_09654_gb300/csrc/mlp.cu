@@ -1,0 +1,799 @@
+// Learned truncation scorer: a two-layer ReLU network on string features, trained and
+// evaluated with hand-written BF16 tensor-core kernels (FP32 accumulation), with an FP32
+// Adam update.  The paper's conclusion proposes predicting the importance of strings with
+// machine learning rather than ranking them by |c| alone; the model is this library's:
+//
+//   features (80): x0 = wt/N (wt = popcount(v|w)), x1 = extent/N (last - first + 1 over the
+//     non-identity sites, 0 for the identity), x2 = ln(max(|c|, 1e-300))/16, and for each
+//     of 16 site bins (site j in bin floor(16 j / N)) the fractions of its sites holding
+//     I, X, Y, Z (x[3 + 4b + t]); x[67..79] = 0.
+//   z = w3 . relu(W2 relu(W1 x + b1) + b2) + b3, W1 128x80, W2 128x128 (rows = outputs).
+//   loss: mean binary cross-entropy on z; update: bias-corrected Adam.
+//   truncation score: ln|c| - gamma dt wt + z (ln|c| after the dissipation factor).
+//
+// The products run on mma.sync m16n8k16 (bf16 in, fp32 accumulate).  Each warp owns 16
+// rows; the accumulator of one layer is repacked in registers as the A operand of the next
+// (the m16n8 C layout of two adjacent column tiles is the m16k16 A layout).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "exact_sum.cuh"
+
+namespace ps {
+namespace {
+
+constexpr int kF = 80;
+constexpr int kHid = 128;
+constexpr int oW1 = 0, oB1 = kHid * kF, oW2 = oB1 + kHid, oB2 = oW2 + kHid * kHid, oW3 = oB2 + kHid,
+              oB3 = oW3 + kHid;
+constexpr int kParams = oB3 + 1;  // 27009
+constexpr int kSF = kF + 8;       // shared row stride (bf16) of K = 80 rows: 44 words, conflict-free fragments
+constexpr int kSH = kHid + 8;     // of K = 128 rows: 68 words
+constexpr int kTrainRows = 64;    // rows per training tile (4 warps x 16)
+constexpr int kSR = kTrainRows + 8;  // stride of the transposed (row-contiguous) tiles: 36 words
+constexpr int kFwdRows = 128;     // rows per inference tile (8 warps x 16)
+
+struct FeatConst {
+  uint64_t bin_mask[16];
+  int bin_size[16];
+  int n_sites;
+};
+
+FeatConst make_featconst(int n) {
+  FeatConst f{};
+  f.n_sites = n;
+  for (int j = 0; j < n; ++j) {
+    const int b = (16 * j) / n;
+    f.bin_mask[b] |= 1ull << j;
+    f.bin_size[b] += 1;
+  }
+  return f;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16);
+}
+
+__device__ __forceinline__ bool bf16_pos(uint32_t pair, int half) {
+  const uint32_t h = (pair >> (16 * half)) & 0xFFFFu;
+  return h != 0 && (h & 0x8000u) == 0;
+}
+
+// Feature k of a string (0 <= k < 80).
+__device__ __forceinline__ float feature(const Rec& r, const FeatConst& fc, int k) {
+  const uint64_t s = r.v | r.w;
+  const float n = (float)fc.n_sites;
+  if (k == 0) return __fdiv_rn((float)__popcll(s), n);
+  if (k == 1) {
+    const int ext = s ? (63 - __clzll((long long)s)) - (__ffsll((long long)s) - 1) + 1 : 0;
+    return __fdiv_rn((float)ext, n);
+  }
+  if (k == 2) return (float)(log(fmax(hypot(r.re, r.im), 1e-300)) / 16.0);
+  if (k >= 67) return 0.0f;
+  const int b = (k - 3) >> 2, t = (k - 3) & 3;
+  const int sz = fc.bin_size[b];
+  if (sz == 0) return 0.0f;
+  const uint64_t m = fc.bin_mask[b];
+  int c;
+  if (t == 1) c = __popcll(r.w & ~r.v & m);
+  else if (t == 2) c = __popcll(r.v & r.w & m);
+  else if (t == 3) c = __popcll(r.v & ~r.w & m);
+  else c = sz - __popcll(s & m);
+  return __fdiv_rn((float)c, (float)sz);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// A fragment (16 x 16) of a row-major bf16 tile with row stride S.
+template <int S>
+__device__ __forceinline__ void load_a(const uint16_t* base, int r0, int k0, int g, int t, uint32_t (&a)[4]) {
+  a[0] = ld32(base + (r0 + g) * S + k0 + 2 * t);
+  a[1] = ld32(base + (r0 + g + 8) * S + k0 + 2 * t);
+  a[2] = ld32(base + (r0 + g) * S + k0 + 2 * t + 8);
+  a[3] = ld32(base + (r0 + g + 8) * S + k0 + 2 * t + 8);
+}
+
+// B fragment (16 x 8) from an [n][k] tile (k contiguous) with row stride S.
+template <int S>
+__device__ __forceinline__ void load_b(const uint16_t* base, int n0, int k0, int g, int t, uint32_t& b0,
+                                       uint32_t& b1) {
+  b0 = ld32(base + (n0 + g) * S + k0 + 2 * t);
+  b1 = ld32(base + (n0 + g) * S + k0 + 2 * t + 8);
+}
+
+// Copy a dense [rows][cols] bf16 matrix into shared memory with row stride S.
+template <int S>
+__device__ __forceinline__ void stage(uint16_t* dst, const uint16_t* __restrict__ src, int rows, int cols) {
+  const int words = cols / 2;
+  for (int i = threadIdx.x; i < rows * words; i += blockDim.x) {
+    const int r = i / words, c = i - r * words;
+    reinterpret_cast<uint32_t*>(dst + r * S)[c] = reinterpret_cast<const uint32_t*>(src + r * cols)[c];
+  }
+}
+
+// Layer 1 and 2 of one warp's 16 rows: returns relu(layer 2) in acc2 (fp32, C layout) and
+// relu(layer 1) packed as bf16 A fragments in h1.
+__device__ __forceinline__ void forward_rows(const uint16_t* xs, int r0, const uint16_t* W1s, const uint16_t* W2s,
+                                             const float* fb1, const float* fb2, int g, int t, uint32_t (&h1)[8][4],
+                                             float (&acc2)[16][4]) {
+  float acc[16][4];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+  for (int ks = 0; ks < kF / 16; ++ks) {
+    uint32_t a[4];
+    load_a<kSF>(xs, r0, 16 * ks, g, t, a);
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+      uint32_t b0, b1;
+      load_b<kSF>(W1s, 8 * nt, 16 * ks, g, t, b0, b1);
+      mma_bf16(acc[nt], a, b0, b1);
+    }
+  }
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int nt = 2 * ks + h, c = 8 * nt + 2 * t;
+      const float e0 = fmaxf(acc[nt][0] + fb1[c], 0.0f), e1 = fmaxf(acc[nt][1] + fb1[c + 1], 0.0f);
+      const float e2 = fmaxf(acc[nt][2] + fb1[c], 0.0f), e3 = fmaxf(acc[nt][3] + fb1[c + 1], 0.0f);
+      h1[ks][2 * h] = pack_bf16(e0, e1);
+      h1[ks][2 * h + 1] = pack_bf16(e2, e3);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.0f;
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks) {
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+      uint32_t b0, b1;
+      load_b<kSH>(W2s, 8 * nt, 16 * ks, g, t, b0, b1);
+      mma_bf16(acc2[nt], h1[ks], b0, b1);
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    const int c = 8 * nt + 2 * t;
+    acc2[nt][0] = fmaxf(acc2[nt][0] + fb2[c], 0.0f);
+    acc2[nt][1] = fmaxf(acc2[nt][1] + fb2[c + 1], 0.0f);
+    acc2[nt][2] = fmaxf(acc2[nt][2] + fb2[c], 0.0f);
+    acc2[nt][3] = fmaxf(acc2[nt][3] + fb2[c + 1], 0.0f);
+  }
+}
+
+// z for rows g and g+8 (every lane of the quad gets both).
+__device__ __forceinline__ void output_rows(const float (&h2)[16][4], const float* fw3, float b3, int t, float& zg,
+                                            float& zg8) {
+  float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    const int c = 8 * nt + 2 * t;
+    s0 += h2[nt][0] * fw3[c] + h2[nt][1] * fw3[c + 1];
+    s1 += h2[nt][2] * fw3[c] + h2[nt][3] * fw3[c + 1];
+  }
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+  zg = s0 + b3;
+  zg8 = s1 + b3;
+}
+
+struct MlpDev {
+  const uint16_t* w1b;   // [128][80] bf16
+  const uint16_t* w2b;   // [128][128] bf16 (rows = outputs)
+  const uint16_t* w2tb;  // [128][128] bf16, transposed
+  const float* p;        // FP32 master parameters
+};
+
+// ---------------------------------------------------------------- inference
+// Per string: optional features (bf16 bits, [n][80]), logit z, and the truncation score
+// ln|c| - gamma_dt wt + z (FP64).
+__global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, int64_t n, FeatConst fc, MlpDev m,
+                                                 double gamma_dt, uint16_t* __restrict__ x_out,
+                                                 float* __restrict__ z_out, double* __restrict__ score_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t* W1s = reinterpret_cast<uint16_t*>(smem);
+  uint16_t* W2s = W1s + kHid * kSF;
+  uint16_t* xs = W2s + kHid * kSH;
+  float* fb1 = reinterpret_cast<float*>(xs + kFwdRows * kSF);
+  float* fb2 = fb1 + kHid;
+  float* fw3 = fb2 + kHid;
+  stage<kSF>(W1s, m.w1b, kHid, kF);
+  stage<kSH>(W2s, m.w2b, kHid, kHid);
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    fb1[i] = m.p[oB1 + i];
+    fb2[i] = m.p[oB2 + i];
+    fw3[i] = m.p[oW3 + i];
+  }
+  const float b3 = m.p[oB3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int64_t tiles = ceil_div_dev(n, kFwdRows);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t base = tile * kFwdRows;
+    __syncthreads();  // staging done / previous tile's xs consumed
+    // two threads per row: even threads features 0..39, odd threads 40..79
+    {
+      const int row = threadIdx.x >> 1, half = threadIdx.x & 1;
+      const int64_t i = base + row;
+      Rec r{0, 0, 0.0, 0.0};
+      const bool valid = i < n;
+      if (valid) r = d[i];
+      for (int k = 40 * half; k < 40 * half + 40; k += 2) {
+        const float f0 = valid ? feature(r, fc, k) : 0.0f, f1 = valid ? feature(r, fc, k + 1) : 0.0f;
+        const uint32_t pr = pack_bf16(f0, f1);
+        *reinterpret_cast<uint32_t*>(xs + row * kSF + k) = pr;
+        if (x_out && valid) *reinterpret_cast<uint32_t*>(x_out + i * kF + k) = pr;
+      }
+    }
+    __syncthreads();
+    uint32_t h1[8][4];
+    float h2[16][4];
+    forward_rows(xs, 16 * warp, W1s, W2s, fb1, fb2, g, t, h1, h2);
+    float zg, zg8;
+    output_rows(h2, fw3, b3, t, zg, zg8);
+    if (t == 0) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t i = base + 16 * warp + g + 8 * e;
+        if (i >= n) continue;
+        const float z = e ? zg8 : zg;
+        if (z_out) z_out[i] = z;
+        if (score_out) {
+          const Rec r = d[i];
+          const double q = __dadd_rn(__dmul_rn(r.re, r.re), __dmul_rn(r.im, r.im));
+          const double wt = (double)__popcll(r.v | r.w);
+          score_out[i] = __dadd_rn(__dsub_rn(__dmul_rn(0.5, log(q)), __dmul_rn(gamma_dt, wt)), (double)z);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- training
+// Fused forward + backward over tiles of 64 rows [i0, i0 + nb) of X with labels y:
+// gradients of the mean BCE are added (fp32 atomics) into grad; the loss sum (already
+// divided by nb) into *loss.
+__global__ void __launch_bounds__(128, 1) k_mlp_train(const Rec* __restrict__ d, int64_t nb, FeatConst fc, MlpDev m,
+                                                      const float* __restrict__ y, float inv_n,
+                                                      float* __restrict__ grad, double* __restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t* W1s = reinterpret_cast<uint16_t*>(smem);
+  uint16_t* W2s = W1s + kHid * kSF;
+  uint16_t* W2Ts = W2s + kHid * kSH;
+  uint16_t* xs = W2Ts + kHid * kSH;
+  uint16_t* xT = xs + kTrainRows * kSF;
+  uint16_t* h1T = xT + kF * kSR;
+  uint16_t* dh2T = h1T + kHid * kSR;
+  uint16_t* dh1T = dh2T + kHid * kSR;
+  float* fb1 = reinterpret_cast<float*>(dh1T + kHid * kSR);
+  float* fb2 = fb1 + kHid;
+  float* fw3 = fb2 + kHid;
+  float* sdb1 = fw3 + kHid;
+  float* sdb2 = sdb1 + kHid;
+  float* sdw3 = sdb2 + kHid;
+  float* sdb3 = sdw3 + kHid;  // [1]
+  stage<kSF>(W1s, m.w1b, kHid, kF);
+  stage<kSH>(W2s, m.w2b, kHid, kHid);
+  stage<kSH>(W2Ts, m.w2tb, kHid, kHid);
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    fb1[i] = m.p[oB1 + i];
+    fb2[i] = m.p[oB2 + i];
+    fw3[i] = m.p[oW3 + i];
+    sdb1[i] = sdb2[i] = sdw3[i] = 0.0f;
+  }
+  if (threadIdx.x == 0) sdb3[0] = 0.0f;
+  const float b3 = m.p[oB3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * warp;
+  double wloss = 0.0;
+  const int64_t tiles = ceil_div_dev(nb, kTrainRows);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t base = tile * kTrainRows;
+    __syncthreads();
+    {  // features: two threads per row
+      const int row = threadIdx.x >> 1, half = threadIdx.x & 1;
+      const int64_t i = base + row;
+      Rec r{0, 0, 0.0, 0.0};
+      const bool valid = i < nb;
+      if (valid) r = d[i];
+      for (int k = 40 * half; k < 40 * half + 40; k += 2) {
+        const float f0 = valid ? feature(r, fc, k) : 0.0f, f1 = valid ? feature(r, fc, k + 1) : 0.0f;
+        const uint32_t pr = pack_bf16(f0, f1);
+        *reinterpret_cast<uint32_t*>(xs + row * kSF + k) = pr;
+        xT[k * kSR + row] = (uint16_t)(pr & 0xFFFFu);
+        xT[(k + 1) * kSR + row] = (uint16_t)(pr >> 16);
+      }
+    }
+    __syncthreads();
+    uint32_t h1[8][4];
+    float h2[16][4];
+    forward_rows(xs, r0, W1s, W2s, fb1, fb2, g, t, h1, h2);
+    // h1 transposed for the weight gradient of layer 2
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 16 * ks + 8 * h + 2 * t;
+        const uint32_t lo = h1[ks][2 * h], hi = h1[ks][2 * h + 1];
+        h1T[c * kSR + r0 + g] = (uint16_t)(lo & 0xFFFFu);
+        h1T[(c + 1) * kSR + r0 + g] = (uint16_t)(lo >> 16);
+        h1T[c * kSR + r0 + g + 8] = (uint16_t)(hi & 0xFFFFu);
+        h1T[(c + 1) * kSR + r0 + g + 8] = (uint16_t)(hi >> 16);
+      }
+    float zg, zg8;
+    output_rows(h2, fw3, b3, t, zg, zg8);
+    const int64_t ig = base + r0 + g, ig8 = ig + 8;
+    const bool vg = ig < nb, vg8 = ig8 < nb;
+    const float yg = vg ? y[ig] : 0.0f, yg8 = vg8 ? y[ig8] : 0.0f;
+    const float dzg = vg ? (1.0f / (1.0f + expf(-zg)) - yg) * inv_n : 0.0f;
+    const float dzg8 = vg8 ? (1.0f / (1.0f + expf(-zg8)) - yg8) * inv_n : 0.0f;
+    if (t == 0) {
+      if (vg) wloss += (double)(fmaxf(zg, 0.0f) - zg * yg + log1pf(expf(-fabsf(zg))));
+      if (vg8) wloss += (double)(fmaxf(zg8, 0.0f) - zg8 * yg8 + log1pf(expf(-fabsf(zg8))));
+    }
+    // output layer: dW3, db3; dh2 = dz w3 (h2 > 0); db2
+    float pw[16][2], pb[16][2];
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+      const int c = 8 * nt + 2 * t;
+      pw[nt][0] = dzg * h2[nt][0] + dzg8 * h2[nt][2];
+      pw[nt][1] = dzg * h2[nt][1] + dzg8 * h2[nt][3];
+      h2[nt][0] = h2[nt][0] > 0.0f ? dzg * fw3[c] : 0.0f;
+      h2[nt][1] = h2[nt][1] > 0.0f ? dzg * fw3[c + 1] : 0.0f;
+      h2[nt][2] = h2[nt][2] > 0.0f ? dzg8 * fw3[c] : 0.0f;
+      h2[nt][3] = h2[nt][3] > 0.0f ? dzg8 * fw3[c + 1] : 0.0f;
+      pb[nt][0] = h2[nt][0] + h2[nt][2];
+      pb[nt][1] = h2[nt][1] + h2[nt][3];
+    }
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int sh = 4; sh < 32; sh <<= 1) {
+          pw[nt][e] += __shfl_xor_sync(0xffffffffu, pw[nt][e], sh);
+          pb[nt][e] += __shfl_xor_sync(0xffffffffu, pb[nt][e], sh);
+        }
+    if (g == 0) {
+#pragma unroll
+      for (int nt = 0; nt < 16; ++nt) {
+        const int c = 8 * nt + 2 * t;
+        atomicAdd(&sdw3[c], pw[nt][0]);
+        atomicAdd(&sdw3[c + 1], pw[nt][1]);
+        atomicAdd(&sdb2[c], pb[nt][0]);
+        atomicAdd(&sdb2[c + 1], pb[nt][1]);
+      }
+    }
+    {
+      float s = (t == 0) ? dzg + dzg8 : 0.0f;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
+      if (lane == 0) atomicAdd(sdb3, s);
+    }
+    // dh2 (bf16): transposed copy for dW2 and A fragments for dh1
+    uint32_t da[8][4];
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int nt = 2 * ks + h, c = 8 * nt + 2 * t;
+        da[ks][2 * h] = pack_bf16(h2[nt][0], h2[nt][1]);
+        da[ks][2 * h + 1] = pack_bf16(h2[nt][2], h2[nt][3]);
+        dh2T[c * kSR + r0 + g] = (uint16_t)(da[ks][2 * h] & 0xFFFFu);
+        dh2T[(c + 1) * kSR + r0 + g] = (uint16_t)(da[ks][2 * h] >> 16);
+        dh2T[c * kSR + r0 + g + 8] = (uint16_t)(da[ks][2 * h + 1] & 0xFFFFu);
+        dh2T[(c + 1) * kSR + r0 + g + 8] = (uint16_t)(da[ks][2 * h + 1] >> 16);
+      }
+    // dh1 = (dh2 W2) * (h1 > 0)
+    float acc[16][4];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+      for (int nt = 0; nt < 16; ++nt) {
+        uint32_t b0, b1;
+        load_b<kSH>(W2Ts, 8 * nt, 16 * ks, g, t, b0, b1);
+        mma_bf16(acc[nt], da[ks], b0, b1);
+      }
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+      const int ks = nt >> 1, h = nt & 1, c = 8 * nt + 2 * t;
+      const uint32_t lo = h1[ks][2 * h], hi = h1[ks][2 * h + 1];
+      const float e0 = bf16_pos(lo, 0) ? acc[nt][0] : 0.0f, e1 = bf16_pos(lo, 1) ? acc[nt][1] : 0.0f;
+      const float e2 = bf16_pos(hi, 0) ? acc[nt][2] : 0.0f, e3 = bf16_pos(hi, 1) ? acc[nt][3] : 0.0f;
+      const uint32_t plo = pack_bf16(e0, e1), phi = pack_bf16(e2, e3);
+      dh1T[c * kSR + r0 + g] = (uint16_t)(plo & 0xFFFFu);
+      dh1T[(c + 1) * kSR + r0 + g] = (uint16_t)(plo >> 16);
+      dh1T[c * kSR + r0 + g + 8] = (uint16_t)(phi & 0xFFFFu);
+      dh1T[(c + 1) * kSR + r0 + g + 8] = (uint16_t)(phi >> 16);
+      pb[nt][0] = e0 + e2;
+      pb[nt][1] = e1 + e3;
+    }
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int sh = 4; sh < 32; sh <<= 1) pb[nt][e] += __shfl_xor_sync(0xffffffffu, pb[nt][e], sh);
+    if (g == 0) {
+#pragma unroll
+      for (int nt = 0; nt < 16; ++nt) {
+        const int c = 8 * nt + 2 * t;
+        atomicAdd(&sdb1[c], pb[nt][0]);
+        atomicAdd(&sdb1[c + 1], pb[nt][1]);
+      }
+    }
+    __syncthreads();
+    // weight gradients over the tile's rows: dW2 = dh2^T h1, dW1 = dh1^T x (K = 64 rows)
+    const int o0 = 32 * warp;
+#pragma unroll 1
+    for (int nc = 0; nc < 4; ++nc) {
+      float wa[2][4][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) wa[mt][j][0] = wa[mt][j][1] = wa[mt][j][2] = wa[mt][j][3] = 0.0f;
+#pragma unroll
+      for (int ks = 0; ks < kTrainRows / 16; ++ks) {
+        uint32_t a0[4], a1[4];
+        load_a<kSR>(dh2T, o0, 16 * ks, g, t, a0);
+        load_a<kSR>(dh2T, o0 + 16, 16 * ks, g, t, a1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint32_t b0, b1;
+          load_b<kSR>(h1T, 32 * nc + 8 * j, 16 * ks, g, t, b0, b1);
+          mma_bf16(wa[0][j], a0, b0, b1);
+          mma_bf16(wa[1][j], a1, b0, b1);
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int o = o0 + 16 * mt + g, i = 32 * nc + 8 * j + 2 * t;
+          atomicAdd(&grad[oW2 + o * kHid + i], wa[mt][j][0]);
+          atomicAdd(&grad[oW2 + o * kHid + i + 1], wa[mt][j][1]);
+          atomicAdd(&grad[oW2 + (o + 8) * kHid + i], wa[mt][j][2]);
+          atomicAdd(&grad[oW2 + (o + 8) * kHid + i + 1], wa[mt][j][3]);
+        }
+    }
+#pragma unroll 1
+    for (int nc = 0; nc < 2; ++nc) {
+      float wa[2][5][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) wa[mt][j][0] = wa[mt][j][1] = wa[mt][j][2] = wa[mt][j][3] = 0.0f;
+#pragma unroll
+      for (int ks = 0; ks < kTrainRows / 16; ++ks) {
+        uint32_t a0[4], a1[4];
+        load_a<kSR>(dh1T, o0, 16 * ks, g, t, a0);
+        load_a<kSR>(dh1T, o0 + 16, 16 * ks, g, t, a1);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          uint32_t b0, b1;
+          load_b<kSR>(xT, 40 * nc + 8 * j, 16 * ks, g, t, b0, b1);
+          mma_bf16(wa[0][j], a0, b0, b1);
+          mma_bf16(wa[1][j], a1, b0, b1);
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const int o = o0 + 16 * mt + g, f = 40 * nc + 8 * j + 2 * t;
+          atomicAdd(&grad[oW1 + o * kF + f], wa[mt][j][0]);
+          atomicAdd(&grad[oW1 + o * kF + f + 1], wa[mt][j][1]);
+          atomicAdd(&grad[oW1 + (o + 8) * kF + f], wa[mt][j][2]);
+          atomicAdd(&grad[oW1 + (o + 8) * kF + f + 1], wa[mt][j][3]);
+        }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    atomicAdd(&grad[oB1 + i], sdb1[i]);
+    atomicAdd(&grad[oB2 + i], sdb2[i]);
+    atomicAdd(&grad[oW3 + i], sdw3[i]);
+  }
+  if (threadIdx.x == 0) atomicAdd(&grad[oB3], sdb3[0]);
+#pragma unroll
+  for (int sh = 1; sh < 32; sh <<= 1) wloss += __shfl_xor_sync(0xffffffffu, wloss, sh);
+  if (lane == 0 && wloss != 0.0) atomicAdd(loss, wloss * (double)inv_n);
+}
+
+// Adam on the FP32 master parameters (the gradient buffer is cleared for the next step),
+// then the BF16 copies the products read.
+__global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m1,
+                           float* __restrict__ m2, float lr, float beta1, float beta2, float eps, float bc1,
+                           float bc2, int update, uint16_t* __restrict__ w1b, uint16_t* __restrict__ w2b,
+                           uint16_t* __restrict__ w2tb) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
+    float x = p[i];
+    if (update) {
+      const float g = grad[i];
+      const float a = beta1 * m1[i] + (1.0f - beta1) * g;
+      const float b = beta2 * m2[i] + (1.0f - beta2) * g * g;
+      m1[i] = a;
+      m2[i] = b;
+      x -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
+      p[i] = x;
+      grad[i] = 0.0f;
+    }
+    if (i < oB1) {
+      w1b[i] = bf16_bits(x);
+    } else if (i >= oW2 && i < oB2) {
+      const int k = i - oW2, o = k / kHid, j = k - o * kHid;
+      w2b[k] = bf16_bits(x);
+      w2tb[j * kHid + o] = bf16_bits(x);
+    }
+  }
+}
+
+constexpr size_t kFwdSmem = (size_t)(kHid * kSF + kHid * kSH + kFwdRows * kSF) * 2 + 3 * kHid * 4;
+constexpr size_t kTrainSmem =
+    (size_t)(kHid * kSF + 2 * kHid * kSH + kTrainRows * kSF + kF * kSR + 3 * kHid * kSR) * 2 + (6 * kHid + 4) * 4;
+
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double gauss(uint64_t& s) {  // Box-Muller on two uniforms from the top 53 bits
+  const double u1 = ((double)(splitmix(s) >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = (double)(splitmix(s) >> 11) * 0x1.0p-53;
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+}  // namespace
+}  // namespace ps
+
+struct pauli_mlp {
+  int n_sites;
+  cudaStream_t stream;
+  float* p;   // parameters
+  float* g;   // gradient accumulator
+  float* m1;  // Adam moments
+  float* m2;
+  uint16_t* w1b;
+  uint16_t* w2b;
+  uint16_t* w2tb;
+  double* loss;
+  int64_t t;  // Adam steps taken
+};
+
+namespace ps {
+
+namespace {
+
+MlpDev dev_view(const pauli_mlp* m) { return MlpDev{m->w1b, m->w2b, m->w2tb, m->p}; }
+
+int refresh_bf16(pauli_mlp* m) {  // BF16 copies from the FP32 parameters, no update
+  PS_LAUNCH("k_mlp_adam", m->stream,
+            k_mlp_adam<<<(kParams + 255) / 256, 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, 0.f, 0.f, 0.f, 0.f,
+                                                                     1.f, 1.f, 0, m->w1b, m->w2b, m->w2tb));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+int smem_attr() {
+  static int done = 0;
+  if (done) return PS_OK;
+  PS_CUDA(cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem));
+  PS_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem));
+  done = 1;
+  return PS_OK;
+}
+
+int fwd_run(const pauli_mlp* m, const Rec* d, int64_t n, cudaStream_t s, double gamma_dt, uint16_t* x, float* z,
+            double* score) {
+  if (n == 0) return PS_OK;
+  PS_TRY(smem_attr());
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kFwdRows), 2 * num_sms()));
+  PS_LAUNCH("k_mlp_fwd", s,
+            k_mlp_fwd<<<grid, 256, kFwdSmem, s>>>(d, n, make_featconst(m->n_sites), dev_view(m), gamma_dt, x, z,
+                                                  score));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+// Gradient of the mean BCE over X's records [i0, i0 + nb) into m->g (added), loss into m->loss.
+int grad_run(pauli_mlp* m, const pauli_sum* X, const float* y, int64_t i0, int64_t nb) {
+  cudaStream_t s = m->stream;
+  if (X->stream != s) PS_CUDA(cudaStreamSynchronize(X->stream));
+  PS_TRY(smem_attr());
+  PS_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(double), s));
+  if (nb == 0) return PS_OK;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb, kTrainRows), num_sms()));
+  PS_LAUNCH("k_mlp_train", s,
+            k_mlp_train<<<grid, 128, kTrainSmem, s>>>(X->d + i0, nb, make_featconst(m->n_sites), dev_view(m), y + i0,
+                                                      1.0f / (float)nb, m->g, m->loss));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+}  // namespace
+
+int mlp_scores(const pauli_mlp* m, const Rec* d, int64_t n, double gamma_dt, cudaStream_t s, double* score) {
+  return fwd_run(m, d, n, s, gamma_dt, nullptr, nullptr, score);
+}
+int mlp_n_sites(const pauli_mlp* m) { return m->n_sites; }
+cudaStream_t mlp_stream(const pauli_mlp* m) { return m->stream; }
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" {
+
+int64_t pauli_mlp_param_count(void) { return kParams; }
+
+int pauli_mlp_create(int n_sites, uint64_t seed, void* cuda_stream, pauli_mlp** out) {
+  if (!out || n_sites < 1 || n_sites > 64) return PS_ERR_INVALID;
+  *out = nullptr;
+  pauli_mlp* m = new pauli_mlp{};
+  m->n_sites = n_sites;
+  m->stream = (cudaStream_t)cuda_stream;
+  cudaStream_t s = m->stream;
+  auto fail = [&](int st) {
+    dev_free(m->p, s);
+    dev_free(m->g, s);
+    dev_free(m->m1, s);
+    dev_free(m->m2, s);
+    dev_free(m->w1b, s);
+    dev_free(m->w2b, s);
+    dev_free(m->w2tb, s);
+    dev_free(m->loss, s);
+    delete m;
+    return st;
+  };
+  int st = PS_OK;
+  if ((st = dev_alloc((void**)&m->p, kParams * sizeof(float), s)) != PS_OK ||
+      (st = dev_alloc((void**)&m->g, kParams * sizeof(float), s)) != PS_OK ||
+      (st = dev_alloc((void**)&m->m1, kParams * sizeof(float), s)) != PS_OK ||
+      (st = dev_alloc((void**)&m->m2, kParams * sizeof(float), s)) != PS_OK ||
+      (st = dev_alloc((void**)&m->w1b, (size_t)kHid * kF * 2, s)) != PS_OK ||
+      (st = dev_alloc((void**)&m->w2b, (size_t)kHid * kHid * 2, s)) != PS_OK ||
+      (st = dev_alloc((void**)&m->w2tb, (size_t)kHid * kHid * 2, s)) != PS_OK ||
+      (st = dev_alloc((void**)&m->loss, sizeof(double), s)) != PS_OK)
+    return fail(st);
+  // He-style initialisation: W1 ~ N(0, 2/80), W2 ~ N(0, 2/128), w3 ~ N(0, 1/128), biases 0
+  std::vector<float> h(kParams, 0.0f);
+  uint64_t state = seed;
+  for (int i = oW1; i < oB1; ++i) h[i] = (float)(gauss(state) * std::sqrt(2.0 / kF));
+  for (int i = oW2; i < oB2; ++i) h[i] = (float)(gauss(state) * std::sqrt(2.0 / kHid));
+  for (int i = oW3; i < oB3; ++i) h[i] = (float)(gauss(state) * std::sqrt(1.0 / kHid));
+  cudaError_t e = cudaMemcpyAsync(m->p, h.data(), kParams * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->g, 0, kParams * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->m1, 0, kParams * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->m2, 0, kParams * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "pauli_mlp_create");
+    return fail(PS_ERR_CUDA);
+  }
+  if ((st = refresh_bf16(m)) != PS_OK) return fail(st);
+  *out = m;
+  return PS_OK;
+}
+
+int pauli_mlp_destroy(pauli_mlp* m) {
+  if (!m) return PS_OK;
+  cudaStream_t s = m->stream;
+  dev_free(m->p, s);
+  dev_free(m->g, s);
+  dev_free(m->m1, s);
+  dev_free(m->m2, s);
+  dev_free(m->w1b, s);
+  dev_free(m->w2b, s);
+  dev_free(m->w2tb, s);
+  dev_free(m->loss, s);
+  delete m;
+  return PS_OK;
+}
+
+int pauli_mlp_get_params(const pauli_mlp* m, float* params, int64_t n) {
+  if (!m || !params || n != kParams) return PS_ERR_INVALID;
+  PS_CUDA(cudaMemcpyAsync(params, m->p, kParams * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+  PS_CUDA(cudaStreamSynchronize(m->stream));
+  return PS_OK;
+}
+
+int pauli_mlp_set_params(pauli_mlp* m, const float* params, int64_t n) {
+  if (!m || !params || n != kParams) return PS_ERR_INVALID;
+  std::vector<float> h(params, params + kParams);
+  PS_CUDA(cudaMemcpyAsync(m->p, h.data(), kParams * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+  PS_CUDA(cudaMemsetAsync(m->g, 0, kParams * sizeof(float), m->stream));
+  PS_CUDA(cudaMemsetAsync(m->m1, 0, kParams * sizeof(float), m->stream));
+  PS_CUDA(cudaMemsetAsync(m->m2, 0, kParams * sizeof(float), m->stream));
+  PS_CUDA(cudaStreamSynchronize(m->stream));
+  m->t = 0;
+  return refresh_bf16(m);
+}
+
+int pauli_mlp_features(const pauli_mlp* m, const pauli_sum* O, uint16_t* x) {
+  if (!m || !O || O->n_sites != m->n_sites || (O->n > 0 && !x)) return PS_ERR_INVALID;
+  if (O->stream != m->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
+  PS_TRY(fwd_run(m, O->d, O->n, m->stream, 0.0, x, nullptr, nullptr));
+  PS_CUDA(cudaStreamSynchronize(m->stream));
+  return PS_OK;
+}
+
+int pauli_mlp_logits(const pauli_mlp* m, const pauli_sum* O, float* z) {
+  if (!m || !O || O->n_sites != m->n_sites || (O->n > 0 && !z)) return PS_ERR_INVALID;
+  if (O->stream != m->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
+  PS_TRY(fwd_run(m, O->d, O->n, m->stream, 0.0, nullptr, z, nullptr));
+  PS_CUDA(cudaStreamSynchronize(m->stream));
+  return PS_OK;
+}
+
+int pauli_mlp_scores(const pauli_mlp* m, const pauli_sum* O, double gamma_dt, double* score) {
+  if (!m || !O || O->n_sites != m->n_sites || (O->n > 0 && !score) || !std::isfinite(gamma_dt))
+    return PS_ERR_INVALID;
+  if (O->stream != m->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
+  PS_TRY(fwd_run(m, O->d, O->n, m->stream, gamma_dt, nullptr, nullptr, score));
+  PS_CUDA(cudaStreamSynchronize(m->stream));
+  return PS_OK;
+}
+
+int pauli_mlp_gradient(pauli_mlp* m, const pauli_sum* X, const float* labels, int64_t i0, int64_t nb, float* grad,
+                       double* loss) {
+  if (!m || !X || X->n_sites != m->n_sites || !grad || i0 < 0 || nb < 0 || i0 + nb > X->n || (nb > 0 && !labels))
+    return PS_ERR_INVALID;
+  PS_CUDA(cudaMemsetAsync(m->g, 0, kParams * sizeof(float), m->stream));
+  PS_TRY(grad_run(m, X, labels, i0, nb));
+  PS_CUDA(cudaMemcpyAsync(grad, m->g, kParams * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+  double l = 0.0;
+  PS_CUDA(cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  PS_CUDA(cudaMemsetAsync(m->g, 0, kParams * sizeof(float), m->stream));
+  PS_CUDA(cudaStreamSynchronize(m->stream));
+  if (loss) *loss = l;
+  return PS_OK;
+}
+
+int pauli_mlp_train_step(pauli_mlp* m, const pauli_sum* X, const float* labels, int64_t i0, int64_t nb, float lr,
+                         double* loss) {
+  if (!m || !X || X->n_sites != m->n_sites || i0 < 0 || nb < 1 || i0 + nb > X->n || !labels || !(lr >= 0.0f))
+    return PS_ERR_INVALID;
+  PS_TRY(grad_run(m, X, labels, i0, nb));
+  m->t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = (float)(1.0 - std::pow(0.9, (double)m->t)), bc2 = (float)(1.0 - std::pow(0.999, (double)m->t));
+  PS_LAUNCH("k_mlp_adam", m->stream,
+            k_mlp_adam<<<(kParams + 255) / 256, 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, lr, b1, b2, 1e-8f,
+                                                                     bc1, bc2, 1, m->w1b, m->w2b, m->w2tb));
+  PS_CUDA(cudaGetLastError());
+  if (loss) {
+    PS_CUDA(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    PS_CUDA(cudaStreamSynchronize(m->stream));
+  }
+  return PS_OK;
+}
+
+int pauli_mlp_labels(const pauli_sum* X, const pauli_sum* target, float* labels) {
+  if (!X || !target || X->n_sites != target->n_sites || (X->n > 0 && !labels)) return PS_ERR_INVALID;
+  if (target->stream != X->stream) PS_CUDA(cudaStreamSynchronize(target->stream));
+  PS_TRY(membership(X->d, X->n, target->d, target->n, X->stream, labels));
+  PS_CUDA(cudaStreamSynchronize(X->stream));
+  return PS_OK;
+}
+
+}  // extern "C"

@@ -92,6 +92,16 @@ __global__ void k_coef_probe(const Rec* __restrict__ O, int64_t n, const ulonglo
   }
 }
 
+// label[i] = 1 if X's i-th string is a key of the table, else 0.
+__global__ void k_member(const Rec* __restrict__ X, int64_t n, const ulonglong2* tkey, const int64_t* tidx,
+                         uint64_t tmask, const long long* ones_idx, float* __restrict__ label) {
+  const long long oi = *ones_idx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Rec r = X[i];
+    label[i] = tp_find(tkey, tidx, tmask, oi, r.v, r.w) >= 0 ? 1.0f : 0.0f;
+  }
+}
+
 __global__ void k_tp_top(const Rec* __restrict__ A, int64_t n, const Rec* __restrict__ B, const ulonglong2* tkey,
                          const int64_t* tidx, uint64_t tmask, const long long* ones_idx, int* top) {
   int m = -100000;
@@ -267,6 +277,30 @@ int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw
     re[j] = h[(size_t)slot_of[(size_t)j]].x;
     im[j] = h[(size_t)slot_of[(size_t)j]].y;
   }
+  return PS_OK;
+}
+
+// Membership of X's strings in T (T's keys distinct): label[i] in {0, 1}, X's storage order.
+int membership(const Rec* X, int64_t nx, const Rec* T, int64_t nt, cudaStream_t s, float* label) {
+  if (nx == 0) return PS_OK;
+  uint64_t slots = 1;
+  while (slots < (uint64_t)(2 * std::max<int64_t>(nt, 1))) slots <<= 1;
+  Buf<ulonglong2> tkey;
+  Buf<int64_t> tidx;
+  Buf<long long> ones;
+  PS_TRY(tkey.alloc(slots, s));
+  PS_TRY(tidx.alloc(slots, s));
+  PS_TRY(ones.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(tkey.p, 0xFF, slots * sizeof(ulonglong2), s));
+  PS_CUDA(cudaMemsetAsync(ones.p, 0xFF, sizeof(long long), s));  // -1: the all-ones key is absent
+  const int nsm = num_sms();
+  if (nt > 0) {
+    int bt = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nt, 256), 4 * nsm));
+    PS_LAUNCH("k_tp_build", s, k_tp_build<<<bt, 256, 0, s>>>(T, nt, tkey.p, tidx.p, slots - 1, ones.p));
+  }
+  int bp = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nx, 256), 8 * nsm));
+  PS_LAUNCH("k_member", s, k_member<<<bp, 256, 0, s>>>(X, nx, tkey.p, tidx.p, slots - 1, ones.p, label));
+  PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 

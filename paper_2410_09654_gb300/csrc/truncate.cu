@@ -7,7 +7,8 @@
 //      never dropping a string of the keep set.
 // Step 4 is a most-significant-digit radix select over the 192-bit rank key
 // (|c|^2 bits, ~v, ~w): all rank keys are distinct, so exactly top_k strings
-// outrank the selected threshold.
+// outrank the selected threshold.  A caller-given score can take the place of |c|^2
+// (the learned truncation ranks by ln|c| - gamma dt wt + z).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -83,12 +84,23 @@ __device__ __forceinline__ void tile_positions(const bool (&f)[kTI], TileRes& sm
   __syncthreads();
 }
 
+// Order-preserving map of a double score to 64 bits: larger score -> larger key; -0 and +0
+// map alike; NaN maps to 0, below every number.
+__device__ __forceinline__ uint64_t score_key(double x) {
+  if (x != x) return 0ull;
+  if (x == 0.0) x = 0.0;
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | (1ull << 63));
+}
+
 // Steps 1-3 with compaction (order of survivors is unspecified).  For a later top-k
-// select it also stores each survivor's |c|^2 bit pattern (non-negative doubles order
-// like their bit patterns) and histograms its top kDigitBits bits.
+// select it also stores each survivor's rank value (the |c|^2 bit pattern: non-negative
+// doubles order like their bit patterns; or, with a score array, the score's key) and
+// histograms its top kDigitBits bits.
 __global__ void __launch_bounds__(kTT) k_filter(const Rec* __restrict__ in, int64_t n, TruncArgs a,
-                                                Rec* __restrict__ out, uint64_t* __restrict__ ab,
-                                                unsigned* __restrict__ hist0, unsigned long long* __restrict__ n_out) {
+                                                const double* __restrict__ score, Rec* __restrict__ out,
+                                                uint64_t* __restrict__ ab, unsigned* __restrict__ hist0,
+                                                unsigned long long* __restrict__ n_out) {
   __shared__ unsigned s_hist[kBins];
   __shared__ TileRes s_res;
   if (hist0) {
@@ -120,7 +132,7 @@ __global__ void __launch_bounds__(kTT) k_filter(const Rec* __restrict__ in, int6
         keep[k] = !(a.max_weight >= 0 && wt > a.max_weight) && !(is_zero(r[k].re) && is_zero(r[k].im));
         if (keep[k] && (a.use_cut || ab)) {
           const double q = sq_sum_cls(r[k].re, r[k].im, a.cls);
-          a2[k] = (uint64_t)__double_as_longlong(q);
+          a2[k] = score ? score_key(score[i]) : (uint64_t)__double_as_longlong(q);
           if (a.use_cut) keep[k] = !(q < a.cut2);
         }
       }
@@ -361,7 +373,8 @@ __global__ void k_debug_divide(double* __restrict__ x, int64_t n, DivConst dc) {
 }  // namespace
 
 // Truncate O in place; `divisor` (if non-null) divides every coefficient first.
-int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor) {
+int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor,
+                 const double* score) {
   cudaStream_t s = O->stream;
   const bool use_gamma = P && P->gamma != 0.0;
   const bool use_w = P && P->max_weight >= 0;
@@ -396,7 +409,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
     PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
   }
   auto tile_grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTile), 8 * nsm)); };
-  PS_LAUNCH("k_filter", s, k_filter<<<tile_grid(O->n), kTT, 0, s>>>(O->d, O->n, a, cand, ab.p, hist.p, cnt.p));
+  PS_LAUNCH("k_filter", s, k_filter<<<tile_grid(O->n), kTT, 0, s>>>(O->d, O->n, a, score, cand, ab.p, hist.p, cnt.p));
   cudaError_t e = cudaGetLastError();
   unsigned long long nc = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nc, cnt.p, sizeof(nc), cudaMemcpyDeviceToHost, s);

@@ -108,6 +108,19 @@ def load(build_if_missing: bool = False):
         "pauli_launch_count": ([], I64),
         "pauli_debug_divide": ([P, I64, ctypes.c_double, P], ctypes.c_int),
         "pauli_trace_product_noalloc": ([P, P, P, P, I64, P, P, P, P, I64, P, F64P, F64P], ctypes.c_int),
+        "pauli_mlp_param_count": ([], I64),
+        "pauli_mlp_create": ([ctypes.c_int, ctypes.c_uint64, P, ctypes.POINTER(P)], ctypes.c_int),
+        "pauli_mlp_destroy": ([P], ctypes.c_int),
+        "pauli_mlp_get_params": ([P, P, I64], ctypes.c_int),
+        "pauli_mlp_set_params": ([P, P, I64], ctypes.c_int),
+        "pauli_mlp_features": ([P, P, P], ctypes.c_int),
+        "pauli_mlp_logits": ([P, P, P], ctypes.c_int),
+        "pauli_mlp_scores": ([P, P, ctypes.c_double, P], ctypes.c_int),
+        "pauli_mlp_gradient": ([P, P, P, I64, I64, P, F64P], ctypes.c_int),
+        "pauli_mlp_train_step": ([P, P, P, I64, I64, ctypes.c_float, F64P], ctypes.c_int),
+        "pauli_mlp_labels": ([P, P, P], ctypes.c_int),
+        "pauli_truncate_scored": ([P, ctypes.POINTER(pauli_trunc_policy), P, ctypes.c_double, P], ctypes.c_int),
+        "pauli_rk4_step_mlp": ([P, P, ctypes.c_double, ctypes.POINTER(pauli_trunc_policy), P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -376,3 +389,108 @@ def pauli_debug_divide(x, b: float, stream=None):
 
 def pauli_debug_fail_alloc_after(n: int):
     _check(load().pauli_debug_fail_alloc_after(int(n)), "pauli_debug_fail_alloc_after")
+
+
+# ------------------------------------------------------------------ learned truncation
+def _dev(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class PauliMLP:
+    """The learned truncation scorer (owns one ``pauli_mlp*``); see include/paulistr.h."""
+
+    def __init__(self, n_sites: int, seed: int = 0, stream=None):
+        lib = load()
+        self._lib = lib
+        self.n_sites = int(n_sites)
+        self.stream = _current_stream() if stream is None else ctypes.c_void_p(stream)
+        h = ctypes.c_void_p()
+        _check(lib.pauli_mlp_create(self.n_sites, ctypes.c_uint64(int(seed)), self.stream, ctypes.byref(h)),
+               "pauli_mlp_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and self._lib is not None:
+            self._lib.pauli_mlp_destroy(h)
+            self.handle = None
+
+
+def pauli_mlp_param_count() -> int:
+    return int(load().pauli_mlp_param_count())
+
+
+def pauli_mlp_get_params(m: PauliMLP) -> np.ndarray:
+    n = pauli_mlp_param_count()
+    out = np.empty(n, np.float32)
+    _check(load().pauli_mlp_get_params(m.handle, out.ctypes.data_as(ctypes.c_void_p), n), "pauli_mlp_get_params")
+    return out
+
+
+def pauli_mlp_set_params(m: PauliMLP, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().pauli_mlp_set_params(m.handle, p.ctypes.data_as(ctypes.c_void_p), len(p)), "pauli_mlp_set_params")
+
+
+def pauli_mlp_features(m: PauliMLP, O: PauliSum):
+    """BF16 bit patterns of the 80 features of O's strings (storage order): int16 CUDA tensor [n, 80]."""
+    import torch
+    x = torch.empty((len(O), 80), dtype=torch.int16, device="cuda")
+    _check(load().pauli_mlp_features(m.handle, O.handle, _dev(x)), "pauli_mlp_features")
+    return x
+
+
+def pauli_mlp_logits(m: PauliMLP, O: PauliSum):
+    import torch
+    z = torch.empty(len(O), dtype=torch.float32, device="cuda")
+    _check(load().pauli_mlp_logits(m.handle, O.handle, _dev(z)), "pauli_mlp_logits")
+    return z
+
+
+def pauli_mlp_scores(m: PauliMLP, O: PauliSum, gamma_dt: float = 0.0):
+    import torch
+    sc = torch.empty(len(O), dtype=torch.float64, device="cuda")
+    _check(load().pauli_mlp_scores(m.handle, O.handle, float(gamma_dt), _dev(sc)), "pauli_mlp_scores")
+    return sc
+
+
+def pauli_mlp_gradient(m: PauliMLP, X: PauliSum, labels, i0: int = 0, nb: int | None = None):
+    """(gradient as a float32 numpy array, loss) over records [i0, i0 + nb) of X."""
+    nb = len(X) - i0 if nb is None else nb
+    g = np.empty(pauli_mlp_param_count(), np.float32)
+    loss = ctypes.c_double()
+    _check(load().pauli_mlp_gradient(m.handle, X.handle, _dev(labels), int(i0), int(nb),
+                                     g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss)), "pauli_mlp_gradient")
+    return g, float(loss.value)
+
+
+def pauli_mlp_train_step(m: PauliMLP, X: PauliSum, labels, i0: int, nb: int, lr: float, want_loss: bool = False):
+    loss = ctypes.c_double()
+    _check(load().pauli_mlp_train_step(m.handle, X.handle, _dev(labels), int(i0), int(nb), float(lr),
+                                       ctypes.byref(loss) if want_loss else None), "pauli_mlp_train_step")
+    return float(loss.value) if want_loss else None
+
+
+def pauli_mlp_labels(X: PauliSum, target: PauliSum):
+    """float32 CUDA tensor: 1 where X's string (storage order) is present in target."""
+    import torch
+    y = torch.empty(len(X), dtype=torch.float32, device="cuda")
+    _check(load().pauli_mlp_labels(X.handle, target.handle, _dev(y)), "pauli_mlp_labels")
+    return y
+
+
+def pauli_truncate_scored(O: PauliSum, pol: pauli_trunc_policy | None, score, keep: PauliSum | None = None,
+                          dt: float = 0.0):
+    """Truncation with the top-k ranked by score (float64 CUDA tensor, O's storage order)."""
+    _check(load().pauli_truncate_scored(O.handle, None if pol is None else ctypes.byref(pol), _h(keep), float(dt),
+                                        _dev(score)), "pauli_truncate_scored")
+    return O
+
+
+def pauli_rk4_step_mlp(H: PauliSum, O: PauliSum, dt: float, pol: pauli_trunc_policy | None = None,
+                       keep: PauliSum | None = None, model: PauliMLP | None = None,
+                       cand_out: PauliSum | None = None):
+    _check(load().pauli_rk4_step_mlp(H.handle, O.handle, float(dt), None if pol is None else ctypes.byref(pol),
+                                     _h(keep), None if model is None else model.handle, _h(cand_out)),
+           "pauli_rk4_step_mlp")
+    return O

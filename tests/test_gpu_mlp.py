@@ -1,0 +1,282 @@
+"""Learned truncation on the GPU against the oracle (oracle/mlp.py): features, logits,
+scores and gradients of the BF16 network to BF16 tolerance; the scored top-k truncation
+and the membership labels exactly; the RK4 step with a scorer against the plain step."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from oracle import mlp as omlp
+from paper_2410_09654_gb300 import inputs as I
+
+from gpu_util import assert_match
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2410_09654_gb300 import paulistr as ps  # noqa: E402
+
+# BF16 keeps 8 significant bits: two roundings of the same value differ by at most one unit
+# in the last place, 2^-7 relative.  Network outputs carry the rounding of inputs, weights and
+# the hidden layer: 2e-2 relative in the norm over a batch (3e-2 for gradients).
+BF16_REL = 2.0 ** -7
+NET_REL = 2e-2
+GRAD_REL = 3e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ps.load(build_if_missing=True)
+
+
+def _params(seed, scale=1.0):
+    """Random FP32 parameters of the network's shapes (He-like scales)."""
+    rng = np.random.default_rng(seed)
+    P = {
+        "W1": rng.standard_normal((128, 80)) * np.sqrt(2 / 80) * scale,
+        "b1": rng.standard_normal(128) * 0.1,
+        "W2": rng.standard_normal((128, 128)) * np.sqrt(2 / 128) * scale,
+        "b2": rng.standard_normal(128) * 0.1,
+        "w3": rng.standard_normal(128) * np.sqrt(1 / 128),
+        "b3": np.array([0.3]),
+    }
+    return omlp.pack(P).astype(np.float32)
+
+
+def _bf16_decode(bits):
+    b = bits.astype(np.int32) & 0xFFFF
+    return (b << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _rel_norm(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _sum(n, arrays):
+    return ps.PauliSum.from_arrays(n, *arrays)
+
+
+@pytest.mark.parametrize("n_sites,m", [(5, 300), (48, 3001), (64, 2000)])
+def test_features_match_oracle(n_sites, m):
+    arr = I.random_sum(11 + n_sites, n_sites, m, kind="complex")
+    model = ps.PauliMLP(n_sites, seed=1)
+    O = _sum(n_sites, arr)
+    x = _bf16_decode(ps.pauli_mlp_features(model, O).cpu().numpy())
+    want = omlp.features(*arr, n_sites)
+    assert x.shape == want.shape
+    err = np.abs(x - want)
+    assert np.all(err <= BF16_REL * np.abs(want) + 1e-30), float(err.max())
+
+
+def test_logits_and_scores_match_oracle():
+    n = 48
+    arr = I.random_sum(3, n, 5000, kind="real", max_support=12)
+    p = _params(7)
+    model = ps.PauliMLP(n, seed=0)
+    ps.pauli_mlp_set_params(model, p)
+    assert np.array_equal(ps.pauli_mlp_get_params(model), p)
+    O = _sum(n, arr)
+    z = ps.pauli_mlp_logits(model, O).cpu().numpy().astype(np.float64)
+    X = omlp.features(*arr, n)
+    zo, _ = omlp.forward(p.astype(np.float64), X)
+    assert _rel_norm(z, zo) < NET_REL, _rel_norm(z, zo)
+    s = ps.pauli_mlp_scores(model, O, 0.05).cpu().numpy()
+    so = omlp.scores(p.astype(np.float64), *arr, n, gamma_dt=0.05)
+    # the ln|c| - gamma dt wt part is FP64; only z carries the BF16 error
+    assert np.max(np.abs((s - z) - (so - zo))) < 1e-6
+    assert _rel_norm(s - (so - zo), zo) < NET_REL
+
+
+def test_zero_network_scores_are_log_abs():
+    n = 20
+    arr = I.random_sum(5, n, 1000, kind="complex")
+    model = ps.PauliMLP(n, seed=0)
+    ps.pauli_mlp_set_params(model, np.zeros(ps.pauli_mlp_param_count(), np.float32))
+    s = ps.pauli_mlp_scores(model, _sum(n, arr), 0.0).cpu().numpy()
+    want = 0.5 * np.log(arr[2] ** 2 + arr[3] ** 2)
+    assert np.allclose(s, want, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("i0,nb", [(0, 3000), (37, 1001), (5, 1)])
+def test_gradient_matches_oracle(i0, nb):
+    n = 48
+    arr = I.random_sum(9, n, 3100, kind="real", max_support=16)
+    rng = np.random.default_rng(4)
+    y = (rng.random(len(arr[0])) < 0.3).astype(np.float32)
+    p = _params(8)
+    model = ps.PauliMLP(n, seed=0)
+    ps.pauli_mlp_set_params(model, p)
+    X = _sum(n, arr)
+    g, loss = ps.pauli_mlp_gradient(model, X, torch.from_numpy(y).cuda(), i0, nb)
+    sl = slice(i0, i0 + nb)
+    Xo = omlp.features(*(a[sl] for a in arr), n)
+    lo, go = omlp.loss_and_grad(p.astype(np.float64), Xo, y[sl].astype(np.float64))
+    assert abs(loss - lo) <= NET_REL * abs(lo), (loss, lo)
+    G, Go = omlp.unpack(g.astype(np.float64)), omlp.unpack(go)
+    for name, _ in omlp.SHAPES:
+        assert _rel_norm(G[name], Go[name]) < GRAD_REL, (name, _rel_norm(G[name], Go[name]))
+    # the parameters did not move
+    assert np.array_equal(ps.pauli_mlp_get_params(model), p)
+
+
+def test_train_step_is_adam():
+    n = 48
+    arr = I.random_sum(12, n, 2048, kind="real", max_support=10)
+    y = (np.random.default_rng(1).random(len(arr[0])) < 0.5).astype(np.float32)
+    p = _params(9)
+    model = ps.PauliMLP(n, seed=0)
+    ps.pauli_mlp_set_params(model, p)
+    X = _sum(n, arr)
+    yd = torch.from_numpy(y).cuda()
+    g, loss0 = ps.pauli_mlp_gradient(model, X, yd, 0, len(arr[0]))
+    lr = 1e-3
+    loss = ps.pauli_mlp_train_step(model, X, yd, 0, len(arr[0]), lr, want_loss=True)
+    assert abs(loss - loss0) < 1e-6 * abs(loss0)
+    d = ps.pauli_mlp_get_params(model).astype(np.float64) - p
+    big = np.abs(g) > 1e-5
+    # first bias-corrected step: -lr g / (|g| + eps), i.e. -lr sign(g) where |g| >> eps
+    assert np.max(np.abs(d[big] + lr * np.sign(g[big]))) < 1e-2 * lr
+    assert np.all(np.abs(d) <= lr * 1.0001 + 1e-7)
+
+
+def test_training_learns_a_rule():
+    # label = weight <= 5 (about a third of these strings): a rule the features carry directly
+    n = 32
+    arr = I.random_sum(21, n, 8192, kind="real", max_support=8)
+    wt = np.array([bin(int(a) | int(b)).count("1") for a, b in zip(arr[0], arr[1])])
+    y = torch.from_numpy((wt <= 5).astype(np.float32)).cuda()
+    model = ps.PauliMLP(n, seed=5)
+    X = _sum(n, arr)
+    first = ps.pauli_mlp_train_step(model, X, y, 0, 8192, 3e-3, want_loss=True)
+    for it in range(300):
+        i0 = (it % 8) * 1024
+        ps.pauli_mlp_train_step(model, X, y, i0, 1024, 3e-3)
+    _, last = ps.pauli_mlp_gradient(model, X, y, 0, 8192)
+    assert last < 0.3 * first, (first, last)
+
+
+def _scored_case(seed, n, m, dyadic):
+    arr = I.random_sum(seed, n, m, kind="complex", dyadic=dyadic)
+    rng = np.random.default_rng(seed + 1)
+    score = rng.choice([-2.0, -0.0, 0.0, 0.75, 3.0, -np.inf, np.nan], len(arr[0]))
+    score = np.where(rng.random(len(arr[0])) < 0.5, rng.standard_normal(len(arr[0])), score)
+    return arr, score
+
+
+@pytest.mark.parametrize("m,top_k,mw,cut,gamma,nkeep", [
+    (1, 1, -1, 0.0, 0.0, 0), (7, 3, -1, 0.0, 0.0, 0), (3000, 1000, -1, 0.0, 0.0, 0),
+    (3000, 999, 20, 0.05, 0.0, 5), (40000, 12345, -1, 0.0, 0.2, 0), (40000, 40000, -1, 0.0, 0.0, 0),
+    (20000, 19999, 30, 0.0, 0.1, 100)])
+def test_truncate_scored_matches_oracle(m, top_k, mw, cut, gamma, nkeep):
+    n = 40
+    arr, score = _scored_case(m + top_k, n, m, dyadic=(m % 2 == 0))
+    keep = None
+    if nkeep:
+        keep = (arr[0][-nkeep:], arr[1][-nkeep:])
+    O = _sum(n, arr)
+    K = None if keep is None else ps.PauliSum.from_arrays(n, keep[0], keep[1], np.ones(nkeep), np.zeros(nkeep))
+    pol = ps.policy(max_weight=mw, cutoff=cut, top_k=top_k, gamma=gamma)
+    ps.pauli_truncate_scored(O, pol, torch.from_numpy(score).cuda(), keep=K, dt=0.5)
+    want = omlp.truncate_scored(*arr, score, max_weight=mw, cutoff=cut, top_k=top_k, gamma=gamma, dt=0.5,
+                                keep=keep)
+    got = O.download()
+    assert_match(got, orc.Op(n, *want), exact=True, what="scored truncation")
+
+
+def test_truncate_scored_empty_and_filters_only():
+    n = 10
+    O = ps.PauliSum(n)
+    ps.pauli_truncate_scored(O, ps.policy(top_k=5), torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert len(O) == 0
+    arr = I.random_sum(2, n, 500, kind="real")
+    O = _sum(n, arr)
+    score = torch.zeros(len(arr[0]), dtype=torch.float64, device="cuda")
+    ps.pauli_truncate_scored(O, ps.policy(max_weight=4), score)
+    want = orc.truncate(orc.Op(n, *arr), max_weight=4)
+    assert_match(O.download(), want, exact=True, what="filters only")
+
+
+def test_labels_are_membership():
+    n = 30
+    arr = I.random_sum(31, n, 5000, kind="real")
+    sel = np.random.default_rng(2).random(len(arr[0])) < 0.4
+    extra = I.random_sum(32, n, 300, kind="real")
+    tv = np.concatenate([arr[0][sel], extra[0]])
+    tw = np.concatenate([arr[1][sel], extra[1]])
+    # extra strings may repeat some of arr's: the target stays a set
+    keys = {}
+    for a, b in zip(tv, tw):
+        keys[(int(a), int(b))] = 1
+    tv = np.array([k[0] for k in keys], np.uint64)
+    tw = np.array([k[1] for k in keys], np.uint64)
+    T = ps.PauliSum.from_arrays(n, tv, tw, np.ones(len(tv)), np.zeros(len(tv)))
+    X = _sum(n, arr)
+    y = ps.pauli_mlp_labels(X, T).cpu().numpy()
+    want = np.array([(int(a), int(b)) in keys for a, b in zip(arr[0], arr[1])], np.float32)
+    assert np.array_equal(y, want)
+
+
+def _chain48():
+    n = 48
+    H = I.tilted_ising_chain(n).arrays()
+    O0 = I.single(n, "Z", 24).arrays()
+    return n, H, O0
+
+
+def test_rk4_zero_network_equals_plain_truncation():
+    n, H, O0 = _chain48()
+    pol = ps.policy(top_k=600, trim_stages=1)
+    model = ps.PauliMLP(n, seed=0)
+    ps.pauli_mlp_set_params(model, np.zeros(ps.pauli_mlp_param_count(), np.float32))
+    Hd, Od = _sum(n, H), _sum(n, O0)
+    ref = orc.Op(n, *O0)
+    Ho = orc.Op(n, *H)
+    for step in range(6):
+        ps.pauli_rk4_step_mlp(Hd, Od, 0.05, pol, model=model)
+        ref = orc.rk4_step(Ho, ref, 0.05, top_k=600, trim_stages=1)
+        assert_match(Od.download(), ref, exact=True, what=f"step {step}")
+
+
+def test_rk4_candidates_are_the_untruncated_step():
+    n, H, O0 = _chain48()
+    Hd, Od = _sum(n, H), _sum(n, O0)
+    Ho, ref = orc.Op(n, *H), orc.Op(n, *O0)
+    pol = ps.policy(top_k=300)
+    C = ps.PauliSum(n)
+    for step in range(4):
+        full = orc.rk4_step(Ho, ref, 0.05)
+        ps.pauli_rk4_step_mlp(Hd, Od, 0.05, pol, cand_out=C)
+        assert_match(C.download(), full, exact=True, what=f"candidates, step {step}")
+        ref = orc.truncate(full, top_k=300)
+        assert_match(Od.download(), ref, exact=True, what=f"step {step}")
+
+
+def test_rk4_with_network_keeps_the_top_scores():
+    # the kept set is the top-k of the candidates by the scores the library computes for them
+    n, H, O0 = _chain48()
+    Hd, Od = _sum(n, H), _sum(n, O0)
+    model = ps.PauliMLP(n, seed=3)
+    pol = ps.policy(top_k=500, trim_stages=1, gamma=0.1)
+    C = ps.PauliSum(n)
+    for step in range(5):
+        ps.pauli_rk4_step_mlp(Hd, Od, 0.05, pol, model=model, cand_out=C)
+    sc = ps.pauli_mlp_scores(model, C, 0.1 * 0.05).cpu().numpy()
+    import ctypes
+    m = len(C)
+    v = torch.empty(m, dtype=torch.int64, device="cuda")
+    w = torch.empty(m, dtype=torch.int64, device="cuda")
+    re = torch.empty(m, dtype=torch.float64, device="cuda")
+    im = torch.empty(m, dtype=torch.float64, device="cuda")
+    got = ctypes.c_int64()
+    ps._check(ps.load().pauli_sum_download_device(C.handle, *[ctypes.c_void_p(t.data_ptr()) for t in (v, w, re, im)],
+                                                   m, ctypes.byref(got)), "download_device")
+    v = v.cpu().numpy().view(np.uint64)
+    w = w.cpu().numpy().view(np.uint64)
+    order = sorted(range(m), key=lambda i: (-sc[i], int(v[i]), int(w[i])))
+    want = {(int(v[i]), int(w[i])) for i in order[:500]}
+    ov, ow, _, _ = Od.download()
+    assert set(zip(ov.tolist(), ow.tolist())) == want
