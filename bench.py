@@ -41,6 +41,9 @@ def workload(top_k: int) -> str:
             f"top {cap} strings kept after each step; timed steps start once |O| has reached {cap}")
 LATTICE_WORKLOAD = ("RK4 on the open 8x8 Heisenberg lattice (336 strings), O(0) = Z at (4,4), dt=0.02, dissipation "
                     "gamma=0.1, top 2^20 strings (cap lowered from 2^23) with trimmed stages, timed once at the cap")
+LEARNED_WORKLOAD = ("RK4 on the open N=48 chain sum ZZ + 1.05 sum X + 0.5 sum Z (143 strings), O(0) = Z_24, "
+                    "dt=0.05, 80 steps (t=4), trimmed stages; top 2^18 strings by the learned score versus by |c|, "
+                    "both against the same run at top 2^22; observable Tr(O(t) Z_24)/2^N after every step")
 RK4_WORKLOAD = "RK4 on the open N=10 chain sum ZZ + 1.05 sum X + 0.5 sum Z, O(0)=Z_1, dt=0.05, 40 steps, weight<=6 then |c|<1e-10"
 
 
@@ -53,6 +56,7 @@ def parse():
     p.add_argument("--top-k", type=int, default=TOP_K)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-truncation comparison")
     return p.parse_args()
 
 
@@ -380,6 +384,11 @@ def main():
                    "steps_per_s": sum_over_ranks(4) / t_lat, "products_per_s": sum_over_ranks(lat_prod) / t_lat,
                    "size": len(Ol)}
 
+    # ---------------------------------------------------------------- learned truncation
+    learned_res = None
+    if not args.no_learned:
+        learned_res = learned_truncation(stream, peaks_bf16=float(peaks.get("bf16_tflops", 1900.0)))
+
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -404,6 +413,7 @@ def main():
             "b_n_timed": bs,
             "rk4": rk4,
             "rk4_lattice": rk4_lattice,
+            "learned_truncation": learned_res,
             "roofline": roof,
             "kernels_per_step_ms": {k: round(v[1], 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1][1])},
             "profiled_region_ms_per_step": prof_ms / args.steps,
@@ -416,6 +426,76 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def learned_truncation(stream, peaks_bf16: float, lg_cap: int = 18, steps: int = 80, iters: int = 4000):
+    """Train the BF16 scorer on the method's own runs (cap M versus 4M, labels 10 steps ahead)
+    and compare the observable error of learned and plain truncation at cap M against a run at
+    16M; also the scoring kernel's time and tensor throughput inside the learned run."""
+    import torch
+    from paper_2410_09654_gb300 import inputs as I, learned as L, paulistr as ps
+    n = 48
+    M = 1 << lg_cap
+    H = ps.PauliSum.from_arrays(n, *I.tilted_ising_chain(n).arrays())
+    O0 = ps.PauliSum.from_arrays(n, *I.single(n, "Z", 24).arrays())
+    pv, pw = I.string("Z", 24)
+    probe = (np.array([pv], np.uint64), np.array([pw], np.uint64))
+    dt = 0.05
+    pol = ps.policy(top_k=M, trim_stages=1)
+    ref, t_ref = L.rk4_observable(H, O0, dt, steps, ps.policy(top_k=16 * M, trim_stages=1), probe)
+    plain, t_plain = L.rk4_observable(H, O0, dt, steps, pol, probe)
+    t0 = time.perf_counter()
+    data = L.collect(H, O0, dt, M, [10, 20, 30, 40, 50, 60], 10)
+    t1 = time.perf_counter()
+    model = ps.PauliMLP(n, seed=1)
+    loss0 = L.mean_loss(model, data)
+    batch = 16384
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    L.train(model, data, iters, batch=batch, lr=1e-3)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    loss1 = L.mean_loss(model, data)
+    mlp, t_mlp = L.rk4_observable(H, O0, dt, steps, pol, probe, model=model)
+    ps.pauli_profile_enable(True)  # a second pass with per-kernel events (its wall time is not used)
+    L.rk4_observable(H, O0, dt, steps, pol, probe, model=model)
+    prof = ps.pauli_profile_report()
+    ps.pauli_profile_enable(False)
+    e_pl = np.abs(plain[:, 0] - ref[:, 0])
+    e_ml = np.abs(mlp[:, 0] - ref[:, 0])
+    fwd_launches, fwd_ms = prof.get("k_mlp_fwd", (0, 0.0))
+    cand = [len(C) for C, _ in data]
+    # the scoring kernel alone on the last candidate set (strings per launch known exactly)
+    C_last = data[-1][0]
+    ps.pauli_mlp_scores(model, C_last, 0.0)
+    ps.pauli_profile_enable(True)
+    for _ in range(5):
+        ps.pauli_mlp_scores(model, C_last, 0.0)
+    kprof = ps.pauli_profile_report()
+    ps.pauli_profile_enable(False)
+    flop_per_string = 2 * (80 * 128 + 128 * 128 + 128)
+    kl, kms = kprof.get("k_mlp_fwd", (0, 0.0))
+    fwd_roof = None
+    if kl:
+        achieved = len(C_last) * flop_per_string / (kms / 1e3 / kl) / 1e12
+        fwd_roof = {"kernel": "k_mlp_fwd", "bound": "tensor", "achieved": achieved, "peak": peaks_bf16,
+                    "unit": "TFLOP/s", "frac": achieved / peaks_bf16,
+                    "peak_kind": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops), kernel timed alone",
+                    "flop_per_string": flop_per_string, "strings_per_launch": len(C_last),
+                    "ms_per_launch": kms / kl}
+    return {
+        "workload": LEARNED_WORKLOAD, "cap": M, "reference_cap": 16 * M,
+        "observable_error_mean": {"plain": float(e_pl.mean()), "learned": float(e_ml.mean())},
+        "observable_error_max": {"plain": float(e_pl.max()), "learned": float(e_ml.max())},
+        "ms_per_step": {"plain": 1e3 * t_plain, "learned": 1e3 * t_mlp, "reference": 1e3 * t_ref},
+        "training": {"candidates": int(sum(cand)), "positive_fraction": L.positive_fraction(data),
+                     "label": "kept in the top 2^18 of the 2^20 run 10 steps later",
+                     "iterations": iters, "batch": batch, "lr": 1e-3, "loss_before": loss0, "loss_after": loss1,
+                     "seconds": t3 - t2, "samples_per_s": iters * batch / (t3 - t2), "collect_seconds": t1 - t0},
+        "scorer_ms_per_step": fwd_ms / steps,
+        "scorer_roofline": fwd_roof,
+        "kernel": "mma.sync m16n8k16 bf16 (fp32 accumulate)",
+    }
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")

@@ -280,3 +280,28 @@ def test_rk4_with_network_keeps_the_top_scores():
     want = {(int(v[i]), int(w[i])) for i in order[:500]}
     ov, ow, _, _ = Od.download()
     assert set(zip(ov.tolist(), ow.tolist())) == want
+
+
+def test_learned_workflow_small():
+    # the training workflow end to end at small caps: data from the method's runs, a loss
+    # that training lowers, and an RK4 run ranked by the trained scorer
+    from paper_2410_09654_gb300 import learned as L
+    n, Ha, O0a = _chain48()
+    H, O0 = _sum(n, Ha), _sum(n, O0a)
+    M = 1 << 10
+    data = L.collect(H, O0, 0.05, M, [5, 10, 15], 5)
+    assert len(data) == 3
+    for C, y in data:
+        assert len(C) > M and y.shape[0] == len(C)
+        assert 0.0 < float(y.mean()) < 1.0
+    model = ps.PauliMLP(n, seed=2)
+    before = L.mean_loss(model, data)
+    L.train(model, data, 400, batch=2048, lr=1e-3)
+    after = L.mean_loss(model, data)
+    assert after < before, (before, after)
+    pv, pw = I.string("Z", 24)
+    probe = (np.array([pv], np.uint64), np.array([pw], np.uint64))
+    obs, _ = L.rk4_observable(H, O0, 0.05, 20, ps.policy(top_k=M, trim_stages=1), probe, model=model)
+    ref, _ = L.rk4_observable(H, O0, 0.05, 20, ps.policy(top_k=16 * M, trim_stages=1), probe)
+    assert np.all(np.isfinite(obs))
+    assert np.max(np.abs(obs - ref)) < 0.05
