@@ -13,7 +13,8 @@ holds an independent dense-matrix checker for tiny systems.
 Every function cites the passage of the paper it follows; see ``oracle.cpp``
 for the arithmetic.  Parity status: all entry points are pinned by the
 ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``; ``mlp.py`` (the learned
-truncation scorer and truncation by an arbitrary score) by ``tests/test_mlp_oracle.py``.
+truncation scorer and truncation by an arbitrary score) by ``tests/test_mlp_oracle.py``;
+the FP32-coefficient compositions at the end of this file by ``tests/test_f32_oracle.py``.
 """
 from __future__ import annotations
 
@@ -321,3 +322,74 @@ def lanczos_step(H: Op, O_prev: Op, O_cur: Op, b_prev: float, max_weight: int = 
     if b == 0.0:
         return 0.0, Op.empty(O_cur.n_sites)
     return b, truncate(divide(A, b), max_weight=max_weight, cutoff=cutoff, top_k=top_k)
+
+
+# ------------------------------------------------------------------ FP32 coefficients
+# Precision mode of the benchmark's FP32 pattern: every stored coefficient is an FP32 number.
+# A merge forms each output from the exact products of its FP32 inputs (24-bit significands
+# multiply exactly in FP64), accumulated in FP64 in the same order as the FP64 path, and
+# rounds the result once to FP32 (round to nearest even); outputs that round to zero are
+# dropped like exact zeros.  Norms, traces and b_n stay FP64 (exact sums of the FP32 values).
+# These functions compose the pinned FP64 entry points above with that rounding, at the
+# points where the method stores a result.
+
+def round32(A: Op) -> Op:
+    """Every coefficient rounded to the nearest FP32 number; strings that become zero dropped."""
+    re = A.re.astype(np.float32).astype(np.float64)
+    im = A.im.astype(np.float32).astype(np.float64)
+    nz = (re != 0.0) | (im != 0.0)
+    return Op(A.n_sites, A.v[nz], A.w[nz], re[nz], im[nz])
+
+
+def times_i(A: Op) -> Op:
+    """i A (exact: a swap of the components and one sign)."""
+    return Op(A.n_sites, A.v, A.w, -A.im, A.re.copy())
+
+
+def truncate_f32(O: Op, max_weight: int = -1, cutoff: float = 0.0, top_k: int = 0, gamma: float = 0.0,
+                 dt: float = 0.0, keep: Op | None = None, divisor: float | None = None) -> Op:
+    """Truncation of an FP32 sum: the division (Lanczos) and the dissipation factor are applied
+    in FP64 and rounded to FP32 before the weight, cutoff and top-k decisions."""
+    X = O if divisor is None else divide(O, divisor)
+    if gamma != 0.0:
+        import math
+        f = np.array([math.exp(-((gamma * dt) * float(k))) for k in range(65)])
+        wt = np.array([bin(int(a) | int(b)).count("1") for a, b in zip(X.v, X.w)], np.int64)
+        X = Op(X.n_sites, X.v, X.w, X.re * f[wt], X.im * f[wt])
+    return truncate(round32(X), max_weight=max_weight, cutoff=cutoff, top_k=top_k, keep=keep)
+
+
+def commutator_f32(H: Op, O: Op) -> Op:
+    return round32(commutator(H, O))
+
+
+def rk4_step_f32(H: Op, O: Op, dt: float, max_weight: int = -1, cutoff: float = 0.0, top_k: int = 0,
+                 gamma: float = 0.0, trim_stages: int = 0, keep: Op | None = None) -> Op:
+    """The RK4 step of ``rk4_step`` with FP32 coefficients: k_j, the stage inputs and the new
+    O are stored in FP32; S = k1 + 2k2 + 2k3 + k4 is formed inside the final merge (FP64)."""
+    h2, h6 = dt / 2.0, dt / 6.0
+
+    def L(X):
+        k = round32(times_i(commutator(H, X)))
+        if trim_stages and top_k > 0:
+            k = truncate(k, top_k=top_k)
+        return k
+
+    k1 = L(O)
+    k2 = L(round32(axpy(O, h2, k1)))
+    k3 = L(round32(axpy(O, h2, k2)))
+    k4 = L(round32(axpy(O, dt, k3)))
+    S = axpy(axpy(axpy(k1, 2.0, k2), 2.0, k3), 1.0, k4)
+    On = round32(axpy(O, h6, S))
+    return truncate_f32(On, max_weight=max_weight, cutoff=cutoff, top_k=top_k, gamma=gamma, dt=dt, keep=keep)
+
+
+def lanczos_step_f32(H: Op, O_prev: Op, O_cur: Op, b_prev: float, max_weight: int = -1,
+                     cutoff: float = 0.0, top_k: int = 0) -> tuple[float, Op]:
+    """``lanczos_step`` with FP32 coefficients: A is stored in FP32, b_n = ||A|| in FP64, and
+    O_n = trunc(A / b_n) rounds the quotient to FP32 before truncating."""
+    A = round32(axpy(commutator(H, O_cur), -float(b_prev), O_prev))
+    b = norm(A)
+    if b == 0.0:
+        return 0.0, Op.empty(O_cur.n_sites)
+    return b, truncate_f32(A, max_weight=max_weight, cutoff=cutoff, top_k=top_k, divisor=b)
