@@ -384,6 +384,11 @@ def main():
                    "steps_per_s": sum_over_ranks(4) / t_lat, "products_per_s": sum_over_ranks(lat_prod) / t_lat,
                    "size": len(Ol)}
 
+    # ---------------------------------------------------------------- FP32 coefficients (2D lattice)
+    f32_res = None
+    if not args.no_learned:
+        f32_res = lattice_f32(stream)
+
     # ---------------------------------------------------------------- learned truncation
     learned_res = None
     if not args.no_learned:
@@ -413,6 +418,7 @@ def main():
             "b_n_timed": bs,
             "rk4": rk4,
             "rk4_lattice": rk4_lattice,
+            "rk4_lattice_f32": f32_res,
             "learned_truncation": learned_res,
             "roofline": roof,
             "kernels_per_step_ms": {k: round(v[1], 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1][1])},
@@ -426,6 +432,49 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+F32_WORKLOAD = ("RK4 on the open 8x8 Heisenberg lattice (336 strings), O(0) = Z at (4,4), dt=0.02, dissipation "
+                "gamma=0.1, top 2^20 strings with trimmed stages, 30 steps (t=0.6) from O(0), once with FP64 and once "
+                "with FP32 coefficients (H and O rounded to FP32; FP64 norms)")
+
+
+def lattice_f32(stream, steps: int = 30):
+    """The 2D workload run with FP64 and with FP32 coefficients from the same start: the error
+    of FP32 per observable (autocorrelation Tr(O(t) Z_c)/2^N and ||O(t)||) and the step times."""
+    import torch
+    from paper_2410_09654_gb300 import inputs as I, paulistr as ps
+    pol = ps.policy(top_k=1 << 20, gamma=0.1, trim_stages=1)
+    Ha = I.heisenberg_2d(8, 8).arrays()
+    Oa = I.single(N_SITES, "Z", 28).arrays()
+    pv, pw = I.string("Z", 28)
+    probe = (np.array([pv], np.uint64), np.array([pw], np.uint64))
+    runs = {}
+    for name, prec in (("f64", ps.PS_COEF_F64), ("f32", ps.PS_COEF_F32)):
+        H = ps.PauliSum.from_arrays(N_SITES, *Ha).set_precision(prec)
+        O = ps.PauliSum.from_arrays(N_SITES, *Oa).set_precision(prec)
+        obs, nrm = [], []
+        t_steps = 0.0
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ps.pauli_rk4_step(H, O, 0.02, pol)
+            e1.record(stream)
+            e1.synchronize()
+            t_steps += e0.elapsed_time(e1)
+            obs.append(ps.pauli_coefficients(O, *probe)[0].real)
+            nrm.append(ps.pauli_norm(O))
+        runs[name] = (np.array(obs), np.array(nrm), t_steps / steps, len(O))
+    a64, n64, t64, s64 = runs["f64"]
+    a32, n32, t32, s32 = runs["f32"]
+    return {"workload": F32_WORKLOAD,
+            "autocorrelation_abs_error_max": float(np.max(np.abs(a32 - a64))),
+            "autocorrelation_rel_error_max": float(np.max(np.abs(a32 - a64) / np.abs(a64))),
+            "autocorrelation_final": {"f64": float(a64[-1]), "f32": float(a32[-1])},
+            "norm_rel_error_max": float(np.max(np.abs(n32 - n64) / n64)),
+            "ms_per_step": {"f64": t64, "f32": t32}, "final_size": {"f64": s64, "f32": s32},
+            "note": "FP32 values in the 32-byte records: the precision study, not a bandwidth saving"}
 
 
 def learned_truncation(stream, peaks_bf16: float, lg_cap: int = 18, steps: int = 80, iters: int = 4000):

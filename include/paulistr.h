@@ -89,6 +89,22 @@ int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, 
 int pauli_sum_size(const pauli_sum* s, int64_t* n);
 int pauli_sum_n_sites(const pauli_sum* s, int* n_sites);
 
+/* Coefficient precision of a sum (FP64 by default).  In an FP32 sum every stored
+ * coefficient is an FP32 number: uploads, copies and every result a call writes into the
+ * sum are rounded to FP32 (round to nearest even) and strings that round to zero are
+ * dropped.  A merge forms each output from the exact products of its inputs (products of
+ * FP32 numbers are exact in FP64), accumulated in FP64 in the FP64 path's order - no less
+ * accurate than a compensated FP32 sum - and rounds once; truncation rounds after the
+ * division and the dissipation factor, before its decisions.  Norms, trace products and
+ * b_n stay FP64 (exact sums of the FP32 values).  Temporaries of RK4 and Lanczos steps take
+ * the precision of the operator being evolved; H's coefficients are used as stored (set H
+ * to FP32 too for an all-FP32 computation).  Setting PS_COEF_F32 rounds the current
+ * contents.  The records keep the 32-byte layout. */
+#define PS_COEF_F64 0
+#define PS_COEF_F32 1
+int pauli_sum_set_precision(pauli_sum* s, int coef_dtype);
+int pauli_sum_precision(const pauli_sum* s, int* coef_dtype);
+
 /* Copy the sum to HOST arrays of capacity cap in canonical order (v, then w,
  * ascending).  *n receives the size; PS_ERR_CAPACITY (nothing written) if cap < size. */
 int pauli_sum_download(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im,

@@ -9,12 +9,18 @@ using namespace ps;
 
 namespace {
 
+// The merge, then (FP32 sums) the single rounding of every output coefficient to FP32.
+int merge_into(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
+  PS_TRY(merge_run(sp, s, out));
+  return round_f32(out);
+}
+
 bool same_sites(const pauli_sum* a, const pauli_sum* b) { return !a || !b || a->n_sites == b->n_sites; }
 
 // A library-internal temporary sum on a given stream.
 struct Tmp {
   pauli_sum s;
-  explicit Tmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0, 0} {}
+  explicit Tmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0, 0, like->f32} {}
   ~Tmp() { dev_free(s.d, s.stream); }
   Tmp(const Tmp&) = delete;
   Tmp& operator=(const Tmp&) = delete;
@@ -43,7 +49,7 @@ int commutator_into(const pauli_sum* H, const pauli_sum* X, int rot, pauli_sum* 
   sp.rot = rot;
   sp.clsH = H->cls;
   sp.clsX = X->cls;
-  return merge_run(sp, out->stream, out);
+  return merge_into(sp, out->stream, out);
 }
 
 bool policy_valid(const pauli_trunc_policy* p) {
@@ -59,7 +65,7 @@ int ts_merge(const pauli_sum* X, int mode, pauli_sum* out) {
   sp.src[0].ts = mode;
   sp.nsrc = 1;
   sp.ring = X->n_sites;
-  return merge_run(sp, out->stream, out);
+  return merge_into(sp, out->stream, out);
 }
 
 // H written out as the list of H0's translates T_0(H0), T_1(H0), ... (not merged).
@@ -111,7 +117,7 @@ int pauli_multiply(const pauli_sum* A, const pauli_sum* B, pauli_sum* out) {
   sp.product = true;
   sp.clsH = A->cls;
   sp.clsX = B->cls;
-  return merge_run(sp, out->stream, out);
+  return merge_into(sp, out->stream, out);
 }
 
 
@@ -163,7 +169,7 @@ int pauli_ts_lanczos_step(const pauli_sum* H0, pauli_sum* O_prev, pauli_sum* O_c
     sp.nsrc = 2;
   }
   sp.ring = O_cur->n_sites;
-  PS_TRY(merge_run(sp, O_cur->stream, &A.s));
+  PS_TRY(merge_into(sp, O_cur->stream, &A.s));
   double n2 = 0.0;
   PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2, O_cur->n_sites));
   const double b = std::sqrt(n2);
@@ -188,7 +194,7 @@ int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_
   sp.src[0] = source(A, Cx{1.0, 0.0});
   sp.src[1] = source(B, Cx{alpha_re, alpha_im});
   sp.nsrc = 2;
-  return merge_run(sp, out->stream, out);
+  return merge_into(sp, out->stream, out);
 }
 
 int pauli_truncate(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt) {
@@ -225,7 +231,7 @@ int rk4_impl(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_poli
     sp.src[0] = source(O, Cx{1.0, 0.0});
     sp.src[1] = source(k, Cx{a, 0.0});
     sp.nsrc = 2;
-    return merge_run(sp, O->stream, &X.s);
+    return merge_into(sp, O->stream, &X.s);
   };
   PS_TRY(L(O, &k1.s));
   PS_TRY(stage_input(&k1.s, h2));
@@ -246,7 +252,7 @@ int rk4_impl(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_poli
   sp.clsPre = O->cls;
   sp.has_post = true;
   sp.post = Cx{h6, 0.0};
-  PS_TRY(merge_run(sp, O->stream, &X.s));
+  PS_TRY(merge_into(sp, O->stream, &X.s));
   if (cand) {
     PS_TRY(sum_reserve(cand, X.s.n, false));
     if (X.s.n > 0)
@@ -308,7 +314,7 @@ int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, 
     sp.src[0] = source(O_prev, Cx{-b_prev, 0.0});
     sp.nsrc = 1;
   }
-  PS_TRY(merge_run(sp, O_cur->stream, &A.s));
+  PS_TRY(merge_into(sp, O_cur->stream, &A.s));
   double n2 = 0.0;
   PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2));
   double b = std::sqrt(n2);

@@ -79,6 +79,7 @@ struct pauli_sum {
   int64_t cap;
   int64_t n;
   int cls;  // coefficient class: bit 0 = real parts may be non-zero, bit 1 = imaginary parts may be
+  int f32;  // FP32 coefficients: every result written into the sum is rounded to FP32
 };
 
 namespace ps {
@@ -353,6 +354,9 @@ int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cuda
 int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw, int64_t nq, cudaStream_t s,
                  double* re, double* im);
 int membership(const Rec* X, int64_t nx, const Rec* T, int64_t nt, cudaStream_t s, float* label);
+// FP32 sums: round every coefficient to FP32 and drop the strings that become zero (no-op
+// for FP64 sums).
+int round_f32(pauli_sum* s);
 
 // mlp.cu: learned truncation score ln|c| - gamma_dt wt + z of every record (storage order)
 int mlp_scores(const pauli_mlp* m, const Rec* d, int64_t n, double gamma_dt, cudaStream_t s, double* score);

@@ -434,7 +434,7 @@ int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const d
   if (!ok) return PS_ERR_INVALID;
   PS_TRY(compute_cls(s->d, n, s->stream, &s->cls));
   s->n = n;
-  return PS_OK;
+  return round_f32(s);
 }
 
 __global__ void k_unpack(const Rec* __restrict__ d, uint64_t* __restrict__ v, uint64_t* __restrict__ w,
@@ -467,7 +467,7 @@ int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, 
     return PS_ERR_INVALID;
   }
   PS_TRY(compute_cls(s->d, n, s->stream, &s->cls));
-  return PS_OK;
+  return round_f32(s);
 }
 
 int pauli_sum_download(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im, int64_t cap,
@@ -514,6 +514,18 @@ int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst) {
   }
   dst->n = src->n;
   dst->cls = src->cls;
+  return round_f32(dst);
+}
+
+int pauli_sum_set_precision(pauli_sum* s, int coef_dtype) {
+  if (!s || (coef_dtype != PS_COEF_F64 && coef_dtype != PS_COEF_F32)) return PS_ERR_INVALID;
+  s->f32 = coef_dtype == PS_COEF_F32;
+  return round_f32(s);
+}
+
+int pauli_sum_precision(const pauli_sum* s, int* coef_dtype) {
+  if (!s || !coef_dtype) return PS_ERR_INVALID;
+  *coef_dtype = s->f32 ? PS_COEF_F32 : PS_COEF_F64;
   return PS_OK;
 }
 

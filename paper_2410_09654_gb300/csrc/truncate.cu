@@ -32,6 +32,7 @@ struct TruncArgs {
   DivConst dc;
   double factor[65];     // exp(-(gamma*dt) w), w = 0..64 (passed by value: no host copy)
   int cls;               // coefficient class of the input: components that may be non-zero
+  int round32;           // FP32 sum: round to FP32 after the division and dissipation
 };
 
 __device__ __forceinline__ double sq_sum(double re, double im) {
@@ -128,6 +129,10 @@ __global__ void __launch_bounds__(kTT) k_filter(const Rec* __restrict__ in, int6
           const double f = a.factor[wt];
           if (a.cls & 1) r[k].re = __dmul_rn(r[k].re, f);
           if (a.cls & 2) r[k].im = __dmul_rn(r[k].im, f);
+        }
+        if (a.round32) {
+          r[k].re = (double)__double2float_rn(r[k].re);
+          r[k].im = (double)__double2float_rn(r[k].im);
         }
         keep[k] = !(a.max_weight >= 0 && wt > a.max_weight) && !(is_zero(r[k].re) && is_zero(r[k].im));
         if (keep[k] && (a.use_cut || ab)) {
@@ -380,7 +385,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   const bool use_w = P && P->max_weight >= 0;
   const bool use_cut = P && P->cutoff > 0.0;
   const bool use_top = P && P->top_k > 0;
-  if (!use_gamma && !use_w && !use_cut && !use_top && !divisor) return PS_OK;
+  if (!use_gamma && !use_w && !use_cut && !use_top && !divisor && !O->f32) return PS_OK;
   if (O->n == 0) return PS_OK;
   const int nsm = num_sms();
 
@@ -395,6 +400,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   a.use_div = divisor != nullptr;
   a.dc = make_divconst(divisor ? *divisor : 1.0);
   a.cls = O->cls ? O->cls : kClsComplex;
+  a.round32 = O->f32;
   if (use_gamma) {
     const double x = P->gamma * dt;
     for (int wt = 0; wt <= 64; ++wt) a.factor[wt] = std::exp(-(x * (double)wt));
@@ -475,6 +481,8 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   }
   return sum_adopt(O, outb, std::max<int64_t>(ocap, 1), (int64_t)nk);
 }
+
+int round_f32(pauli_sum* s) { return s->f32 ? truncate_run(s, nullptr, nullptr, 0.0, nullptr) : PS_OK; }
 
 }  // namespace ps
 

@@ -26,6 +26,8 @@ PS_ERR_CUDA = 4
 PS_ERR_TIMEOUT = 5
 PS_ERR_KRYLOV_EXHAUSTED = 6
 PS_ERR_NOMEM = 7
+PS_COEF_F64 = 0
+PS_COEF_F32 = 1
 
 _lib = None
 
@@ -108,6 +110,8 @@ def load(build_if_missing: bool = False):
         "pauli_launch_count": ([], I64),
         "pauli_debug_divide": ([P, I64, ctypes.c_double, P], ctypes.c_int),
         "pauli_trace_product_noalloc": ([P, P, P, P, I64, P, P, P, P, I64, P, F64P, F64P], ctypes.c_int),
+        "pauli_sum_set_precision": ([P, ctypes.c_int], ctypes.c_int),
+        "pauli_sum_precision": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "pauli_mlp_param_count": ([], I64),
         "pauli_mlp_create": ([ctypes.c_int, ctypes.c_uint64, P, ctypes.POINTER(P)], ctypes.c_int),
         "pauli_mlp_destroy": ([P], ctypes.c_int),
@@ -226,8 +230,20 @@ class PauliSum:
         v, w, re, im = self.download()
         return {(int(a), int(b)): complex(c, d) for a, b, c, d in zip(v, w, re, im)}
 
+    def set_precision(self, coef_dtype: int) -> "PauliSum":
+        """PS_COEF_F32: FP32 coefficients from now on (rounds the contents); PS_COEF_F64: FP64."""
+        _check(self._lib.pauli_sum_set_precision(self.handle, int(coef_dtype)), "pauli_sum_set_precision")
+        return self
+
+    def precision(self) -> int:
+        d = ctypes.c_int()
+        _check(self._lib.pauli_sum_precision(self.handle, ctypes.byref(d)), "pauli_sum_precision")
+        return int(d.value)
+
     def copy(self) -> "PauliSum":
         out = PauliSum(self.n_sites, len(self), self.stream.value)
+        if self.precision() == PS_COEF_F32:
+            out.set_precision(PS_COEF_F32)
         _check(self._lib.pauli_sum_copy(self.handle, out.handle), "pauli_sum_copy")
         return out
 
@@ -237,20 +253,20 @@ def _h(s):
 
 
 def pauli_commutator(H: PauliSum, O: PauliSum, out: PauliSum | None = None) -> PauliSum:
-    out = out or PauliSum(O.n_sites, 0, O.stream.value)
+    out = out if out is not None else PauliSum(O.n_sites, 0, O.stream.value)
     _check(load().pauli_commutator(H.handle, O.handle, out.handle), "pauli_commutator")
     return out
 
 
 def pauli_multiply(A: PauliSum, B: PauliSum, out: PauliSum | None = None) -> PauliSum:
     """A B (operator product; A is the outer operand, at most 61439 strings)."""
-    out = out or PauliSum(B.n_sites, 0, B.stream.value)
+    out = out if out is not None else PauliSum(B.n_sites, 0, B.stream.value)
     _check(load().pauli_multiply(A.handle, B.handle, out.handle), "pauli_multiply")
     return out
 
 
 def pauli_add(A: PauliSum, alpha: complex, B: PauliSum, out: PauliSum | None = None) -> PauliSum:
-    out = out or PauliSum(A.n_sites, 0, A.stream.value)
+    out = out if out is not None else PauliSum(A.n_sites, 0, A.stream.value)
     alpha = complex(alpha)
     _check(load().pauli_add(A.handle, alpha.real, alpha.imag, B.handle, out.handle), "pauli_add")
     return out
@@ -283,19 +299,19 @@ def pauli_lanczos_step(H: PauliSum, O_prev: PauliSum, O_cur: PauliSum, b_prev: f
 
 # translation-symmetric generators (periodic chain of n_sites sites)
 def pauli_ts_expand(G: PauliSum, out: PauliSum | None = None) -> PauliSum:
-    out = out or PauliSum(G.n_sites, 0, G.stream.value)
+    out = out if out is not None else PauliSum(G.n_sites, 0, G.stream.value)
     _check(load().pauli_ts_expand(G.handle, out.handle), "pauli_ts_expand")
     return out
 
 
 def pauli_ts_canonicalize(X: PauliSum, out: PauliSum | None = None) -> PauliSum:
-    out = out or PauliSum(X.n_sites, 0, X.stream.value)
+    out = out if out is not None else PauliSum(X.n_sites, 0, X.stream.value)
     _check(load().pauli_ts_canonicalize(X.handle, out.handle), "pauli_ts_canonicalize")
     return out
 
 
 def pauli_ts_commutator(H0: PauliSum, O0: PauliSum, out: PauliSum | None = None) -> PauliSum:
-    out = out or PauliSum(O0.n_sites, 0, O0.stream.value)
+    out = out if out is not None else PauliSum(O0.n_sites, 0, O0.stream.value)
     _check(load().pauli_ts_commutator(H0.handle, O0.handle, out.handle), "pauli_ts_commutator")
     return out
 
@@ -494,3 +510,11 @@ def pauli_rk4_step_mlp(H: PauliSum, O: PauliSum, dt: float, pol: pauli_trunc_pol
                                      _h(keep), None if model is None else model.handle, _h(cand_out)),
            "pauli_rk4_step_mlp")
     return O
+
+
+def pauli_sum_set_precision(S: PauliSum, coef_dtype: int) -> PauliSum:
+    return S.set_precision(coef_dtype)
+
+
+def pauli_sum_precision(S: PauliSum) -> int:
+    return S.precision()
