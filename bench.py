@@ -389,6 +389,11 @@ def main():
     if not args.no_learned:
         f32_res = lattice_f32(stream)
 
+    # ---------------------------------------------------------------- batched disorder realisations
+    batch_res = None
+    if not args.no_learned:
+        batch_res = batched_instances(stream)
+
     # ---------------------------------------------------------------- learned truncation
     learned_res = None
     if not args.no_learned:
@@ -419,6 +424,7 @@ def main():
             "rk4": rk4,
             "rk4_lattice": rk4_lattice,
             "rk4_lattice_f32": f32_res,
+            "batched_instances": batch_res,
             "learned_truncation": learned_res,
             "roofline": roof,
             "kernels_per_step_ms": {k: round(v[1], 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1][1])},
@@ -432,6 +438,71 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+BATCH_WORKLOAD = ("RK4 of 512 disorder realisations of the random-field XXZ chain N=32 (125 strings: XX+YY+ZZ bonds "
+                  "+ h_i Z_i, h_i ~ U[-W, W] from SplitMix64 seeded 20241012 + instance, W = 0.5 / 2 / 5 for instances "
+                  "0-170 / 171-341 / 342-511), O(0) = Z_16, dt=0.05, trimmed stages, uneven per-instance caps "
+                  "2^(8 + instance mod 7) (256 to 16384; the description's 2^14-2^20 scaled down 64x), timed once "
+                  "every instance has run 12 steps")
+
+
+def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3, loop_sample: int = 32):
+    """All instances in one tagged sum (pauli_batch_rk4_step) against the single-instance
+    path looped over a sample of the instances (scaled to all): instance-steps/s and
+    products/s of both."""
+    import torch
+    from paper_2410_09654_gb300 import inputs as I, paulistr as ps
+    n, shift = 32, 32
+    N = shift + 9
+    W = [0.5 if b <= 170 else (2.0 if b <= 341 else 5.0) for b in range(n_inst)]
+    Hs = [I.random_field_xxz_chain(n, W[b], b).arrays() for b in range(n_inst)]
+    caps = np.array([1 << (8 + b % 7) for b in range(n_inst)], np.int64)
+    hcoef = np.stack([h[2] for h in Hs])
+    Hc = ps.PauliSum.from_arrays(N, Hs[0][0], Hs[0][1], np.ones(len(Hs[0][0])), np.zeros(len(Hs[0][0])))
+    B = ps.PauliBatch(Hc, hcoef, shift, caps)
+    z = I.single(n, "Z", 16).arrays()
+    v = np.array([int(z[0][0]) | (b << shift) for b in range(n_inst)], np.uint64)
+    O = ps.PauliSum.from_arrays(N, v, np.zeros(n_inst, np.uint64), np.ones(n_inst), np.zeros(n_inst))
+    for _ in range(ramp):
+        ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
+    sizes = ps.pauli_batch_counts(B, O)
+    prod = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(timed):
+        prod += 4 * len(Hs[0][0]) * len(O)
+        ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
+    torch.cuda.synchronize()
+    t_b = (time.perf_counter() - t0) / timed
+    # the single-instance path on a sample spread over the caps and disorder strengths
+    pick = np.linspace(0, n_inst - 1, loop_sample).astype(int)
+    t_loop, prod_loop = 0.0, 0
+    for b in pick:
+        H = ps.PauliSum.from_arrays(n, *Hs[b])
+        Ob = ps.PauliSum.from_arrays(n, *z)
+        pol = ps.policy(top_k=int(caps[b]), trim_stages=1)
+        for _ in range(ramp):
+            ps.pauli_rk4_step(H, Ob, 0.05, pol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(timed):
+            prod_loop += 4 * len(Hs[b][0]) * len(Ob)
+            ps.pauli_rk4_step(H, Ob, 0.05, pol)
+        torch.cuda.synchronize()
+        t_loop += time.perf_counter() - t0
+    scale = n_inst / loop_sample
+    t_loop_all = t_loop / timed * scale  # seconds per step of all instances, looped
+    return {"workload": BATCH_WORKLOAD, "instances": n_inst, "strings": int(sizes.sum()),
+            "strings_per_instance_min_max": [int(sizes.min()), int(sizes.max())],
+            "batched": {"ms_per_step": 1e3 * t_b, "instance_steps_per_s": n_inst / t_b,
+                        "products_per_s": prod / timed / t_b},
+            "looped_single_instance": {"ms_per_step": 1e3 * t_loop_all, "instance_steps_per_s": n_inst / t_loop_all,
+                                       "products_per_s": prod_loop / t_loop * 1.0,
+                                       "sample": f"{loop_sample} instances spread over the caps, scaled to {n_inst}"},
+            "speedup": t_loop_all / t_b,
+            "not_built": "one persistent graph-captured launch and the autotuner: each step is a sequence of "
+                         "launches with host synchronisation on data-dependent sizes"}
 
 
 F32_WORKLOAD = ("RK4 on the open 8x8 Heisenberg lattice (336 strings), O(0) = Z at (4,4), dt=0.02, dissipation "

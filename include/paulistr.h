@@ -318,6 +318,39 @@ int pauli_truncate_scored(pauli_sum* O, const pauli_trunc_policy* policy, const 
 int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
                        const pauli_sum* keep, const pauli_mlp* model, pauli_sum* cand_out);
 
+/* ------------------------------------------------------------------ batched instances
+ * Many independent problems with the same H strings but their own H coefficients (for
+ * example disorder realisations of a chain, H_b = common terms + sum_i h_i^(b) Z_i) and
+ * their own truncation caps, evolved together in one sum.  A string of instance b carries
+ * b in its v bits from tag_shift up (Z letters on sites above the physical ones):
+ * key = (v | b << tag_shift, w).  These bits are transparent to the method (H's strings
+ * have none, so every product keeps the tag of its O string) and no result mixes
+ * instances.  Results equal those of each instance run alone. */
+typedef struct pauli_batch pauli_batch; /* opaque */
+
+/* H: the common strings (1..256 of them, real coefficients; the values are not used),
+ * no bits at or above tag_shift.  hcoef: HOST array [n_inst][H size] (row b = the
+ * coefficients of instance b's H, in H's string order; read during the call).  caps:
+ * HOST array [n_inst] of per-instance top-k sizes (<= 0 or caps NULL: no cap).
+ * 1 <= n_inst <= 4096; the tags must fit below H's n_sites (tag_shift + bits(n_inst - 1)
+ * <= n_sites). */
+int pauli_batch_create(const pauli_sum* H, const double* hcoef, int n_inst, int tag_shift, const int64_t* caps,
+                       pauli_batch** out);
+int pauli_batch_destroy(pauli_batch* b);
+/* One RK4 step (as pauli_rk4_step) of every instance of O: the products use each string's
+ * instance coefficients; with trim_stages each k_j is cut to its instance's cap; the new O
+ * is cut to the caps (top-k by |c|^2, ties to the smaller key, per instance).  O must hold
+ * real coefficients and only valid tags (PS_ERR_INVALID otherwise); O's precision applies. */
+int pauli_batch_rk4_step(const pauli_batch* b, const pauli_sum* H, pauli_sum* O, double dt, int trim_stages);
+/* Per-instance top-k of O to the caps. */
+int pauli_batch_truncate(const pauli_batch* b, pauli_sum* O);
+/* Strings per instance (HOST [n_inst]); PS_ERR_INVALID if a string has a tag >= n_inst or
+ * w bits at or above tag_shift. */
+int pauli_batch_counts(const pauli_batch* b, const pauli_sum* O, int64_t* counts);
+/* ||O_b|| = sqrt(sum |c|^2) per instance (HOST [n_inst]); FP64 sums whose addition order is
+ * not fixed (the last bits may differ between runs). */
+int pauli_batch_norms(const pauli_batch* b, const pauli_sum* O, double* norms);
+
 /* ------------------------------------------------------------------ profiling */
 /* Enable (1) or disable (0) per-kernel timing: every kernel launch of the library is
  * bracketed by CUDA events recorded on its launching stream.  Enabling clears the totals. */

@@ -393,3 +393,12 @@ def lanczos_step_f32(H: Op, O_prev: Op, O_cur: Op, b_prev: float, max_weight: in
     if b == 0.0:
         return 0.0, Op.empty(O_cur.n_sites)
     return b, truncate_f32(A, max_weight=max_weight, cutoff=cutoff, top_k=top_k, divisor=b)
+
+
+# ------------------------------------------------------------------ batched instances
+def batch_rk4_step(H_list, O_list, dt: float, caps, trim_stages: int = 0):
+    """Independent instances (disorder realisations): ``rk4_step`` of each (H_b, O_b) with its
+    own cap as top_k (cap <= 0: none).  The batched CUDA path must equal this instance by
+    instance; the instance tag bits it adds to the keys are removed before comparing."""
+    return [rk4_step(H, O, dt, top_k=max(int(c), 0), trim_stages=trim_stages)
+            for H, O, c in zip(H_list, O_list, caps)]

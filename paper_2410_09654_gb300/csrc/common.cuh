@@ -339,6 +339,11 @@ struct MergeSpec {
   bool has_post = false;
   Cx post{1.0, 0.0};
   int clsH = kClsComplex, clsX = kClsComplex, clsPre = kClsComplex;  // coefficient classes of the operands
+  // Batched instances (optional): the coefficient of H term h for a string x of instance
+  // b = x.v >> hb_shift is hbatch[b * nH + h] (the real factor of H's component); H's own
+  // coefficients only fix the class.  Needs the table emission of full records.
+  const double* hbatch = nullptr;
+  int hb_shift = 0;
 };
 int merge_run(const MergeSpec& spec, cudaStream_t s, pauli_sum* out);
 int ts_translates(const Rec* G, int64_t n, int ring, cudaStream_t s, Rec* out);

@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(kEmitThreads, 5) k_emit_tab(const Rec* __restr
                                                   unsigned long long* __restrict__ cur,
                                                   uint64_t* __restrict__ entries, Contrib* __restrict__ fout,
                                                   unsigned long long* __restrict__ total,
-                                                  unsigned long long* __restrict__ next_tile) {
+                                                  unsigned long long* __restrict__ next_tile,
+                                                  const double* __restrict__ hb, int hb_shift) {
   constexpr int S = tab_stride(NW);
   constexpr int kTabWords = kTabPos * kTabVals * S;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -444,7 +445,13 @@ __global__ void __launch_bounds__(kEmitThreads, 5) k_emit_tab(const Rec* __restr
         const int ph = (product_phase(hk.x, hk.y, xv, xw) + es.rot + es.uH + es.uX) & 3;
         r.v = hk.x ^ xv;
         r.w = hk.y ^ xw;
-        r.val = neg_if(scaled(hs.s, hs.e, xs, 1), (ph & 2) != 0);
+        double hsv = hs.s;
+        int hse = hs.e;
+        if (hb) {  // batched instances: the H coefficients of x's instance (tag = v >> hb_shift)
+          hsv = hb[(size_t)(xv >> hb_shift) * (size_t)nh + h];
+          hse = kNoPow2;
+        }
+        r.val = neg_if(scaled(hsv, hse, xs, 1), (ph & 2) != 0);
         r.code = h;
         r.pad = 0;
       }
@@ -499,7 +506,7 @@ template <bool FULL, int NW>
 int launch_emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, const uint32_t* fH,
                     const HScal* hscal, int nh, const uint32_t* T, const EmitScalars& es,
                     unsigned long long* cur, uint64_t* entries, Contrib* fout, unsigned long long* total, int nsm,
-                    cudaStream_t s) {
+                    cudaStream_t s, const double* hb, int hb_shift) {
   Buf<unsigned long long> next_tile;
   PS_TRY(next_tile.alloc(1, s));
   PS_CUDA(cudaMemsetAsync(next_tile.p, 0, sizeof(unsigned long long), s));
@@ -509,7 +516,7 @@ int launch_emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, 
   int per_sm = 0;
   PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit_tab<FULL, NW>, kEmitThreads, sm));
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * nsm, ceil_div(nX, kEmitThreads)));
-  PS_LAUNCH("k_emit_products", s, k_emit_tab<FULL, NW><<<grid, kEmitThreads, sm, s>>>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, next_tile.p));
+  PS_LAUNCH("k_emit_products", s, k_emit_tab<FULL, NW><<<grid, kEmitThreads, sm, s>>>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, next_tile.p, hb, hb_shift));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -517,12 +524,13 @@ int launch_emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, 
 template <bool FULL>
 int emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, const uint32_t* fH, const HScal* hscal,
              int nh, const uint32_t* T, const EmitScalars& es, unsigned long long* cur,
-             uint64_t* entries, Contrib* fout, unsigned long long* total, int nsm, cudaStream_t s) {
+             uint64_t* entries, Contrib* fout, unsigned long long* total, int nsm, cudaStream_t s,
+             const double* hb = nullptr, int hb_shift = 0) {
   const int nw = (nh + 31) / 32;
-  if (nw <= 2) return launch_emit_tab<FULL, 2>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
-  if (nw <= 4) return launch_emit_tab<FULL, 4>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
-  if (nw <= 6) return launch_emit_tab<FULL, 6>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
-  return launch_emit_tab<FULL, 8>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s);
+  if (nw <= 2) return launch_emit_tab<FULL, 2>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s, hb, hb_shift);
+  if (nw <= 4) return launch_emit_tab<FULL, 4>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s, hb, hb_shift);
+  if (nw <= 6) return launch_emit_tab<FULL, 6>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s, hb, hb_shift);
+  return launch_emit_tab<FULL, 8>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, nsm, s, hb, hb_shift);
 }
 
 // Emission of an extra source (code kCodeSrc + i) or of the pre operand (kCodePre): FULL, the
@@ -1667,6 +1675,8 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   const bool ranked_wide = !ranked && !has_ts && ncode_h + sp.nsrc <= RankGeom<16>::kBits;
   const bool full = structured && ranked && (uint64_t)bound_total * sizeof(Contrib) <= kFullBudget;
   if (has_ts && !full) return PS_ERR_INVALID;  // representatives need full records: one component
+  // per-instance H coefficients ride on the table emission of full records
+  if (sp.hbatch && nX > 0 && !(full && sp.nH <= kMaskBits && !sp.product)) return PS_ERR_INVALID;
 
   auto pow2_exp = [](double x) -> int {
     uint64_t b;
@@ -1772,7 +1782,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_TRY(tab.alloc((size_t)kTabPos * kTabVals * stride, s));
     PS_LAUNCH("k_anti_table", s, k_anti_table<<<(kTabPos * kTabVals + 255) / 256, 256, 0, s>>>(sp.H, sp.nH, stride, tab.p));
     PS_CUDA(cudaGetLastError());
-    if (full) PS_TRY(emit_tab<true>(sp.X, fX.p, nX, sp.H, fH.p, hscal.p, sp.nH, tab.p, es, cur.p, nullptr, fent.p, counters.p, nsm, s));
+    if (full) PS_TRY(emit_tab<true>(sp.X, fX.p, nX, sp.H, fH.p, hscal.p, sp.nH, tab.p, es, cur.p, nullptr, fent.p, counters.p, nsm, s, sp.hbatch, sp.hb_shift));
     else PS_TRY(emit_tab<false>(sp.X, fX.p, nX, sp.H, fH.p, nullptr, sp.nH, tab.p, es, cur.p, entries.p, nullptr, counters.p, nsm, s));
   } else if (nX > 0) {
     for (int h0 = 0; h0 < sp.nH; h0 += kHChunk) {

@@ -110,6 +110,12 @@ def load(build_if_missing: bool = False):
         "pauli_launch_count": ([], I64),
         "pauli_debug_divide": ([P, I64, ctypes.c_double, P], ctypes.c_int),
         "pauli_trace_product_noalloc": ([P, P, P, P, I64, P, P, P, P, I64, P, F64P, F64P], ctypes.c_int),
+        "pauli_batch_create": ([P, P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)], ctypes.c_int),
+        "pauli_batch_destroy": ([P], ctypes.c_int),
+        "pauli_batch_rk4_step": ([P, P, P, ctypes.c_double, ctypes.c_int], ctypes.c_int),
+        "pauli_batch_truncate": ([P, P], ctypes.c_int),
+        "pauli_batch_counts": ([P, P, P], ctypes.c_int),
+        "pauli_batch_norms": ([P, P, P], ctypes.c_int),
         "pauli_sum_set_precision": ([P, ctypes.c_int], ctypes.c_int),
         "pauli_sum_precision": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "pauli_mlp_param_count": ([], I64),
@@ -518,3 +524,52 @@ def pauli_sum_set_precision(S: PauliSum, coef_dtype: int) -> PauliSum:
 
 def pauli_sum_precision(S: PauliSum) -> int:
     return S.precision()
+
+
+# ------------------------------------------------------------------ batched instances
+class PauliBatch:
+    """Per-instance H coefficients and caps of instance-tagged sums (owns one ``pauli_batch*``)."""
+
+    def __init__(self, H: PauliSum, hcoef, tag_shift: int, caps=None):
+        lib = load()
+        self._lib = lib
+        hc = np.ascontiguousarray(hcoef, dtype=np.float64)
+        if hc.ndim != 2:
+            raise ValueError("hcoef must be [n_inst, |H|]")
+        self.n_inst = int(hc.shape[0])
+        self.tag_shift = int(tag_shift)
+        cp = None if caps is None else np.ascontiguousarray(caps, dtype=np.int64)
+        h = ctypes.c_void_p()
+        _check(lib.pauli_batch_create(H.handle, hc.ctypes.data_as(ctypes.c_void_p), self.n_inst, self.tag_shift,
+                                      None if cp is None else cp.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)),
+               "pauli_batch_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and self._lib is not None:
+            self._lib.pauli_batch_destroy(h)
+            self.handle = None
+
+
+def pauli_batch_rk4_step(B: PauliBatch, H: PauliSum, O: PauliSum, dt: float, trim_stages: int = 0) -> PauliSum:
+    _check(load().pauli_batch_rk4_step(B.handle, H.handle, O.handle, float(dt), int(trim_stages)),
+           "pauli_batch_rk4_step")
+    return O
+
+
+def pauli_batch_truncate(B: PauliBatch, O: PauliSum) -> PauliSum:
+    _check(load().pauli_batch_truncate(B.handle, O.handle), "pauli_batch_truncate")
+    return O
+
+
+def pauli_batch_counts(B: PauliBatch, O: PauliSum) -> np.ndarray:
+    out = np.zeros(B.n_inst, np.int64)
+    _check(load().pauli_batch_counts(B.handle, O.handle, out.ctypes.data_as(ctypes.c_void_p)), "pauli_batch_counts")
+    return out
+
+
+def pauli_batch_norms(B: PauliBatch, O: PauliSum) -> np.ndarray:
+    out = np.zeros(B.n_inst, np.float64)
+    _check(load().pauli_batch_norms(B.handle, O.handle, out.ctypes.data_as(ctypes.c_void_p)), "pauli_batch_norms")
+    return out
