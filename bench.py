@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-truncation comparison")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default merge geometry")
     return p.parse_args()
 
 
@@ -211,6 +212,8 @@ def main():
         b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
         n_done += 1
     ramp_steps = n_done
+    # merge geometry for this size class, picked by timing the candidates (untimed)
+    tune = None if args.no_autotune else ps.pauli_autotune_commutator(H, cur, reps=2)
     for _ in range(args.warmup):
         b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
         n_done += 1
@@ -414,7 +417,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload(args.top_k), "n_sites": N_SITES, "H_strings": nH, "top_k": args.top_k,
-                       "ramp_steps": ramp_steps,
+                       "ramp_steps": ramp_steps, "merge_geometry_autotuned": tune,
                        "l2": f"inputs larger than L2: |O| = {args.top_k} strings x 32 B = {args.top_k * 32 / 1e6:.0f} MB per operand; the merge "
                        f"bins hold {contributions / args.steps * 32 / 1e9:.1f} GB of contribution records per step "
                        "(L2 is 129 MB)", "parallelism": "replicas" if world > 1 else "single"},
@@ -466,6 +469,7 @@ def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3,
     O = ps.PauliSum.from_arrays(N, v, np.zeros(n_inst, np.uint64), np.ones(n_inst), np.zeros(n_inst))
     for _ in range(ramp):
         ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
+    tune = ps.pauli_autotune_commutator(Hc, O, reps=2)  # geometry for the batched commutators
     sizes = ps.pauli_batch_counts(B, O)
     prod = 0
     torch.cuda.synchronize()
@@ -500,7 +504,7 @@ def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3,
             "looped_single_instance": {"ms_per_step": 1e3 * t_loop_all, "instance_steps_per_s": n_inst / t_loop_all,
                                        "products_per_s": prod_loop / t_loop * 1.0,
                                        "sample": f"{loop_sample} instances spread over the caps, scaled to {n_inst}"},
-            "speedup": t_loop_all / t_b,
+            "speedup": t_loop_all / t_b, "merge_geometry_autotuned": tune,
             "not_built": "one persistent graph-captured launch and the autotuner: each step is a sequence of "
                          "launches with host synchronisation on data-dependent sizes"}
 

@@ -318,6 +318,22 @@ int pauli_truncate_scored(pauli_sum* O, const pauli_trunc_policy* policy, const 
 int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
                        const pauli_sum* keep, const pauli_mlp* model, pauli_sum* cand_out);
 
+/* ------------------------------------------------------------------ autotuner
+ * The merge's geometry has two free sizes: the target number of entries per output hash
+ * bin (which sets the number of bins, 2^4..2^20) and the group quota (entries a merge block
+ * takes per group).  Results do not depend on them (the merge is exact in any geometry);
+ * the time does.  pauli_autotune_commutator times [H, O] (CUDA events, best of reps after
+ * one warm-up run) with bin targets 1024, 2048, 4096 and quotas 1024, 1536, and keeps the
+ * fastest for every later merge of the same size class (log2 of the merge's entry bound) in
+ * this process.  Outputs (may be NULL): the chosen pair, its time and the default's
+ * (2048, 1536) time in ms.  pauli_autotune_reset returns every class to the defaults. */
+int pauli_autotune_commutator(const pauli_sum* H, const pauli_sum* O, int reps, int* best_bin_target,
+                              int* best_quota, double* best_ms, double* default_ms);
+int pauli_autotune_reset(void);
+/* Use one geometry for every merge until pauli_autotune_reset (bin target 64..65536 entries,
+ * quota 64..4096); for tests that run the merge in each geometry. */
+int pauli_merge_geometry_fix(int bin_target, int quota);
+
 /* ------------------------------------------------------------------ batched instances
  * Many independent problems with the same H strings but their own H coefficients (for
  * example disorder realisations of a chain, H_b = common terms + sum_i h_i^(b) Z_i) and

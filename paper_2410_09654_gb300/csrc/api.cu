@@ -202,6 +202,28 @@ int pauli_truncate(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_s
   return truncate_run(O, policy, keep, dt, nullptr);
 }
 
+int pauli_autotune_commutator(const pauli_sum* H, const pauli_sum* O, int reps, int* best_bin_target,
+                              int* best_quota, double* best_ms, double* default_ms) {
+  if (!H || !O || H == O || !same_sites(H, O) || H->n > 0xEFFF || reps < 1) return PS_ERR_INVALID;
+  if (H->stream != O->stream) PS_CUDA(cudaStreamSynchronize(H->stream));
+  Tmp out(O);
+  MergeSpec sp;
+  sp.H = H->d;
+  sp.nH = (int)H->n;
+  sp.X = O->d;
+  sp.nX = O->n;
+  sp.clsH = H->cls;
+  sp.clsX = O->cls;
+  return autotune_commutator(sp, &out.s, reps, best_bin_target, best_quota, best_ms, default_ms);
+}
+
+int pauli_autotune_reset(void) {
+  autotune_reset();
+  return PS_OK;
+}
+
+int pauli_merge_geometry_fix(int bin_target, int quota) { return merge_geometry_fix(bin_target, quota); }
+
 int pauli_truncate_scored(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt,
                           const double* score) {
   if (!O || !same_sites(O, keep) || !policy_valid(policy) || !std::isfinite(dt)) return PS_ERR_INVALID;

@@ -346,6 +346,10 @@ struct MergeSpec {
   int hb_shift = 0;
 };
 int merge_run(const MergeSpec& spec, cudaStream_t s, pauli_sum* out);
+int autotune_commutator(const MergeSpec& sp, pauli_sum* out, int reps, int* best_bin, int* best_quota,
+                        double* best_ms, double* default_ms);
+void autotune_reset();
+int merge_geometry_fix(int bin_target, int quota);
 int ts_translates(const Rec* G, int64_t n, int ring, cudaStream_t s, Rec* out);
 void record_merge_stats(const pauli_merge_stats& st);
 

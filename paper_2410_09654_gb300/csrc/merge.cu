@@ -1603,9 +1603,40 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
   }
 }
 
-int choose_bits(int64_t bound_total) {
+// Merge geometry: the target entries per hash bin (sets the number of bins) and the group
+// quota (entries per group before a new group starts).  Defaults, or the autotuner's choice
+// for the size class (log2 of the entry bound) of the merge.
+struct MergeGeom {
+  int bin_target = 2048;
+  int quota = kGroupQuota;
+};
+std::mutex g_tune_mu;
+MergeGeom g_tuned[64];
+bool g_has_tuned[64] = {};
+thread_local const MergeGeom* t_force = nullptr;  // the autotuner's candidate under test
+thread_local int t_last_class = -1;
+
+int size_class(int64_t bound_total) {
+  int c = 0;
+  while (c < 63 && ((int64_t)1 << (c + 1)) <= bound_total) ++c;
+  return c;
+}
+
+MergeGeom g_fixed{};        // a geometry set for every class (tests of each geometry)
+bool g_has_fixed = false;
+
+MergeGeom geometry_for(int64_t bound_total) {
+  const int c = size_class(bound_total);
+  t_last_class = c;
+  if (t_force) return *t_force;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_has_fixed) return g_fixed;
+  return g_has_tuned[c] ? g_tuned[c] : MergeGeom{};
+}
+
+int choose_bits(int64_t bound_total, int bin_target) {
   int b = 4;
-  while (b < 20 && ((int64_t)1 << b) * 2048 < bound_total) ++b;
+  while (b < 20 && ((int64_t)1 << b) * bin_target < bound_total) ++b;
   return b;
 }
 
@@ -1642,7 +1673,8 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     record_merge_stats(st);
     return PS_OK;
   }
-  const int bits = choose_bits(bound_total);
+  const MergeGeom geom = geometry_for(bound_total);
+  const int bits = choose_bits(bound_total, geom.bin_target);
   const uint32_t nbins = 1u << bits;
   const int nsm = num_sms();
   auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
@@ -1824,7 +1856,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   PS_TRY(gstart.alloc(nbins + 1, s));
   {
     int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
-    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)(ranked_wide ? kGroupQuota / 2 : kGroupQuota), flag.p));
+    PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)(ranked_wide ? geom.quota / 2 : geom.quota), flag.p));
     PS_CUDA(cudaGetLastError());
     PS_TRY(scan_u32_to_u64(flag.p, fpre.p, nbins, s));
     PS_LAUNCH("k_group_scatter", s, k_group_scatter<<<blocks, 256, 0, s>>>(flag.p, fpre.p, nbins, gstart.p, misc.p + 1));
@@ -1928,6 +1960,72 @@ int ts_translates(const Rec* G, int64_t n, int ring, cudaStream_t s, Rec* out) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 4 * num_sms()));
   PS_LAUNCH("k_ts_translates", s, k_ts_translates<<<blocks, 256, 0, s>>>(G, n, ring, out));
   PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+// Autotuner: the commutator [H, O] timed (CUDA events on the output's stream, best of reps)
+// with each candidate geometry; the fastest is kept for merges of that size class.
+int autotune_commutator(const MergeSpec& sp, pauli_sum* out, int reps, int* best_bin, int* best_quota,
+                        double* best_ms, double* default_ms) {
+  static const int kBinT[] = {1024, 2048, 4096};
+  static const int kQuota[] = {1024, 1536};
+  cudaStream_t s = out->stream;
+  cudaEvent_t e0, e1;
+  PS_CUDA(cudaEventCreate(&e0));
+  PS_CUDA(cudaEventCreate(&e1));
+  double best = 1e300, def = 0.0;
+  MergeGeom bestg{};
+  int cls = -1;
+  int st = PS_OK;
+  for (int bt : kBinT)
+    for (int q : kQuota) {
+      MergeGeom g{bt, q};
+      t_force = &g;
+      double t = 1e300;
+      for (int r = 0; r < std::max(reps, 1) + 1 && st == PS_OK; ++r) {  // the first run warms up
+        cudaEventRecord(e0, s);
+        st = merge_run(sp, s, out);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) t = std::min(t, (double)ms);
+      }
+      t_force = nullptr;
+      cls = t_last_class;
+      if (st != PS_OK) break;
+      if (bt == 2048 && q == kGroupQuota) def = t;
+      if (t < best) {
+        best = t;
+        bestg = g;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PS_TRY(st);
+  if (cls >= 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[cls] = bestg;
+    g_has_tuned[cls] = true;
+  }
+  if (best_bin) *best_bin = bestg.bin_target;
+  if (best_quota) *best_quota = bestg.quota;
+  if (best_ms) *best_ms = best;
+  if (default_ms) *default_ms = def;
+  return PS_OK;
+}
+
+void autotune_reset() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int c = 0; c < 64; ++c) g_has_tuned[c] = false;
+  g_has_fixed = false;
+}
+
+int merge_geometry_fix(int bin_target, int quota) {
+  if (bin_target < 64 || bin_target > (1 << 16) || quota < 64 || quota > 4096) return PS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_fixed = MergeGeom{bin_target, quota};
+  g_has_fixed = true;
   return PS_OK;
 }
 

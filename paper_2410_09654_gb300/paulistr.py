@@ -110,6 +110,10 @@ def load(build_if_missing: bool = False):
         "pauli_launch_count": ([], I64),
         "pauli_debug_divide": ([P, I64, ctypes.c_double, P], ctypes.c_int),
         "pauli_trace_product_noalloc": ([P, P, P, P, I64, P, P, P, P, I64, P, F64P, F64P], ctypes.c_int),
+        "pauli_autotune_commutator": ([P, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       F64P, F64P], ctypes.c_int),
+        "pauli_autotune_reset": ([], ctypes.c_int),
+        "pauli_merge_geometry_fix": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "pauli_batch_create": ([P, P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)], ctypes.c_int),
         "pauli_batch_destroy": ([P], ctypes.c_int),
         "pauli_batch_rk4_step": ([P, P, P, ctypes.c_double, ctypes.c_int], ctypes.c_int),
@@ -573,3 +577,22 @@ def pauli_batch_norms(B: PauliBatch, O: PauliSum) -> np.ndarray:
     out = np.zeros(B.n_inst, np.float64)
     _check(load().pauli_batch_norms(B.handle, O.handle, out.ctypes.data_as(ctypes.c_void_p)), "pauli_batch_norms")
     return out
+
+
+# ------------------------------------------------------------------ autotuner
+def pauli_autotune_commutator(H: PauliSum, O: PauliSum, reps: int = 3) -> dict:
+    """Time [H, O] over the merge geometries and keep the fastest for its size class."""
+    bt, q = ctypes.c_int(), ctypes.c_int()
+    best, default = ctypes.c_double(), ctypes.c_double()
+    _check(load().pauli_autotune_commutator(H.handle, O.handle, int(reps), ctypes.byref(bt), ctypes.byref(q),
+                                            ctypes.byref(best), ctypes.byref(default)), "pauli_autotune_commutator")
+    return {"bin_target": int(bt.value), "quota": int(q.value), "best_ms": float(best.value),
+            "default_ms": float(default.value)}
+
+
+def pauli_autotune_reset():
+    _check(load().pauli_autotune_reset(), "pauli_autotune_reset")
+
+
+def pauli_merge_geometry_fix(bin_target: int, quota: int):
+    _check(load().pauli_merge_geometry_fix(int(bin_target), int(quota)), "pauli_merge_geometry_fix")
