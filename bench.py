@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-truncation comparison")
     p.add_argument("--no-autotune", action="store_true", help="keep the default merge geometry")
+    p.add_argument("--merge-geometry", default=None,
+                   help="BIN_TARGET,QUOTA: fix the merge geometry instead of tuning it (profiling runs)")
     return p.parse_args()
 
 
@@ -213,7 +215,12 @@ def main():
         n_done += 1
     ramp_steps = n_done
     # merge geometry for this size class, picked by timing the candidates (untimed)
-    tune = None if args.no_autotune else ps.pauli_autotune_commutator(H, cur, reps=2)
+    if args.merge_geometry:
+        bt, q = (int(x) for x in args.merge_geometry.split(","))
+        ps.pauli_merge_geometry_fix(bt, q)
+        tune = {"bin_target": bt, "quota": q, "fixed": True}
+    else:
+        tune = None if args.no_autotune else ps.pauli_autotune_commutator(H, cur, reps=2)
     for _ in range(args.warmup):
         b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
         n_done += 1
@@ -395,7 +402,7 @@ def main():
     # ---------------------------------------------------------------- batched disorder realisations
     batch_res = None
     if not args.no_learned:
-        batch_res = batched_instances(stream)
+        batch_res = batched_instances(stream, fixed_geometry=bool(args.merge_geometry))
 
     # ---------------------------------------------------------------- learned truncation
     learned_res = None
@@ -450,7 +457,8 @@ BATCH_WORKLOAD = ("RK4 of 512 disorder realisations of the random-field XXZ chai
                   "every instance has run 12 steps")
 
 
-def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3, loop_sample: int = 32):
+def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3, loop_sample: int = 32,
+                      fixed_geometry: bool = False):
     """All instances in one tagged sum (pauli_batch_rk4_step) against the single-instance
     path looped over a sample of the instances (scaled to all): instance-steps/s and
     products/s of both."""
@@ -469,7 +477,7 @@ def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3,
     O = ps.PauliSum.from_arrays(N, v, np.zeros(n_inst, np.uint64), np.ones(n_inst), np.zeros(n_inst))
     for _ in range(ramp):
         ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
-    tune = ps.pauli_autotune_commutator(Hc, O, reps=2)  # geometry for the batched commutators
+    tune = None if fixed_geometry else ps.pauli_autotune_commutator(Hc, O, reps=2)  # batched commutators
     sizes = ps.pauli_batch_counts(B, O)
     prod = 0
     torch.cuda.synchronize()
