@@ -263,8 +263,10 @@ int pauli_last_merge_stats(pauli_merge_stats* out);
  *     of 16 site bins (site j, 0-based, in bin floor(16 j / N)) the fractions of the bin's
  *     sites holding I, X, Y, Z at x[3 + 4b + 0..3] (zeros for an empty bin); x[67..79] = 0;
  *   z = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 (W1 128x80, W2 128x128, rows = outputs);
- *   truncation score = ln|c| - gamma dt wt + z (ln|c| after the dissipation factor), so a
- *     network that outputs 0 ranks exactly as |c| does.
+ *   truncation score = ln|c| - gamma dt wt + z (ln|c| after the dissipation factor), ranked
+ *     through the equivalent rank value |c|^2 e^(2 (z - gamma dt wt)) = e^(2 score), which is
+ *     |c|^2 bit for bit when z - gamma dt wt = 0: a network that outputs 0 ranks exactly as
+ *     |c| does (without dissipation).
  * Flat FP32 parameter layout (pauli_mlp_param_count() = 27009 floats): W1 (row-major),
  * b1 (128), W2 (row-major), b2 (128), w3 (128), b3 (1).
  * All calls are ordered on the model's stream; sums on another stream are synchronised
@@ -283,7 +285,8 @@ int pauli_mlp_set_params(pauli_mlp* m, const float* params, int64_t n);
 /* Per string of O in storage order, into DEVICE arrays (caller-owned):
  *   features: x[80 * i + k] as BF16 bit patterns (round to nearest even);
  *   logits:   z[i] (FP32);
- *   scores:   score[i] = ln|c_i| - gamma_dt wt_i + z_i (FP64; -inf for c = 0).
+ *   scores:   rank[i] = |c_i|^2 e^(2 (z_i - gamma_dt wt_i)) (FP64; 0 for c = 0), the values
+ *             the learned truncation ranks by (pass them to pauli_truncate_scored).
  * O must have the model's n_sites.  Each call synchronises the model's stream. */
 int pauli_mlp_features(const pauli_mlp* m, const pauli_sum* O, uint16_t* x);
 int pauli_mlp_logits(const pauli_mlp* m, const pauli_sum* O, float* z);
@@ -323,7 +326,7 @@ int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_
  * bin (which sets the number of bins, 2^4..2^20) and the group quota (entries a merge block
  * takes per group).  Results do not depend on them (the merge is exact in any geometry);
  * the time does.  pauli_autotune_commutator times [H, O] (CUDA events, best of reps after
- * one warm-up run) with bin targets 1024, 2048, 4096 and quotas 1024, 1536, and keeps the
+ * one warm-up run) with bin targets 1024, 2048, 4096, 8192 and quotas 1024, 1536, and keeps the
  * fastest for every later merge of the same size class (log2 of the merge's entry bound) in
  * this process.  Outputs (may be NULL): the chosen pair, its time and the default's
  * (2048, 1536) time in ms.  pauli_autotune_reset returns every class to the defaults. */

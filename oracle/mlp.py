@@ -30,7 +30,8 @@ Parity: every function here is pinned by ``tests/test_mlp_oracle.py`` (features 
 per-site letter counting, the network by closed-form special cases and positive
 homogeneity, gradients by central finite differences of the forward pass, Adam by
 its closed-form first step, the scored truncation by brute force and by its
-reduction to the pinned |c| truncation of ``oracle.truncate``).
+reduction to the pinned |c| truncation of ``oracle.truncate``; rank values by their
+closed form for a zero network and their order against the scores).
 """
 from __future__ import annotations
 
@@ -139,6 +140,18 @@ def scores(p: np.ndarray, v, w, re, im, n_sites: int, gamma_dt: float = 0.0) -> 
     a2 = np.asarray(re, np.float64) ** 2 + np.asarray(im, np.float64) ** 2
     with np.errstate(divide="ignore"):
         return 0.5 * np.log(a2) - gamma_dt * wt + z  # -inf for c = 0
+
+
+def rank_values(p: np.ndarray, v, w, re, im, n_sites: int, gamma_dt: float = 0.0) -> np.ndarray:
+    """|c|^2 e^{2 (z - gamma dt wt)} = exp(2 score): the same order as ``scores`` without a
+    logarithm, and exactly |c|^2 when the exponent is zero (the ranking quantity the library
+    computes for learned truncation)."""
+    X = features(v, w, re, im, n_sites)
+    z, _ = forward(p, X)
+    wt = np.array([bin(int(a) | int(b)).count("1") for a, b in zip(v, w)], np.float64)
+    q = np.asarray(re, np.float64) ** 2 + np.asarray(im, np.float64) ** 2
+    e = 2.0 * (z - gamma_dt * wt)
+    return np.where(e == 0.0, q, q * np.exp(e))
 
 
 def truncate_scored(v, w, re, im, score, max_weight: int = -1, cutoff: float = 0.0, top_k: int = 0,

@@ -9,7 +9,13 @@
 //     I, X, Y, Z (x[3 + 4b + t]); x[67..79] = 0.
 //   z = w3 . relu(W2 relu(W1 x + b1) + b2) + b3, W1 128x80, W2 128x128 (rows = outputs).
 //   loss: mean binary cross-entropy on z; update: bias-corrected Adam.
-//   truncation score: ln|c| - gamma dt wt + z (ln|c| after the dissipation factor).
+//   truncation score: ln|c| - gamma dt wt + z (ln|c| after the dissipation factor), ranked
+//     through the order-equivalent rank value |c|^2 e^(2 (z - gamma dt wt)), which is |c|^2
+//     itself when the exponent is zero.
+//
+// Only the rank value's |c|^2 and one product are FP64 (the FP64 rate of this part is low):
+// ln|c| for the feature is FP32 from the exponent and leading mantissa bits of the larger
+// component, and the rescaling factor is a power of two times exp2 of a fraction in FP32.
 //
 // The products run on mma.sync m16n8k16 (bf16 in, fp32 accumulate).  Each warp owns 16
 // rows; the accumulator of one layer is repacked in registers as the A operand of the next
@@ -41,11 +47,17 @@ struct FeatConst {
   uint64_t bin_mask[16];
   int bin_size[16];
   int n_sites;
+  float x2_floor;  // ln(1e-300) / 16
+  float ln2;       // ln 2
+  float log2e;     // log2(e)
 };
 
 FeatConst make_featconst(int n) {
   FeatConst f{};
   f.n_sites = n;
+  f.x2_floor = (float)(std::log(1e-300) / 16.0);
+  f.ln2 = (float)std::log(2.0);
+  f.log2e = (float)(1.0 / std::log(2.0));
   for (int j = 0; j < n; ++j) {
     const int b = (16 * j) / n;
     f.bin_mask[b] |= 1ull << j;
@@ -65,6 +77,36 @@ __device__ __forceinline__ bool bf16_pos(uint32_t pair, int half) {
   return h != 0 && (h & 0x8000u) == 0;
 }
 
+// ln(max(|c|, 1e-300)) / 16 in FP32: with a = max(|re|, |im|) = m 2^e (m in [1, 2), from the
+// leading 23 mantissa bits) and b the other component, ln|c| = e ln 2 + ln m + ln(1 + (b/a)^2)/2.
+// Integer and FP32 operations only.
+__device__ __forceinline__ float feature_lnc(double re, double im, const FeatConst& fc) {
+  const uint64_t ua = (uint64_t)__double_as_longlong(re) & 0x7FFFFFFFFFFFFFFFull;
+  const uint64_t ub = (uint64_t)__double_as_longlong(im) & 0x7FFFFFFFFFFFFFFFull;
+  const uint64_t hi = ua > ub ? ua : ub, lo = ua > ub ? ub : ua;  // non-negative doubles order like bits
+  if (hi < 0x01A56E1FC2F8F359ull) return fc.x2_floor;              // below 1e-300 (and zeros)
+  const int ea = (int)(hi >> 52), el = (int)(lo >> 52);
+  const float mh = __int_as_float(0x3F800000 | (int)((hi >> 29) & 0x7FFFFF));
+  float r = 0.0f;
+  if (el > 0 && ea - el < 60) {
+    const float ml = __int_as_float(0x3F800000 | (int)((lo >> 29) & 0x7FFFFF));
+    r = ldexpf(__fdiv_rn(ml, mh), el - ea);
+  }
+  const float lnc = (float)(ea - 1023) * fc.ln2 + logf(mh) + 0.5f * log1pf(r * r);
+  return lnc * 0.0625f;
+}
+
+// Rank value |c|^2 e^(2 (z - gdt wt)): exactly q when the exponent is zero; otherwise
+// q * exp2(f) * 2^k with t = 2 (z - gdt wt) log2(e) = k + f, k integer, f in [0, 1).
+__device__ __forceinline__ double rank_value(double q, float z, float gdt_wt, const FeatConst& fc) {
+  float t = 2.0f * (z - gdt_wt);
+  if (t == 0.0f || q == 0.0) return q;
+  t = fminf(fmaxf(t * fc.log2e, -2000.0f), 2000.0f);
+  const float kf = floorf(t);
+  const double p = __dmul_rn(q, (double)exp2f(t - kf));
+  return scalbn(p, (int)kf);
+}
+
 // Feature k of a string (0 <= k < 80).
 __device__ __forceinline__ float feature(const Rec& r, const FeatConst& fc, int k) {
   const uint64_t s = r.v | r.w;
@@ -74,7 +116,7 @@ __device__ __forceinline__ float feature(const Rec& r, const FeatConst& fc, int 
     const int ext = s ? (63 - __clzll((long long)s)) - (__ffsll((long long)s) - 1) + 1 : 0;
     return __fdiv_rn((float)ext, n);
   }
-  if (k == 2) return (float)(log(fmax(hypot(r.re, r.im), 1e-300)) / 16.0);
+  if (k == 2) return feature_lnc(r.re, r.im, fc);
   if (k >= 67) return 0.0f;
   const int b = (k - 3) >> 2, t = (k - 3) & 3;
   const int sz = fc.bin_size[b];
@@ -202,8 +244,8 @@ struct MlpDev {
 };
 
 // ---------------------------------------------------------------- inference
-// Per string: optional features (bf16 bits, [n][80]), logit z, and the truncation score
-// ln|c| - gamma_dt wt + z (FP64).
+// Per string: optional features (bf16 bits, [n][80]), logit z, and the rank value
+// |c|^2 e^(2 (z - gamma_dt wt)) (FP64) that orders strings like ln|c| - gamma_dt wt + z.
 __global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, int64_t n, FeatConst fc, MlpDev m,
                                                  double gamma_dt, uint16_t* __restrict__ x_out,
                                                  float* __restrict__ z_out, double* __restrict__ score_out) {
@@ -222,6 +264,7 @@ __global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, i
     fw3[i] = m.p[oW3 + i];
   }
   const float b3 = m.p[oB3];
+  const float gdt_f = (float)gamma_dt;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   const int64_t tiles = ceil_div_dev(n, kFwdRows);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -257,8 +300,7 @@ __global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, i
         if (score_out) {
           const Rec r = d[i];
           const double q = __dadd_rn(__dmul_rn(r.re, r.re), __dmul_rn(r.im, r.im));
-          const double wt = (double)__popcll(r.v | r.w);
-          score_out[i] = __dadd_rn(__dsub_rn(__dmul_rn(0.5, log(q)), __dmul_rn(gamma_dt, wt)), (double)z);
+          score_out[i] = rank_value(q, z, gdt_f * (float)__popcll(r.v | r.w), fc);
         }
       }
     }

@@ -85,20 +85,20 @@ def test_logits_and_scores_match_oracle():
     zo, _ = omlp.forward(p.astype(np.float64), X)
     assert _rel_norm(z, zo) < NET_REL, _rel_norm(z, zo)
     s = ps.pauli_mlp_scores(model, O, 0.05).cpu().numpy()
-    so = omlp.scores(p.astype(np.float64), *arr, n, gamma_dt=0.05)
-    # the ln|c| - gamma dt wt part is FP64; only z carries the BF16 error
-    assert np.max(np.abs((s - z) - (so - zo))) < 1e-6
-    assert _rel_norm(s - (so - zo), zo) < NET_REL
+    so = omlp.rank_values(p.astype(np.float64), *arr, n, gamma_dt=0.05)
+    # rank values exp(2 score): the ln|c| - gamma dt wt part of 0.5 ln(rank) is exact to FP32
+    # rounding of the rescaling factor; only z carries the BF16 error
+    assert np.max(np.abs((0.5 * np.log(s) - z) - (0.5 * np.log(so) - zo))) < 1e-5
+    assert _rel_norm(0.5 * np.log(s) - (0.5 * np.log(so) - zo), zo) < NET_REL
 
 
-def test_zero_network_scores_are_log_abs():
+def test_zero_network_rank_values_are_abs2():
     n = 20
     arr = I.random_sum(5, n, 1000, kind="complex")
     model = ps.PauliMLP(n, seed=0)
     ps.pauli_mlp_set_params(model, np.zeros(ps.pauli_mlp_param_count(), np.float32))
     s = ps.pauli_mlp_scores(model, _sum(n, arr), 0.0).cpu().numpy()
-    want = 0.5 * np.log(arr[2] ** 2 + arr[3] ** 2)
-    assert np.allclose(s, want, rtol=1e-15, atol=0)
+    assert np.array_equal(s, arr[2] * arr[2] + arr[3] * arr[3])  # |c|^2, bit for bit
 
 
 @pytest.mark.parametrize("i0,nb", [(0, 3000), (37, 1001), (5, 1)])

@@ -168,6 +168,22 @@ def test_scores_zero_network_is_log_abs_after_dissipation():
     assert abs(s[0] - (math.log(0.5) - 0.05 * 2)) < 1e-15
 
 
+def test_rank_values_zero_network_and_order():
+    v, w = I.string("X", 1, "Y", 3)
+    p = np.zeros(mlp.N_PARAMS)
+    r = mlp.rank_values(p, [v], [w], [0.3], [-0.4], 8)
+    assert r[0] == 0.3 * 0.3 + 0.4 * 0.4  # exactly |c|^2 when the exponent is zero
+    r = mlp.rank_values(p, [v], [w], [0.3], [-0.4], 8, gamma_dt=0.05)
+    assert abs(r[0] - 0.25 * math.exp(-0.2)) < 1e-16
+    # a random network: rank values order the strings as the scores do (exp(2 score))
+    arr = I.random_sum(4, 12, 200, kind="complex")
+    q = _rand_params(6, 0.2)
+    sc = mlp.scores(q, *arr, 12, gamma_dt=0.01)
+    rv = mlp.rank_values(q, *arr, 12, gamma_dt=0.01)
+    assert np.allclose(np.log(rv), 2 * sc, rtol=0, atol=1e-12)
+    assert np.array_equal(np.argsort(-rv, kind="stable"), np.argsort(-sc, kind="stable"))
+
+
 def _random_op(seed, n, m, dyadic=False):
     rng = np.random.default_rng(seed)
     keys = set()
