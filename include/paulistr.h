@@ -326,7 +326,7 @@ int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_
  * bin (which sets the number of bins, 2^4..2^20) and the group quota (entries a merge block
  * takes per group).  Results do not depend on them (the merge is exact in any geometry);
  * the time does.  pauli_autotune_commutator times [H, O] (CUDA events, best of reps after
- * one warm-up run) with bin targets 1024, 2048, 4096, 8192 and quotas 1024, 1536, and keeps the
+ * one warm-up run) with bin targets 1024, 2048, 4096 and quotas 1024, 1536, and keeps the
  * fastest for every later merge of the same size class (log2 of the merge's entry bound) in
  * this process.  Outputs (may be NULL): the chosen pair, its time and the default's
  * (2048, 1536) time in ms.  pauli_autotune_reset returns every class to the defaults. */

@@ -1967,7 +1967,7 @@ int ts_translates(const Rec* G, int64_t n, int ring, cudaStream_t s, Rec* out) {
 // with each candidate geometry; the fastest is kept for merges of that size class.
 int autotune_commutator(const MergeSpec& sp, pauli_sum* out, int reps, int* best_bin, int* best_quota,
                         double* best_ms, double* default_ms) {
-  static const int kBinT[] = {1024, 2048, 4096, 8192};
+  static const int kBinT[] = {1024, 2048, 4096};
   static const int kQuota[] = {1024, 1536};
   cudaStream_t s = out->stream;
   cudaEvent_t e0, e1;
