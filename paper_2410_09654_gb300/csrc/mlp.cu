@@ -46,6 +46,8 @@ constexpr int kFwdRows = 128;     // rows per inference tile (8 warps x 16)
 struct FeatConst {
   uint64_t bin_mask[16];
   int bin_size[16];
+  float inv_size[16];  // 1 / bin size (0 for an empty bin)
+  float inv_n;         // 1 / N
   int n_sites;
   float x2_floor;  // ln(1e-300) / 16
   float ln2;       // ln 2
@@ -63,6 +65,8 @@ FeatConst make_featconst(int n) {
     f.bin_mask[b] |= 1ull << j;
     f.bin_size[b] += 1;
   }
+  for (int b = 0; b < 16; ++b) f.inv_size[b] = f.bin_size[b] ? (float)(1.0 / f.bin_size[b]) : 0.0f;
+  f.inv_n = (float)(1.0 / n);
   return f;
 }
 
@@ -107,27 +111,45 @@ __device__ __forceinline__ double rank_value(double q, float z, float gdt_wt, co
   return scalbn(p, (int)kf);
 }
 
-// Feature k of a string (0 <= k < 80).
+// Feature k of a string (0 <= k < 80); k is a compile-time constant at every call, so the
+// branches fold.  Fractions are products with the reciprocal (within one FP32 unit of the
+// quotient, below BF16 resolution).
 __device__ __forceinline__ float feature(const Rec& r, const FeatConst& fc, int k) {
   const uint64_t s = r.v | r.w;
-  const float n = (float)fc.n_sites;
-  if (k == 0) return __fdiv_rn((float)__popcll(s), n);
+  if (k == 0) return (float)__popcll(s) * fc.inv_n;
   if (k == 1) {
     const int ext = s ? (63 - __clzll((long long)s)) - (__ffsll((long long)s) - 1) + 1 : 0;
-    return __fdiv_rn((float)ext, n);
+    return (float)ext * fc.inv_n;
   }
   if (k == 2) return feature_lnc(r.re, r.im, fc);
   if (k >= 67) return 0.0f;
   const int b = (k - 3) >> 2, t = (k - 3) & 3;
-  const int sz = fc.bin_size[b];
-  if (sz == 0) return 0.0f;
   const uint64_t m = fc.bin_mask[b];
   int c;
   if (t == 1) c = __popcll(r.w & ~r.v & m);
   else if (t == 2) c = __popcll(r.v & r.w & m);
   else if (t == 3) c = __popcll(r.v & ~r.w & m);
-  else c = sz - __popcll(s & m);
-  return __fdiv_rn((float)c, (float)sz);
+  else c = fc.bin_size[b] - __popcll(s & m);
+  return (float)c * fc.inv_size[b];
+}
+
+// Features [44 HALF, 44 HALF + 44) (HALF 0) or [44, 80) (HALF 1) of one string, stored as
+// BF16 pairs into a shared row (and optionally a global row and a transposed shared tile).
+template <int HALF>
+__device__ __forceinline__ void store_features(const Rec& r, bool valid, const FeatConst& fc, uint16_t* xs_row,
+                                               uint16_t* x_glob, uint16_t* xT, int sr, int row) {
+  constexpr int k0 = HALF ? 44 : 0, k1 = HALF ? 80 : 44;
+#pragma unroll
+  for (int k = k0; k < k1; k += 2) {
+    const float f0 = valid ? feature(r, fc, k) : 0.0f, f1 = valid ? feature(r, fc, k + 1) : 0.0f;
+    const uint32_t pr = pack_bf16(f0, f1);
+    *reinterpret_cast<uint32_t*>(xs_row + k) = pr;
+    if (x_glob) *reinterpret_cast<uint32_t*>(x_glob + k) = pr;
+    if (xT) {
+      xT[k * sr + row] = (uint16_t)(pr & 0xFFFFu);
+      xT[(k + 1) * sr + row] = (uint16_t)(pr >> 16);
+    }
+  }
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -270,19 +292,16 @@ __global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, i
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t base = tile * kFwdRows;
     __syncthreads();  // staging done / previous tile's xs consumed
-    // two threads per row: even threads features 0..39, odd threads 40..79
+    // two warps per 32 rows: the even warp writes features 0..43, the odd one 44..79
     {
-      const int row = threadIdx.x >> 1, half = threadIdx.x & 1;
+      const int row = (warp >> 1) * 32 + lane;
       const int64_t i = base + row;
       Rec r{0, 0, 0.0, 0.0};
       const bool valid = i < n;
       if (valid) r = d[i];
-      for (int k = 40 * half; k < 40 * half + 40; k += 2) {
-        const float f0 = valid ? feature(r, fc, k) : 0.0f, f1 = valid ? feature(r, fc, k + 1) : 0.0f;
-        const uint32_t pr = pack_bf16(f0, f1);
-        *reinterpret_cast<uint32_t*>(xs + row * kSF + k) = pr;
-        if (x_out && valid) *reinterpret_cast<uint32_t*>(x_out + i * kF + k) = pr;
-      }
+      uint16_t* xg = (x_out && valid) ? x_out + i * kF : nullptr;
+      if (warp & 1) store_features<1>(r, valid, fc, xs + row * kSF, xg, nullptr, 0, row);
+      else store_features<0>(r, valid, fc, xs + row * kSF, xg, nullptr, 0, row);
     }
     __syncthreads();
     uint32_t h1[8][4];
@@ -348,19 +367,14 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const Rec* __restrict__ d,
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t base = tile * kTrainRows;
     __syncthreads();
-    {  // features: two threads per row
-      const int row = threadIdx.x >> 1, half = threadIdx.x & 1;
+    {  // features: two warps per 32 rows (even warp features 0..43, odd warp 44..79)
+      const int row = (warp >> 1) * 32 + lane;
       const int64_t i = base + row;
       Rec r{0, 0, 0.0, 0.0};
       const bool valid = i < nb;
       if (valid) r = d[i];
-      for (int k = 40 * half; k < 40 * half + 40; k += 2) {
-        const float f0 = valid ? feature(r, fc, k) : 0.0f, f1 = valid ? feature(r, fc, k + 1) : 0.0f;
-        const uint32_t pr = pack_bf16(f0, f1);
-        *reinterpret_cast<uint32_t*>(xs + row * kSF + k) = pr;
-        xT[k * kSR + row] = (uint16_t)(pr & 0xFFFFu);
-        xT[(k + 1) * kSR + row] = (uint16_t)(pr >> 16);
-      }
+      if (warp & 1) store_features<1>(r, valid, fc, xs + row * kSF, nullptr, xT, kSR, row);
+      else store_features<0>(r, valid, fc, xs + row * kSF, nullptr, xT, kSR, row);
     }
     __syncthreads();
     uint32_t h1[8][4];
