@@ -100,15 +100,31 @@ __device__ __forceinline__ float feature_lnc(double re, double im, const FeatCon
   return lnc * 0.0625f;
 }
 
-// Rank value |c|^2 e^(2 (z - gdt wt)): exactly q when the exponent is zero; otherwise
-// q * exp2(f) * 2^k with t = 2 (z - gdt wt) log2(e) = k + f, k integer, f in [0, 1).
-__device__ __forceinline__ double rank_value(double q, float z, float gdt_wt, const FeatConst& fc) {
+// Rank value |c|^2 e^(2 (z - gdt wt)): exactly q = |c|^2 when the exponent is zero; otherwise
+// q * exp2(f) * 2^k with t = 2 (z - gdt wt) log2(e) = k + f, k integer, f in [0, 1).  FP64
+// work: the squares of the non-zero components and one product (the FP32 factor in [1, 2)
+// is widened and the power of two applied on the integer pipe when the result stays normal).
+__device__ __forceinline__ double rank_value(double re, double im, float z, float gdt_wt, const FeatConst& fc) {
+  const bool zr = ((uint64_t)__double_as_longlong(re) << 1) == 0, zi = ((uint64_t)__double_as_longlong(im) << 1) == 0;
+  if (zr && zi) return 0.0;
+  const double q = zi ? __dmul_rn(re, re) : (zr ? __dmul_rn(im, im) : __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)));
   float t = 2.0f * (z - gdt_wt);
-  if (t == 0.0f || q == 0.0) return q;
+  if (t == 0.0f) return q;
   t = fminf(fmaxf(t * fc.log2e, -2000.0f), 2000.0f);
   const float kf = floorf(t);
-  const double p = __dmul_rn(q, (double)exp2f(t - kf));
-  return scalbn(p, (int)kf);
+  const int k = (int)kf;
+  const uint32_t fb = (uint32_t)__float_as_int(exp2f(t - kf));  // in [1, 2]
+  double mul;
+  if ((fb >> 23) == 127u) {
+    mul = __longlong_as_double((long long)((0x3FFull << 52) | ((uint64_t)(fb & 0x7FFFFF) << 29)));
+  } else {
+    mul = (double)__int_as_float((int)fb);  // exp2f rounded up to exactly 2
+  }
+  const double p = __dmul_rn(q, mul);
+  const uint64_t pb = (uint64_t)__double_as_longlong(p);
+  const int e = (int)((pb >> 52) & 0x7FF);
+  if (e > 0 && e + k >= 1 && e + k <= 2046) return __longlong_as_double((long long)(pb + ((uint64_t)(int64_t)k << 52)));
+  return scalbn(p, k);
 }
 
 // Feature k of a string (0 <= k < 80); k is a compile-time constant at every call, so the
@@ -179,6 +195,20 @@ __device__ __forceinline__ void load_b(const uint16_t* base, int n0, int k0, int
   b1 = ld32(base + (n0 + g) * S + k0 + 2 * t + 8);
 }
 
+// B fragments of two adjacent n tiles (n0..n0+7 and n0+8..n0+15) at k0 with one ldmatrix.x4:
+// lane L supplies the row address of matrix L/8 (tile (L/16), k half (L/8)&1), 16-byte
+// aligned (S even multiples of 8 elements, k0 a multiple of 8).
+template <int S>
+__device__ __forceinline__ void load_b2(const uint16_t* base, int n0, int k0, int lane, uint32_t& b0a, uint32_t& b1a,
+                                        uint32_t& b0b, uint32_t& b1b) {
+  const int mtx = lane >> 3, row = lane & 7;
+  const uint16_t* p = base + (n0 + ((mtx >> 1) << 3) + row) * S + k0 + ((mtx & 1) << 3);
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(b0a), "=r"(b1a), "=r"(b0b), "=r"(b1b)
+               : "r"(addr));
+}
+
 // Copy a dense [rows][cols] bf16 matrix into shared memory with row stride S.
 template <int S>
 __device__ __forceinline__ void stage(uint16_t* dst, const uint16_t* __restrict__ src, int rows, int cols) {
@@ -197,15 +227,17 @@ __device__ __forceinline__ void forward_rows(const uint16_t* xs, int r0, const u
   float acc[16][4];
 #pragma unroll
   for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int ks = 0; ks < kF / 16; ++ks) {
     uint32_t a[4];
     load_a<kSF>(xs, r0, 16 * ks, g, t, a);
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      uint32_t b0, b1;
-      load_b<kSF>(W1s, 8 * nt, 16 * ks, g, t, b0, b1);
-      mma_bf16(acc[nt], a, b0, b1);
+    for (int np = 0; np < 8; ++np) {
+      uint32_t b0, b1, b2, b3;
+      load_b2<kSF>(W1s, 16 * np, 16 * ks, lane, b0, b1, b2, b3);
+      mma_bf16(acc[2 * np], a, b0, b1);
+      mma_bf16(acc[2 * np + 1], a, b2, b3);
     }
   }
 #pragma unroll
@@ -224,10 +256,11 @@ __device__ __forceinline__ void forward_rows(const uint16_t* xs, int r0, const u
 #pragma unroll
   for (int ks = 0; ks < 8; ++ks) {
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      uint32_t b0, b1;
-      load_b<kSH>(W2s, 8 * nt, 16 * ks, g, t, b0, b1);
-      mma_bf16(acc2[nt], h1[ks], b0, b1);
+    for (int np = 0; np < 8; ++np) {
+      uint32_t b0, b1, b2, b3;
+      load_b2<kSH>(W2s, 16 * np, 16 * ks, lane, b0, b1, b2, b3);
+      mma_bf16(acc2[2 * np], h1[ks], b0, b1);
+      mma_bf16(acc2[2 * np + 1], h1[ks], b2, b3);
     }
   }
 #pragma unroll
@@ -318,8 +351,7 @@ __global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, i
         if (z_out) z_out[i] = z;
         if (score_out) {
           const Rec r = d[i];
-          const double q = __dadd_rn(__dmul_rn(r.re, r.re), __dmul_rn(r.im, r.im));
-          score_out[i] = rank_value(q, z, gdt_f * (float)__popcll(r.v | r.w), fc);
+          score_out[i] = rank_value(r.re, r.im, z, gdt_f * (float)__popcll(r.v | r.w), fc);
         }
       }
     }
@@ -463,10 +495,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const Rec* __restrict__ d,
 #pragma unroll
     for (int ks = 0; ks < 8; ++ks)
 #pragma unroll
-      for (int nt = 0; nt < 16; ++nt) {
-        uint32_t b0, b1;
-        load_b<kSH>(W2Ts, 8 * nt, 16 * ks, g, t, b0, b1);
-        mma_bf16(acc[nt], da[ks], b0, b1);
+      for (int np = 0; np < 8; ++np) {
+        uint32_t b0, b1, b2, b3;
+        load_b2<kSH>(W2Ts, 16 * np, 16 * ks, lane, b0, b1, b2, b3);
+        mma_bf16(acc[2 * np], da[ks], b0, b1);
+        mma_bf16(acc[2 * np + 1], da[ks], b2, b3);
       }
 #pragma unroll
     for (int nt = 0; nt < 16; ++nt) {
