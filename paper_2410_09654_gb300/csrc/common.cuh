@@ -97,7 +97,6 @@ inline int cls_mul(int a, int b) {                                              
   return a == b ? kClsReal : kClsImag;
 }
 inline int cls_of(double re, double im) { return (re != 0.0 ? 1 : 0) | (im != 0.0 ? 2 : 0); }
-int compute_cls(const Rec* d, int64_t n, cudaStream_t s, int* cls);  // reduction over a sum
 
 int sum_reserve(pauli_sum* s, int64_t cap, bool keep_contents);
 int sum_adopt(pauli_sum* s, Rec* d, int64_t cap, int64_t n);  // take ownership of a buffer
@@ -298,8 +297,6 @@ class KTimer {
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int num_sms();
-int check_keys_device(const Rec* d, int64_t n, uint64_t mask, cudaStream_t s, bool* ok);
-int check_distinct_device(const Rec* d, int64_t n, cudaStream_t s, bool* ok);
 
 // Exclusive prefix sum of n unsigned values into out[0..n]; out[n] = total (device only).
 int scan_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s);

@@ -222,54 +222,7 @@ void host_key_with_hash(uint32_t target, int bits, uint64_t* v, uint64_t* w) {
 }
 
 // ----------------------------------------------------------------------------- coefficient class
-__global__ void k_cls(const Rec* __restrict__ d, int64_t n, int* cls) {
-  int c = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    Rec r = d[i];
-    c |= (((__double_as_longlong(r.re) << 1) != 0) ? 1 : 0) | (((__double_as_longlong(r.im) << 1) != 0) ? 2 : 0);
-  }
-  for (int o = 16; o > 0; o >>= 1) c |= __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicOr(cls, c);
-}
-
-int compute_cls(const Rec* d, int64_t n, cudaStream_t s, int* cls) {
-  *cls = 0;
-  if (n == 0) return PS_OK;
-  Buf<int> c;
-  PS_TRY(c.alloc(1, s));
-  PS_CUDA(cudaMemsetAsync(c.p, 0, sizeof(int), s));
-  int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 4 * num_sms());
-  PS_LAUNCH("k_cls", s, k_cls<<<blocks, 256, 0, s>>>(d, n, c.p));
-  PS_CUDA(cudaGetLastError());
-  PS_CUDA(cudaMemcpyAsync(cls, c.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PS_CUDA(cudaStreamSynchronize(s));
-  return PS_OK;
-}
-
 // ----------------------------------------------------------------------------- validation kernels
-__global__ void k_check_bits(const Rec* __restrict__ d, int64_t n, uint64_t inv_mask, int* bad) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (; i < n; i += stride)
-    if ((d[i].v | d[i].w) & inv_mask) atomicOr(bad, 1);
-}
-
-int check_keys_device(const Rec* d, int64_t n, uint64_t mask, cudaStream_t s, bool* ok) {
-  *ok = true;
-  if (n == 0 || mask == ~0ull) return PS_OK;
-  Buf<int> bad;
-  PS_TRY(bad.alloc(1, s));
-  PS_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-  int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
-  PS_LAUNCH("k_check_bits", s, k_check_bits<<<blocks, 256, 0, s>>>(d, n, ~mask, bad.p));
-  PS_CUDA(cudaGetLastError());
-  int h = 0;
-  PS_CUDA(cudaMemcpyAsync(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PS_CUDA(cudaStreamSynchronize(s));
-  *ok = (h == 0);
-  return PS_OK;
-}
-
 __device__ __forceinline__ uint32_t mix32(uint64_t v, uint64_t w) {
   uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w + 0x632BE59BD9B4E019ull);
   h ^= h >> 32;
@@ -314,26 +267,19 @@ __global__ void k_distinct(const Rec* __restrict__ d, int64_t n, ulonglong2* tab
   }
 }
 
-int check_distinct_device(const Rec* d, int64_t n, cudaStream_t s, bool* ok) {
-  *ok = true;
-  if (n <= 1) return PS_OK;
+// The distinctness check without its synchronisation: *dup is set if two keys are equal
+// (the table is sized and filled here and must live until the stream has run the kernel).
+int distinct_launch(const Rec* d, int64_t n, cudaStream_t s, Buf<ulonglong2>& table, int* dup, int* ones) {
   uint64_t slots = 1;
   while (slots < (uint64_t)(2 * n)) slots <<= 1;
-  Buf<ulonglong2> table;
-  Buf<int> flags;
   PS_TRY(table.alloc(slots, s));
-  PS_TRY(flags.alloc(2, s));
   PS_CUDA(cudaMemsetAsync(table.p, 0xFF, slots * sizeof(ulonglong2), s));
-  PS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
   int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
-  PS_LAUNCH("k_distinct", s, k_distinct<<<blocks, 256, 0, s>>>(d, n, table.p, slots - 1, flags.p, flags.p + 1));
+  PS_LAUNCH("k_distinct", s, k_distinct<<<blocks, 256, 0, s>>>(d, n, table.p, slots - 1, dup, ones));
   PS_CUDA(cudaGetLastError());
-  int h[2];
-  PS_CUDA(cudaMemcpyAsync(h, flags.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-  PS_CUDA(cudaStreamSynchronize(s));
-  *ok = (h[0] == 0);
   return PS_OK;
 }
+
 
 }  // namespace ps
 
@@ -398,11 +344,27 @@ int pauli_sum_size(const pauli_sum* s, int64_t* n) {
   return PS_OK;
 }
 
+// Pack four arrays into records and validate in the same pass: flags[0] = 1 if a string has
+// bits outside the key mask, flags[1] |= the coefficient class (bit 0: a non-zero real part,
+// bit 1: a non-zero imaginary part).
 __global__ void k_pack(Rec* __restrict__ d, const uint64_t* __restrict__ v, const uint64_t* __restrict__ w,
-                       const double* __restrict__ re, const double* __restrict__ im, int64_t n) {
+                       const double* __restrict__ re, const double* __restrict__ im, int64_t n, uint64_t inv_mask,
+                       int* __restrict__ flags) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (; i < n; i += stride) d[i] = Rec{v[i], w[i], re[i], im[i]};
+  int bad = 0, c = 0;
+  for (; i < n; i += stride) {
+    const Rec r{v[i], w[i], re[i], im[i]};
+    d[i] = r;
+    bad |= ((r.v | r.w) & inv_mask) != 0;
+    c |= (((__double_as_longlong(r.re) << 1) != 0) ? 1 : 0) | (((__double_as_longlong(r.im) << 1) != 0) ? 2 : 0);
+  }
+  bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
+  c = __reduce_or_sync(0xffffffffu, (unsigned)c);
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(&flags[0], 1);
+    if (c) atomicOr(&flags[1], c);
+  }
 }
 
 int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re, const double* im,
@@ -410,9 +372,15 @@ int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const d
   if (!s || n < 0 || (n > 0 && (!v || !w || !re || !im))) return PS_ERR_INVALID;
   PS_TRY(sum_reserve(s, n, false));
   s->n = 0;
+  // four host->device copies into a staging area; one pass packs the records and checks the
+  // key bits and the coefficient class, one inserts the keys for the distinctness check; a
+  // single synchronisation reads every flag (the caller's host arrays may be released then)
+  Buf<uint64_t> stage;
+  Buf<int> flags;
+  Buf<ulonglong2> table;
+  PS_TRY(flags.alloc(4, s->stream));
+  PS_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int), s->stream));
   if (n > 0) {
-    // four host->device copies into a staging area, then one packing kernel
-    Buf<uint64_t> stage;
     PS_TRY(stage.alloc((size_t)n * 4, s->stream));
     uint64_t* dv = stage.p;
     uint64_t* dw = stage.p + n;
@@ -424,15 +392,16 @@ int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const d
     PS_CUDA(cudaMemcpyAsync(dre, re, bytes, cudaMemcpyHostToDevice, s->stream));
     PS_CUDA(cudaMemcpyAsync(dim, im, bytes, cudaMemcpyHostToDevice, s->stream));
     int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
-    PS_LAUNCH("k_pack", s->stream, k_pack<<<blocks, 256, 0, s->stream>>>(s->d, dv, dw, dre, dim, n));
+    PS_LAUNCH("k_pack", s->stream,
+              k_pack<<<blocks, 256, 0, s->stream>>>(s->d, dv, dw, dre, dim, n, ~key_mask(s->n_sites), flags.p));
     PS_CUDA(cudaGetLastError());
   }
-  bool ok = true;
-  PS_TRY(check_keys_device(s->d, n, key_mask(s->n_sites), s->stream, &ok));
-  if (ok) PS_TRY(check_distinct_device(s->d, n, s->stream, &ok));
-  PS_CUDA(cudaStreamSynchronize(s->stream));  // the caller's host arrays may be released on return
-  if (!ok) return PS_ERR_INVALID;
-  PS_TRY(compute_cls(s->d, n, s->stream, &s->cls));
+  if (n > 1) PS_TRY(distinct_launch(s->d, n, s->stream, table, flags.p + 2, flags.p + 3));
+  int h[4] = {0, 0, 0, 0};
+  PS_CUDA(cudaMemcpyAsync(h, flags.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  PS_CUDA(cudaStreamSynchronize(s->stream));
+  if (h[0] || h[2]) return PS_ERR_INVALID;
+  s->cls = h[1];
   s->n = n;
   return round_f32(s);
 }
@@ -454,19 +423,22 @@ int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, 
                             const double* im, int64_t n) {
   if (!s || n < 0 || (n > 0 && (!v || !w || !re || !im))) return PS_ERR_INVALID;
   PS_TRY(sum_reserve(s, n, false));
+  s->n = 0;
+  Buf<int> flags;
+  PS_TRY(flags.alloc(2, s->stream));
+  PS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s->stream));
   if (n > 0) {
     int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
-    PS_LAUNCH("k_pack", s->stream, k_pack<<<blocks, 256, 0, s->stream>>>(s->d, v, w, re, im, n));
+    PS_LAUNCH("k_pack", s->stream,
+              k_pack<<<blocks, 256, 0, s->stream>>>(s->d, v, w, re, im, n, ~key_mask(s->n_sites), flags.p));
     PS_CUDA(cudaGetLastError());
   }
+  int h[2] = {0, 0};
+  PS_CUDA(cudaMemcpyAsync(h, flags.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  PS_CUDA(cudaStreamSynchronize(s->stream));
+  if (h[0]) return PS_ERR_INVALID;
+  s->cls = h[1];
   s->n = n;
-  bool ok = true;
-  PS_TRY(check_keys_device(s->d, n, key_mask(s->n_sites), s->stream, &ok));
-  if (!ok) {
-    s->n = 0;
-    return PS_ERR_INVALID;
-  }
-  PS_TRY(compute_cls(s->d, n, s->stream, &s->cls));
   return round_f32(s);
 }
 
