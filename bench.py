@@ -595,6 +595,17 @@ def learned_truncation(stream, peaks_bf16: float, lg_cap: int = 18, steps: int =
     ps.pauli_profile_enable(False)
     e_pl = np.abs(plain[:, 0] - ref[:, 0])
     e_ml = np.abs(mlp[:, 0] - ref[:, 0])
+    # plain truncation at larger caps: the cap it needs to reach the learned error at M
+    larger = {}
+    for f in (2, 4):
+        obs_f, t_f = L.rk4_observable(H, O0, dt, steps, ps.policy(top_k=f * M, trim_stages=1), probe)
+        larger[f * M] = (float(np.abs(obs_f[:, 0] - ref[:, 0]).mean()), 1e3 * t_f)
+    equal = None
+    for cap_f, (err_f, ms_f) in sorted(larger.items()):
+        if err_f <= float(e_ml.mean()):
+            equal = {"plain_cap": cap_f, "plain_ms_per_step": ms_f, "learned_ms_per_step": 1e3 * t_mlp,
+                     "speedup_at_equal_error": ms_f / (1e3 * t_mlp)}
+            break
     fwd_launches, fwd_ms = prof.get("k_mlp_fwd", (0, 0.0))
     cand = [len(C) for C, _ in data]
     # the scoring kernel alone on the last candidate set (strings per launch known exactly)
@@ -620,6 +631,8 @@ def learned_truncation(stream, peaks_bf16: float, lg_cap: int = 18, steps: int =
         "observable_error_mean": {"plain": float(e_pl.mean()), "learned": float(e_ml.mean())},
         "observable_error_max": {"plain": float(e_pl.max()), "learned": float(e_ml.max())},
         "ms_per_step": {"plain": 1e3 * t_plain, "learned": 1e3 * t_mlp, "reference": 1e3 * t_ref},
+        "plain_at_larger_caps": {str(k): {"observable_error_mean": e, "ms_per_step": t} for k, (e, t) in larger.items()},
+        "equal_error": equal,
         "training": {"candidates": int(sum(cand)), "positive_fraction": L.positive_fraction(data),
                      "label": "kept in the top 2^18 of the 2^20 run 10 steps later",
                      "iterations": iters, "batch": batch, "lr": 1e-3, "loss_before": loss0, "loss_after": loss1,
