@@ -96,3 +96,28 @@ def mean_loss(model, data) -> float:
 def positive_fraction(data) -> float:
     s = sum(float(y.sum().item()) for _, y in data)
     return s / max(sum(len(C) for C, _ in data), 1)
+
+
+def scorer_workload(cap_log2: int = 18, steps: int = 40, reps: int = 3, seed: int = 1) -> int:
+    """The scorer's and the trainer's kernels on real candidates: RK4 on the N=48 chain
+    sum ZZ + 1.05 sum X + 0.5 sum Z from Z_24 (dt 0.05, trimmed stages, cap 2^cap_log2) for
+    `steps` steps keeping the last step's candidates, then `reps` scorings of all of them
+    and `reps` training steps on the first 16384.  Returns the number of candidates."""
+    import torch
+    from . import inputs as I
+    n = 48
+    H = ps.PauliSum.from_arrays(n, *I.tilted_ising_chain(n).arrays())
+    O = ps.PauliSum.from_arrays(n, *I.single(n, "Z", 24).arrays())
+    pol = ps.policy(top_k=1 << cap_log2, trim_stages=1)
+    C = ps.PauliSum(n)
+    for _ in range(steps):
+        ps.pauli_rk4_step_mlp(H, O, 0.05, pol, cand_out=C)
+    model = ps.PauliMLP(n, seed=seed)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    y = (torch.rand(len(C), device="cuda", generator=g) < 0.5).float()
+    for _ in range(reps):
+        ps.pauli_mlp_scores(model, C, 0.0)
+    for _ in range(reps):
+        ps.pauli_mlp_train_step(model, C, y, 0, min(16384, len(C)), 1e-3)
+    torch.cuda.synchronize()
+    return len(C)
