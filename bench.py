@@ -403,6 +403,7 @@ def main():
     batch_res = None
     if not args.no_learned:
         batch_res = batched_instances(stream, fixed_geometry=bool(args.merge_geometry))
+        batch_res["full_caps"] = batched_instances_full(stream)
 
     # ---------------------------------------------------------------- learned truncation
     learned_res = None
@@ -515,6 +516,86 @@ def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3,
             "speedup": t_loop_all / t_b, "merge_geometry_autotuned": tune,
             "not_built": "one persistent graph-captured launch and the autotuner: each step is a sequence of "
                          "launches with host synchronisation on data-dependent sizes"}
+
+
+BATCH_FULL_WORKLOAD = ("the same 512 realisations with the description's caps 2^(14 + instance mod 7) (16384 to "
+                       "1048576 strings), in groups of instances whose caps add up to at most 2^22 (one tagged sum "
+                       "and one pauli_batch per group, so that a merge's entry bound stays within its budget); "
+                       "timed once every instance has run 16 steps")
+
+
+def batched_instances_full(stream, n_inst: int = 512, ramp: int = 16, timed: int = 2, group_cap: int = 1 << 22):
+    """The batched realisations at the full per-instance caps, grouped by cap, against the
+    single-instance path looped over two instances of every cap (scaled to all)."""
+    import torch
+    from paper_2410_09654_gb300 import inputs as I, paulistr as ps
+    n, shift = 32, 32
+    W = [0.5 if b <= 170 else (2.0 if b <= 341 else 5.0) for b in range(n_inst)]
+    caps = np.array([1 << (14 + b % 7) for b in range(n_inst)], np.int64)
+    z = I.single(n, "Z", 16).arrays()
+    # groups: instances sorted by cap, filled greedily up to group_cap strings of caps
+    order = sorted(range(n_inst), key=lambda b: (caps[b], b))
+    groups, cur, tot = [], [], 0
+    for b in order:
+        if cur and tot + caps[b] > group_cap:
+            groups.append(cur)
+            cur, tot = [], 0
+        cur.append(b)
+        tot += caps[b]
+    if cur:
+        groups.append(cur)
+    runs = []
+    for g in groups:
+        tb = max(1, (len(g) - 1).bit_length())
+        N = shift + tb
+        Hs = [I.random_field_xxz_chain(n, W[b], b).arrays() for b in g]
+        Hc = ps.PauliSum.from_arrays(N, Hs[0][0], Hs[0][1], np.ones(len(Hs[0][0])), np.zeros(len(Hs[0][0])))
+        B = ps.PauliBatch(Hc, np.stack([h[2] for h in Hs]), shift, caps[g])
+        v = np.array([int(z[0][0]) | (j << shift) for j in range(len(g))], np.uint64)
+        O = ps.PauliSum.from_arrays(N, v, np.zeros(len(g), np.uint64), np.ones(len(g)), np.zeros(len(g)))
+        runs.append((B, Hc, O, len(Hs[0][0])))
+    for _ in range(ramp):
+        for B, Hc, O, _nh in runs:
+            ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
+    strings = sum(len(O) for _, _, O, _ in runs)
+    prod = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(timed):
+        for B, Hc, O, nh in runs:
+            prod += 4 * nh * len(O)
+            ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
+    torch.cuda.synchronize()
+    t_b = (time.perf_counter() - t0) / timed
+    del runs
+    # single-instance path: two instances of every cap class, scaled by the class sizes
+    t_loop_all, prod_loop, t_loop = 0.0, 0, 0.0
+    for c in range(7):
+        members = [b for b in range(n_inst) if b % 7 == c]
+        t_c = 0.0
+        for b in (members[0], members[len(members) // 2]):
+            H = ps.PauliSum.from_arrays(n, *I.random_field_xxz_chain(n, W[b], b).arrays())
+            Ob = ps.PauliSum.from_arrays(n, *z)
+            pol = ps.policy(top_k=int(caps[b]), trim_stages=1)
+            for _ in range(ramp):
+                ps.pauli_rk4_step(H, Ob, 0.05, pol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(timed):
+                prod_loop += 4 * len(H) * len(Ob)
+                ps.pauli_rk4_step(H, Ob, 0.05, pol)
+            torch.cuda.synchronize()
+            dt_ = time.perf_counter() - t0
+            t_c += dt_
+            t_loop += dt_
+        t_loop_all += t_c / 2 / timed * len(members)
+    return {"workload": BATCH_FULL_WORKLOAD, "instances": n_inst, "groups": len(groups), "strings": int(strings),
+            "batched": {"ms_per_step": 1e3 * t_b, "instance_steps_per_s": n_inst / t_b,
+                        "products_per_s": prod / timed / t_b},
+            "looped_single_instance": {"ms_per_step": 1e3 * t_loop_all, "instance_steps_per_s": n_inst / t_loop_all,
+                                       "products_per_s": prod_loop / t_loop,
+                                       "sample": "two instances per cap class, scaled to the 512"},
+            "speedup": t_loop_all / t_b}
 
 
 F32_WORKLOAD = ("RK4 on the open 8x8 Heisenberg lattice (336 strings), O(0) = Z at (4,4), dt=0.02, dissipation "
