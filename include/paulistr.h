@@ -58,6 +58,7 @@ extern "C" {
 #define PS_ERR_KRYLOV_EXHAUSTED 6 /* Lanczos: b_n == 0 (the Krylov space closed); b_out is 0 */
 #define PS_ERR_NOMEM 7            /* device allocation failed */
 #define PS_ERR_UNCERTAIN 8        /* reserved */
+#define PS_ERR_IO 9               /* a checkpoint file could not be written or read, or is not one */
 
 const char* pauli_status_string(int status);
 /* Text of the last CUDA error seen by the library on this thread ("" if none). */
@@ -115,6 +116,18 @@ int pauli_sum_download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, doub
                               int64_t cap, int64_t* n);
 
 int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst);
+
+/* Checkpoint / resume of long runs.  pauli_sum_save writes the sum to a file: an 8-byte
+ * magic "PSUMCKP1", u32 version (1), u32 n_sites, u32 precision (PS_COEF_*), u32 n_meta,
+ * u64 string count, n_meta f64 caller values (for example t, the step, the b_n so far),
+ * the records {u64 v, u64 w, f64 re, f64 im} in canonical order (v, then w), and a u64
+ * FNV-1a checksum of everything before it; all little-endian.  pauli_sum_load replaces the
+ * contents of s (which must have the file's n_sites) and its precision, and copies up to
+ * meta_cap caller values into meta (*n_meta receives the stored count).  Errors: PS_ERR_IO
+ * (cannot open or write, short or corrupt file, wrong magic, version or checksum),
+ * PS_ERR_INVALID (bad arguments, n_sites mismatch).  Both synchronise the sum's stream. */
+int pauli_sum_save(const pauli_sum* s, const char* path, const double* meta, int64_t n_meta);
+int pauli_sum_load(pauli_sum* s, const char* path, double* meta, int64_t meta_cap, int64_t* n_meta);
 
 /* ------------------------------------------------------------------ algebra */
 

@@ -95,6 +95,7 @@ bool ts_ok(const pauli_sum* s) { return s && s->n_sites >= 2; }
 extern "C" {
 
 int pauli_commutator(const pauli_sum* H, const pauli_sum* O, pauli_sum* out) {
+  NvtxRange nvtx("pauli_commutator");
   if (!H || !O || !out || out == H || out == O) return PS_ERR_INVALID;
   if (!same_sites(H, O) || !same_sites(O, out)) return PS_ERR_INVALID;
   if (H->n > 0xEFFF) return PS_ERR_INVALID;
@@ -104,6 +105,7 @@ int pauli_commutator(const pauli_sum* H, const pauli_sum* O, pauli_sum* out) {
 }
 
 int pauli_multiply(const pauli_sum* A, const pauli_sum* B, pauli_sum* out) {
+  NvtxRange nvtx("pauli_multiply");
   if (!A || !B || !out || out == A || out == B) return PS_ERR_INVALID;
   if (!same_sites(A, B) || !same_sites(B, out)) return PS_ERR_INVALID;
   if (A->n > 0xEFFF) return PS_ERR_INVALID;
@@ -198,6 +200,7 @@ int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_
 }
 
 int pauli_truncate(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt) {
+  NvtxRange nvtx("pauli_truncate");
   if (!O || !same_sites(O, keep) || !policy_valid(policy) || !std::isfinite(dt)) return PS_ERR_INVALID;
   return truncate_run(O, policy, keep, dt, nullptr);
 }
@@ -239,16 +242,19 @@ namespace {
 // cand (optional) receives the step's result before that truncation.
 int rk4_impl(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy, const pauli_sum* keep,
              const pauli_mlp* model, pauli_sum* cand) {
+  NvtxRange nvtx(model ? "rk4_step (learned truncation)" : "rk4_step");
   const double h2 = dt / 2.0, h6 = dt / 6.0;
   const bool trim = policy && policy->trim_stages && policy->top_k > 0;
   pauli_trunc_policy stage{-1, 0.0, policy ? policy->top_k : 0, 0.0, 0};
   Tmp k1(O), k2(O), k3(O), k4(O), X(O);
   auto L = [&](const pauli_sum* in, pauli_sum* k) -> int {
+    NvtxRange r("k_j = i[H, X]");
     PS_TRY(commutator_into(H, in, 1, k));
     if (trim) PS_TRY(truncate_run(k, &stage, nullptr, dt, nullptr));
     return PS_OK;
   };
   auto stage_input = [&](const pauli_sum* k, double a) -> int {  // X = O + a k
+    NvtxRange r("stage input");
     MergeSpec sp;
     sp.src[0] = source(O, Cx{1.0, 0.0});
     sp.src[1] = source(k, Cx{a, 0.0});
@@ -319,6 +325,7 @@ int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_
 
 int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev,
                        const pauli_trunc_policy* policy, double* b_out) {
+  NvtxRange nvtx("pauli_lanczos_step");
   if (!H || !O_prev || !O_cur || !b_out || O_prev == O_cur || H == O_prev || H == O_cur) return PS_ERR_INVALID;
   if (!same_sites(H, O_cur) || !same_sites(O_prev, O_cur) || !policy_valid(policy) || !std::isfinite(b_prev))
     return PS_ERR_INVALID;

@@ -334,6 +334,7 @@ int pauli_batch_truncate(const pauli_batch* b, pauli_sum* O) {
 }
 
 int pauli_batch_rk4_step(const pauli_batch* b, const pauli_sum* H, pauli_sum* O, double dt, int trim_stages) {
+  NvtxRange nvtx("pauli_batch_rk4_step");
   if (!b || !H || !O || H == O || H->n != b->nH || H->n_sites != O->n_sites || !std::isfinite(dt))
     return PS_ERR_INVALID;
   if ((O->cls & kClsImag) || (H->cls & kClsImag)) return PS_ERR_INVALID;  // real coefficients (single-component products)

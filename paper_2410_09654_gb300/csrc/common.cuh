@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstddef>
@@ -292,6 +293,16 @@ class KTimer {
     ::ps::KTimer _kt(name, stream);  \
     __VA_ARGS__;                     \
   } while (0)
+
+// ----------------------------------------------------------------------------- tracing
+// An NVTX range for the scope of one library call (header-only NVTX: a no-op unless a
+// profiler is attached), so that timelines show steps and their phases by name.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ----------------------------------------------------------------------------- misc
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -835,6 +835,7 @@ int pauli_mlp_logits(const pauli_mlp* m, const pauli_sum* O, float* z) {
 }
 
 int pauli_mlp_scores(const pauli_mlp* m, const pauli_sum* O, double gamma_dt, double* score) {
+  NvtxRange nvtx("pauli_mlp_scores");
   if (!m || !O || O->n_sites != m->n_sites || (O->n > 0 && !score) || !std::isfinite(gamma_dt))
     return PS_ERR_INVALID;
   if (O->stream != m->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
@@ -860,6 +861,7 @@ int pauli_mlp_gradient(pauli_mlp* m, const pauli_sum* X, const float* labels, in
 
 int pauli_mlp_train_step(pauli_mlp* m, const pauli_sum* X, const float* labels, int64_t i0, int64_t nb, float lr,
                          double* loss) {
+  NvtxRange nvtx("pauli_mlp_train_step");
   if (!m || !X || X->n_sites != m->n_sites || i0 < 0 || nb < 1 || i0 + nb > X->n || !labels || !(lr >= 0.0f))
     return PS_ERR_INVALID;
   PS_TRY(grad_run(m, X, labels, i0, nb));

@@ -299,6 +299,7 @@ const char* pauli_status_string(int status) {
     case PS_ERR_KRYLOV_EXHAUSTED: return "Krylov space exhausted (b_n = 0)";
     case PS_ERR_NOMEM: return "device out of memory";
     case PS_ERR_UNCERTAIN: return "result rounding uncertain";
+    case PS_ERR_IO: return "checkpoint file error";
     default: return "unknown status";
   }
 }
@@ -498,6 +499,101 @@ int pauli_sum_set_precision(pauli_sum* s, int coef_dtype) {
 int pauli_sum_precision(const pauli_sum* s, int* coef_dtype) {
   if (!s || !coef_dtype) return PS_ERR_INVALID;
   *coef_dtype = s->f32 ? PS_COEF_F32 : PS_COEF_F64;
+  return PS_OK;
+}
+
+// ----------------------------------------------------------------------------- checkpoint
+namespace {
+
+constexpr char kCkpMagic[8] = {'P', 'S', 'U', 'M', 'C', 'K', 'P', '1'};
+
+struct Fnv {
+  uint64_t h = 0xCBF29CE484222325ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 0x100000001B3ull;
+    }
+  }
+};
+
+bool put(std::FILE* f, Fnv& fnv, const void* p, size_t n) {
+  fnv.add(p, n);
+  return std::fwrite(p, 1, n, f) == n;
+}
+
+bool get(std::FILE* f, Fnv& fnv, void* p, size_t n) {
+  if (std::fread(p, 1, n, f) != n) return false;
+  fnv.add(p, n);
+  return true;
+}
+
+}  // namespace
+
+int pauli_sum_save(const pauli_sum* s, const char* path, const double* meta, int64_t n_meta) {
+  if (!s || !path || n_meta < 0 || n_meta > (1 << 20) || (n_meta > 0 && !meta)) return PS_ERR_INVALID;
+  const int64_t n = s->n;
+  std::vector<uint64_t> v((size_t)n), w((size_t)n);
+  std::vector<double> re((size_t)n), im((size_t)n);
+  int64_t got = 0;
+  PS_TRY(pauli_sum_download(s, v.data(), w.data(), re.data(), im.data(), n, &got));
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return PS_ERR_IO;
+  Fnv fnv;
+  const uint32_t hdr[4] = {1u, (uint32_t)s->n_sites, (uint32_t)(s->f32 ? PS_COEF_F32 : PS_COEF_F64), (uint32_t)n_meta};
+  const uint64_t cnt = (uint64_t)n;
+  bool ok = put(f, fnv, kCkpMagic, 8) && put(f, fnv, hdr, sizeof(hdr)) && put(f, fnv, &cnt, 8);
+  if (ok && n_meta > 0) ok = put(f, fnv, meta, (size_t)n_meta * sizeof(double));
+  for (int64_t i = 0; ok && i < n; ++i) {
+    const Rec r{v[(size_t)i], w[(size_t)i], re[(size_t)i], im[(size_t)i]};
+    ok = put(f, fnv, &r, sizeof(r));
+  }
+  const uint64_t sum = fnv.h;
+  if (ok) ok = std::fwrite(&sum, 1, 8, f) == 8;
+  if (std::fclose(f) != 0) ok = false;
+  return ok ? PS_OK : PS_ERR_IO;
+}
+
+int pauli_sum_load(pauli_sum* s, const char* path, double* meta, int64_t meta_cap, int64_t* n_meta) {
+  if (!s || !path || meta_cap < 0 || (meta_cap > 0 && !meta)) return PS_ERR_INVALID;
+  std::FILE* f = std::fopen(path, "rb");
+  if (!f) return PS_ERR_IO;
+  Fnv fnv;
+  char magic[8];
+  uint32_t hdr[4];
+  uint64_t cnt = 0;
+  bool ok = get(f, fnv, magic, 8) && std::memcmp(magic, kCkpMagic, 8) == 0 && get(f, fnv, hdr, sizeof(hdr)) &&
+            hdr[0] == 1u && hdr[2] <= (uint32_t)PS_COEF_F32 && hdr[3] <= (1u << 20) && get(f, fnv, &cnt, 8) &&
+            cnt < ((uint64_t)1 << 40);
+  std::vector<double> m(ok ? hdr[3] : 0);
+  if (ok && !m.empty()) ok = get(f, fnv, m.data(), m.size() * sizeof(double));
+  std::vector<uint64_t> v, w;
+  std::vector<double> re, im;
+  if (ok) {
+    v.resize((size_t)cnt);
+    w.resize((size_t)cnt);
+    re.resize((size_t)cnt);
+    im.resize((size_t)cnt);
+  }
+  for (uint64_t i = 0; ok && i < cnt; ++i) {
+    Rec r;
+    ok = get(f, fnv, &r, sizeof(r));
+    v[i] = r.v;
+    w[i] = r.w;
+    re[i] = r.re;
+    im[i] = r.im;
+  }
+  uint64_t sum = 0;
+  if (ok) ok = std::fread(&sum, 1, 8, f) == 8 && sum == fnv.h;
+  std::fclose(f);
+  if (!ok) return PS_ERR_IO;
+  if ((int)hdr[1] != s->n_sites) return PS_ERR_INVALID;
+  s->f32 = 0;  // the stored values are loaded as they are; the precision is restored after
+  PS_TRY(pauli_sum_upload(s, v.data(), w.data(), re.data(), im.data(), (int64_t)cnt));
+  s->f32 = hdr[2] == (uint32_t)PS_COEF_F32;
+  if (n_meta) *n_meta = (int64_t)m.size();
+  for (int64_t i = 0; i < std::min<int64_t>(meta_cap, (int64_t)m.size()); ++i) meta[i] = m[(size_t)i];
   return PS_OK;
 }
 

@@ -26,6 +26,7 @@ PS_ERR_CUDA = 4
 PS_ERR_TIMEOUT = 5
 PS_ERR_KRYLOV_EXHAUSTED = 6
 PS_ERR_NOMEM = 7
+PS_ERR_IO = 9
 PS_COEF_F64 = 0
 PS_COEF_F32 = 1
 
@@ -89,6 +90,8 @@ def load(build_if_missing: bool = False):
         "pauli_sum_download": ([P, U64P, U64P, F64P, F64P, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_sum_download_device": ([P, P, P, P, P, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_sum_copy": ([P, P], ctypes.c_int),
+        "pauli_sum_save": ([P, ctypes.c_char_p, P, I64], ctypes.c_int),
+        "pauli_sum_load": ([P, ctypes.c_char_p, P, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_commutator": ([P, P, P], ctypes.c_int),
         "pauli_multiply": ([P, P, P], ctypes.c_int),
         "pauli_add": ([P, ctypes.c_double, ctypes.c_double, P, P], ctypes.c_int),
@@ -249,6 +252,20 @@ class PauliSum:
         d = ctypes.c_int()
         _check(self._lib.pauli_sum_precision(self.handle, ctypes.byref(d)), "pauli_sum_precision")
         return int(d.value)
+
+    def save(self, path: str, meta=()):
+        """Checkpoint: the sum (canonical order), its precision and caller values (meta)."""
+        m = np.ascontiguousarray(meta, dtype=np.float64)
+        _check(self._lib.pauli_sum_save(self.handle, os.fsencode(path), m.ctypes.data_as(ctypes.c_void_p) if len(m) else None,
+                                        len(m)), "pauli_sum_save")
+
+    def load(self, path: str, meta_cap: int = 1 << 16) -> np.ndarray:
+        """Resume from a checkpoint; returns the stored caller values."""
+        m = np.zeros(meta_cap, np.float64)
+        nm = ctypes.c_int64()
+        _check(self._lib.pauli_sum_load(self.handle, os.fsencode(path), m.ctypes.data_as(ctypes.c_void_p), meta_cap,
+                                        ctypes.byref(nm)), "pauli_sum_load")
+        return m[:min(int(nm.value), meta_cap)].copy()
 
     def copy(self) -> "PauliSum":
         out = PauliSum(self.n_sites, len(self), self.stream.value)
