@@ -117,6 +117,15 @@ int pauli_sum_download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, doub
 
 int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst);
 
+/* Reorder the storage of s (contents unchanged) so that strings in the same bucket of the
+ * merge's output hash are adjacent: the order in which merges already return their results.
+ * An operand in that order lets the emission of [H, s] reserve output slots for a warp's
+ * neighbouring strings in few bins; an operand uploaded in canonical (sorted) order runs
+ * about a quarter slower at the Lanczos benchmark size.  Results never depend on storage
+ * order, but the order of a sum used as H (the left operand) is Alg. 1's outer-loop order:
+ * do not reorder such a sum.  Asynchronous on s's stream. */
+int pauli_sum_sort_by_hash(pauli_sum* s);
+
 /* Checkpoint / resume of long runs.  pauli_sum_save writes the sum to a file: an 8-byte
  * magic "PSUMCKP1", u32 version (1), u32 n_sites, u32 precision (PS_COEF_*), u32 n_meta,
  * u64 string count, n_meta f64 caller values (for example t, the step, the b_n so far),

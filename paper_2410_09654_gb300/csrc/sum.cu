@@ -348,6 +348,31 @@ int pauli_sum_size(const pauli_sum* s, int64_t* n) {
 // Pack four arrays into records and validate in the same pass: flags[0] = 1 if a string has
 // bits outside the key mask, flags[1] |= the coefficient class (bit 0: a non-zero real part,
 // bit 1: a non-zero imaginary part).
+// ----------------------------------------------------------------------------- hash order
+// The first kOrdBits rows of the merge's output hash F.  Merge outputs come out grouped by
+// F's low rows; an operand in that order lets a warp of an emission reserve output slots for
+// neighbouring strings in few bins.  pauli_sum_sort_by_hash puts any sum in that order.
+constexpr int kOrdBits = 16;
+__constant__ uint64_t c_ordA[kOrdBits], c_ordB[kOrdBits];
+
+__global__ void k_ord_key(const Rec* __restrict__ d, int64_t n, uint32_t* __restrict__ key,
+                          unsigned* __restrict__ hist) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Rec r = d[i];
+    uint32_t f = 0;
+#pragma unroll
+    for (int j = 0; j < kOrdBits; ++j) f |= (uint32_t)(__popcll((r.v & c_ordA[j]) ^ (r.w & c_ordB[j])) & 1) << j;
+    key[i] = f;
+    atomicAdd(&hist[f], 1u);
+  }
+}
+
+__global__ void k_ord_scatter(const Rec* __restrict__ d, int64_t n, const uint32_t* __restrict__ key,
+                              unsigned long long* __restrict__ cur, Rec* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[atomicAdd(&cur[key[i]], 1ull)] = d[i];
+}
+
 __global__ void k_pack(Rec* __restrict__ d, const uint64_t* __restrict__ v, const uint64_t* __restrict__ w,
                        const double* __restrict__ re, const double* __restrict__ im, int64_t n, uint64_t inv_mask,
                        int* __restrict__ flags) {
@@ -595,6 +620,42 @@ int pauli_sum_load(pauli_sum* s, const char* path, double* meta, int64_t meta_ca
   if (n_meta) *n_meta = (int64_t)m.size();
   for (int64_t i = 0; i < std::min<int64_t>(meta_cap, (int64_t)m.size()); ++i) meta[i] = m[(size_t)i];
   return PS_OK;
+}
+
+int pauli_sum_sort_by_hash(pauli_sum* s) {
+  if (!s) return PS_ERR_INVALID;
+  const int64_t n = s->n;
+  if (n <= 1) return PS_OK;
+  cudaStream_t st = s->stream;
+  static std::once_flag once;
+  static cudaError_t up = cudaSuccess;
+  std::call_once(once, [] {
+    up = cudaMemcpyToSymbol(c_ordA, g_rows.a, kOrdBits * sizeof(uint64_t));
+    if (up == cudaSuccess) up = cudaMemcpyToSymbol(c_ordB, g_rows.b, kOrdBits * sizeof(uint64_t));
+  });
+  PS_CUDA(up);
+  constexpr int64_t nb = (int64_t)1 << kOrdBits;
+  Buf<uint32_t> key, hist;
+  Buf<uint64_t> off;
+  PS_TRY(key.alloc((size_t)n, st));
+  PS_TRY(hist.alloc((size_t)nb, st));
+  PS_TRY(off.alloc((size_t)nb + 1, st));
+  PS_CUDA(cudaMemsetAsync(hist.p, 0, nb * sizeof(uint32_t), st));
+  const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
+  PS_LAUNCH("k_ord_key", st, k_ord_key<<<blocks, 256, 0, st>>>(s->d, n, key.p, hist.p));
+  PS_CUDA(cudaGetLastError());
+  PS_TRY(scan_u32_to_u64(hist.p, off.p, nb, st));
+  Rec* out = nullptr;
+  PS_TRY(dev_alloc((void**)&out, (size_t)n * sizeof(Rec), st));
+  PS_LAUNCH("k_ord_scatter", st,
+            k_ord_scatter<<<blocks, 256, 0, st>>>(s->d, n, key.p, reinterpret_cast<unsigned long long*>(off.p), out));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    dev_free(out, st);
+    set_cuda_error(e, "pauli_sum_sort_by_hash");
+    return PS_ERR_CUDA;
+  }
+  return sum_adopt(s, out, n, n);
 }
 
 }  // extern "C"

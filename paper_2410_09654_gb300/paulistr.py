@@ -90,6 +90,7 @@ def load(build_if_missing: bool = False):
         "pauli_sum_download": ([P, U64P, U64P, F64P, F64P, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_sum_download_device": ([P, P, P, P, P, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_sum_copy": ([P, P], ctypes.c_int),
+        "pauli_sum_sort_by_hash": ([P], ctypes.c_int),
         "pauli_sum_save": ([P, ctypes.c_char_p, P, I64], ctypes.c_int),
         "pauli_sum_load": ([P, ctypes.c_char_p, P, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_commutator": ([P, P, P], ctypes.c_int),
@@ -252,6 +253,11 @@ class PauliSum:
         d = ctypes.c_int()
         _check(self._lib.pauli_sum_precision(self.handle, ctypes.byref(d)), "pauli_sum_precision")
         return int(d.value)
+
+    def sort_by_hash(self) -> "PauliSum":
+        """Storage in the merge's output-hash order (for right operands; never for an H)."""
+        _check(self._lib.pauli_sum_sort_by_hash(self.handle), "pauli_sum_sort_by_hash")
+        return self
 
     def save(self, path: str, meta=()):
         """Checkpoint: the sum (canonical order), its precision and caller values (meta)."""

@@ -109,3 +109,18 @@ def test_bad_files_are_errors(tmp_path):
     with pytest.raises(ps.PauliError) as e:
         S.save(str(tmp_path / "no_such_dir" / "x.ckp"))
     assert e.value.status == ps.PS_ERR_IO
+
+
+def test_sort_by_hash_keeps_contents_and_results():
+    n = 64
+    Ha = I.xxz_chain(n).arrays()
+    Oa = I.random_sum(8, n, 60000, kind="real", max_support=12)
+    O = ps.PauliSum.from_arrays(n, *Oa)
+    S = ps.PauliSum.from_arrays(n, *Oa).sort_by_hash()
+    assert_match(S.download(), orc.Op(n, *O.download()), exact=True, what="contents")
+    H = ps.PauliSum.from_arrays(n, *Ha)
+    a = ps.pauli_commutator(H, O)
+    b = ps.pauli_commutator(H, S)
+    assert_match(b.download(), orc.Op(n, *a.download()), exact=True, what="commutator of the sorted operand")
+    one = ps.PauliSum.from_arrays(n, *I.single(n, "X", 3).arrays()).sort_by_hash()
+    assert len(one) == 1 and len(ps.PauliSum(n).sort_by_hash()) == 0
