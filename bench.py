@@ -364,7 +364,7 @@ def main():
     Z1 = I.single(n10, "Z", 1).arrays()
     rk_pol = ps.policy(max_weight=6, cutoff=1e-10)
     Or = ps.PauliSum.from_arrays(n10, *Z1)
-    for _ in range(3):
+    for _ in range(40):  # untimed warm-up: the same trajectory once (the operator grows every step)
         ps.pauli_rk4_step(Hr, Or, 0.05, rk_pol)
     Or = ps.PauliSum.from_arrays(n10, *Z1)
     Z1s = ps.PauliSum.from_arrays(n10, *Z1)
