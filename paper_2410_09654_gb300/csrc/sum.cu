@@ -614,8 +614,13 @@ int pauli_sum_load(pauli_sum* s, const char* path, double* meta, int64_t meta_ca
   std::fclose(f);
   if (!ok) return PS_ERR_IO;
   if ((int)hdr[1] != s->n_sites) return PS_ERR_INVALID;
-  s->f32 = 0;  // the stored values are loaded as they are; the precision is restored after
-  PS_TRY(pauli_sum_upload(s, v.data(), w.data(), re.data(), im.data(), (int64_t)cnt));
+  const int old_f32 = s->f32;
+  s->f32 = 0;  // the stored values are loaded as they are; the file's precision is set after
+  const int st = pauli_sum_upload(s, v.data(), w.data(), re.data(), im.data(), (int64_t)cnt);
+  if (st != PS_OK) {
+    s->f32 = old_f32;
+    return st;
+  }
   s->f32 = hdr[2] == (uint32_t)PS_COEF_F32;
   if (n_meta) *n_meta = (int64_t)m.size();
   for (int64_t i = 0; i < std::min<int64_t>(meta_cap, (int64_t)m.size()); ++i) meta[i] = m[(size_t)i];
