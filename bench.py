@@ -389,6 +389,10 @@ def main():
         ps.pauli_rk4_step(Hl, Ol, 0.02, lat_pol)
         if len(Ol) >= lat_cap and i >= 24:
             break
+    # merge geometry for the lattice's size class (untimed), unless fixed or disabled
+    lat_tune = None
+    if not args.merge_geometry and not args.no_autotune:
+        lat_tune = ps.pauli_autotune_commutator(Hl, Ol, reps=1)
     lat_prod = 0
     barrier()
     evl0 = torch.cuda.Event(enable_timing=True)
@@ -402,7 +406,7 @@ def main():
     t_lat = max_over_ranks(evl0.elapsed_time(evl1)) / 1e3
     rk4_lattice = {"workload": LATTICE_WORKLOAD, "ms_per_step": 1e3 * t_lat / 2,
                    "steps_per_s": sum_over_ranks(2) / t_lat, "products_per_s": sum_over_ranks(lat_prod) / t_lat,
-                   "size": len(Ol)}
+                   "size": len(Ol), "merge_geometry_autotuned": lat_tune}
 
     # ---------------------------------------------------------------- FP32 coefficients (2D lattice)
     f32_res = None
