@@ -619,3 +619,93 @@ def pauli_autotune_reset():
 
 def pauli_merge_geometry_fix(bin_target: int, quota: int):
     _check(load().pauli_merge_geometry_fix(int(bin_target), int(quota)), "pauli_merge_geometry_fix")
+
+
+# ------------------------------------------------------------------ the remaining C names
+# Module-level functions with the C ABI's names for the calls the classes above wrap
+# (construction, destruction, data movement, status strings); argument marshalling only.
+def pauli_status_string(status: int) -> str:
+    return load().pauli_status_string(int(status)).decode()
+
+
+def pauli_last_cuda_error() -> str:
+    return load().pauli_last_cuda_error().decode()
+
+
+def pauli_sum_create(n_sites: int, capacity: int = 0, stream=None) -> PauliSum:
+    return PauliSum(n_sites, capacity, stream)
+
+
+def pauli_sum_destroy(S: PauliSum):
+    S.__del__()
+
+
+def pauli_sum_upload(S: PauliSum, v, w, re, im) -> PauliSum:
+    S.upload(v, w, re, im)
+    return S
+
+
+def pauli_sum_upload_device(S: PauliSum, v, w, re, im) -> PauliSum:
+    S.upload_device(v, w, re, im)
+    return S
+
+
+def pauli_sum_size(S: PauliSum) -> int:
+    return len(S)
+
+
+def pauli_sum_n_sites(S: PauliSum) -> int:
+    n = ctypes.c_int()
+    _check(load().pauli_sum_n_sites(S.handle, ctypes.byref(n)), "pauli_sum_n_sites")
+    return int(n.value)
+
+
+def pauli_sum_download(S: PauliSum):
+    """(v, w, re, im) numpy arrays in canonical order."""
+    return S.download()
+
+
+def pauli_sum_download_device(S: PauliSum):
+    """(v, w, re, im) CUDA tensors (int64 bit patterns of the masks, float64) in storage order."""
+    import torch
+    m = len(S)
+    t = [torch.empty(m, dtype=dt, device="cuda") for dt in (torch.int64, torch.int64, torch.float64, torch.float64)]
+    got = ctypes.c_int64()
+    _check(load().pauli_sum_download_device(S.handle, *[ctypes.c_void_p(x.data_ptr()) for x in t], m,
+                                            ctypes.byref(got)), "pauli_sum_download_device")
+    return tuple(t)
+
+
+def pauli_sum_copy(src: PauliSum, dst: PauliSum | None = None) -> PauliSum:
+    if dst is None:
+        return src.copy()
+    _check(load().pauli_sum_copy(src.handle, dst.handle), "pauli_sum_copy")
+    return dst
+
+
+def pauli_sum_sort_by_hash(S: PauliSum) -> PauliSum:
+    return S.sort_by_hash()
+
+
+def pauli_sum_save(S: PauliSum, path: str, meta=()):
+    S.save(path, meta)
+
+
+def pauli_sum_load(S: PauliSum, path: str, meta_cap: int = 1 << 16) -> np.ndarray:
+    return S.load(path, meta_cap)
+
+
+def pauli_mlp_create(n_sites: int, seed: int = 0, stream=None) -> PauliMLP:
+    return PauliMLP(n_sites, seed, stream)
+
+
+def pauli_mlp_destroy(m: PauliMLP):
+    m.__del__()
+
+
+def pauli_batch_create(H: PauliSum, hcoef, tag_shift: int, caps=None) -> PauliBatch:
+    return PauliBatch(H, hcoef, tag_shift, caps)
+
+
+def pauli_batch_destroy(B: PauliBatch):
+    B.__del__()

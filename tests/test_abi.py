@@ -69,3 +69,9 @@ def test_product_path_does_not_touch_the_oracle():
                 text = open(os.path.join(root, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_every_declared_function_has_a_binding_of_the_same_name():
+    from paper_2410_09654_gb300 import paulistr as ps
+    missing = [n for n in ps.declared_symbols() if not callable(getattr(ps, n, None))]
+    assert not missing, missing
