@@ -14,7 +14,8 @@ Every function cites the passage of the paper it follows; see ``oracle.cpp``
 for the arithmetic.  Parity status: all entry points are pinned by the
 ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``; ``mlp.py`` (the learned
 truncation scorer and truncation by an arbitrary score) by ``tests/test_mlp_oracle.py``;
-the FP32-coefficient compositions at the end of this file by ``tests/test_f32_oracle.py``.
+the FP32-coefficient compositions at the end of this file by ``tests/test_f32_oracle.py``;
+``multiword.py`` (masks wider than 64 sites) by ``tests/test_multiword_oracle.py``.
 """
 from __future__ import annotations
 
