@@ -94,6 +94,8 @@ __global__ void k_na_top(SoA P, int64_t n, SoA T, NaScratch* s, uint64_t tmask) 
     if (j < 0) continue;
     double ar = P.re[i], ai = P.im[i], br = T.re[j], bi = T.im[j];
     m = max(m, max(max(prod_top(ar, br), prod_top(ai, bi)), max(prod_top(ar, bi), prod_top(ai, br))));
+    // a non-finite factor in a matched pair makes both parts NaN (as pauli_trace_product)
+    if (nonfinite_top(ar) > 0 || nonfinite_top(ai) > 0 || nonfinite_top(br) > 0 || nonfinite_top(bi) > 0) m = kTopNaN;
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(&s->top, m);
@@ -101,7 +103,7 @@ __global__ void k_na_top(SoA P, int64_t n, SoA T, NaScratch* s, uint64_t tmask) 
 
 __global__ void __launch_bounds__(kRedThreads) k_na_acc(SoA P, int64_t n, SoA T, NaScratch* s, uint64_t tmask) {
   const int t = s->top;
-  if (t <= -100000) return;
+  if (t <= -100000 || t >= kTopInf) return;
   const int wlo = ((t - 190 + kBias) & ~31) - kBias;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     s->wlo[0] = wlo;
@@ -143,18 +145,24 @@ extern "C" int pauli_trace_product_noalloc(const uint64_t* av, const uint64_t* a
   const SoA P = swap ? B : A, T = swap ? A : B;
   const int64_t np = swap ? nb : na, nt = swap ? na : nb;
   if (nt > kNaMaxTabled) return PS_ERR_CAPACITY;  // the smaller operand exceeds the fixed scratch
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (s) {  // the scratch address is the current device's: the stream must belong to it
+    int cur = 0, sdev = 0;
+    PS_CUDA(cudaGetDevice(&cur));
+    PS_CUDA(cudaStreamGetDevice(s, &sdev));
+    if (sdev != cur) return PS_ERR_INVALID;
+  }
   NaScratch* sc = nullptr;
   PS_TRY(na_scratch(&sc));
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   uint64_t slots = 1;
   while (slots < (uint64_t)(2 * nt)) slots <<= 1;
   // clear the part of the scratch this call reads: the used table slots and the accumulators
   PS_CUDA(cudaMemsetAsync(sc->key, 0xFF, slots * sizeof(ulonglong2), s));
   PS_CUDA(cudaMemsetAsync(sc->acc, 0, sizeof(sc->acc), s));
-  long long init_ones = -1;
-  int init_top = -100000;
-  PS_CUDA(cudaMemcpyAsync(&sc->ones_idx, &init_ones, sizeof(init_ones), cudaMemcpyHostToDevice, s));
-  PS_CUDA(cudaMemcpyAsync(&sc->top, &init_top, sizeof(init_top), cudaMemcpyHostToDevice, s));
+  // ones_idx = -1 (all bytes 0xFF); top = 0x80808080, below the -100000 "no product" mark
+  // (memsets: no host copy from pageable memory)
+  PS_CUDA(cudaMemsetAsync(&sc->ones_idx, 0xFF, sizeof(sc->ones_idx), s));
+  PS_CUDA(cudaMemsetAsync(&sc->top, 0x80, sizeof(sc->top), s));
   const int nsm = num_sms();
   int bt = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nt, 256), 4 * nsm));
   int bp = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(np, kRedThreads), 4 * nsm));
@@ -171,6 +179,10 @@ extern "C" int pauli_trace_product_noalloc(const uint64_t* av, const uint64_t* a
   PS_CUDA(cudaMemcpyAsync(wlo, sc->wlo, sizeof(wlo), cudaMemcpyDeviceToHost, s));
   PS_CUDA(cudaStreamSynchronize(s));
   if (top <= -100000) return PS_OK;
+  if (top >= kTopInf) {
+    *re = *im = std::nan("");
+    return PS_OK;
+  }
   std::vector<long long> fre(h.begin() + kWinDigits, h.begin() + kNaSpan);
   std::vector<long long> fim(h.begin() + kNaSpan + kWinDigits, h.end());
   *re = round_exact(fre, h.data(), wlo[0]);
