@@ -28,6 +28,12 @@
  *
  * Errors: every entry point returns a status (PS_OK = 0).  On error, output
  * sums are left empty or unchanged and nothing aborts; no device code traps.
+ *
+ * Non-finite values: uploads reject NaN and +-Inf coefficients (PS_ERR_INVALID).  Arithmetic
+ * that overflows follows IEEE rules (a merge may produce +-Inf or NaN coefficients; a NaN
+ * coefficient ranks lowest in truncation).  pauli_norm then returns +Inf (NaN if any
+ * coefficient is NaN), pauli_trace_product returns NaN in both parts when a matched pair holds
+ * a non-finite factor, and the Lanczos steps return PS_ERR_NONFINITE without rotating.
  * pauli_status_string() gives a description.
  *
  * Determinism: for every string, the contributions to its coefficient are added
@@ -54,11 +60,12 @@ extern "C" {
 #define PS_ERR_CAPACITY 2         /* a caller-provided capacity is too small (download) */
 #define PS_ERR_TABLE_FULL 3       /* a merge table could not be resolved even after splitting */
 #define PS_ERR_CUDA 4             /* a CUDA runtime call failed; see pauli_last_cuda_error() */
-#define PS_ERR_TIMEOUT 5          /* a bounded device-side wait gave up */
+#define PS_ERR_TIMEOUT 5          /* reserved: no kernel of this library waits on another agent */
 #define PS_ERR_KRYLOV_EXHAUSTED 6 /* Lanczos: b_n == 0 (the Krylov space closed); b_out is 0 */
 #define PS_ERR_NOMEM 7            /* device allocation failed */
 #define PS_ERR_UNCERTAIN 8        /* reserved */
 #define PS_ERR_IO 9               /* a checkpoint file could not be written or read, or is not one */
+#define PS_ERR_NONFINITE 10       /* Lanczos: b_n is +Inf or NaN (a coefficient overflowed); b_out holds it */
 
 const char* pauli_status_string(int status);
 /* Text of the last CUDA error seen by the library on this thread ("" if none). */
@@ -251,6 +258,8 @@ int pauli_coefficients(const pauli_sum* O, const uint64_t* qv, const uint64_t* q
  *   bv, bw, bre, bim: DEVICE arrays of B's nb strings; both caller-owned, read only;
  *     strings within each operand must be distinct;
  *   cuda_stream: the cudaStream_t the work is ordered on (NULL: legacy default stream);
+ *     it must belong to the current device (the scratch is looked up per device);
+ *     a stream of another device gives PS_ERR_INVALID;
  *   re, im: HOST doubles receiving the result; the call synchronises the stream.
  * Scratch lives in one fixed device array of about 6 MiB inside the library (held by
  * every GPU that loads it, until exit): no cudaMalloc, cudaFree or allocating library
@@ -383,6 +392,10 @@ int pauli_batch_destroy(pauli_batch* b);
  * is cut to the caps (top-k by |c|^2, ties to the smaller key, per instance).  O must hold
  * real coefficients and only valid tags (PS_ERR_INVALID otherwise); O's precision applies. */
 int pauli_batch_rk4_step(const pauli_batch* b, const pauli_sum* H, pauli_sum* O, double dt, int trim_stages);
+/* n_steps (>= 0) such steps in a row, the same as n_steps calls of pauli_batch_rk4_step.  On
+ * an error the steps already taken stay applied and *steps_done (nullable) says how many. */
+int pauli_batch_rk4_steps(const pauli_batch* b, const pauli_sum* H, pauli_sum* O, double dt, int trim_stages,
+                          int n_steps, int* steps_done);
 /* Per-instance top-k of O to the caps. */
 int pauli_batch_truncate(const pauli_batch* b, pauli_sum* O);
 /* Strings per instance (HOST [n_inst]); PS_ERR_INVALID if a string has a tag >= n_inst or
@@ -407,6 +420,10 @@ int64_t pauli_launch_count(void);
 /* Make the next n-th device allocation of the library fail (n >= 1; 0 disables).
  * Host-side fault injection for tests; it never touches the GPU. */
 int pauli_debug_fail_alloc_after(int64_t n);
+/* The merge's 32-bit output hash F(v, w) (a GF(2)-linear map of the 128 key bits; a
+ * merge bins strings by its low bits and splits crowded bins by the next ones) of n HOST
+ * strings into the HOST array out.  Host-only; for tests that build colliding inputs. */
+int pauli_debug_output_hash(const uint64_t* v, const uint64_t* w, int64_t n, uint32_t* out);
 /* Divide n DEVICE doubles in place by b with the division used by the Lanczos
  * normalisation (correctly rounded, equal to the IEEE quotient); synchronises the stream.
  * For tests of that arithmetic. */

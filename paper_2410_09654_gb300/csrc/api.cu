@@ -176,6 +176,7 @@ int pauli_ts_lanczos_step(const pauli_sum* H0, pauli_sum* O_prev, pauli_sum* O_c
   PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2, O_cur->n_sites));
   const double b = std::sqrt(n2);
   *b_out = b;
+  if (!std::isfinite(b)) return PS_ERR_NONFINITE;
   if (b == 0.0) return PS_ERR_KRYLOV_EXHAUSTED;
   pauli_trunc_policy p{-1, 0.0, 0, 0.0, 0};
   if (policy) {
@@ -348,6 +349,7 @@ int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, 
   PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2));
   double b = std::sqrt(n2);
   *b_out = b;
+  if (!std::isfinite(b)) return PS_ERR_NONFINITE;
   if (b == 0.0) return PS_ERR_KRYLOV_EXHAUSTED;
   pauli_trunc_policy p{-1, 0.0, 0, 0.0, 0};
   if (policy) {

@@ -53,6 +53,17 @@ __device__ __forceinline__ int prod_top(double x, double y) {
   return a.e + b.e + 106;
 }
 
+// Markers of the exponent bound for sums holding a non-finite coefficient (above every
+// finite bound; NaN above Inf so that atomicMax keeps it): the result is then +Inf or NaN,
+// as the IEEE sum would be, and the accumulation pass does nothing.
+constexpr int kTopInf = 1 << 29, kTopNaN = (1 << 29) + 1;
+
+__device__ __forceinline__ int nonfinite_top(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if (((b >> 52) & 0x7FF) != 0x7FF) return -100000;
+  return (b & ((1ull << 52) - 1)) ? kTopNaN : kTopInf;
+}
+
 struct Win {
   uint64_t w[4];  // 256-bit two's complement
 };

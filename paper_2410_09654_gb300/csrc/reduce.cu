@@ -29,6 +29,7 @@ __global__ void k_norm_top(const Rec* __restrict__ d, int64_t n, int* top) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     Rec r = d[i];
     m = max(m, max(prod_top(r.re, r.re), prod_top(r.im, r.im)));
+    m = max(m, max(nonfinite_top(r.re), nonfinite_top(r.im)));
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(top, m);
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_acc(const Rec* __restrict_
                                                           long long* gwin, long long* full, int* wlo_out, int ring,
                                                           uint64_t divmask) {
   int t = *top;
-  if (t <= -100000) return;
+  if (t <= -100000 || t >= kTopInf) return;
   int wlo = ((t - 190 + kBias) & ~31) - kBias;  // 32-aligned: terms < 2^222, 33 bits of headroom
   if (blockIdx.x == 0 && threadIdx.x == 0) *wlo_out = wlo;
   Win acc{{0, 0, 0, 0}};
@@ -111,6 +112,9 @@ __global__ void k_tp_top(const Rec* __restrict__ A, int64_t n, const Rec* __rest
     if (j < 0) continue;
     Rec b = B[j];
     m = max(m, max(max(prod_top(a.re, b.re), prod_top(a.im, b.im)), max(prod_top(a.re, b.im), prod_top(a.im, b.re))));
+    // a non-finite factor in a matched pair makes both parts NaN
+    if (nonfinite_top(a.re) > 0 || nonfinite_top(a.im) > 0 || nonfinite_top(b.re) > 0 || nonfinite_top(b.im) > 0)
+      m = kTopNaN;
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) {
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tp_acc(const Rec* __restrict__ 
                                                         long long* full_re, long long* gwin_im, long long* full_im,
                                                         int* wlo_out) {
   int t = *top;
-  if (t <= -100000) return;
+  if (t <= -100000 || t >= kTopInf) return;
   int wlo = ((t - 190 + kBias) & ~31) - kBias;
   if (blockIdx.x == 0 && threadIdx.x == 0) *wlo_out = wlo;
   Win ar{{0, 0, 0, 0}}, ai{{0, 0, 0, 0}};
@@ -172,6 +176,10 @@ int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) 
   PS_CUDA(cudaMemcpyAsync(hi, ints.p, sizeof(hi), cudaMemcpyDeviceToHost, s));
   PS_CUDA(cudaStreamSynchronize(s));
   if (hi[0] <= -100000) return PS_OK;
+  if (hi[0] >= kTopInf) {
+    *out = hi[0] == kTopNaN ? std::nan("") : HUGE_VAL;
+    return PS_OK;
+  }
   std::vector<long long> full(h.begin() + kWinDigits, h.end());
   *out = round_exact(full, h.data(), hi[1]);
   return PS_OK;
@@ -217,6 +225,10 @@ int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cuda
   PS_CUDA(cudaMemcpyAsync(hi, ints.p, sizeof(hi), cudaMemcpyDeviceToHost, s));
   PS_CUDA(cudaStreamSynchronize(s));
   if (hi[0] <= -100000) return PS_OK;
+  if (hi[0] >= kTopInf) {
+    *re = *im = std::nan("");
+    return PS_OK;
+  }
   std::vector<long long> fre(h.begin() + kWinDigits, h.begin() + span);
   std::vector<long long> fim(h.begin() + span + kWinDigits, h.end());
   *re = round_exact(fre, h.data(), hi[1]);

@@ -299,6 +299,7 @@ const char* pauli_status_string(int status) {
     case PS_ERR_KRYLOV_EXHAUSTED: return "Krylov space exhausted (b_n = 0)";
     case PS_ERR_NOMEM: return "device out of memory";
     case PS_ERR_UNCERTAIN: return "result rounding uncertain";
+    case PS_ERR_NONFINITE: return "non-finite norm (a coefficient overflowed or is NaN)";
     case PS_ERR_IO: return "checkpoint file error";
     default: return "unknown status";
   }
@@ -308,6 +309,12 @@ const char* pauli_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
 int pauli_debug_fail_alloc_after(int64_t n) {
   g_fail_after.store(n < 0 ? 0 : n);
+  return PS_OK;
+}
+
+int pauli_debug_output_hash(const uint64_t* v, const uint64_t* w, int64_t n, uint32_t* out) {
+  if (n < 0 || (n > 0 && (!v || !w || !out))) return PS_ERR_INVALID;
+  for (int64_t i = 0; i < n; ++i) out[i] = host_hash(v[i], w[i], kHashRows);
   return PS_OK;
 }
 
@@ -383,6 +390,8 @@ __global__ void k_pack(Rec* __restrict__ d, const uint64_t* __restrict__ v, cons
     const Rec r{v[i], w[i], re[i], im[i]};
     d[i] = r;
     bad |= ((r.v | r.w) & inv_mask) != 0;
+    // non-finite coefficients (exponent all ones) are rejected like out-of-range key bits
+    bad |= ((__double_as_longlong(r.re) >> 52) & 0x7FF) == 0x7FF || ((__double_as_longlong(r.im) >> 52) & 0x7FF) == 0x7FF;
     c |= (((__double_as_longlong(r.re) << 1) != 0) ? 1 : 0) | (((__double_as_longlong(r.im) << 1) != 0) ? 2 : 0);
   }
   bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);

@@ -27,6 +27,7 @@ PS_ERR_TIMEOUT = 5
 PS_ERR_KRYLOV_EXHAUSTED = 6
 PS_ERR_NOMEM = 7
 PS_ERR_IO = 9
+PS_ERR_NONFINITE = 10
 PS_COEF_F64 = 0
 PS_COEF_F32 = 1
 
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = False):
         "pauli_norm": ([P, F64P], ctypes.c_int),
         "pauli_last_merge_stats": ([ctypes.POINTER(pauli_merge_stats)], ctypes.c_int),
         "pauli_debug_fail_alloc_after": ([I64], ctypes.c_int),
+        "pauli_debug_output_hash": ([P, P, I64, P], ctypes.c_int),
         "pauli_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "pauli_profile_report": ([ctypes.c_char_p, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_launch_count": ([], I64),
@@ -121,6 +123,8 @@ def load(build_if_missing: bool = False):
         "pauli_batch_create": ([P, P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)], ctypes.c_int),
         "pauli_batch_destroy": ([P], ctypes.c_int),
         "pauli_batch_rk4_step": ([P, P, P, ctypes.c_double, ctypes.c_int], ctypes.c_int),
+        "pauli_batch_rk4_steps": ([P, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "pauli_batch_truncate": ([P, P], ctypes.c_int),
         "pauli_batch_counts": ([P, P, P], ctypes.c_int),
         "pauli_batch_norms": ([P, P, P], ctypes.c_int),
@@ -440,6 +444,15 @@ def pauli_debug_fail_alloc_after(n: int):
     _check(load().pauli_debug_fail_alloc_after(int(n)), "pauli_debug_fail_alloc_after")
 
 
+def pauli_debug_output_hash(v, w) -> np.ndarray:
+    """The merge's 32-bit output hash of host strings (host-side; for tests)."""
+    v, w = _u64(v), _u64(w)
+    out = np.zeros(len(v), np.uint32)
+    _check(load().pauli_debug_output_hash(v.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                                          len(v), out.ctypes.data_as(ctypes.c_void_p)), "pauli_debug_output_hash")
+    return out
+
+
 # ------------------------------------------------------------------ learned truncation
 def _dev(t):
     return ctypes.c_void_p(t.data_ptr())
@@ -582,6 +595,14 @@ class PauliBatch:
 def pauli_batch_rk4_step(B: PauliBatch, H: PauliSum, O: PauliSum, dt: float, trim_stages: int = 0) -> PauliSum:
     _check(load().pauli_batch_rk4_step(B.handle, H.handle, O.handle, float(dt), int(trim_stages)),
            "pauli_batch_rk4_step")
+    return O
+
+
+def pauli_batch_rk4_steps(B: PauliBatch, H: PauliSum, O: PauliSum, dt: float, n_steps: int,
+                          trim_stages: int = 0) -> PauliSum:
+    done = ctypes.c_int()
+    _check(load().pauli_batch_rk4_steps(B.handle, H.handle, O.handle, float(dt), int(trim_stages), int(n_steps),
+                                        ctypes.byref(done)), "pauli_batch_rk4_steps")
     return O
 
 

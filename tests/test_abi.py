@@ -75,3 +75,17 @@ def test_every_declared_function_has_a_binding_of_the_same_name():
     from paper_2410_09654_gb300 import paulistr as ps
     missing = [n for n in ps.declared_symbols() if not callable(getattr(ps, n, None))]
     assert not missing, missing
+
+
+def test_output_hash_hook_is_linear_without_gpu(lib):
+    """The merge's output hash is GF(2)-linear: F(a ^ b) = F(a) ^ F(b) (host-side hook)."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 2**63, size=(2, 200), dtype=np.int64).astype(np.uint64) * np.uint64(2)
+    b = rng.integers(0, 2**63, size=(2, 200), dtype=np.int64).astype(np.uint64) + np.uint64(1)
+    fa = ps.pauli_debug_output_hash(a[0], a[1])
+    fb = ps.pauli_debug_output_hash(b[0], b[1])
+    fab = ps.pauli_debug_output_hash(a[0] ^ b[0], a[1] ^ b[1])
+    assert np.array_equal(fab, fa ^ fb)
+    assert not ps.pauli_debug_output_hash(np.zeros(1, np.uint64), np.zeros(1, np.uint64)).any()
+    assert len(set(fa.tolist())) > 190  # spreads distinct keys
