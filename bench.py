@@ -230,17 +230,19 @@ def main():
     # that the timed loop and the end-to-end leg run the same states (the recursion is
     # deterministic)
     snaps = []
+    start = (prev.copy(), cur.copy(), b)  # the timed and the profiled region both start here
+    start_step = n_done + 1               # index n of the first timed b_n
     if not args.no_e2e:
-        keep_prev, keep_cur, keep_b = prev.copy(), cur.copy(), b
         for _ in range(max(1, min(args.steps, 4))):
             snaps.append((prev.download(), cur.download(), b))
             b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
-        prev, cur, b = keep_prev, keep_cur, keep_b
+    prev, cur, b = start[0].copy(), start[1].copy(), start[2]
 
     # ---------------------------------------------------------------- timed region
     # K Lanczos steps, un-instrumented; the per-kernel CUDA-event timings come from a second
-    # timed region of K further steps of the same workload (events recorded by the library on
-    # each kernel's launching stream), so that event recording does not slow the headline.
+    # pass over the same K steps, restarted from the same device state (events recorded by the
+    # library on each kernel's launching stream), so that event recording does not slow the
+    # headline and the per-kernel times describe exactly the timed steps.
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
     products = 0
@@ -267,8 +269,11 @@ def main():
     ms = ev0.elapsed_time(ev1)
     value, ms_max, products_all = R.job_rate(products, ms)
     merged_rate = sum_over_ranks(merged) / (ms_max / 1e3)
+    contrib_rate = sum_over_ranks(contributions) / (ms_max / 1e3)
 
-    # per-kernel durations over a second timed region (same K steps, events on)
+    # per-kernel durations over the same K steps again, from the same start state (events on)
+    prev, cur, b = start[0].copy(), start[1].copy(), start[2]
+    prof_bs = []
     ps.pauli_profile_enable(True)
     barrier()
     prof_products = 0
@@ -282,6 +287,7 @@ def main():
         prof_products += nH * len(cur)
         prof_src += len(prev)  # O_{n-1} enters the merge as a source term
         b = ps.pauli_lanczos_step(H, prev, cur, b, pol)
+        prof_bs.append(b)
         st = ps.pauli_last_merge_stats()
         prof_contrib += st["contributions"]
         prof_merged += st["merged"]
@@ -290,6 +296,8 @@ def main():
     prof = ps.pauli_profile_report()
     ps.pauli_profile_enable(False)
     prof_ms = evp0.elapsed_time(evp1)
+    assert prof_bs == bs, "the profiled pass must repeat the timed steps"
+    del start
 
     # ---------------------------------------------------------------- roofline of the dominant kernel
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -444,7 +452,9 @@ def main():
                        f"bins hold {contributions / args.steps * 32 / 1e9:.1f} GB of contribution records per step "
                        "(L2 is 129 MB)", "parallelism": "replicas" if world > 1 else "single"},
             "merged_strings_per_s": merged_rate,
+            "contributions_per_s": contrib_rate,
             "contributions_per_step": contributions / args.steps,
+            "timed_steps_n": [start_step, start_step + args.steps - 1],
             "b_n_timed": bs,
             "rk4": rk4,
             "rk4_lattice": rk4_lattice,
@@ -454,6 +464,7 @@ def main():
             "roofline": roof,
             "kernels_per_step_ms": {k: round(v[1], 4) for k, v in sorted(per_step.items(), key=lambda kv: -kv[1][1])},
             "profiled_region_ms_per_step": prof_ms / args.steps,
+            "profiled_region": "the timed steps again, from the same device state, with per-kernel CUDA events",
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
