@@ -328,6 +328,17 @@ int pauli_batch_norms(const pauli_batch* b, const pauli_sum* O, double* norms) {
   return PS_OK;
 }
 
+int pauli_batch_rk4_steps(const pauli_batch* b, const pauli_sum* H, pauli_sum* O, double dt, int trim_stages,
+                          int n_steps, int* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (n_steps < 0) return PS_ERR_INVALID;
+  for (int k = 0; k < n_steps; ++k) {
+    PS_TRY(pauli_batch_rk4_step(b, H, O, dt, trim_stages));
+    if (steps_done) *steps_done = k + 1;
+  }
+  return PS_OK;
+}
+
 int pauli_batch_truncate(const pauli_batch* b, pauli_sum* O) {
   if (!b || !O) return PS_ERR_INVALID;
   return batch_truncate(b, O);

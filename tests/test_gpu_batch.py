@@ -115,3 +115,23 @@ def test_batch_rejects_bad_tags_and_shapes():
         ps.PauliBatch(Hc, np.zeros((n_inst, len(Hs[0][0]))), n + 2)  # tags would not fit below n_sites
     with pytest.raises(ps.PauliError):
         ps.PauliBatch(Hc, np.zeros((n_inst, len(Hs[0][0]))), n - 1)  # H has bits at the tag position
+
+
+def test_batch_rk4_steps_equals_single_steps():
+    """pauli_batch_rk4_steps(n) is n calls of pauli_batch_rk4_step; checked against the
+    oracle's per-instance steps."""
+    n, n_inst = 10, 9
+    N, Hs, Hc, B, caps = _setup(n, n_inst, lambda b: 1 << (5 + b % 4))
+    O0 = [I.single(n, "Z", 5).arrays() for _ in range(n_inst)]
+    O = ps.PauliSum.from_arrays(N, *_tagged(O0, n))
+    ps.pauli_batch_rk4_steps(B, Hc, O, 0.05, 4, trim_stages=1)
+    ref = [orc.Op(n, *o) for o in O0]
+    Ho = [orc.Op(n, *h) for h in Hs]
+    for _ in range(4):
+        ref = orc.batch_rk4_step(Ho, ref, 0.05, caps, trim_stages=1)
+    got = _untag(O.download(), n, n_inst)
+    for b in range(n_inst):
+        assert_match(got[b], ref[b], exact=True, what=f"instance {b}")
+    before = O.download()
+    ps.pauli_batch_rk4_steps(B, Hc, O, 0.05, 0)  # zero steps: unchanged
+    assert all(np.array_equal(x, y) for x, y in zip(O.download(), before))

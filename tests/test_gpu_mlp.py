@@ -305,3 +305,28 @@ def test_learned_workflow_small():
     ref, _ = L.rk4_observable(H, O0, 0.05, 20, ps.policy(top_k=16 * M, trim_stages=1), probe)
     assert np.all(np.isfinite(obs))
     assert np.max(np.abs(obs - ref)) < 0.05
+
+
+def test_learned_truncation_lowers_observable_error_at_the_same_cap():
+    """What the trained network gains over plain |c| truncation: on the N=48 chain at cap
+    2^18 (the benchmark's learned-truncation workload: O(0) = Z_24, dt 0.05, 80 steps,
+    trimmed stages), the mean error of Tr(O(t) Z_24)/2^N against the same run at cap 2^22
+    is lower with the learned score than with |c| alone.  Training data and labels come from
+    the method's own runs (cap 2^18 against 2^20, ten steps ahead)."""
+    from paper_2410_09654_gb300 import learned as L
+    n, Ha, O0a = _chain48()
+    H, O0 = _sum(n, Ha), _sum(n, O0a)
+    M = 1 << 18
+    dt, steps = 0.05, 80
+    pv, pw = I.string("Z", 24)
+    probe = (np.array([pv], np.uint64), np.array([pw], np.uint64))
+    pol = ps.policy(top_k=M, trim_stages=1)
+    ref, _ = L.rk4_observable(H, O0, dt, steps, ps.policy(top_k=16 * M, trim_stages=1), probe)
+    plain, _ = L.rk4_observable(H, O0, dt, steps, pol, probe)
+    data = L.collect(H, O0, dt, M, [10, 20, 30, 40, 50, 60], 10)
+    model = ps.PauliMLP(n, seed=1)
+    L.train(model, data, 4000, batch=16384, lr=1e-3)
+    learned, _ = L.rk4_observable(H, O0, dt, steps, pol, probe, model=model)
+    e_plain = float(np.abs(plain[:, 0] - ref[:, 0]).mean())
+    e_learned = float(np.abs(learned[:, 0] - ref[:, 0]).mean())
+    assert e_learned < 0.85 * e_plain, (e_learned, e_plain)
