@@ -198,6 +198,8 @@ def test_download_into_too_small_capacity():
     lib = ps.load()
     buf = [np.zeros(10, np.uint64), np.zeros(10, np.uint64), np.zeros(10), np.zeros(10)]
     got = ctypes.c_int64()
-    st = lib.pauli_sum_download(S.handle, *[b.ctypes.data_as(ctypes.c_void_p) for b in buf], 10, ctypes.byref(got))
+    ptrs = [buf[0].ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), buf[1].ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+            buf[2].ctypes.data_as(ctypes.POINTER(ctypes.c_double)), buf[3].ctypes.data_as(ctypes.POINTER(ctypes.c_double))]
+    st = lib.pauli_sum_download(S.handle, *ptrs, 10, ctypes.byref(got))
     assert st == ps.PS_ERR_CAPACITY and got.value == 50
     assert not any(b.any() for b in buf)  # nothing written
