@@ -1,6 +1,8 @@
 """Pins of the multi-word oracle (oracle/multiword.py, masks of any width): equality with the
 single-word C++ oracle for N <= 64, dense matrices on local supports that straddle the word
 boundary at site 64, and invariance under moving an operator by whole words.  CPU only."""
+import math
+
 import numpy as np
 import pytest
 
@@ -95,3 +97,105 @@ def test_product_phase_table_on_far_sites():
     assert mw.product(Y, Z) == (X, 1)
     assert mw.product(Z, X) == (Y, 1)
     assert mw.anticommute(X, Y) and not mw.anticommute(X, X)
+
+
+# ----------------------------------------------------------------------------- truncation, RK4 with
+# dissipation, Lanczos and trace products (the rest of the path for masks of any width)
+def _dict(arrays):
+    return dict(_terms(arrays))
+
+
+def _shift(terms, s):
+    return [((k[0] << s, k[1] << s), c) for k, c in terms]
+
+
+def test_truncate_dissipation_keep_equals_single_word_oracle():
+    n = 20
+    A = I.random_sum(31, n, 600, kind="complex", max_support=7)
+    keep_arr = (A[0][::37], A[1][::37], np.ones(len(A[0][::37])), np.zeros(len(A[0][::37])))
+    for kw in (dict(gamma=0.3, dt=0.1), dict(max_weight=5, cutoff=0.05), dict(top_k=150, gamma=0.2, dt=0.05),
+               dict(top_k=100, max_weight=6)):
+        got = mw.truncate(_dict(A), keep=set(zip(map(int, keep_arr[0]), map(int, keep_arr[1]))), **kw)
+        want = _as_dict(orc.truncate(orc.Op(n, *A), keep=orc.Op(n, *keep_arr), **kw))
+        assert got.keys() == want.keys() and all(got[k] == want[k] for k in want), kw
+
+
+def test_rk4_with_dissipation_and_trimmed_stages_equals_single_word_oracle():
+    n = 10
+    Ha = I.tilted_ising_chain(n).arrays()
+    O = _dict(I.single(n, "Z", 1).arrays())
+    ref = orc.Op(n, *I.single(n, "Z", 1).arrays())
+    for _ in range(5):
+        O = mw.rk4_step(_terms(Ha), O, 0.05, top_k=120, gamma=0.1, trim_stages=1)
+        ref = orc.rk4_step(orc.Op(n, *Ha), ref, 0.05, top_k=120, gamma=0.1, trim_stages=1)
+        want = _as_dict(ref)
+        assert O.keys() == want.keys() and all(O[k] == want[k] for k in want)
+
+
+def test_lanczos_step_equals_single_word_oracle():
+    n = 12
+    Ha = I.xxz_chain(n, 0.5).arrays()
+    prev, cur = {}, _dict(I.uniform_sum(n, "X").arrays())
+    rprev, rcur = orc.Op.empty(n), orc.Op(n, *I.uniform_sum(n, "X").arrays())
+    b = rb = 0.0
+    for _ in range(6):
+        b, nxt = mw.lanczos_step(_terms(Ha), prev, cur, b, top_k=400)
+        rb, rnxt = orc.lanczos_step(orc.Op(n, *Ha), rprev, rcur, rb, top_k=400)
+        prev, cur, rprev, rcur = cur, nxt, rcur, rnxt
+        assert b == rb
+        want = _as_dict(rcur)
+        assert cur.keys() == want.keys() and all(cur[k] == want[k] for k in want)
+
+
+def test_trace_product_equals_single_word_oracle():
+    n = 40
+    rng = np.random.default_rng(4)
+    v, w = I.random_strings(rng, n, 900)
+    A = (v[:600], w[:600], rng.standard_normal(600), rng.standard_normal(600))
+    B = (v[300:], w[300:], rng.standard_normal(600) * 1e-5, rng.standard_normal(600))
+    assert mw.trace_product(_dict(A), _dict(B)) == orc.trace_product(orc.Op(n, *A), orc.Op(n, *B))
+
+
+def test_lanczos_printed_example_across_the_word_boundary():
+    # the paper's worked example (open XX chain of 10 sites + X on site 4, O_0 = X_1) placed on
+    # sites 60..69 of a 128-site chain: both mask words are used, and every printed O_n and
+    # the b_n implied by its normalisation are reproduced (letters and signs mapped as in the
+    # single-word golden test)
+    from test_oracle_pins import _load_golden
+    golden = _load_golden("lanczos_xx_defect_n10.txt")
+    n, s = 10, 59
+    b = I.xx_chain(n)
+    b.add(1.0, "X", 4)
+    H = _shift(_terms(b.arrays()), s)
+    prev, cur, bp = {}, dict(_shift(_terms(I.single(n, "X", 1).arrays()), s)), 0.0
+    ops, bs = {1: cur}, []
+    for step in range(2, 8):
+        bp, nxt = mw.lanczos_step(H, prev, cur, bp, cutoff=1e-10)
+        bs.append(bp)
+        prev, cur = cur, nxt
+        ops[step] = cur
+    assert any((k[0] | k[1]) >> 64 for k in ops[7]) and any((k[0] | k[1]) & ((1 << 64) - 1) for k in ops[7])
+    letters = {(0, 0): "1", (0, 1): "X", (1, 0): "Z", (1, 1): "Y"}
+    relabel = {"1": "1", "X": "X", "Y": "Z", "Z": "Y"}
+    for step, printed in golden.items():
+        got = {"".join(letters[((k[0] >> (s + i)) & 1, (k[1] >> (s + i)) & 1)] for i in range(n)): c
+               for k, c in ops[step].items()}
+        want = {"".join(relabel[ch] for ch in p): c * (-1) ** (step - 1) for p, c in printed.items()}
+        assert set(got) == set(want), step
+        for p in want:
+            assert abs(got[p] - want[p]) < 6e-11, (step, p)
+    assert np.allclose(bs[:6], [2, 2, 2, 2 * math.sqrt(2), 2 * math.sqrt(3), math.sqrt(50 / 3)], rtol=1e-14)
+
+
+def test_lanczos_open_xx_chain_of_100_sites_is_constant():
+    # closed form: open XX chain from an edge X_1 has b_n = 2 until the Krylov space closes
+    n = 100
+    H = []
+    for j in range(n - 1):
+        H.append(((0, (1 << j) | (1 << (j + 1))), 1.0 + 0j))                      # X_j X_{j+1}
+        H.append((((1 << j) | (1 << (j + 1)), (1 << j) | (1 << (j + 1))), 1.0 + 0j))  # Y_j Y_{j+1}
+    prev, cur, b = {}, {(0, 1): 1.0 + 0j}, 0.0
+    for _ in range(12):
+        b, nxt = mw.lanczos_step(H, prev, cur, b)
+        assert b == 2.0
+        prev, cur = cur, nxt
