@@ -12,6 +12,15 @@
  *   - A Pauli string on n_sites <= 64 sites is a pair of uint64 masks (v, w).
  *     Bit i-1 is site i; v is the Z bit and w the X bit (tau table).  Bits at or
  *     above n_sites must be zero.
+ *   - Wider registers (the paper's masks have any length): for 65 <= n_sites <= 256 each
+ *     mask is W = 2 (n_sites <= 128) or W = 4 (n_sites <= 256) uint64 words, and every
+ *     array of masks a call reads or writes holds W words per string, row-major (string i
+ *     at [i*W, i*W + W)); word k holds sites 64k+1 .. 64k+64.  Canonical order compares v,
+ *     then w, as unsigned W-word integers.  Sums of this width support uploads, downloads,
+ *     copies, pauli_commutator, pauli_add, pauli_truncate, pauli_rk4_step,
+ *     pauli_lanczos_step, pauli_trace_product and pauli_norm (the same results as the
+ *     one-word path: same summation order, same truncation rules; H at most 61439 strings);
+ *     every other entry point returns PS_ERR_INVALID for them.
  *   - A coefficient multiplies the Hermitian string
  *     P(v,w) = (-i)^{popcount(v & w)} Z^v X^w  (site letters I, X, Y, Z).
  *   - Coefficients are complex FP64, passed as separate real and imaginary arrays.
@@ -74,7 +83,7 @@ const char* pauli_last_cuda_error(void);
 /* ------------------------------------------------------------------ sums */
 typedef struct pauli_sum pauli_sum; /* opaque, device resident */
 
-/* Create an empty sum on n_sites (1..64) sites.  capacity is a hint (strings);
+/* Create an empty sum on n_sites (1..256) sites.  capacity is a hint (strings);
  * sums grow as needed.  cuda_stream: cudaStream_t the sum's work is ordered on. */
 int pauli_sum_create(int n_sites, int64_t capacity, void* cuda_stream, pauli_sum** out);
 int pauli_sum_destroy(pauli_sum* s);

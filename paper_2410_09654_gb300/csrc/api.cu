@@ -20,7 +20,7 @@ bool same_sites(const pauli_sum* a, const pauli_sum* b) { return !a || !b || a->
 // A library-internal temporary sum on a given stream.
 struct Tmp {
   pauli_sum s;
-  explicit Tmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0, 0, like->f32} {}
+  explicit Tmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0, 0, like->f32, like->W} {}
   ~Tmp() { dev_free(s.d, s.stream); }
   Tmp(const Tmp&) = delete;
   Tmp& operator=(const Tmp&) = delete;
@@ -52,9 +52,9 @@ int commutator_into(const pauli_sum* H, const pauli_sum* X, int rot, pauli_sum* 
   return merge_into(sp, out->stream, out);
 }
 
-bool policy_valid(const pauli_trunc_policy* p) {
+bool policy_valid(const pauli_trunc_policy* p, const pauli_sum* O = nullptr) {
   if (!p) return true;
-  return std::isfinite(p->cutoff) && std::isfinite(p->gamma) && p->max_weight <= 64;
+  return std::isfinite(p->cutoff) && std::isfinite(p->gamma) && p->max_weight <= (O ? 64 * O->W : 64);
 }
 
 // translation symmetry
@@ -101,6 +101,7 @@ int pauli_commutator(const pauli_sum* H, const pauli_sum* O, pauli_sum* out) {
   if (H->n > 0xEFFF) return PS_ERR_INVALID;
   if (H->stream != out->stream) PS_CUDA(cudaStreamSynchronize(H->stream));
   if (O->stream != out->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
+  if (O->W > 1) return wide_api::commutator(H, O, 0, out);
   return commutator_into(H, O, 0, out);
 }
 
@@ -108,6 +109,7 @@ int pauli_multiply(const pauli_sum* A, const pauli_sum* B, pauli_sum* out) {
   NvtxRange nvtx("pauli_multiply");
   if (!A || !B || !out || out == A || out == B) return PS_ERR_INVALID;
   if (!same_sites(A, B) || !same_sites(B, out)) return PS_ERR_INVALID;
+  PS_NARROW(A);
   if (A->n > 0xEFFF) return PS_ERR_INVALID;
   if (A->stream != out->stream) PS_CUDA(cudaStreamSynchronize(A->stream));
   if (B->stream != out->stream) PS_CUDA(cudaStreamSynchronize(B->stream));
@@ -124,18 +126,22 @@ int pauli_multiply(const pauli_sum* A, const pauli_sum* B, pauli_sum* out) {
 
 
 int pauli_ts_expand(const pauli_sum* G, pauli_sum* out) {
+  PS_NARROW(G);
   if (!ts_ok(G) || !out || out == G || !same_sites(G, out)) return PS_ERR_INVALID;
   if (G->stream != out->stream) PS_CUDA(cudaStreamSynchronize(G->stream));
   return ts_merge(G, kTsExpand, out);
 }
 
 int pauli_ts_canonicalize(const pauli_sum* X, pauli_sum* out) {
+  PS_NARROW(X);
   if (!ts_ok(X) || !out || out == X || !same_sites(X, out)) return PS_ERR_INVALID;
   if (X->stream != out->stream) PS_CUDA(cudaStreamSynchronize(X->stream));
   return ts_merge(X, kTsCanon, out);
 }
 
 int pauli_ts_commutator(const pauli_sum* H0, const pauli_sum* O0, pauli_sum* out) {
+  PS_NARROW(H0);
+  PS_NARROW(O0);
   if (!ts_ok(H0) || !ts_ok(O0) || !out || out == H0 || out == O0) return PS_ERR_INVALID;
   if (!same_sites(H0, O0) || !same_sites(O0, out)) return PS_ERR_INVALID;
   if (H0->stream != out->stream) PS_CUDA(cudaStreamSynchronize(H0->stream));
@@ -144,6 +150,7 @@ int pauli_ts_commutator(const pauli_sum* H0, const pauli_sum* O0, pauli_sum* out
 }
 
 int pauli_ts_norm(const pauli_sum* O0, double* out) {
+  PS_NARROW(O0);
   if (!ts_ok(O0) || !out) return PS_ERR_INVALID;
   double n2 = 0.0;
   PS_TRY(exact_norm2(O0->d, O0->n, O0->stream, &n2, O0->n_sites));
@@ -153,6 +160,8 @@ int pauli_ts_norm(const pauli_sum* O0, double* out) {
 
 int pauli_ts_lanczos_step(const pauli_sum* H0, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev,
                           const pauli_trunc_policy* policy, double* b_out) {
+  PS_NARROW(H0);
+  PS_NARROW(O_cur);
   if (!ts_ok(H0) || !O_prev || !O_cur || !b_out || O_prev == O_cur || H0 == O_prev || H0 == O_cur)
     return PS_ERR_INVALID;
   if (!same_sites(H0, O_cur) || !same_sites(O_prev, O_cur) || !policy_valid(policy) || !std::isfinite(b_prev))
@@ -193,6 +202,7 @@ int pauli_ts_lanczos_step(const pauli_sum* H0, pauli_sum* O_prev, pauli_sum* O_c
 int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_sum* B, pauli_sum* out) {
   if (!A || !B || !out || out == A || out == B) return PS_ERR_INVALID;
   if (!same_sites(A, B) || !same_sites(A, out)) return PS_ERR_INVALID;
+  if (A->W > 1) return wide_api::add(A, Cx{alpha_re, alpha_im}, B, out);
   MergeSpec sp;
   sp.src[0] = source(A, Cx{1.0, 0.0});
   sp.src[1] = source(B, Cx{alpha_re, alpha_im});
@@ -202,12 +212,14 @@ int pauli_add(const pauli_sum* A, double alpha_re, double alpha_im, const pauli_
 
 int pauli_truncate(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt) {
   NvtxRange nvtx("pauli_truncate");
-  if (!O || !same_sites(O, keep) || !policy_valid(policy) || !std::isfinite(dt)) return PS_ERR_INVALID;
+  if (!O || !same_sites(O, keep) || !policy_valid(policy, O) || !std::isfinite(dt)) return PS_ERR_INVALID;
+  if (O->W > 1) return wide_api::truncate(O, policy, keep, dt, nullptr);
   return truncate_run(O, policy, keep, dt, nullptr);
 }
 
 int pauli_autotune_commutator(const pauli_sum* H, const pauli_sum* O, int reps, int* best_bin_target,
                               int* best_quota, double* best_ms, double* default_ms) {
+  PS_NARROW(O);
   if (!H || !O || H == O || !same_sites(H, O) || H->n > 0xEFFF || reps < 1) return PS_ERR_INVALID;
   if (H->stream != O->stream) PS_CUDA(cudaStreamSynchronize(H->stream));
   Tmp out(O);
@@ -230,6 +242,7 @@ int pauli_merge_geometry_fix(int bin_target, int quota) { return merge_geometry_
 
 int pauli_truncate_scored(pauli_sum* O, const pauli_trunc_policy* policy, const pauli_sum* keep, double dt,
                           const double* score) {
+  PS_NARROW(O);
   if (!O || !same_sites(O, keep) || !policy_valid(policy) || !std::isfinite(dt)) return PS_ERR_INVALID;
   if (O->n > 0 && !score) return PS_ERR_INVALID;
   return truncate_run(O, policy, keep, dt, nullptr, score);
@@ -310,12 +323,14 @@ extern "C" {
 int pauli_rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
                    const pauli_sum* keep) {
   if (!H || !O || H == O || !same_sites(H, O) || !same_sites(O, keep)) return PS_ERR_INVALID;
-  if (!policy_valid(policy) || !std::isfinite(dt) || H->n > 0xEFFF) return PS_ERR_INVALID;
+  if (!policy_valid(policy, O) || !std::isfinite(dt) || H->n > 0xEFFF) return PS_ERR_INVALID;
+  if (O->W > 1) return wide_api::rk4_step(H, O, dt, policy, keep);
   return rk4_impl(H, O, dt, policy, keep, nullptr, nullptr);
 }
 
 int pauli_rk4_step_mlp(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* policy,
                        const pauli_sum* keep, const pauli_mlp* model, pauli_sum* cand_out) {
+  PS_NARROW(O);
   if (!H || !O || H == O || !same_sites(H, O) || !same_sites(O, keep) || !same_sites(O, cand_out)) return PS_ERR_INVALID;
   if (cand_out == O || cand_out == H) return PS_ERR_INVALID;
   if (!policy_valid(policy) || !std::isfinite(dt) || H->n > 0xEFFF) return PS_ERR_INVALID;
@@ -328,10 +343,11 @@ int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, 
                        const pauli_trunc_policy* policy, double* b_out) {
   NvtxRange nvtx("pauli_lanczos_step");
   if (!H || !O_prev || !O_cur || !b_out || O_prev == O_cur || H == O_prev || H == O_cur) return PS_ERR_INVALID;
-  if (!same_sites(H, O_cur) || !same_sites(O_prev, O_cur) || !policy_valid(policy) || !std::isfinite(b_prev))
+  if (!same_sites(H, O_cur) || !same_sites(O_prev, O_cur) || !policy_valid(policy, O_cur) || !std::isfinite(b_prev))
     return PS_ERR_INVALID;
   if (H->n > 0xEFFF) return PS_ERR_INVALID;
   *b_out = 0.0;
+  if (O_cur->W > 1) return wide_api::lanczos_step(H, O_prev, O_cur, b_prev, policy, b_out);
   Tmp A(O_cur);
   MergeSpec sp;
   sp.H = H->d;
@@ -367,12 +383,14 @@ int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, 
 int pauli_trace_product(const pauli_sum* A, const pauli_sum* B, double* re, double* im) {
   if (!A || !B || !re || !im || !same_sites(A, B)) return PS_ERR_INVALID;
   if (A->stream != B->stream) PS_CUDA(cudaStreamSynchronize(B->stream));
+  if (A->W > 1) return wide_api::trace_product(A, B, re, im);
   return exact_trace_product(A->d, A->n, B->d, B->n, A->stream, re, im);
 }
 
 int pauli_coefficients(const pauli_sum* O, const uint64_t* qv, const uint64_t* qw, int64_t nq, double* re,
                        double* im) {
   if (!O || nq < 0 || (nq > 0 && (!qv || !qw || !re || !im))) return PS_ERR_INVALID;
+  PS_NARROW(O);
   const uint64_t inv = O->n_sites >= 64 ? 0ull : ~((1ull << O->n_sites) - 1ull);
   for (int64_t j = 0; j < nq; ++j)
     if ((qv[j] | qw[j]) & inv) return PS_ERR_INVALID;
@@ -382,6 +400,11 @@ int pauli_coefficients(const pauli_sum* O, const uint64_t* qv, const uint64_t* q
 int pauli_norm(const pauli_sum* O, double* out) {
   if (!O || !out) return PS_ERR_INVALID;
   double n2 = 0.0;
+  if (O->W > 1) {
+    PS_TRY(wide_api::norm2(O, &n2));
+    *out = std::sqrt(n2);
+    return PS_OK;
+  }
   PS_TRY(exact_norm2(O->d, O->n, O->stream, &n2));
   *out = std::sqrt(n2);
   return PS_OK;

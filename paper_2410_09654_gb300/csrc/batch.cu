@@ -227,7 +227,7 @@ int batch_truncate(const pauli_batch* B, pauli_sum* O) {
 
 struct BTmp {
   pauli_sum s;
-  explicit BTmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0, 0, like->f32} {}
+  explicit BTmp(const pauli_sum* like) : s{like->n_sites, like->stream, nullptr, 0, 0, 0, like->f32, like->W} {}
   ~BTmp() { dev_free(s.d, s.stream); }
   BTmp(const BTmp&) = delete;
   BTmp& operator=(const BTmp&) = delete;
@@ -253,6 +253,7 @@ extern "C" {
 
 int pauli_batch_create(const pauli_sum* H, const double* hcoef, int n_inst, int tag_shift, const int64_t* caps,
                        pauli_batch** out) {
+  PS_NARROW(H);
   if (!out) return PS_ERR_INVALID;
   *out = nullptr;
   if (!H || !hcoef || n_inst < 1 || n_inst > 4096 || tag_shift < 1 || tag_shift > 63) return PS_ERR_INVALID;
@@ -302,6 +303,7 @@ int pauli_batch_destroy(pauli_batch* b) {
 }
 
 int pauli_batch_counts(const pauli_batch* b, const pauli_sum* O, int64_t* counts) {
+  PS_NARROW(O);
   if (!b || !O || !counts) return PS_ERR_INVALID;
   std::vector<unsigned long long> h;
   PS_TRY(counts_run(b, O, h));
@@ -310,6 +312,7 @@ int pauli_batch_counts(const pauli_batch* b, const pauli_sum* O, int64_t* counts
 }
 
 int pauli_batch_norms(const pauli_batch* b, const pauli_sum* O, double* norms) {
+  PS_NARROW(O);
   if (!b || !O || !norms) return PS_ERR_INVALID;
   cudaStream_t s = O->stream;
   std::vector<double> h((size_t)b->n_inst, 0.0);
@@ -340,11 +343,13 @@ int pauli_batch_rk4_steps(const pauli_batch* b, const pauli_sum* H, pauli_sum* O
 }
 
 int pauli_batch_truncate(const pauli_batch* b, pauli_sum* O) {
+  PS_NARROW(O);
   if (!b || !O) return PS_ERR_INVALID;
   return batch_truncate(b, O);
 }
 
 int pauli_batch_rk4_step(const pauli_batch* b, const pauli_sum* H, pauli_sum* O, double dt, int trim_stages) {
+  PS_NARROW(O);
   NvtxRange nvtx("pauli_batch_rk4_step");
   if (!b || !H || !O || H == O || H->n != b->nH || H->n_sites != O->n_sites || !std::isfinite(dt))
     return PS_ERR_INVALID;

@@ -81,6 +81,7 @@ struct pauli_sum {
   int64_t n;
   int cls;  // coefficient class: bit 0 = real parts may be non-zero, bit 1 = imaginary parts may be
   int f32;  // FP32 coefficients: every result written into the sum is rounded to FP32
+  int W;    // 64-bit words per mask: 1 (n_sites <= 64), 2 (<= 128) or 4 (<= 256)
 };
 
 namespace ps {
@@ -98,6 +99,16 @@ inline int cls_mul(int a, int b) {                                              
   return a == b ? kClsReal : kClsImag;
 }
 inline int cls_of(double re, double im) { return (re != 0.0 ? 1 : 0) | (im != 0.0 ? 2 : 0); }
+
+// Words per mask and bytes per record for a site count: one word up to 64 sites (the 32-byte
+// record {v, w, re, im}), else 2 or 4 words per mask (records of 16 W + 16 bytes).
+inline int words_for(int n_sites) { return n_sites <= 64 ? 1 : (n_sites <= 128 ? 2 : 4); }
+inline size_t rec_bytes(int W) { return W == 1 ? sizeof(Rec) : (size_t)(16 * W + 16); }
+// Entry points that exist only for one-word masks reject wider sums.
+#define PS_NARROW(s)                                    \
+  do {                                                  \
+    if ((s) && (s)->W > 1) return PS_ERR_INVALID;       \
+  } while (0)
 
 int sum_reserve(pauli_sum* s, int64_t cap, bool keep_contents);
 int sum_adopt(pauli_sum* s, Rec* d, int64_t cap, int64_t n);  // take ownership of a buffer
@@ -374,6 +385,23 @@ int membership(const Rec* X, int64_t nx, const Rec* T, int64_t nt, cudaStream_t 
 // FP32 sums: round every coefficient to FP32 and drop the strings that become zero (no-op
 // for FP64 sums).
 int round_f32(pauli_sum* s);
+
+// wide.cu: the path for masks of 2 or 4 words (n_sites 65..256); masks are passed as
+// row-major arrays of W words per string (word k holds sites 64k+1 .. 64k+64).
+namespace wide_api {
+int upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re, const double* im, int64_t n,
+           bool host);
+int download(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im);
+int download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im);
+int commutator(const pauli_sum* H, const pauli_sum* O, int rot, pauli_sum* out);
+int add(const pauli_sum* A, Cx alpha, const pauli_sum* B, pauli_sum* out);
+int truncate(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor);
+int rk4_step(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_policy* P, const pauli_sum* keep);
+int lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, double b_prev, const pauli_trunc_policy* P,
+                 double* b_out);
+int trace_product(const pauli_sum* A, const pauli_sum* B, double* re, double* im);
+int norm2(const pauli_sum* O, double* out);
+}  // namespace wide_api
 
 // mlp.cu: learned truncation score ln|c| - gamma_dt wt + z of every record (storage order)
 int mlp_scores(const pauli_mlp* m, const Rec* d, int64_t n, double gamma_dt, cudaStream_t s, double* score);

@@ -819,6 +819,7 @@ int pauli_mlp_set_params(pauli_mlp* m, const float* params, int64_t n) {
 }
 
 int pauli_mlp_features(const pauli_mlp* m, const pauli_sum* O, uint16_t* x) {
+  PS_NARROW(O);
   if (!m || !O || O->n_sites != m->n_sites || (O->n > 0 && !x)) return PS_ERR_INVALID;
   if (O->stream != m->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
   PS_TRY(fwd_run(m, O->d, O->n, m->stream, 0.0, x, nullptr, nullptr));
@@ -827,6 +828,7 @@ int pauli_mlp_features(const pauli_mlp* m, const pauli_sum* O, uint16_t* x) {
 }
 
 int pauli_mlp_logits(const pauli_mlp* m, const pauli_sum* O, float* z) {
+  PS_NARROW(O);
   if (!m || !O || O->n_sites != m->n_sites || (O->n > 0 && !z)) return PS_ERR_INVALID;
   if (O->stream != m->stream) PS_CUDA(cudaStreamSynchronize(O->stream));
   PS_TRY(fwd_run(m, O->d, O->n, m->stream, 0.0, nullptr, z, nullptr));
@@ -835,6 +837,7 @@ int pauli_mlp_logits(const pauli_mlp* m, const pauli_sum* O, float* z) {
 }
 
 int pauli_mlp_scores(const pauli_mlp* m, const pauli_sum* O, double gamma_dt, double* score) {
+  PS_NARROW(O);
   NvtxRange nvtx("pauli_mlp_scores");
   if (!m || !O || O->n_sites != m->n_sites || (O->n > 0 && !score) || !std::isfinite(gamma_dt))
     return PS_ERR_INVALID;
@@ -846,6 +849,7 @@ int pauli_mlp_scores(const pauli_mlp* m, const pauli_sum* O, double gamma_dt, do
 
 int pauli_mlp_gradient(pauli_mlp* m, const pauli_sum* X, const float* labels, int64_t i0, int64_t nb, float* grad,
                        double* loss) {
+  PS_NARROW(X);
   if (!m || !X || X->n_sites != m->n_sites || !grad || i0 < 0 || nb < 0 || i0 + nb > X->n || (nb > 0 && !labels))
     return PS_ERR_INVALID;
   PS_CUDA(cudaMemsetAsync(m->g, 0, kParams * sizeof(float), m->stream));
@@ -861,6 +865,7 @@ int pauli_mlp_gradient(pauli_mlp* m, const pauli_sum* X, const float* labels, in
 
 int pauli_mlp_train_step(pauli_mlp* m, const pauli_sum* X, const float* labels, int64_t i0, int64_t nb, float lr,
                          double* loss) {
+  PS_NARROW(X);
   NvtxRange nvtx("pauli_mlp_train_step");
   if (!m || !X || X->n_sites != m->n_sites || i0 < 0 || nb < 1 || i0 + nb > X->n || !labels || !(lr >= 0.0f))
     return PS_ERR_INVALID;
@@ -880,6 +885,7 @@ int pauli_mlp_train_step(pauli_mlp* m, const pauli_sum* X, const float* labels, 
 }
 
 int pauli_mlp_labels(const pauli_sum* X, const pauli_sum* target, float* labels) {
+  PS_NARROW(X);
   if (!X || !target || X->n_sites != target->n_sites || (X->n > 0 && !labels)) return PS_ERR_INVALID;
   if (target->stream != X->stream) PS_CUDA(cudaStreamSynchronize(target->stream));
   PS_TRY(membership(X->d, X->n, target->d, target->n, X->stream, labels));

@@ -137,8 +137,9 @@ int sum_reserve(pauli_sum* s, int64_t cap, bool keep_contents) {
   if (cap <= s->cap) return PS_OK;
   int64_t nc = std::max<int64_t>(cap, 64);
   Rec* d = nullptr;
-  PS_TRY(dev_alloc((void**)&d, (size_t)nc * sizeof(Rec), s->stream));
-  if (keep_contents && s->n > 0) PS_CUDA(cudaMemcpyAsync(d, s->d, (size_t)s->n * sizeof(Rec), cudaMemcpyDeviceToDevice, s->stream));
+  const size_t rb = rec_bytes(s->W);
+  PS_TRY(dev_alloc((void**)&d, (size_t)nc * rb, s->stream));
+  if (keep_contents && s->n > 0) PS_CUDA(cudaMemcpyAsync(d, s->d, (size_t)s->n * rb, cudaMemcpyDeviceToDevice, s->stream));
   dev_free(s->d, s->stream);
   s->d = d;
   s->cap = nc;
@@ -319,10 +320,10 @@ int pauli_debug_output_hash(const uint64_t* v, const uint64_t* w, int64_t n, uin
 }
 
 int pauli_sum_create(int n_sites, int64_t capacity, void* cuda_stream, pauli_sum** out) {
-  if (!out || n_sites < 1 || n_sites > 64 || capacity < 0) return PS_ERR_INVALID;
+  if (!out || n_sites < 1 || n_sites > 256 || capacity < 0) return PS_ERR_INVALID;
   *out = nullptr;
   PS_TRY(upload_hash_tables());
-  pauli_sum* s = new pauli_sum{n_sites, (cudaStream_t)cuda_stream, nullptr, 0, 0, 0};
+  pauli_sum* s = new pauli_sum{n_sites, (cudaStream_t)cuda_stream, nullptr, 0, 0, 0, 0, words_for(n_sites)};
   int st = sum_reserve(s, std::max<int64_t>(capacity, 64), false);
   if (st != PS_OK) {
     delete s;
@@ -405,6 +406,7 @@ __global__ void k_pack(Rec* __restrict__ d, const uint64_t* __restrict__ v, cons
 int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re, const double* im,
                      int64_t n) {
   if (!s || n < 0 || (n > 0 && (!v || !w || !re || !im))) return PS_ERR_INVALID;
+  if (s->W > 1) return wide_api::upload(s, v, w, re, im, n, true);
   PS_TRY(sum_reserve(s, n, false));
   s->n = 0;
   // four host->device copies into a staging area; one pass packs the records and checks the
@@ -457,6 +459,7 @@ __global__ void k_unpack(const Rec* __restrict__ d, uint64_t* __restrict__ v, ui
 int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re,
                             const double* im, int64_t n) {
   if (!s || n < 0 || (n > 0 && (!v || !w || !re || !im))) return PS_ERR_INVALID;
+  if (s->W > 1) return wide_api::upload(s, v, w, re, im, n, false);
   PS_TRY(sum_reserve(s, n, false));
   s->n = 0;
   Buf<int> flags;
@@ -485,6 +488,7 @@ int pauli_sum_download(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re,
   if (cap < s->n) return PS_ERR_CAPACITY;
   if (s->n == 0) return PS_OK;
   if (!v || !w || !re || !im) return PS_ERR_INVALID;
+  if (s->W > 1) return wide_api::download(s, v, w, re, im);
   std::vector<Rec> h((size_t)s->n);
   PS_CUDA(cudaMemcpyAsync(h.data(), s->d, (size_t)s->n * sizeof(Rec), cudaMemcpyDeviceToHost, s->stream));
   PS_CUDA(cudaStreamSynchronize(s->stream));
@@ -505,6 +509,7 @@ int pauli_sum_download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, doub
   if (cap < s->n) return PS_ERR_CAPACITY;
   if (s->n == 0) return PS_OK;
   if (!v || !w || !re || !im) return PS_ERR_INVALID;
+  if (s->W > 1) return wide_api::download_device(s, v, w, re, im);
   int blocks = (int)std::min<int64_t>(ceil_div(s->n, 256), 8 * num_sms());
   PS_LAUNCH("k_unpack", s->stream, k_unpack<<<blocks, 256, 0, s->stream>>>(s->d, v, w, re, im, s->n));
   PS_CUDA(cudaGetLastError());
@@ -517,7 +522,7 @@ int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst) {
   PS_TRY(sum_reserve(dst, src->n, false));
   if (src->n > 0) {
     if (src->stream != dst->stream) PS_CUDA(cudaStreamSynchronize(src->stream));
-    PS_CUDA(cudaMemcpyAsync(dst->d, src->d, (size_t)src->n * sizeof(Rec), cudaMemcpyDeviceToDevice, dst->stream));
+    PS_CUDA(cudaMemcpyAsync(dst->d, src->d, (size_t)src->n * rec_bytes(src->W), cudaMemcpyDeviceToDevice, dst->stream));
   }
   dst->n = src->n;
   dst->cls = src->cls;
@@ -526,6 +531,7 @@ int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst) {
 
 int pauli_sum_set_precision(pauli_sum* s, int coef_dtype) {
   if (!s || (coef_dtype != PS_COEF_F64 && coef_dtype != PS_COEF_F32)) return PS_ERR_INVALID;
+  if (s->W > 1 && coef_dtype != PS_COEF_F64) return PS_ERR_INVALID;
   s->f32 = coef_dtype == PS_COEF_F32;
   return round_f32(s);
 }
@@ -567,6 +573,7 @@ bool get(std::FILE* f, Fnv& fnv, void* p, size_t n) {
 
 int pauli_sum_save(const pauli_sum* s, const char* path, const double* meta, int64_t n_meta) {
   if (!s || !path || n_meta < 0 || n_meta > (1 << 20) || (n_meta > 0 && !meta)) return PS_ERR_INVALID;
+  PS_NARROW(s);
   const int64_t n = s->n;
   std::vector<uint64_t> v((size_t)n), w((size_t)n);
   std::vector<double> re((size_t)n), im((size_t)n);
@@ -591,6 +598,7 @@ int pauli_sum_save(const pauli_sum* s, const char* path, const double* meta, int
 
 int pauli_sum_load(pauli_sum* s, const char* path, double* meta, int64_t meta_cap, int64_t* n_meta) {
   if (!s || !path || meta_cap < 0 || (meta_cap > 0 && !meta)) return PS_ERR_INVALID;
+  PS_NARROW(s);
   std::FILE* f = std::fopen(path, "rb");
   if (!f) return PS_ERR_IO;
   Fnv fnv;
@@ -638,6 +646,7 @@ int pauli_sum_load(pauli_sum* s, const char* path, double* meta, int64_t meta_ca
 
 int pauli_sum_sort_by_hash(pauli_sum* s) {
   if (!s) return PS_ERR_INVALID;
+  PS_NARROW(s);
   const int64_t n = s->n;
   if (n <= 1) return PS_OK;
   cudaStream_t st = s->stream;

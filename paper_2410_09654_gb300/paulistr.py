@@ -183,13 +183,20 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def words_for(n_sites: int) -> int:
+    """64-bit words per mask: 1 up to 64 sites, 2 up to 128, 4 up to 256."""
+    return 1 if n_sites <= 64 else (2 if n_sites <= 128 else 4)
+
+
 class PauliSum:
-    """A device-resident Pauli sum (owns one ``pauli_sum*``)."""
+    """A device-resident Pauli sum (owns one ``pauli_sum*``).  Above 64 sites the masks v, w
+    are (n, W) uint64 arrays (word k holds sites 64k+1 .. 64k+64), W = words_for(n_sites)."""
 
     def __init__(self, n_sites: int, capacity: int = 0, stream=None):
         lib = load()
         self._lib = lib
         self.n_sites = int(n_sites)
+        self.W = words_for(self.n_sites)
         self.stream = _current_stream() if stream is None else ctypes.c_void_p(stream)
         h = ctypes.c_void_p()
         _check(lib.pauli_sum_create(self.n_sites, int(capacity), self.stream, ctypes.byref(h)), "pauli_sum_create")
@@ -204,22 +211,26 @@ class PauliSum:
     # ------------------------------------------------------------ data movement
     @classmethod
     def from_arrays(cls, n_sites: int, v, w, re, im, stream=None) -> "PauliSum":
-        s = cls(n_sites, len(v), stream)
+        s = cls(n_sites, len(re), stream)
         s.upload(v, w, re, im)
         return s
 
     def upload(self, v, w, re, im):
         """Host upload (numpy arrays); order kept."""
-        v, w, re, im = _u64(v), _u64(w), _f64(re), _f64(im)
-        n = len(v)
+        re, im = _f64(re), _f64(im)
+        n = len(re)
+        v = _u64(v).reshape(-1)
+        w = _u64(w).reshape(-1)
+        if len(v) != n * self.W or len(w) != n * self.W:
+            raise ValueError(f"masks must hold {self.W} word(s) per string")
         U64P = ctypes.POINTER(ctypes.c_uint64)
         F64P = ctypes.POINTER(ctypes.c_double)
         _check(self._lib.pauli_sum_upload(self.handle, v.ctypes.data_as(U64P), w.ctypes.data_as(U64P),
                                           re.ctypes.data_as(F64P), im.ctypes.data_as(F64P), n), "pauli_sum_upload")
 
     def upload_device(self, v, w, re, im):
-        """Device upload from torch CUDA tensors (uint64/int64, float64)."""
-        n = int(v.numel())
+        """Device upload from torch CUDA tensors (uint64/int64 masks of W words per string, float64)."""
+        n = int(re.numel())
         _check(self._lib.pauli_sum_upload_device(self.handle, ctypes.c_void_p(v.data_ptr()),
                                                  ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(re.data_ptr()),
                                                  ctypes.c_void_p(im.data_ptr()), n), "pauli_sum_upload_device")
@@ -232,8 +243,8 @@ class PauliSum:
     def download(self):
         """(v, w, re, im) numpy arrays in canonical order (v, then w ascending)."""
         n = len(self)
-        v = np.empty(n, np.uint64)
-        w = np.empty(n, np.uint64)
+        v = np.empty(n * self.W, np.uint64)
+        w = np.empty(n * self.W, np.uint64)
         re = np.empty(n, np.float64)
         im = np.empty(n, np.float64)
         got = ctypes.c_int64()
@@ -242,10 +253,16 @@ class PauliSum:
         _check(self._lib.pauli_sum_download(self.handle, v.ctypes.data_as(U64P), w.ctypes.data_as(U64P),
                                             re.ctypes.data_as(F64P), im.ctypes.data_as(F64P), n,
                                             ctypes.byref(got)), "pauli_sum_download")
+        if self.W > 1:
+            return v.reshape(n, self.W), w.reshape(n, self.W), re, im
         return v, w, re, im
 
     def to_dict(self) -> dict:
+        """{(v, w): c} with the masks as Python integers (any width)."""
         v, w, re, im = self.download()
+        if self.W > 1:
+            join = lambda row: sum(int(x) << (64 * k) for k, x in enumerate(row))  # noqa: E731
+            return {(join(a), join(b)): complex(c, d) for a, b, c, d in zip(v, w, re, im)}
         return {(int(a), int(b)): complex(c, d) for a, b, c, d in zip(v, w, re, im)}
 
     def set_precision(self, coef_dtype: int) -> "PauliSum":
@@ -690,10 +707,13 @@ def pauli_sum_download_device(S: PauliSum):
     """(v, w, re, im) CUDA tensors (int64 bit patterns of the masks, float64) in storage order."""
     import torch
     m = len(S)
-    t = [torch.empty(m, dtype=dt, device="cuda") for dt in (torch.int64, torch.int64, torch.float64, torch.float64)]
+    t = [torch.empty(m * S.W, dtype=torch.int64, device="cuda"), torch.empty(m * S.W, dtype=torch.int64, device="cuda"),
+         torch.empty(m, dtype=torch.float64, device="cuda"), torch.empty(m, dtype=torch.float64, device="cuda")]
     got = ctypes.c_int64()
     _check(load().pauli_sum_download_device(S.handle, *[ctypes.c_void_p(x.data_ptr()) for x in t], m,
                                             ctypes.byref(got)), "pauli_sum_download_device")
+    if S.W > 1:
+        t[0], t[1] = t[0].view(m, S.W), t[1].view(m, S.W)
     return tuple(t)
 
 
