@@ -17,6 +17,7 @@
 //      then the sources in order).  That is exactly the order in which Alg. 1 with H
 //      in the outer loop adds them, so the result is independent of scheduling.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -362,6 +363,7 @@ __global__ void k_anti_table(const Rec* __restrict__ H, int nH, int stride, uint
   }
 }
 
+bool g_emit_blk = getenv("PS_EMIT_WARP") == nullptr;  // block-level emission (A/B switch while both exist)
 constexpr int kRing = 64;  // per-warp ring of queued (lane, h) codes
 constexpr int kRingMask = kRing - 1;
 
@@ -502,6 +504,166 @@ __global__ void __launch_bounds__(kEmitThreads, 5) k_emit_tab(const Rec* __restr
   if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
 }
 
+// Block-level table emission.  A block takes 256 neighbouring x (hash order), one per
+// thread, and forms their anticommutation bitmaps from the nibble table.  Then, for each
+// 32-term word of the bitmaps: one ballot per term and warp gives, per (warp, term), the lanes
+// that anticommute with it; a scan over the 32 terms and the 8 warps gives every (term, x) pair
+// its position in a block-local list ordered by term, then by x; the threads then build the
+// list's entries independently (consecutive threads: one term over neighbouring x, so a
+// warp's entries fall in few bins and reserve them with one atomic per distinct bin) and write
+// them.  No per-term serial chain: every step is a block-parallel pass.
+constexpr int kBlkX = kEmitThreads;              // x per block chunk
+constexpr int kBlkCodes = kBlkX * 32;            // (x, term) pairs of one bitmap word at most
+
+template <bool FULL, int NW>
+__global__ void __launch_bounds__(kEmitThreads, 4) k_emit_blk(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
+                                                  int64_t nX, const Rec* __restrict__ H,
+                                                  const uint32_t* __restrict__ fH,
+                                                  const HScal* __restrict__ hscal, int nh,
+                                                  const uint32_t* __restrict__ T, EmitScalars es,
+                                                  unsigned long long* __restrict__ cur,
+                                                  uint64_t* __restrict__ entries, Contrib* __restrict__ fout,
+                                                  unsigned long long* __restrict__ total,
+                                                  const double* __restrict__ hb, int hb_shift) {
+  constexpr int S = tab_stride(NW);
+  constexpr int kTabWords = kTabPos * kTabVals * S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  ulonglong2* s_hk = reinterpret_cast<ulonglong2*>(s_tab + kTabWords);
+  HScal* s_hs = reinterpret_cast<HScal*>(s_hk + nh);                     // FULL only
+  uint32_t* s_hf = reinterpret_cast<uint32_t*>(s_hs + (FULL ? nh : 0));
+  __shared__ ulonglong2 s_xk[kBlkX];
+  __shared__ double s_xs[FULL ? kBlkX : 1];
+  __shared__ uint32_t s_xf[kBlkX];
+  __shared__ uint32_t s_bal[kEmitThreads / 32][32];   // lanes of warp w anticommuting with term b
+  __shared__ uint32_t s_off[kEmitThreads / 32][32];   // list position of (warp w, term b)'s first pair
+  __shared__ uint16_t s_code[kBlkCodes];              // (x << 5 | b) in term-then-x order
+  __shared__ uint32_t s_n;
+  for (int i = threadIdx.x; i < kTabWords; i += blockDim.x) s_tab[i] = T[i];
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+    s_hk[i] = make_ulonglong2(H[i].v, H[i].w);
+    if constexpr (FULL) s_hs[i] = hscal[i];
+    s_hf[i] = fH[i];
+  }
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long emitted = 0;  // thread 0's count
+  const int64_t chunks = ceil_div_dev(nX, kBlkX);
+  for (int64_t chunk = blockIdx.x; chunk < chunks; chunk += gridDim.x) {
+    __syncthreads();  // the previous chunk's x cache and lists are done
+    const int64_t i = chunk * kBlkX + tid;
+    const bool valid = i < nX;
+    ulonglong2 xk = make_ulonglong2(0, 0);
+    if (valid) {
+      xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
+      if constexpr (FULL) s_xs[tid] = es.uX ? X[i].im : X[i].re;
+      s_xf[tid] = fX[i];
+    }
+    s_xk[tid] = xk;
+    uint32_t A[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) A[k] = 0u;
+    if (valid) {
+#pragma unroll
+      for (int p = 0; p < kTabPos; ++p) {
+        const uint64_t m = p < 16 ? xk.x : xk.y;
+        const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
+        const uint32_t* row = s_tab + (p * kTabVals + nib) * S;
+#pragma unroll
+        for (int k = 0; k < NW; k += 2) {
+          const uint2 t = *reinterpret_cast<const uint2*>(row + k);
+          A[k] ^= t.x;
+          A[k + 1] ^= t.y;
+        }
+      }
+    }
+#pragma unroll 1
+    for (int k = 0; k < NW; ++k) {
+      if (32 * k >= nh) break;  // block-uniform
+      uint32_t a = 0;
+#pragma unroll
+      for (int q = 0; q < NW; ++q)
+        if (q == k) a = A[q];
+      // ballots: lane b keeps the mask of term 32k + b
+      uint32_t mine = 0;
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (a >> b) & 1u);
+        if (lane == b) mine = m;
+      }
+      s_bal[warp][lane] = mine;
+      __syncthreads();
+      if (warp == 0) {  // per term b (lane): offsets over the warps, then a scan over the terms
+        uint32_t run = 0, c[kEmitThreads / 32];
+#pragma unroll
+        for (int w = 0; w < kEmitThreads / 32; ++w) {
+          c[w] = run;
+          run += __popc(s_bal[w][lane]);
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        const uint32_t base = incl - run;
+#pragma unroll
+        for (int w = 0; w < kEmitThreads / 32; ++w) s_off[w][lane] = base + c[w];
+        if (lane == 31) s_n = incl;
+      }
+      __syncthreads();
+      // every set bit of this thread's word: its pair's list position
+      const uint32_t lt = (1u << lane) - 1u;
+      for (uint32_t bits = a; bits; bits &= bits - 1u) {
+        const int b = __ffs(bits) - 1;
+        const uint32_t pos = s_off[warp][b] + __popc(s_bal[warp][b] & lt);
+        s_code[pos] = (uint16_t)((tid << 5) | b);
+      }
+      __syncthreads();
+      const uint32_t n = s_n;
+      if (tid == 0) emitted += n;
+      for (uint32_t e0 = 0; e0 < n; e0 += kEmitThreads) {
+        const uint32_t e = e0 + tid;
+        const bool act = e < n;
+        uint32_t xl = 0, h = 0;
+        if (act) {
+          const uint32_t c = s_code[e];
+          xl = c >> 5;
+          h = 32u * (uint32_t)k + (c & 31u);
+        }
+        Contrib r;
+        uint32_t p = 0;
+        if (act) {
+          const ulonglong2 x = s_xk[xl];
+          p = s_xf[xl] ^ s_hf[h];
+          if constexpr (FULL) {
+            const ulonglong2 hk = s_hk[h];
+            const HScal hs = s_hs[h];
+            const int ph = (product_phase(hk.x, hk.y, x.x, x.y) + es.rot + es.uH + es.uX) & 3;
+            r.v = hk.x ^ x.x;
+            r.w = hk.y ^ x.y;
+            double hsv = hs.s;
+            int hse = hs.e;
+            if (hb) {  // batched instances: the H coefficients of x's instance (tag = v >> hb_shift)
+              hsv = hb[(size_t)(x.x >> hb_shift) * (size_t)nh + h];
+              hse = kNoPow2;
+            }
+            r.val = neg_if(scaled(hsv, hse, s_xs[xl], 1), (ph & 2) != 0);
+            r.code = h;
+            r.pad = 0;
+          }
+        }
+        const uint64_t at = reserve_slot(cur, p, act, lane);
+        if (act) {
+          if constexpr (FULL) fout[at] = r;
+          else entries[at] = ((uint64_t)(chunk * kBlkX + xl) << 16) | (uint64_t)h;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0 && emitted) atomicAdd(total, emitted);
+}
+
 template <bool FULL, int NW>
 int launch_emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, const uint32_t* fH,
                     const HScal* hscal, int nh, const uint32_t* T, const EmitScalars& es,
@@ -510,6 +672,17 @@ int launch_emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, 
   Buf<unsigned long long> next_tile;
   PS_TRY(next_tile.alloc(1, s));
   PS_CUDA(cudaMemsetAsync(next_tile.p, 0, sizeof(unsigned long long), s));
+  if (g_emit_blk) {
+    const size_t sm = (size_t)kTabPos * kTabVals * tab_stride(NW) * sizeof(uint32_t) +
+                      (size_t)nh * (sizeof(ulonglong2) + (FULL ? sizeof(HScal) : 0) + sizeof(uint32_t));
+    PS_CUDA(cudaFuncSetAttribute(k_emit_blk<FULL, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit_blk<FULL, NW>, kEmitThreads, sm));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * nsm, ceil_div(nX, kBlkX)));
+    PS_LAUNCH("k_emit_products", s, k_emit_blk<FULL, NW><<<grid, kEmitThreads, sm, s>>>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, hb, hb_shift));
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+  }
   const size_t sm = (size_t)kTabPos * kTabVals * tab_stride(NW) * sizeof(uint32_t) +
                     (size_t)(kEmitThreads / 32) * kRing * sizeof(uint32_t) + (size_t)nh * (sizeof(ulonglong2) + (FULL ? sizeof(HScal) : 0) + sizeof(uint32_t));
   PS_CUDA(cudaFuncSetAttribute(k_emit_tab<FULL, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
