@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-truncation comparison")
     p.add_argument("--no-autotune", action="store_true", help="keep the default merge geometry")
+    p.add_argument("--lanczos-only", action="store_true",
+                   help="only the Lanczos headline (profiling runs): no RK4, lattice or pattern lines")
     p.add_argument("--merge-geometry", default=None,
                    help="BIN_TARGET,QUOTA: fix the merge geometry instead of tuning it (profiling runs)")
     return p.parse_args()
@@ -253,6 +255,7 @@ def main():
     products = 0
     merged = 0
     contributions = 0
+    groups = split_groups = 0
     bs = []
     barrier()
     clocks.start()
@@ -266,6 +269,8 @@ def main():
         st = ps.pauli_last_merge_stats()
         merged += st["merged"]
         contributions += st["contributions"]
+        groups += st["groups"]
+        split_groups += st["split_groups"]
         bs.append(b)
     ev1.record(stream)
     barrier()
@@ -371,6 +376,18 @@ def main():
                "states": f"the first {len(host)} input states of the timed loop, uploaded from pinned host arrays",
                "api": "pauli_sum_upload x2 (pinned host arrays) + pauli_sum_sort_by_hash x2 + pauli_lanczos_step (b_n to host)"}
 
+    if args.lanczos_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "Pauli products/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                              "profile_only": True, "kernels_per_step_ms": {k: round(v[1], 4) for k, v in per_step.items()},
+                              "merge_groups_per_step": groups / args.steps,
+                              "merge_split_groups_per_step": split_groups / args.steps,
+                              "roofline": roof}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     # ---------------------------------------------------------------- RK4 steps/s (N=10 chain)
     n10 = 10
     Hr = ps.PauliSum.from_arrays(n10, *I.tilted_ising_chain(n10).arrays())
@@ -459,6 +476,7 @@ def main():
             "merged_strings_per_s": merged_rate,
             "contributions_per_s": contrib_rate,
             "contributions_per_step": contributions / args.steps,
+            "merge_groups_per_step": groups / args.steps, "merge_split_groups_per_step": split_groups / args.steps,
             "timed_steps_n": [start_step, start_step + args.steps - 1],
             "b_n_timed": bs,
             "rk4": rk4,

@@ -188,7 +188,7 @@ struct __align__(16) Contrib {
 struct __align__(16) HScal {
   double s;
   int e;
-  int pad;
+  int pvw;  // popcount(v & w) of the H term (its share of the product phase)
 };
 
 // Scalars of the single-component arithmetic (see build_scalar).
@@ -212,7 +212,7 @@ __global__ void k_h_prep(const Rec* __restrict__ H, int nh, int bits, int uH, ui
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int E = (int)((b >> 52) & 0x7FF);
     const bool p2 = (b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046;
-    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, 0};
+    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, __popcll(h.v & h.w)};
   }
 }
 
@@ -253,6 +253,23 @@ __device__ __forceinline__ uint64_t reserve_slot(unsigned long long* __restrict_
   if (act && lane == leader) b = atomicAdd(&cur[p], (unsigned long long)__popc(mm));
   b = __shfl_sync(0xffffffffu, b, leader);
   return b + (uint32_t)__popc(mm & ((1u << lane) - 1u));
+}
+
+// Reservation for a warp whose active lanes are a prefix and whose equal bins tend to sit in
+// adjacent lanes: one atomic per run of equal bins (a bin split over several runs takes one
+// per run), no match over the warp.
+__device__ __forceinline__ uint64_t reserve_run(unsigned long long* __restrict__ cur, uint32_t p, bool act, int lane) {
+  const uint32_t pp = __shfl_up_sync(0xffffffffu, p, 1);
+  const unsigned active = __ballot_sync(0xffffffffu, act);
+  const unsigned starts = __ballot_sync(0xffffffffu, act && (lane == 0 || pp != p));
+  const unsigned le = 0xffffffffu >> (31 - lane);  // lanes 0..lane
+  const int leader = 31 - __clz(starts & le);
+  const unsigned above = starts & ~le;
+  const int next = above ? __ffs(above) - 1 : __popc(active);
+  unsigned long long b = 0;
+  if (act && lane == leader) b = atomicAdd(&cur[p], (unsigned long long)(next - lane));
+  b = __shfl_sync(0xffffffffu, b, leader & 31);
+  return b + (uint64_t)(lane - leader);
 }
 
 // Emission of the products for |H| > 256 and of operator products (ALL: every pair, not only
@@ -535,6 +552,7 @@ __global__ void __launch_bounds__(kEmitThreads, 4) k_emit_blk(const Rec* __restr
   __shared__ ulonglong2 s_xk[kBlkX];
   __shared__ double s_xs[FULL ? kBlkX : 1];
   __shared__ uint32_t s_xf[kBlkX];
+  __shared__ int s_xp[FULL ? kBlkX : 1];  // popcount(v & w) of x
   __shared__ uint32_t s_bal[kEmitThreads / 32][32];   // lanes of warp w anticommuting with term b
   __shared__ uint32_t s_off[kEmitThreads / 32][32];   // list position of (warp w, term b)'s first pair
   __shared__ uint16_t s_code[kBlkCodes];              // (x << 5 | b) in term-then-x order
@@ -555,7 +573,10 @@ __global__ void __launch_bounds__(kEmitThreads, 4) k_emit_blk(const Rec* __restr
     ulonglong2 xk = make_ulonglong2(0, 0);
     if (valid) {
       xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
-      if constexpr (FULL) s_xs[tid] = es.uX ? X[i].im : X[i].re;
+      if constexpr (FULL) {
+        s_xs[tid] = es.uX ? X[i].im : X[i].re;
+        s_xp[tid] = __popcll(xk.x & xk.y) - es.rot - es.uH - es.uX;  // constant part of the phase
+      }
       s_xf[tid] = fX[i];
     }
     s_xk[tid] = xk;
@@ -638,9 +659,10 @@ __global__ void __launch_bounds__(kEmitThreads, 4) k_emit_blk(const Rec* __restr
           if constexpr (FULL) {
             const ulonglong2 hk = s_hk[h];
             const HScal hs = s_hs[h];
-            const int ph = (product_phase(hk.x, hk.y, x.x, x.y) + es.rot + es.uH + es.uX) & 3;
             r.v = hk.x ^ x.x;
             r.w = hk.y ^ x.y;
+            // product phase k = pop(vc & wc) - pop(vh & wh) - pop(vx & wx) + 2 pop(wh & vx)
+            const int ph = (__popcll(r.v & r.w) - hs.pvw - s_xp[xl] + 2 * __popcll(hk.y & x.x)) & 3;
             double hsv = hs.s;
             int hse = hs.e;
             if (hb) {  // batched instances: the H coefficients of x's instance (tag = v >> hb_shift)
@@ -652,7 +674,7 @@ __global__ void __launch_bounds__(kEmitThreads, 4) k_emit_blk(const Rec* __restr
             r.pad = 0;
           }
         }
-        const uint64_t at = reserve_slot(cur, p, act, lane);
+        const uint64_t at = reserve_run(cur, p, act, lane);
         if (act) {
           if constexpr (FULL) fout[at] = r;
           else entries[at] = ((uint64_t)(chunk * kBlkX + xl) << 16) | (uint64_t)h;
@@ -1376,14 +1398,43 @@ struct RankGeom {
   static constexpr int kEnt = W <= 8 ? kCap : kCap / 2;
 };
 
+// Next-group prefetch (ranked merge with at most six mask words, where shared memory has room):
+// while a group is merged, its successor's header and bin table are copied into shared memory
+// with cp.async and its entries are prefetched into L2 with bulk prefetches, so the next setup
+// and load phase do not wait on DRAM.
+template <int W>
+struct PfGeom {
+  static constexpr int kBins = W <= 6 ? 256 : 1;  // bins of a prefetchable group
+  static constexpr bool kOn = W <= 6;
+};
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2_bulk(const void* gsrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
+
 template <bool S, int W>
 struct RankSmem {
   using G = RankGeom<W>;
+  GroupHead pfh;                              // header of the prefetched next group
+  uint64_t pfbase[PfGeom<W>::kBins];          // its bin starts
+  uint64_t pfcpre[PfGeom<W>::kBins + 1];      // its bins' entry prefix
+  uint32_t pf_g;                              // the group whose header and bins are in pf*, or kNone
   ulonglong2 key[G::kTab];
   uint32_t mask[G::kTab][G::kWords];  // order codes present per slot
   uint16_t pre[G::kTab];
   uint16_t ulist[G::kTab];
   uint16_t run[G::kTab];        // start of the slot's run in seg[]
+  uint16_t rlen[G::kTab];       // length of the slot's run (popcount of its mask)
   double ere[G::kEnt];
   double eim[S ? 1 : G::kEnt];
   uint16_t ebit[G::kEnt];         // order bit of the entry (kNone16: pre operand)
@@ -1449,7 +1500,9 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
     s.n_u = s.n_e = s.n_out = s.n_seg = 0;
     s.flags = 0;
     s.cur_sent = a.sent_lo;
+    s.pf_g = kNone;
   }
+  constexpr bool PF = PfGeom<W>::kOn;
   // Groups are claimed from a shared counter.  The next group is claimed while the current
   // one's setup runs, by the last warp's lane 0 (no bin-table work: a group has fewer bins
   // than the first 480 threads), so the claim's round trip overlaps the header and table
@@ -1462,7 +1515,8 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
     __syncthreads();  // g read by all before the next claim overwrites it
     if (g >= ngroups) break;
     if (tid == kClaimTid) s.h_g = atomicAdd(a.next_group, 1u);
-    const GroupHead gh = a.heads[g];
+    const bool pf_hit = PF && s.pf_g == g;  // header and bins already in shared memory
+    const GroupHead gh = pf_hit ? s.pfh : a.heads[g];
     const uint32_t lo = gh.lo, hi = gh.hi;
     const uint64_t e0 = gh.e0;
     const uint64_t E = gh.E;
@@ -1478,8 +1532,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       __syncthreads();
       if (tid == 0) s.cur_sent = sent;
     }
-    for (uint32_t i = tid; i <= nb; i += kMergeThreads) s.gpre[i] = (uint32_t)(a.cpre[lo + i] - e0);
-    for (uint32_t i = tid; i < nb; i += kMergeThreads) s.gbase[i] = a.base[lo + i];
+    if (pf_hit) {
+      for (uint32_t i = tid; i <= nb; i += kMergeThreads) s.gpre[i] = (uint32_t)(s.pfcpre[i] - e0);
+      for (uint32_t i = tid; i < nb; i += kMergeThreads) s.gbase[i] = s.pfbase[i];
+    } else {
+      for (uint32_t i = tid; i <= nb; i += kMergeThreads) s.gpre[i] = (uint32_t)(a.cpre[lo + i] - e0);
+      for (uint32_t i = tid; i < nb; i += kMergeThreads) s.gbase[i] = a.base[lo + i];
+    }
     __syncthreads();
 
     int level0 = 0;
@@ -1489,6 +1548,16 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       continue;
     }
     if (level0 > 0 && tid == 0) atomicAdd(a.split_groups, 1u);
+    // the next group (claimed during this setup): its header now, its bins after phase 2, its
+    // entries into L2 after phase 3
+    const uint32_t gn = s.h_g;
+    bool pf_first = PF && gn < ngroups;  // block-uniform; cleared after the group's first pass
+    if (pf_first && tid == 0) {
+      s.pf_g = kNone;
+      cp_async16(&s.pfh, &a.heads[gn]);
+      cp_async16(reinterpret_cast<char*>(&s.pfh) + 16, reinterpret_cast<const char*>(&a.heads[gn]) + 16);
+      cp_async_commit();
+    }
 
     for (uint32_t sub0 = 0; sub0 < (1u << level0); ++sub0) {
      int stk_level[2 * kHashRows + 2];
@@ -1598,7 +1667,9 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         }
       }
       __syncthreads();
+      if (pf_first && tid == 0) cp_async_wait_all();  // the next header (visible after the next barrier)
       if (s.flags) {
+        pf_first = false;
         rank_release(s, sent);
         if (level >= 16 || a.bits + level + 1 > kHashRows || sp + 2 > 2 * kHashRows + 2) {
           if (tid == 0) atomicOr(a.err, 2);
@@ -1634,10 +1705,20 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         wb = __shfl_sync(0xffffffffu, wb, 31);
         if (u < n_u) {
           s.run[slot] = (uint16_t)(wb + incl - c);
+          s.rlen[slot] = (uint16_t)c;
           atomicAdd(&s_hist[G::kBits - c], 1u);  // longest runs first
         }
       }
       __syncthreads();
+      if (pf_first) {  // the next group's bin table into shared memory
+        const GroupHead nh = s.pfh;
+        const uint32_t nb2 = nh.hi - nh.lo;
+        if (nh.E != 0 && nb2 <= (uint32_t)PfGeom<W>::kBins && (uint32_t)tid <= nb2) {
+          cp_async8(&s.pfcpre[tid], &a.cpre[nh.lo + tid]);
+          if ((uint32_t)tid < nb2) cp_async8(&s.pfbase[tid], &a.base[nh.lo + tid]);
+        }
+        cp_async_commit();
+      }
       if (tid < 32) {  // exclusive scan of the run-length counters, 9 per lane, before phase 3
         constexpr int kPer = (G::kBits + 1 + 31) / 32;
         uint32_t v[kPer], t = 0;
@@ -1675,6 +1756,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         s.seg[pos] = s.ere[e];
         if constexpr (!S) s.segim[pos] = s.eim[e];
       }
+      if (pf_first) cp_async_wait_all();  // this thread's bin-table copies (visible after the barrier)
       __syncthreads();
       // ---- phase 3b: strings ordered by run length, longest first, so that the lanes of a
       // warp add runs of nearly equal length in phase 4 (the adds of a warp cost as much as
@@ -1683,12 +1765,24 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       uint16_t* s_order = s.eslot;
       for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
         const uint32_t slot = s.ulist[u];
-        uint32_t n = 0;
-#pragma unroll
-        for (int w = 0; w < G::kWords; ++w) n += __popc(s.mask[slot][w]);
+        const uint32_t n = s.rlen[slot];
         s_order[atomicAdd(&s_hist[G::kBits - n], 1u)] = (uint16_t)slot;
       }
       __syncthreads();
+      if (pf_first) {  // the next group's entries into L2; its header and bins are ready
+        const GroupHead nh = s.pfh;
+        const uint32_t nb2 = nh.hi - nh.lo;
+        if (nh.E != 0 && nb2 <= (uint32_t)PfGeom<W>::kBins) {
+          if constexpr (FULL) {
+            if ((uint32_t)tid < nb2) {
+              const uint64_t cnt = s.pfcpre[tid + 1] - s.pfcpre[tid];
+              if (cnt) prefetch_l2_bulk(a.fent + s.pfbase[tid], (uint32_t)(cnt * sizeof(Contrib)));
+            }
+          }
+          if (tid == 0) s.pf_g = gn;
+        }
+        pf_first = false;
+      }
       // ---- phase 4: per string, add its run in order, apply the combination, stage.  The
       // fold uses plain IEEE adds: they differ from skipping zero terms only in the sign of
       // a zero sum, and strings whose value is zero are dropped.
@@ -1699,9 +1793,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         uint32_t slot = 0;
         if (u < n_u) {
           slot = s_order[u];
-          uint32_t n = 0;
-#pragma unroll
-          for (int w = 0; w < G::kWords; ++w) n += __popc(s.mask[slot][w]);
+          const uint32_t n = s.rlen[slot];
           const uint32_t b0 = s.run[slot];
           Cx acc{0.0, 0.0};
           if (n > 0) {
@@ -2077,7 +2169,11 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   size_t sm;
   void (*kern)(MergeArgs);
   const char* kname;
-  if (ranked) {
+  if (ranked && full && ncode_h + sp.nsrc <= 192) {  // six mask words suffice
+    sm = sizeof(RankSmem<true, 6>);
+    kern = k_merge_rank<true, true, 6>;
+    kname = "k_merge_rank_f";
+  } else if (ranked) {
     sm = structured ? sizeof(RankSmem<true, 8>) : sizeof(RankSmem<false, 8>);
     kern = full ? k_merge_rank<true, true, 8> : (structured ? k_merge_rank<true, false, 8> : k_merge_rank<false, false, 8>);
     kname = full ? "k_merge_rank_f" : (structured ? "k_merge_rank_s" : "k_merge_rank");
