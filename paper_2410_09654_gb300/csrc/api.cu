@@ -9,11 +9,8 @@ using namespace ps;
 
 namespace {
 
-// The merge, then (FP32 sums) the single rounding of every output coefficient to FP32.
-int merge_into(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
-  PS_TRY(merge_run(sp, s, out));
-  return round_f32(out);
-}
+// The merge (into an FP32 sum it rounds every output coefficient once to FP32 itself).
+int merge_into(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) { return merge_run(sp, s, out); }
 
 bool same_sites(const pauli_sum* a, const pauli_sum* b) { return !a || !b || a->n_sites == b->n_sites; }
 

@@ -233,10 +233,7 @@ struct BTmp {
   BTmp& operator=(const BTmp&) = delete;
 };
 
-int merge_r(const MergeSpec& sp, pauli_sum* out) {
-  PS_TRY(merge_run(sp, out->stream, out));
-  return round_f32(out);
-}
+int merge_r(const MergeSpec& sp, pauli_sum* out) { return merge_run(sp, out->stream, out); }
 
 MergeSource src_of(const pauli_sum* p, double a) {
   MergeSource m{p->d, p->n, Cx{a, 0.0}};

@@ -852,6 +852,7 @@ struct MergeArgs {
   unsigned long long* out_n;
   unsigned long long out_cap;
   int* err;               // bit 0: capacity, bit 1: unresolved table overflow
+  int round32;            // FP32 output sum: every result rounded once to FP32 before the zero test
   unsigned* split_groups;
   ulonglong2 sent_lo, sent_hi;  // empty-slot keys for groups in the lower / upper half
   // structured (single-component) mode: every coefficient is s * i^u with s real
@@ -900,7 +901,11 @@ struct MergeSmem {
 template <int TAB = kTable, class SM>
 __device__ __forceinline__ int table_insert(SM& s, ulonglong2 c, ulonglong2 sent, bool& fresh) {
   fresh = false;
-  uint32_t slot = table_hash(c.x, c.y) & (TAB - 1);
+  // double hashing: an odd step from the hash's high bits (every slot is reachable), so
+  // that neighbouring home slots do not build the long clusters of linear probing
+  const uint32_t h = table_hash(c.x, c.y);
+  uint32_t slot = h & (TAB - 1);
+  const uint32_t step = (h >> 20) | 1u;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
     ulonglong2 k = s.key[slot];
     if (k.x == c.x && k.y == c.y) return (int)slot;
@@ -912,7 +917,7 @@ __device__ __forceinline__ int table_insert(SM& s, ulonglong2 c, ulonglong2 sent
       }
       if (old.x == c.x && old.y == c.y) return (int)slot;
     }
-    slot = (slot + 1) & (TAB - 1);
+    slot = (slot + step) & (TAB - 1);
   }
   return -1;
 }
@@ -957,6 +962,15 @@ __device__ __forceinline__ void build_scalar(const MergeArgs& a, uint32_t code, 
     key = make_ulonglong2(y.v, y.w);
     double sy = a.src_uy[si] ? y.im : y.re;
     t = neg_if(scaled(a.src_s[si], a.src_e[si], sy, 0), (a.src_q[si] & 2) != 0);
+  }
+}
+
+// FP32 output sums: the result rounded once to FP32 (round to nearest even), before the test
+// that drops exact zeros, so that values rounding to zero are dropped too.
+__device__ __forceinline__ void round_out(Cx& r, int round32) {
+  if (round32) {
+    r.re = (double)__double2float_rn(r.re);
+    r.im = (double)__double2float_rn(r.im);
   }
 }
 
@@ -1315,6 +1329,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(MergeArgs a) {
           uint32_t n = 0;
           if (chain_sum_regs<S, 4>(s, slot, acc, n)) {
             r = finish(a, s, acc, n, pe);
+            round_out(r, a.round32);
             flag = !(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16);
           } else {
             deferred = true;
@@ -1347,6 +1362,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge(MergeArgs a) {
             chain_sum_long(s, slot, acc, n);
           }
           r = finish(a, s, acc, n, pe);
+          round_out(r, a.round32);
           flag = !(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16);
         }
         stage_result(s, flag, r, slot, lane);
@@ -1826,6 +1842,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
               r = acc;
             }
           }
+          round_out(r, a.round32);
           flag = !(is_zero(r.re) && is_zero(r.im)) && (n > 0 || pe != kNone16);
         }
         const unsigned m = __ballot_sync(0xffffffffu, flag);
@@ -2161,6 +2178,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   a.out_n = counters.p + 1;
   a.out_cap = (unsigned long long)out_cap;
   a.err = err.p;
+  a.round32 = out->f32;
   a.split_groups = misc.p + 2;
   uint64_t kv, kw;
   host_key_with_hash(nbins / 2, bits, &kv, &kw);  // hash in the upper half: empty key for lower-half groups
