@@ -441,7 +441,7 @@ def main():
     # ---------------------------------------------------------------- FP32 coefficients (2D lattice)
     f32_res = None
     if not args.no_learned:
-        f32_res = lattice_f32(stream)
+        f32_res = lattice_f32(stream, Hl, Ol, lat_pol)
 
     # ---------------------------------------------------------------- batched disorder realisations
     batch_res = None
@@ -647,13 +647,16 @@ def batched_instances_full(stream, n_inst: int = 512, ramp: int = 16, timed: int
 
 
 F32_WORKLOAD = ("RK4 on the open 8x8 Heisenberg lattice (336 strings), O(0) = Z at (4,4), dt=0.02, dissipation "
-                "gamma=0.1, top 2^20 strings with trimmed stages, 30 steps (t=0.6) from O(0), once with FP64 and once "
-                "with FP32 coefficients (H and O rounded to FP32; FP64 norms)")
+                "gamma=0.1, top 2^20 strings with trimmed stages, 30 steps (t=0.6) from O(0), with FP64 coefficients, "
+                "FP32 coefficients (FP64 accumulation of exact products) and FP32 arithmetic with compensated sums "
+                "(H and O rounded to FP32; FP64 norms); step times also at the 2^23 cap from the FP64 run's state")
 
 
-def lattice_f32(stream, steps: int = 30):
-    """The 2D workload run with FP64 and with FP32 coefficients from the same start: the error
-    of FP32 per observable (autocorrelation Tr(O(t) Z_c)/2^N and ||O(t)||) and the step times."""
+def lattice_f32(stream, Hl, Ol, lat_pol, steps: int = 30):
+    """The 2D workload run with FP64, FP32 and compensated-FP32 coefficients from the same start:
+    the error of each FP32 mode per observable (autocorrelation Tr(O(t) Z_c)/2^N and ||O(t)||),
+    the step times of the study, and the step times at the 2^23 cap (two steps from the FP64
+    lattice run's state at the cap, converted to each precision)."""
     import torch
     from paper_2410_09654_gb300 import inputs as I, paulistr as ps
     pol = ps.policy(top_k=1 << 20, gamma=0.1, trim_stages=1)
@@ -661,8 +664,22 @@ def lattice_f32(stream, steps: int = 30):
     Oa = I.single(N_SITES, "Z", 28).arrays()
     pv, pw = I.string("Z", 28)
     probe = (np.array([pv], np.uint64), np.array([pw], np.uint64))
+    at_cap = {}
+    for name, prec in (("f64", ps.PS_COEF_F64), ("f32", ps.PS_COEF_F32), ("f32c", ps.PS_COEF_F32C)):
+        Hp = Hl.copy().set_precision(prec)
+        Op_ = Ol.copy().set_precision(prec)
+        ps.pauli_rk4_step(Hp, Op_, 0.02, lat_pol)  # untimed: the cache holds this precision's sizes
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            ps.pauli_rk4_step(Hp, Op_, 0.02, lat_pol)
+        e1.record(stream)
+        e1.synchronize()
+        at_cap[name] = e0.elapsed_time(e1) / 2
+        del Hp, Op_
     runs = {}
-    for name, prec in (("f64", ps.PS_COEF_F64), ("f32", ps.PS_COEF_F32)):
+    for name, prec in (("f64", ps.PS_COEF_F64), ("f32", ps.PS_COEF_F32), ("f32c", ps.PS_COEF_F32C)):
         H = ps.PauliSum.from_arrays(N_SITES, *Ha).set_precision(prec)
         O = ps.PauliSum.from_arrays(N_SITES, *Oa).set_precision(prec)
         obs, nrm = [], []
@@ -679,14 +696,18 @@ def lattice_f32(stream, steps: int = 30):
             nrm.append(ps.pauli_norm(O))
         runs[name] = (np.array(obs), np.array(nrm), t_steps / steps, len(O))
     a64, n64, t64, s64 = runs["f64"]
-    a32, n32, t32, s32 = runs["f32"]
-    return {"workload": F32_WORKLOAD,
-            "autocorrelation_abs_error_max": float(np.max(np.abs(a32 - a64))),
-            "autocorrelation_rel_error_max": float(np.max(np.abs(a32 - a64) / np.abs(a64))),
-            "autocorrelation_final": {"f64": float(a64[-1]), "f32": float(a32[-1])},
-            "norm_rel_error_max": float(np.max(np.abs(n32 - n64) / n64)),
-            "ms_per_step": {"f64": t64, "f32": t32}, "final_size": {"f64": s64, "f32": s32},
-            "note": "FP32 values in the 32-byte records: the precision study, not a bandwidth saving"}
+    out = {"workload": F32_WORKLOAD, "ms_per_step_at_2p23_cap": at_cap,
+           "ms_per_step": {k: v[2] for k, v in runs.items()}, "final_size": {k: v[3] for k, v in runs.items()},
+           "autocorrelation_final": {k: float(v[0][-1]) for k, v in runs.items()}}
+    for name in ("f32", "f32c"):
+        a, nrm = runs[name][0], runs[name][1]
+        out[name + "_error_vs_f64"] = {
+            "autocorrelation_abs_max": float(np.max(np.abs(a - a64))),
+            "autocorrelation_rel_max": float(np.max(np.abs(a - a64) / np.abs(a64))),
+            "norm_rel_max": float(np.max(np.abs(nrm - n64) / n64))}
+    out["note"] = ("f32: FP32 values, exact products accumulated in FP64; f32c: FP32 products and "
+                   "Sum2-compensated FP32 sums; both store FP32 values in the 32-byte records")
+    return out
 
 
 def learned_truncation(stream, peaks_bf16: float, lg_cap: int = 18, steps: int = 80, iters: int = 4000):

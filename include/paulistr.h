@@ -119,6 +119,15 @@ int pauli_sum_n_sites(const pauli_sum* s, int* n_sites);
  * contents.  The records keep the 32-byte layout. */
 #define PS_COEF_F64 0
 #define PS_COEF_F32 1
+/* FP32 arithmetic with compensated sums: like PS_COEF_F32 for storage, truncation, norms and
+ * b_n, but a merge computes every term in FP32 (product terms 2 i^(k+rot) RN32(h x), source
+ * terms RN32(alpha y), with h, x, alpha rounded to FP32 first) and adds a string's terms in
+ * Alg. 1's order with the compensated sum Sum2 of Ogita, Rump and Oishi (Knuth's TwoSum on the
+ * running sum, the errors summed in FP32, one final rounding); with a post factor the output is
+ * RN32(pre + RN32(post acc)).  The sums must be single-component (real or imaginary
+ * coefficients throughout) and H at most 508 terms (ranked merges); other merges return
+ * PS_ERR_INVALID.  A merge writing into such a sum uses this arithmetic. */
+#define PS_COEF_F32C 2
 int pauli_sum_set_precision(pauli_sum* s, int coef_dtype);
 int pauli_sum_precision(const pauli_sum* s, int* coef_dtype);
 

@@ -17,7 +17,6 @@
 //      then the sources in order).  That is exactly the order in which Alg. 1 with H
 //      in the outer loop adds them, so the result is independent of scheduling.
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -188,13 +187,17 @@ struct __align__(16) Contrib {
 struct __align__(16) HScal {
   double s;
   int e;
-  int pvw;  // popcount(v & w) of the H term (its share of the product phase)
+  int pvw;   // popcount(v & w) of the H term (its share of the product phase)
+  float sf;  // s rounded to FP32 (the factor of the FP32 arithmetic)
+  int pad;
 };
 
 // Scalars of the single-component arithmetic (see build_scalar).
 struct EmitScalars {
+  int f32c;  // FP32 arithmetic: terms rounded once to FP32 (see prod32)
   int rot, uH, uX;
   double src_s[4];
+  float src_sf[4];  // src_s rounded to FP32
   int src_e[4], src_q[4], src_uy[4];
   int pre_u;
 };
@@ -212,7 +215,7 @@ __global__ void k_h_prep(const Rec* __restrict__ H, int nh, int bits, int uH, ui
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int E = (int)((b >> 52) & 0x7FF);
     const bool p2 = (b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046;
-    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, __popcll(h.v & h.w)};
+    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, __popcll(h.v & h.w), __double2float_rn(v), 0};
   }
 }
 
@@ -241,6 +244,68 @@ __device__ __forceinline__ double scaled(double s, int e, double y, int extra) {
   }
   double p = __dmul_rn(s, y);
   return extra ? twice(p) : p;
+}
+
+// FP32 arithmetic with compensated sums (output sums of precision PS_COEF_F32C): a term is
+// the FP32 product RN32(RN32(s) RN32(y)), doubled exactly for a commutator product; a
+// string's terms are added by Sum2 (Ogita, Rump, Oishi: TwoSum of the running sum, errors
+// added in FP32, one final rounding) in the same order as the FP64 fold.
+// FP32 numbers held in doubles and floats converted into each other on the integer pipe (the
+// values are exact FP32 numbers, so no rounding is involved): on this GPU the FP64 unit, which
+// would otherwise do the conversions, is the narrowest pipe.
+__device__ __forceinline__ float f32_exact(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & ((1ull << 52) - 1);
+  uint32_t f;
+  if (e == 0) {
+    f = sign;  // +-0 (an FP32 number is never an FP64 subnormal)
+  } else if (e == 0x7FF) {
+    f = sign | 0x7F800000u | (uint32_t)(m >> 29) | (m ? 0x400000u : 0u);  // inf, nan
+  } else {
+    const int e32 = e - 1023 + 127;
+    f = e32 >= 1 ? sign | ((uint32_t)e32 << 23) | (uint32_t)(m >> 29)
+                 : sign | (uint32_t)((m | (1ull << 52)) >> (30 - e32));  // FP32 subnormal
+  }
+  return __uint_as_float(f);
+}
+
+__device__ __forceinline__ double f64_of(float x) {
+  const uint32_t f = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
+  const uint32_t e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu;
+  unsigned long long b;
+  if (e == 0xFFu) {
+    b = sign | 0x7FF0000000000000ull | ((unsigned long long)m << 29);
+  } else if (e != 0) {
+    b = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0) {
+    b = sign;
+  } else {  // subnormal: m 2^-149 with its top bit at position p
+    const int p = 31 - __clz(m);
+    b = sign | ((unsigned long long)(p - 149 + 1023) << 52) | (((unsigned long long)m << (52 - p)) & ((1ull << 52) - 1));
+  }
+  return __longlong_as_double((long long)b);
+}
+
+// s: the FP32 scalar (H coefficient, alpha or post) already rounded; y: an FP32 number.
+__device__ __forceinline__ double prod32(float s, double y, int extra) {
+  float p = __fmul_rn(s, f32_exact(y));
+  if (extra) p = __fmul_rn(2.0f, p);
+  return f64_of(p);
+}
+
+__device__ __forceinline__ void two_sum32(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ double add_rn32(double a, double b) {  // FP32 sum, zero terms skipped
+  if (is_zero(b)) return a;
+  if (is_zero(a)) return b;
+  return f64_of(__fadd_rn(f32_exact(a), f32_exact(b)));
 }
 
 // Bin cursors: cur[p] starts at the bin's first slot (base[p]) and one 64-bit atomic add
@@ -378,147 +443,6 @@ __global__ void k_anti_table(const Rec* __restrict__ H, int nH, int stride, uint
     }
     T[t * stride + k] = word;
   }
-}
-
-bool g_emit_blk = getenv("PS_EMIT_WARP") == nullptr;  // block-level emission (A/B switch while both exist)
-constexpr int kRing = 64;  // per-warp ring of queued (lane, h) codes
-constexpr int kRingMask = kRing - 1;
-
-template <bool FULL, int NW>
-__global__ void __launch_bounds__(kEmitThreads, 5) k_emit_tab(const Rec* __restrict__ X, const uint32_t* __restrict__ fX,
-                                                  int64_t nX, const Rec* __restrict__ H,
-                                                  const uint32_t* __restrict__ fH,
-                                                  const HScal* __restrict__ hscal, int nh,
-                                                  const uint32_t* __restrict__ T, EmitScalars es,
-                                                  unsigned long long* __restrict__ cur,
-                                                  uint64_t* __restrict__ entries, Contrib* __restrict__ fout,
-                                                  unsigned long long* __restrict__ total,
-                                                  unsigned long long* __restrict__ next_tile,
-                                                  const double* __restrict__ hb, int hb_shift) {
-  constexpr int S = tab_stride(NW);
-  constexpr int kTabWords = kTabPos * kTabVals * S;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_ring = s_tab + kTabWords;
-  ulonglong2* s_hk = reinterpret_cast<ulonglong2*>(s_ring + (kEmitThreads / 32) * kRing);
-  HScal* s_hs = reinterpret_cast<HScal*>(s_hk + nh);  // FULL only
-  uint32_t* s_hf = reinterpret_cast<uint32_t*>(s_hs + (FULL ? nh : 0));
-  for (int i = threadIdx.x; i < kTabWords; i += blockDim.x) s_tab[i] = T[i];
-  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
-    s_hk[i] = make_ulonglong2(H[i].v, H[i].w);
-    if constexpr (FULL) s_hs[i] = hscal[i];
-    s_hf[i] = fH[i];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* q = s_ring + warp * kRing;
-  uint32_t emitted = 0;  // warp-uniform
-  for (;;) {  // tiles of 32 x, handed out one at a time
-    unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(next_tile, 1ull);
-    const int64_t t0 = (int64_t)__shfl_sync(0xffffffffu, tile, 0) * 32;
-    if (t0 >= nX) break;
-    const int64_t i = t0 + lane;
-    const bool valid = i < nX;
-    ulonglong2 xk = make_ulonglong2(0, 0);
-    double sy = 0.0;
-    uint32_t fx = 0;
-    if (valid) {
-      xk = *reinterpret_cast<const ulonglong2*>(&X[i]);
-      if constexpr (FULL) sy = es.uX ? X[i].im : X[i].re;
-      fx = fX[i];
-    }
-    // anticommutation bitmap of this lane's x
-    uint32_t A[NW];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) A[k] = 0u;
-    if (valid) {
-#pragma unroll
-      for (int p = 0; p < kTabPos; ++p) {
-        const uint64_t m = p < 16 ? xk.x : xk.y;
-        const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
-        const uint32_t* row = s_tab + (p * kTabVals + nib) * S;
-#pragma unroll
-        for (int k = 0; k < NW; k += 2) {
-          const uint2 t = *reinterpret_cast<const uint2*>(row + k);
-          A[k] ^= t.x;
-          A[k + 1] ^= t.y;
-        }
-      }
-    }
-    uint32_t head = 0, tail = 0;  // ring positions (warp-uniform), taken mod kRing
-    // entries for the codes at ring positions [head, head + n): lane l takes head + l
-    auto flush = [&](int n) {
-      const bool act = lane < n;
-      const uint32_t c = act ? q[(head + lane) & kRingMask] : 0u;
-      const int src = (int)(c >> 16);
-      const uint32_t h = c & 0xFFFFu;
-      const uint32_t pfx = __shfl_sync(0xffffffffu, fx, src);
-      Contrib r;
-      if constexpr (FULL) {
-        const uint64_t xv = __shfl_sync(0xffffffffu, xk.x, src);
-        const uint64_t xw = __shfl_sync(0xffffffffu, xk.y, src);
-        const double xs = __shfl_sync(0xffffffffu, sy, src);
-        const ulonglong2 hk = s_hk[h];
-        const HScal hs = s_hs[h];
-        const int ph = (product_phase(hk.x, hk.y, xv, xw) + es.rot + es.uH + es.uX) & 3;
-        r.v = hk.x ^ xv;
-        r.w = hk.y ^ xw;
-        double hsv = hs.s;
-        int hse = hs.e;
-        if (hb) {  // batched instances: the H coefficients of x's instance (tag = v >> hb_shift)
-          hsv = hb[(size_t)(xv >> hb_shift) * (size_t)nh + h];
-          hse = kNoPow2;
-        }
-        r.val = neg_if(scaled(hsv, hse, xs, 1), (ph & 2) != 0);
-        r.code = h;
-        r.pad = 0;
-      }
-      const uint64_t at = reserve_slot(cur, pfx ^ s_hf[h], act, lane);
-      if (act) {
-        if constexpr (FULL) fout[at] = r;
-        else entries[at] = ((uint64_t)(t0 + src) << 16) | (uint64_t)h;
-      }
-      __syncwarp();
-      head += n;
-      emitted += n;
-    };
-    // h-major queue order (the x of a tile are neighbours in hash order, so the entries of
-    // one h land in few bins): per h, a ballot of the lanes whose bitmap has bit h
-#pragma unroll 1
-    for (uint32_t hb = 0; hb < 32u * NW; hb += 32u) {
-      uint32_t a = A[0];
-#pragma unroll
-      for (int k = 0; k + 1 < NW; ++k) A[k] = A[k + 1];
-      A[NW - 1] = 0u;
-      uint32_t any = __ballot_sync(0xffffffffu, a != 0u) ? 1u : 0u;
-      if (!any) continue;
-      // h offsets of this word that some lane has (OR over the warp)
-      uint32_t word_or = a;
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) word_or |= __shfl_xor_sync(0xffffffffu, word_or, d);
-      while (word_or) {
-        const int b = __ffs(word_or) - 1;
-        word_or &= word_or - 1u;
-        const bool anti = (a >> b) & 1u;
-        const unsigned m = __ballot_sync(0xffffffffu, anti);
-        if (anti) q[(tail + __popc(m & ((1u << lane) - 1u))) & kRingMask] = ((uint32_t)lane << 16) | (hb + (uint32_t)b);
-        tail += __popc(m);
-        if (tail - head >= 32u) {
-          __syncwarp();
-          flush(32);
-        }
-      }
-    }
-    __syncwarp();
-    if (tail != head) flush((int)(tail - head));
-  }
-  __shared__ unsigned long long s_tot;
-  if (threadIdx.x == 0) s_tot = 0;
-  __syncthreads();
-  if (lane == 0 && emitted) atomicAdd(&s_tot, (unsigned long long)emitted);
-  __syncthreads();
-  if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
 }
 
 // Block-level table emission.  A block takes 256 neighbouring x (hash order), one per
@@ -669,7 +593,8 @@ __global__ void __launch_bounds__(kEmitThreads, 4) k_emit_blk(const Rec* __restr
               hsv = hb[(size_t)(x.x >> hb_shift) * (size_t)nh + h];
               hse = kNoPow2;
             }
-            r.val = neg_if(scaled(hsv, hse, s_xs[xl], 1), (ph & 2) != 0);
+            r.val = neg_if(es.f32c ? prod32(hb ? __double2float_rn(hsv) : hs.sf, s_xs[xl], 1) : scaled(hsv, hse, s_xs[xl], 1),
+                           (ph & 2) != 0);
             r.code = h;
             r.pad = 0;
           }
@@ -691,27 +616,13 @@ int launch_emit_tab(const Rec* X, const uint32_t* fX, int64_t nX, const Rec* H, 
                     const HScal* hscal, int nh, const uint32_t* T, const EmitScalars& es,
                     unsigned long long* cur, uint64_t* entries, Contrib* fout, unsigned long long* total, int nsm,
                     cudaStream_t s, const double* hb, int hb_shift) {
-  Buf<unsigned long long> next_tile;
-  PS_TRY(next_tile.alloc(1, s));
-  PS_CUDA(cudaMemsetAsync(next_tile.p, 0, sizeof(unsigned long long), s));
-  if (g_emit_blk) {
-    const size_t sm = (size_t)kTabPos * kTabVals * tab_stride(NW) * sizeof(uint32_t) +
-                      (size_t)nh * (sizeof(ulonglong2) + (FULL ? sizeof(HScal) : 0) + sizeof(uint32_t));
-    PS_CUDA(cudaFuncSetAttribute(k_emit_blk<FULL, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int per_sm = 0;
-    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit_blk<FULL, NW>, kEmitThreads, sm));
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * nsm, ceil_div(nX, kBlkX)));
-    PS_LAUNCH("k_emit_products", s, k_emit_blk<FULL, NW><<<grid, kEmitThreads, sm, s>>>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, hb, hb_shift));
-    PS_CUDA(cudaGetLastError());
-    return PS_OK;
-  }
   const size_t sm = (size_t)kTabPos * kTabVals * tab_stride(NW) * sizeof(uint32_t) +
-                    (size_t)(kEmitThreads / 32) * kRing * sizeof(uint32_t) + (size_t)nh * (sizeof(ulonglong2) + (FULL ? sizeof(HScal) : 0) + sizeof(uint32_t));
-  PS_CUDA(cudaFuncSetAttribute(k_emit_tab<FULL, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                    (size_t)nh * (sizeof(ulonglong2) + (FULL ? sizeof(HScal) : 0) + sizeof(uint32_t));
+  PS_CUDA(cudaFuncSetAttribute(k_emit_blk<FULL, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int per_sm = 0;
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit_tab<FULL, NW>, kEmitThreads, sm));
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * nsm, ceil_div(nX, kEmitThreads)));
-  PS_LAUNCH("k_emit_products", s, k_emit_tab<FULL, NW><<<grid, kEmitThreads, sm, s>>>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, next_tile.p, hb, hb_shift));
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit_blk<FULL, NW>, kEmitThreads, sm));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * nsm, ceil_div(nX, kBlkX)));
+  PS_LAUNCH("k_emit_products", s, k_emit_blk<FULL, NW><<<grid, kEmitThreads, sm, s>>>(X, fX, nX, H, fH, hscal, nh, T, es, cur, entries, fout, total, hb, hb_shift));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -754,7 +665,8 @@ __global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, ui
       } else {
         const uint32_t si = code - kCodeSrc;
         const double sy = es.src_uy[si] ? y.im : y.re;
-        val = neg_if(scaled(es.src_s[si], es.src_e[si], sy, 0), (es.src_q[si] & 2) != 0);
+        val = neg_if(es.f32c ? prod32(es.src_sf[si], sy, 0) : scaled(es.src_s[si], es.src_e[si], sy, 0),
+                     (es.src_q[si] & 2) != 0);
       }
       if (ts == kTsExpand) {
         for (int k = 0; k < ring; ++k) {
@@ -853,6 +765,9 @@ struct MergeArgs {
   unsigned long long out_cap;
   int* err;               // bit 0: capacity, bit 1: unresolved table overflow
   int round32;            // FP32 output sum: every result rounded once to FP32 before the zero test
+  int f32c;               // FP32 arithmetic with compensated sums (single-component ranked merges)
+  float src_sf[4];        // src_s and post_s rounded to FP32
+  float post_sf;
   unsigned* split_groups;
   ulonglong2 sent_lo, sent_hi;  // empty-slot keys for groups in the lower / upper half
   // structured (single-component) mode: every coefficient is s * i^u with s real
@@ -953,7 +868,7 @@ __device__ __forceinline__ void build_scalar(const MergeArgs& a, uint32_t code, 
     key = make_ulonglong2(h.v ^ y.v, h.w ^ y.w);
     int q = (product_phase(h.v, h.w, y.v, y.w) + a.rot + a.uH + a.uX) & 3;
     double sy = a.uX ? y.im : y.re;
-    t = neg_if(scaled(hs.s, hs.e, sy, 1), (q & 2) != 0);
+    t = neg_if(a.f32c ? prod32(hs.sf, sy, 1) : scaled(hs.s, hs.e, sy, 1), (q & 2) != 0);
   } else if (code == kCodePre) {
     key = make_ulonglong2(y.v, y.w);
     t = a.pre_u ? y.im : y.re;
@@ -961,7 +876,7 @@ __device__ __forceinline__ void build_scalar(const MergeArgs& a, uint32_t code, 
     const uint32_t si = code - kCodeSrc;
     key = make_ulonglong2(y.v, y.w);
     double sy = a.src_uy[si] ? y.im : y.re;
-    t = neg_if(scaled(a.src_s[si], a.src_e[si], sy, 0), (a.src_q[si] & 2) != 0);
+    t = neg_if(a.f32c ? prod32(a.src_sf[si], sy, 0) : scaled(a.src_s[si], a.src_e[si], sy, 0), (a.src_q[si] & 2) != 0);
   }
 }
 
@@ -1812,17 +1727,31 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           const uint32_t n = s.rlen[slot];
           const uint32_t b0 = s.run[slot];
           Cx acc{0.0, 0.0};
-          if (n > 0) {
-            acc.re = s.seg[b0];
-            if constexpr (!S) acc.im = s.segim[b0];
-          }
-          for (uint32_t i = 1; i < n; ++i) {
-            acc.re = __dadd_rn(acc.re, s.seg[b0 + i]);
-            if constexpr (!S) acc.im = __dadd_rn(acc.im, s.segim[b0 + i]);
+          if (S && a.f32c) {  // Sum2 in FP32
+            float sum = n > 0 ? f32_exact(s.seg[b0]) : 0.0f, err = 0.0f;
+            for (uint32_t i = 1; i < n; ++i) {
+              float e;
+              two_sum32(sum, f32_exact(s.seg[b0 + i]), sum, e);
+              err = __fadd_rn(err, e);
+            }
+            acc.re = f64_of(__fadd_rn(sum, err));
+          } else {
+            if (n > 0) {
+              acc.re = s.seg[b0];
+              if constexpr (!S) acc.im = s.segim[b0];
+            }
+            for (uint32_t i = 1; i < n; ++i) {
+              acc.re = __dadd_rn(acc.re, s.seg[b0 + i]);
+              if constexpr (!S) acc.im = __dadd_rn(acc.im, s.segim[b0 + i]);
+            }
           }
           const uint32_t pe = s.pre[slot];
           if constexpr (S) {
-            if (a.has_post) {
+            if (a.has_post && a.f32c) {
+              const double sc = (n > 0) ? neg_if(prod32(a.post_sf, acc.re, 0), (a.post_q & 2) != 0) : 0.0;
+              if (pe != kNone16) r.re = (n > 0) ? add_rn32(s.ere[pe], sc) : s.ere[pe];
+              else r.re = sc;
+            } else if (a.has_post) {
               double sc = (n > 0) ? neg_if(__dmul_rn(a.post_s, acc.re), (a.post_q & 2) != 0) : 0.0;
               if (pe != kNone16) r.re = (n > 0) ? add_rn(s.ere[pe], sc) : s.ere[pe];
               else r.re = sc;
@@ -1989,6 +1918,9 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   const bool ranked_wide = !ranked && !has_ts && ncode_h + sp.nsrc <= RankGeom<16>::kBits;
   const bool full = structured && ranked && (uint64_t)bound_total * sizeof(Contrib) <= kFullBudget;
   if (has_ts && !full) return PS_ERR_INVALID;  // representatives need full records: one component
+  // FP32 arithmetic with compensated sums: single-component ranked merges
+  const int f32c = out->f32 == 2 ? 1 : 0;
+  if (f32c && !(structured && (ranked || ranked_wide))) return PS_ERR_INVALID;
   // per-instance H coefficients ride on the table emission of full records
   if (sp.hbatch && nX > 0 && !(full && sp.nH <= kMaskBits && !sp.product)) return PS_ERR_INVALID;
 
@@ -2019,12 +1951,16 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     a.pre_u = sp.clsPre == kClsImag;
     int up = cls_scalar(sp.post) == kClsImag;
     a.post_s = up ? sp.post.im : sp.post.re;
+    a.post_sf = (float)a.post_s;
     a.post_q = up + (acc_cls == kClsImag);
     a.out_imag = out_cls == kClsImag;
+    es.f32c = out->f32 == 2 ? 1 : 0;
     es.rot = sp.rot;
     es.uH = a.uH;
     es.uX = a.uX;
     for (int i = 0; i < 4; ++i) {
+      a.src_sf[i] = (float)a.src_s[i];
+      es.src_sf[i] = a.src_sf[i];
       es.src_s[i] = a.src_s[i];
       es.src_e[i] = a.src_e[i];
       es.src_q[i] = a.src_q[i];
@@ -2179,6 +2115,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   a.out_cap = (unsigned long long)out_cap;
   a.err = err.p;
   a.round32 = out->f32;
+  a.f32c = f32c;
   a.split_groups = misc.p + 2;
   uint64_t kv, kw;
   host_key_with_hash(nbins / 2, bits, &kv, &kw);  // hash in the upper half: empty key for lower-half groups

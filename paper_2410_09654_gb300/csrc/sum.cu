@@ -530,15 +530,16 @@ int pauli_sum_copy(const pauli_sum* src, pauli_sum* dst) {
 }
 
 int pauli_sum_set_precision(pauli_sum* s, int coef_dtype) {
-  if (!s || (coef_dtype != PS_COEF_F64 && coef_dtype != PS_COEF_F32)) return PS_ERR_INVALID;
+  if (!s || (coef_dtype != PS_COEF_F64 && coef_dtype != PS_COEF_F32 && coef_dtype != PS_COEF_F32C))
+    return PS_ERR_INVALID;
   if (s->W > 1 && coef_dtype != PS_COEF_F64) return PS_ERR_INVALID;
-  s->f32 = coef_dtype == PS_COEF_F32;
+  s->f32 = coef_dtype;  // 0 FP64, 1 FP32, 2 FP32 with compensated sums
   return round_f32(s);
 }
 
 int pauli_sum_precision(const pauli_sum* s, int* coef_dtype) {
   if (!s || !coef_dtype) return PS_ERR_INVALID;
-  *coef_dtype = s->f32 ? PS_COEF_F32 : PS_COEF_F64;
+  *coef_dtype = s->f32;
   return PS_OK;
 }
 
@@ -582,7 +583,7 @@ int pauli_sum_save(const pauli_sum* s, const char* path, const double* meta, int
   std::FILE* f = std::fopen(path, "wb");
   if (!f) return PS_ERR_IO;
   Fnv fnv;
-  const uint32_t hdr[4] = {1u, (uint32_t)s->n_sites, (uint32_t)(s->f32 ? PS_COEF_F32 : PS_COEF_F64), (uint32_t)n_meta};
+  const uint32_t hdr[4] = {1u, (uint32_t)s->n_sites, (uint32_t)s->f32, (uint32_t)n_meta};
   const uint64_t cnt = (uint64_t)n;
   bool ok = put(f, fnv, kCkpMagic, 8) && put(f, fnv, hdr, sizeof(hdr)) && put(f, fnv, &cnt, 8);
   if (ok && n_meta > 0) ok = put(f, fnv, meta, (size_t)n_meta * sizeof(double));
@@ -638,7 +639,7 @@ int pauli_sum_load(pauli_sum* s, const char* path, double* meta, int64_t meta_ca
     s->f32 = old_f32;
     return st;
   }
-  s->f32 = hdr[2] == (uint32_t)PS_COEF_F32;
+  s->f32 = hdr[2] <= (uint32_t)PS_COEF_F32C ? (int)hdr[2] : 0;
   if (n_meta) *n_meta = (int64_t)m.size();
   for (int64_t i = 0; i < std::min<int64_t>(meta_cap, (int64_t)m.size()); ++i) meta[i] = m[(size_t)i];
   return PS_OK;

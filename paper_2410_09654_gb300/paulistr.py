@@ -30,6 +30,7 @@ PS_ERR_IO = 9
 PS_ERR_NONFINITE = 10
 PS_COEF_F64 = 0
 PS_COEF_F32 = 1
+PS_COEF_F32C = 2
 
 _lib = None
 
@@ -266,7 +267,8 @@ class PauliSum:
         return {(int(a), int(b)): complex(c, d) for a, b, c, d in zip(v, w, re, im)}
 
     def set_precision(self, coef_dtype: int) -> "PauliSum":
-        """PS_COEF_F32: FP32 coefficients from now on (rounds the contents); PS_COEF_F64: FP64."""
+        """PS_COEF_F32 / PS_COEF_F32C: FP32 coefficients from now on (rounds the contents), the
+        latter with FP32 arithmetic and compensated sums in merges; PS_COEF_F64: FP64."""
         _check(self._lib.pauli_sum_set_precision(self.handle, int(coef_dtype)), "pauli_sum_set_precision")
         return self
 
@@ -296,8 +298,8 @@ class PauliSum:
 
     def copy(self) -> "PauliSum":
         out = PauliSum(self.n_sites, len(self), self.stream.value)
-        if self.precision() == PS_COEF_F32:
-            out.set_precision(PS_COEF_F32)
+        if self.precision() != PS_COEF_F64:
+            out.set_precision(self.precision())
         _check(self._lib.pauli_sum_copy(self.handle, out.handle), "pauli_sum_copy")
         return out
 
