@@ -383,6 +383,7 @@ def main():
                               "profile_only": True, "kernels_per_step_ms": {k: round(v[1], 4) for k, v in per_step.items()},
                               "merge_groups_per_step": groups / args.steps,
                               "merge_split_groups_per_step": split_groups / args.steps,
+                              "launches_before_timed": launches0, "gpu_launches": launches,
                               "roofline": roof}), flush=True)
         if world > 1:
             dist.destroy_process_group()
