@@ -772,7 +772,7 @@ def learned_truncation(stream, peaks_bf16: float, lg_cap: int = 18, steps: int =
     fwd_roof = None
     if kl:
         achieved = len(C_last) * flop_per_string / (kms / 1e3 / kl) / 1e12
-        fwd_roof = {"kernel": "k_mlp_fwd", "bound": "tensor", "achieved": achieved, "peak": peaks_bf16,
+        fwd_roof = {"kernel": "k_mlp_fwd_tc", "bound": "tensor", "achieved": achieved, "peak": peaks_bf16,
                     "unit": "TFLOP/s", "frac": achieved / peaks_bf16,
                     "peak_kind": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops), kernel timed alone",
                     "flop_per_string": flop_per_string, "strings_per_launch": len(C_last),
@@ -790,7 +790,8 @@ def learned_truncation(stream, peaks_bf16: float, lg_cap: int = 18, steps: int =
                      "seconds": t3 - t2, "samples_per_s": iters * batch / (t3 - t2), "collect_seconds": t1 - t0},
         "scorer_ms_per_step": fwd_ms / steps,
         "scorer_roofline": fwd_roof,
-        "kernel": "mma.sync m16n8k16 bf16 (fp32 accumulate)",
+        "kernel": "scorer: tcgen05.mma kind::f16 (bf16 operands in shared memory, fp32 accumulators in tensor memory); "
+                  "training: mma.sync m16n8k16 bf16",
     }
 
 

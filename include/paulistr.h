@@ -69,7 +69,7 @@ extern "C" {
 #define PS_ERR_CAPACITY 2         /* a caller-provided capacity is too small (download) */
 #define PS_ERR_TABLE_FULL 3       /* a merge table could not be resolved even after splitting */
 #define PS_ERR_CUDA 4             /* a CUDA runtime call failed; see pauli_last_cuda_error() */
-#define PS_ERR_TIMEOUT 5          /* reserved: no kernel of this library waits on another agent */
+#define PS_ERR_TIMEOUT 5          /* a bounded device-side wait gave up (the learned scorer's wait on its tensor-core products) */
 #define PS_ERR_KRYLOV_EXHAUSTED 6 /* Lanczos: b_n == 0 (the Krylov space closed); b_out is 0 */
 #define PS_ERR_NOMEM 7            /* device allocation failed */
 #define PS_ERR_UNCERTAIN 8        /* reserved */

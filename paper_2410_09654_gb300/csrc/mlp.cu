@@ -17,9 +17,10 @@
 // ln|c| for the feature is FP32 from the exponent and leading mantissa bits of the larger
 // component, and the rescaling factor is a power of two times exp2 of a fraction in FP32.
 //
-// The products run on mma.sync m16n8k16 (bf16 in, fp32 accumulate).  Each warp owns 16
-// rows; the accumulator of one layer is repacked in registers as the A operand of the next
-// (the m16n8 C layout of two adjacent column tiles is the m16k16 A layout).
+// Inference (the scorer inside the RK4 step) runs on tcgen05.mma with TMEM accumulators
+// (k_mlp_fwd_tc).  Training runs on mma.sync m16n8k16 (bf16 in, fp32 accumulate): each warp
+// owns 16 rows; the accumulator of one layer is repacked in registers as the A operand of the
+// next (the m16n8 C layout of two adjacent column tiles is the m16k16 A layout).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,7 +42,6 @@ constexpr int kSF = kF + 8;       // shared row stride (bf16) of K = 80 rows: 44
 constexpr int kSH = kHid + 8;     // of K = 128 rows: 68 words
 constexpr int kTrainRows = 64;    // rows per training tile (4 warps x 16)
 constexpr int kSR = kTrainRows + 8;  // stride of the transposed (row-contiguous) tiles: 36 words
-constexpr int kFwdRows = 128;     // rows per inference tile (8 warps x 16)
 
 struct FeatConst {
   uint64_t bin_mask[16];
@@ -298,56 +298,221 @@ struct MlpDev {
   const float* p;        // FP32 master parameters
 };
 
-// ---------------------------------------------------------------- inference
-// Per string: optional features (bf16 bits, [n][80]), logit z, and the rank value
-// |c|^2 e^(2 (z - gamma_dt wt)) (FP64) that orders strings like ln|c| - gamma_dt wt + z.
-__global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, int64_t n, FeatConst fc, MlpDev m,
-                                                 double gamma_dt, uint16_t* __restrict__ x_out,
-                                                 float* __restrict__ z_out, double* __restrict__ score_out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t* W1s = reinterpret_cast<uint16_t*>(smem);
-  uint16_t* W2s = W1s + kHid * kSF;
-  uint16_t* xs = W2s + kHid * kSH;
-  float* fb1 = reinterpret_cast<float*>(xs + kFwdRows * kSF);
+// ---------------------------------------------------------------- inference on tcgen05
+// The same network on the fifth-generation tensor cores: per tile of 128 strings, the BF16
+// operands sit in shared memory in the no-swizzle K-major layout of tcgen05.mma (8-row x
+// 16-byte core matrices: core (r/8, k/8) of a [rows][K] tile at ((r/8)(K/8) + k/8) 128 bytes,
+// row r%8 at 16 (r%8), element k%8 at 2 (k%8); descriptors: leading offset 128 bytes between
+// cores along K, stride offset (K/8) 128 bytes between cores along M or N), one thread issues
+// the M = N = 128 products (K = 80 in five steps of 16, then K = 128 in eight), the FP32
+// accumulators live in tensor memory (columns 0..127 layer 1, 128..255 layer 2, one lane per
+// string), and every thread reads its string's row back with tcgen05.ld for the bias, ReLU and
+// output epilogues.  Completion goes through an mbarrier whose waits are bounded: a wait that
+// gives up sets *err and the kernel stops cleanly.
+constexpr int kTcRows = 128;
+constexpr uint32_t kTcCols = 256;                   // tensor-memory columns per block
+constexpr int kTcA1 = kTcRows * kF * 2;             // bytes: features tile [128][80]
+constexpr int kTcA2 = kTcRows * kHid * 2;           // h1 tile [128][128]
+constexpr int kTcW1 = kHid * kF * 2;                // W1 [128][80]
+constexpr int kTcW2 = kHid * kHid * 2;              // W2 [128][128]
+constexpr int kTcOffA1 = 0, kTcOffA2 = kTcOffA1 + kTcA1, kTcOffW1 = kTcOffA2 + kTcA2, kTcOffW2 = kTcOffW1 + kTcW1,
+              kTcOffF = kTcOffW2 + kTcW2;
+constexpr size_t kTcSmem = (size_t)kTcOffF + 3 * kHid * 4 + 2 * kTcRows * 4 + 64 + 1024;  // + alignment slack
+constexpr long long kTcWaitLimit = 1ll << 26;       // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ uint32_t core_off(int r, int k, int K) {  // byte offset in a core-matrix tile
+  return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // version 1, no swizzle
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kHid >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+               ::"r"(dtm), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Wait for the mbarrier phase with the given parity; false when the bounded wait gave up.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  for (long long i = 0; i < kTcWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Features [k0, k1) of one string as BF16 pairs into its row of the core-matrix feature tile.
+template <int HALF>
+__device__ __forceinline__ void store_features_tc(const Rec& r, bool valid, const FeatConst& fc, unsigned char* a1,
+                                                  int row, uint16_t* x_glob) {
+  constexpr int k0 = HALF ? 44 : 0, k1 = HALF ? 80 : 44;
+#pragma unroll
+  for (int k = k0; k < k1; k += 2) {
+    const float f0 = valid ? feature(r, fc, k) : 0.0f, f1 = valid ? feature(r, fc, k + 1) : 0.0f;
+    const uint32_t pr = pack_bf16(f0, f1);
+    *reinterpret_cast<uint32_t*>(a1 + core_off(row, k, kF)) = pr;
+    if (x_glob) *reinterpret_cast<uint32_t*>(x_glob + k) = pr;
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) k_mlp_fwd_tc(const Rec* __restrict__ d, int64_t n, FeatConst fc, MlpDev m,
+                                                    double gamma_dt, uint16_t* __restrict__ x_out,
+                                                    float* __restrict__ z_out, double* __restrict__ score_out,
+                                                    int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* a1 = sm + kTcOffA1;
+  unsigned char* a2 = sm + kTcOffA2;
+  unsigned char* w1 = sm + kTcOffW1;
+  unsigned char* w2 = sm + kTcOffW2;
+  float* fb1 = reinterpret_cast<float*>(sm + kTcOffF);
   float* fb2 = fb1 + kHid;
   float* fw3 = fb2 + kHid;
-  stage<kSF>(W1s, m.w1b, kHid, kF);
-  stage<kSH>(W2s, m.w2b, kHid, kHid);
-  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+  float* zpart = fw3 + kHid;                                   // [2][128] partial output sums
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(zpart + 2 * kTcRows);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // weights into the core-matrix layout (B operands: [n][k], K contiguous), biases, w3
+  for (int i = tid; i < kHid * kF / 2; i += blockDim.x) {
+    const int nn = (2 * i) / kF, k = (2 * i) % kF;
+    *reinterpret_cast<uint32_t*>(w1 + core_off(nn, k, kF)) = reinterpret_cast<const uint32_t*>(m.w1b)[i];
+  }
+  for (int i = tid; i < kHid * kHid / 2; i += blockDim.x) {
+    const int nn = (2 * i) / kHid, k = (2 * i) % kHid;
+    *reinterpret_cast<uint32_t*>(w2 + core_off(nn, k, kHid)) = reinterpret_cast<const uint32_t*>(m.w2b)[i];
+  }
+  for (int i = tid; i < kHid; i += blockDim.x) {
     fb1[i] = m.p[oB1 + i];
     fb2[i] = m.p[oB2 + i];
     fw3[i] = m.p[oW3 + i];
   }
+  const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(mbar);
+  if (tid == 0) {
+    *s_err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // tensor memory: 256 columns (two accumulators of 128 x 128 FP32)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(tmem_slot)), "r"(kTcCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sa1 = (uint32_t)__cvta_generic_to_shared(a1), sa2 = (uint32_t)__cvta_generic_to_shared(a2);
+  const uint32_t sw1 = (uint32_t)__cvta_generic_to_shared(w1), sw2 = (uint32_t)__cvta_generic_to_shared(w2);
   const float b3 = m.p[oB3];
   const float gdt_f = (float)gamma_dt;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const int64_t tiles = ceil_div_dev(n, kFwdRows);
+  const int row = 32 * (warp & 3) + lane;   // this thread's string (tensor-memory lane) in the tile
+  const int half = warp >> 2;                 // accumulator columns [64 half, 64 half + 64)
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  uint32_t parity = 0;
+  const int64_t tiles = ceil_div_dev(n, kTcRows);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t base = tile * kFwdRows;
-    __syncthreads();  // staging done / previous tile's xs consumed
-    // two warps per 32 rows: the even warp writes features 0..43, the odd one 44..79
-    {
-      const int row = (warp >> 1) * 32 + lane;
-      const int64_t i = base + row;
+    const int64_t base = tile * kTcRows;
+    {  // features: two warps per 32 strings (the even warp 0..43, the odd one 44..79)
+      const int frow = (warp >> 1) * 32 + lane;
+      const int64_t i = base + frow;
       Rec r{0, 0, 0.0, 0.0};
       const bool valid = i < n;
       if (valid) r = d[i];
       uint16_t* xg = (x_out && valid) ? x_out + i * kF : nullptr;
-      if (warp & 1) store_features<1>(r, valid, fc, xs + row * kSF, xg, nullptr, 0, row);
-      else store_features<0>(r, valid, fc, xs + row * kSF, xg, nullptr, 0, row);
+      if (warp & 1) store_features_tc<1>(r, valid, fc, a1, frow, xg);
+      else store_features_tc<0>(r, valid, fc, a1, frow, xg);
     }
+    fence_async_smem();
+    tc_before_sync();
     __syncthreads();
-    uint32_t h1[8][4];
-    float h2[16][4];
-    forward_rows(xs, 16 * warp, W1s, W2s, fb1, fb2, g, t, h1, h2);
-    float zg, zg8;
-    output_rows(h2, fw3, b3, t, zg, zg8);
-    if (t == 0) {
+    tc_after_sync();
+    if (tid == 0) {  // layer 1: D1 = X W1^T, K = 80
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int64_t i = base + 16 * warp + g + 8 * e;
-        if (i >= n) continue;
-        const float z = e ? zg8 : zg;
+      for (int ks = 0; ks < kF / 16; ++ks)
+        tc_mma(tmem, umma_desc(sa1 + ks * 256, 128, (kF / 8) * 128), umma_desc(sw1 + ks * 256, 128, (kF / 8) * 128),
+               ks > 0);
+      tc_commit(mbar_a);
+    }
+    if (!tc_wait(mbar_a, parity)) atomicOr(s_err, 1);
+    parity ^= 1u;
+    tc_after_sync();
+    {  // epilogue 1: relu(D1 + b1) as BF16 into the h1 tile (this thread's row, 64 columns)
+      for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
+        float v[16];
+        tc_ld16(tmem + lane_addr + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const float e0 = fmaxf(v[j] + fb1[c0 + j], 0.0f), e1 = fmaxf(v[j + 1] + fb1[c0 + j + 1], 0.0f);
+          *reinterpret_cast<uint32_t*>(a2 + core_off(row, c0 + j, kHid)) = pack_bf16(e0, e1);
+        }
+      }
+    }
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (*s_err) break;
+    if (tid == 0) {  // layer 2: D2 = H1 W2^T, K = 128
+#pragma unroll
+      for (int ks = 0; ks < kHid / 16; ++ks)
+        tc_mma(tmem + 128, umma_desc(sa2 + ks * 256, 128, (kHid / 8) * 128),
+               umma_desc(sw2 + ks * 256, 128, (kHid / 8) * 128), ks > 0);
+      tc_commit(mbar_a);
+    }
+    if (!tc_wait(mbar_a, parity)) atomicOr(s_err, 1);
+    parity ^= 1u;
+    tc_after_sync();
+    {  // epilogue 2: relu(D2 + b2) . w3 over this thread's 64 columns
+      float acc = 0.0f;
+      for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
+        float v[16];
+        tc_ld16(tmem + lane_addr + 128u + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc += fmaxf(v[j] + fb2[c0 + j], 0.0f) * fw3[c0 + j];
+      }
+      zpart[half * kTcRows + row] = acc;
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (*s_err) break;
+    if (half == 0) {
+      const int64_t i = base + row;
+      if (i < n) {
+        const float z = zpart[row] + zpart[kTcRows + row] + b3;
         if (z_out) z_out[i] = z;
         if (score_out) {
           const Rec r = d[i];
@@ -356,6 +521,12 @@ __global__ void __launch_bounds__(256, 2) k_mlp_fwd(const Rec* __restrict__ d, i
       }
     }
   }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  if (tid == 0 && *s_err) atomicOr(err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
 // ---------------------------------------------------------------- training
@@ -635,7 +806,6 @@ __global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ grad, floa
   }
 }
 
-constexpr size_t kFwdSmem = (size_t)(kHid * kSF + kHid * kSH + kFwdRows * kSF) * 2 + 3 * kHid * 4;
 constexpr size_t kTrainSmem =
     (size_t)(kHid * kSF + 2 * kHid * kSH + kTrainRows * kSF + kF * kSR + 3 * kHid * kSR) * 2 + (6 * kHid + 4) * 4;
 
@@ -686,7 +856,7 @@ int refresh_bf16(pauli_mlp* m) {  // BF16 copies from the FP32 parameters, no up
 int smem_attr() {
   static int done = 0;
   if (done) return PS_OK;
-  PS_CUDA(cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem));
+  PS_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
   PS_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem));
   done = 1;
   return PS_OK;
@@ -696,12 +866,18 @@ int fwd_run(const pauli_mlp* m, const Rec* d, int64_t n, cudaStream_t s, double 
             double* score) {
   if (n == 0) return PS_OK;
   PS_TRY(smem_attr());
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kFwdRows), 2 * num_sms()));
+  Buf<int> err;
+  PS_TRY(err.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTcRows), 2 * num_sms()));
   PS_LAUNCH("k_mlp_fwd", s,
-            k_mlp_fwd<<<grid, 256, kFwdSmem, s>>>(d, n, make_featconst(m->n_sites), dev_view(m), gamma_dt, x, z,
-                                                  score));
+            k_mlp_fwd_tc<<<grid, 256, kTcSmem, s>>>(d, n, make_featconst(m->n_sites), dev_view(m), gamma_dt, x, z,
+                                                     score, err.p));
   PS_CUDA(cudaGetLastError());
-  return PS_OK;
+  int herr = 0;
+  PS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  return herr ? PS_ERR_TIMEOUT : PS_OK;
 }
 
 // Gradient of the mean BCE over X's records [i0, i0 + nb) into m->g (added), loss into m->loss.
