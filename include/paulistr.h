@@ -446,6 +446,11 @@ int pauli_debug_output_hash(const uint64_t* v, const uint64_t* w, int64_t n, uin
  * normalisation (correctly rounded, equal to the IEEE quotient); synchronises the stream.
  * For tests of that arithmetic. */
 int pauli_debug_divide(double* x, int64_t n, double b, void* cuda_stream);
+/* The learned scorer's bounded wait on its tensor-core products: with no_products != 0 the
+ * scorer issues no products (so its wait can only run out), and every wait gives up after
+ * wait_limit polls (default 2^26).  For tests of the PS_ERR_TIMEOUT path; it never leaves work
+ * in flight. */
+int pauli_debug_mlp_wait(int no_products, int64_t wait_limit);
 
 #ifdef __cplusplus
 }

@@ -344,8 +344,8 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
 }
 
 // Wait for the mbarrier phase with the given parity; false when the bounded wait gave up.
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
-  for (long long i = 0; i < kTcWaitLimit; ++i) {
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}\n"
@@ -389,7 +389,7 @@ __device__ __forceinline__ void store_features_tc(const Rec& r, bool valid, cons
 __global__ void __launch_bounds__(256, 2) k_mlp_fwd_tc(const Rec* __restrict__ d, int64_t n, FeatConst fc, MlpDev m,
                                                     double gamma_dt, uint16_t* __restrict__ x_out,
                                                     float* __restrict__ z_out, double* __restrict__ score_out,
-                                                    int* __restrict__ err) {
+                                                    int* __restrict__ err, int no_products, long long wait_limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* a1 = sm + kTcOffA1;
@@ -459,16 +459,20 @@ __global__ void __launch_bounds__(256, 2) k_mlp_fwd_tc(const Rec* __restrict__ d
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (tid == 0) {  // layer 1: D1 = X W1^T, K = 80
+    if (tid == 0 && !no_products) {  // layer 1: D1 = X W1^T, K = 80
 #pragma unroll
       for (int ks = 0; ks < kF / 16; ++ks)
         tc_mma(tmem, umma_desc(sa1 + ks * 256, 128, (kF / 8) * 128), umma_desc(sw1 + ks * 256, 128, (kF / 8) * 128),
                ks > 0);
       tc_commit(mbar_a);
     }
-    if (!tc_wait(mbar_a, parity)) atomicOr(s_err, 1);
+    if (!tc_wait(mbar_a, parity, wait_limit)) atomicOr(s_err, 1);
     parity ^= 1u;
     tc_after_sync();
+    tc_before_sync();
+    __syncthreads();  // every thread has seen the wait's outcome
+    tc_after_sync();
+    if (*s_err) break;
     {  // epilogue 1: relu(D1 + b1) as BF16 into the h1 tile (this thread's row, 64 columns)
       for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
         float v[16];
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(256, 2) k_mlp_fwd_tc(const Rec* __restrict__ d
                umma_desc(sw2 + ks * 256, 128, (kHid / 8) * 128), ks > 0);
       tc_commit(mbar_a);
     }
-    if (!tc_wait(mbar_a, parity)) atomicOr(s_err, 1);
+    if (!tc_wait(mbar_a, parity, wait_limit)) atomicOr(s_err, 1);
     parity ^= 1u;
     tc_after_sync();
     {  // epilogue 2: relu(D2 + b2) . w3 over this thread's 64 columns
@@ -862,6 +866,11 @@ int smem_attr() {
   return PS_OK;
 }
 
+// Test hook (pauli_debug_mlp_wait): the scorer issues no products and gives up its first wait
+// after `limit` polls, so that the timeout path runs without any tensor-core work in flight.
+int g_mlp_no_products = 0;
+long long g_mlp_wait_limit = kTcWaitLimit;
+
 int fwd_run(const pauli_mlp* m, const Rec* d, int64_t n, cudaStream_t s, double gamma_dt, uint16_t* x, float* z,
             double* score) {
   if (n == 0) return PS_OK;
@@ -872,7 +881,7 @@ int fwd_run(const pauli_mlp* m, const Rec* d, int64_t n, cudaStream_t s, double 
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTcRows), 2 * num_sms()));
   PS_LAUNCH("k_mlp_fwd", s,
             k_mlp_fwd_tc<<<grid, 256, kTcSmem, s>>>(d, n, make_featconst(m->n_sites), dev_view(m), gamma_dt, x, z,
-                                                     score, err.p));
+                                                     score, err.p, g_mlp_no_products, g_mlp_wait_limit));
   PS_CUDA(cudaGetLastError());
   int herr = 0;
   PS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -957,6 +966,13 @@ int pauli_mlp_create(int n_sites, uint64_t seed, void* cuda_stream, pauli_mlp** 
   }
   if ((st = refresh_bf16(m)) != PS_OK) return fail(st);
   *out = m;
+  return PS_OK;
+}
+
+int pauli_debug_mlp_wait(int no_products, int64_t wait_limit) {
+  if (wait_limit < 1) return PS_ERR_INVALID;
+  g_mlp_no_products = no_products ? 1 : 0;
+  g_mlp_wait_limit = wait_limit;
   return PS_OK;
 }
 

@@ -112,6 +112,7 @@ def load(build_if_missing: bool = False):
         "pauli_last_merge_stats": ([ctypes.POINTER(pauli_merge_stats)], ctypes.c_int),
         "pauli_debug_fail_alloc_after": ([I64], ctypes.c_int),
         "pauli_debug_output_hash": ([P, P, I64, P], ctypes.c_int),
+        "pauli_debug_mlp_wait": ([ctypes.c_int, I64], ctypes.c_int),
         "pauli_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "pauli_profile_report": ([ctypes.c_char_p, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_launch_count": ([], I64),
@@ -461,6 +462,10 @@ def pauli_debug_divide(x, b: float, stream=None):
 
 def pauli_debug_fail_alloc_after(n: int):
     _check(load().pauli_debug_fail_alloc_after(int(n)), "pauli_debug_fail_alloc_after")
+
+
+def pauli_debug_mlp_wait(no_products: int = 0, wait_limit: int = 1 << 26):
+    _check(load().pauli_debug_mlp_wait(int(no_products), int(wait_limit)), "pauli_debug_mlp_wait")
 
 
 def pauli_debug_output_hash(v, w) -> np.ndarray:

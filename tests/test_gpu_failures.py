@@ -203,3 +203,23 @@ def test_download_into_too_small_capacity():
     st = lib.pauli_sum_download(S.handle, *ptrs, 10, ctypes.byref(got))
     assert st == ps.PS_ERR_CAPACITY and got.value == 50
     assert not any(b.any() for b in buf)  # nothing written
+
+
+def test_scorer_wait_that_runs_out_returns_timeout():
+    # the scorer's wait on its tensor-core products is bounded: with the products switched off
+    # (a signal that never comes) the call returns PS_ERR_TIMEOUT and the library stays usable
+    from oracle import mlp as omlp
+    n = 20
+    arr = I.random_sum(3, n, 700, kind="real")
+    O = ps.PauliSum.from_arrays(n, *arr)  # storage order = upload order
+    model = ps.PauliMLP(n, seed=4)
+    ps.pauli_debug_mlp_wait(1, 1000)
+    try:
+        with pytest.raises(ps.PauliError) as e:
+            ps.pauli_mlp_scores(model, O, 0.0)
+        assert e.value.status == ps.PS_ERR_TIMEOUT
+    finally:
+        ps.pauli_debug_mlp_wait(0, 1 << 26)
+    z = ps.pauli_mlp_logits(model, O).cpu().numpy().astype(np.float64)
+    want, _ = omlp.forward(ps.pauli_mlp_get_params(model).astype(np.float64), omlp.features(*arr, n))
+    assert np.linalg.norm(z - want) <= 2e-2 * max(np.linalg.norm(want), 1.0)
