@@ -357,10 +357,13 @@ def main():
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         host = [([pin(x) for x in sp], [pin(x) for x in sc], sb) for sp, sc, sb in snaps]
         e_prev, e_cur = ps.PauliSum(N_SITES, args.top_k), ps.PauliSum(N_SITES, args.top_k)
+        # pinned host buffers receiving each step's new operator O_{n+1} (storage order)
+        out_host = [torch.empty(args.top_k, dtype=dt).pin_memory()
+                    for dt in (torch.int64, torch.int64, torch.float64, torch.float64)]
         barrier()
         t0 = time.perf_counter()
         e_prod = 0
-        h2d = 0
+        h2d = d2h = 0
         for hp, hc, sb in host:  # the timed loop's first states, each from host arrays
             e_prev.upload(*hp)
             e_cur.upload(*hc)
@@ -369,12 +372,18 @@ def main():
             e_prod += nH * len(hc[0])
             h2d += 32 * (len(hc[0]) + len(hp[0]))
             ps.pauli_lanczos_step(H, e_prev, e_cur, sb, pol)  # b_n read back to the host
+            res = ps.pauli_sum_download_device(e_cur)  # O_{n+1} back to host memory
+            for dst, src in zip(out_host, res):
+                dst[:src.numel()].copy_(src, non_blocking=True)
+            d2h += 8 + 32 * int(res[2].numel())
+            torch.cuda.current_stream().synchronize()
         barrier()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": sum_over_ranks(e_prod) / t_e2e, "unit": "Pauli products/s",
-               "h2d_bytes_per_step": int(h2d / len(host)), "d2h_bytes_per_step": 8,
+               "h2d_bytes_per_step": int(h2d / len(host)), "d2h_bytes_per_step": int(d2h / len(host)),
                "states": f"the first {len(host)} input states of the timed loop, uploaded from pinned host arrays",
-               "api": "pauli_sum_upload x2 (pinned host arrays) + pauli_sum_sort_by_hash x2 + pauli_lanczos_step (b_n to host)"}
+               "api": "pauli_sum_upload x2 (pinned host arrays) + pauli_sum_sort_by_hash x2 + pauli_lanczos_step "
+                      "(b_n to host) + pauli_sum_download_device of O_{n+1} copied to pinned host arrays"}
 
     if args.lanczos_only:
         if rank == 0:
