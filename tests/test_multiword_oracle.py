@@ -49,11 +49,13 @@ def _local(key, lo):
     return key[0] >> lo, key[1] >> lo
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_commutator_across_the_word_boundary_against_dense(seed):
-    # strings on sites 62..67 of a 128-site chain: both words of a two-word mask; the exact
-    # commutator from 2^6 x 2^6 matrices on that window, moved back to the global sites
-    lo, width, N = 61, 6, 128
+@pytest.mark.parametrize("seed,lo,N", [(0, 61, 128), (1, 61, 128), (2, 61, 128),
+                                        (3, 125, 256), (4, 189, 256), (5, 250, 256)])
+def test_commutator_across_the_word_boundary_against_dense(seed, lo, N):
+    # strings on a 6-site window that straddles a word boundary (sites 62..67 of a 128-site
+    # chain, 126..131 and 190..195 of a 256-site chain) or ends on the last site (251..256):
+    # the exact commutator from 2^6 x 2^6 matrices on that window, moved back to the global sites
+    width = 6
     rng = np.random.default_rng(seed)
 
     def rand_terms(m):
@@ -66,7 +68,12 @@ def test_commutator_across_the_word_boundary_against_dense(seed):
 
     H, O = rand_terms(6), rand_terms(10)
     got = mw.commutator(H, O)
-    assert any((k[0] | k[1]) >> 64 for k in got) and any((k[0] | k[1]) & ((1 << 64) - 1) for k in got)
+    if lo % 64 > 58:
+        word = lo // 64  # both words of the boundary are used
+        lowmask = (1 << (64 * (word + 1))) - 1
+        assert any((k[0] | k[1]) >> (64 * (word + 1)) for k in got)
+        assert any((k[0] | k[1]) & lowmask for k in got)
+    assert all(((k[0] | k[1]) >> N) == 0 for k in got)
     loc = lambda terms: orc.Op(width, [_local(k, lo)[0] for k, _ in terms], [_local(k, lo)[1] for k, _ in terms],  # noqa: E731
                                 [c.real for _, c in terms], [c.imag for _, c in terms])
     m = dense.commutator(dense.op_matrix(loc(H), width), dense.op_matrix(loc(O), width))
@@ -74,7 +81,6 @@ def test_commutator_across_the_word_boundary_against_dense(seed):
     assert got.keys() == want.keys()
     for k, c in want.items():
         assert abs(got[k] - c) <= 1e-12 * max(1.0, abs(c))
-    assert N > 64
 
 
 def test_moving_by_whole_words_moves_the_result():
@@ -97,6 +103,10 @@ def test_product_phase_table_on_far_sites():
     assert mw.product(Y, Z) == (X, 1)
     assert mw.product(Z, X) == (Y, 1)
     assert mw.anticommute(X, Y) and not mw.anticommute(X, X)
+    # the same on site 256, the last site of a four-word mask
+    X, Y, Z = (0, 1 << 255), (1 << 255, 1 << 255), (1 << 255, 0)
+    assert mw.product(X, Y) == (Z, 1) and mw.product(Y, Z) == (X, 1) and mw.product(Z, X) == (Y, 1)
+    assert mw.product(Y, X) == (Z, 3)
 
 
 # ----------------------------------------------------------------------------- truncation, RK4 with
