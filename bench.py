@@ -82,11 +82,17 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            # nvidia-smi takes a moment to start: wait (bounded) for its first sample, so that
+            # the samples kept (those from here on) cover the timed region that follows
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
+        self.i0 = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -102,7 +108,8 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        kept = self.lines[self.i0:] or self.lines[-1:]
+        for ln in kept:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -372,9 +379,8 @@ def main():
             e_prod += nH * len(hc[0])
             h2d += 32 * (len(hc[0]) + len(hp[0]))
             ps.pauli_lanczos_step(H, e_prev, e_cur, sb, pol)  # b_n read back to the host
-            res = ps.pauli_sum_download_device(e_cur)  # O_{n+1} back to host memory
-            for dst, src in zip(out_host, res):
-                dst[:src.numel()].copy_(src, non_blocking=True)
+            # O_{n+1} back to pinned host memory, written there by the library's unpacking kernel
+            res = ps.pauli_sum_download_device(e_cur, out=out_host)
             d2h += 8 + 32 * int(res[2].numel())
             torch.cuda.current_stream().synchronize()
         barrier()
@@ -382,8 +388,9 @@ def main():
         e2e = {"value": sum_over_ranks(e_prod) / t_e2e, "unit": "Pauli products/s",
                "h2d_bytes_per_step": int(h2d / len(host)), "d2h_bytes_per_step": int(d2h / len(host)),
                "states": f"the first {len(host)} input states of the timed loop, uploaded from pinned host arrays",
-               "api": "pauli_sum_upload x2 (pinned host arrays) + pauli_sum_sort_by_hash x2 + pauli_lanczos_step "
-                      "(b_n to host) + pauli_sum_download_device of O_{n+1} copied to pinned host arrays"}
+               "api": "pauli_sum_upload x2 (pinned host arrays, read by the packing kernel over the host link) + "
+                      "pauli_sum_sort_by_hash x2 + pauli_lanczos_step (b_n to host) + pauli_sum_download_device of "
+                      "O_{n+1} into pinned host arrays"}
 
     if args.lanczos_only:
         if rank == 0:

@@ -92,13 +92,16 @@ int pauli_sum_destroy(pauli_sum* s);
  * (caller-owned, read during the call).  Strings must be distinct (a repeated
  * string is PS_ERR_INVALID) and have no bits at or above n_sites.  The given
  * order is kept; for a sum used as the left operand H of a commutator this is
- * the order of the outer loop of Alg. 1.  Exact-zero coefficients are kept. */
+ * the order of the outer loop of Alg. 1.  Exact-zero coefficients are kept.
+ * Arrays in pinned host memory mapped into the device's address space are read by the
+ * packing kernel directly over the host link; other host arrays go through a staging copy. */
 int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re,
                      const double* im, int64_t n);
 
-/* Same as pauli_sum_upload but v, w, re, im are DEVICE pointers (n elements each);
- * only the bit-range check is done (on the device); distinctness is the caller's
- * responsibility. */
+/* Same as pauli_sum_upload but v, w, re, im are DEVICE pointers (n elements each) on the
+ * current device, or pinned host memory mapped into its address space; any other pointer
+ * (pageable host memory, another device's memory) is PS_ERR_INVALID.  Only the bit-range
+ * check is done (on the device); distinctness is the caller's responsibility. */
 int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re,
                             const double* im, int64_t n);
 
@@ -136,7 +139,11 @@ int pauli_sum_precision(const pauli_sum* s, int* coef_dtype);
 int pauli_sum_download(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im,
                        int64_t cap, int64_t* n);
 
-/* Copy the sum to DEVICE arrays in storage order (unspecified order). */
+/* Copy the sum to DEVICE arrays in storage order (unspecified order), ordered on the sum's
+ * stream (not synchronised).  The arrays may also be pinned host memory mapped into the
+ * device's address space: the unpacking kernel then writes them over the host link, and they
+ * are complete once the stream has run it.  Any other pointer (pageable host memory, another
+ * device's memory) is PS_ERR_INVALID. */
 int pauli_sum_download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, double* re, double* im,
                               int64_t cap, int64_t* n);
 

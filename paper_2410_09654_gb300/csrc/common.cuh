@@ -184,6 +184,23 @@ inline uint64_t proper_divisor_mask(int n) {
 // Exactly-rounded FP64 operations without contraction into FMA.
 __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
 
+// Slot hash of a string key for the open-addressing tables (global and shared memory):
+// MurmurHash3's 64-bit finaliser (Appleby; invertible, every input bit reaches every output
+// bit) applied to w, XORed into v, and applied again.  A plain product by an odd constant is
+// not enough here: it carries bits upward only, so strings that differ only in the top bits
+// of a mask word (sites 57-64, for instance) would share most of their hash.
+__device__ __forceinline__ uint64_t fmix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xFF51AFD7ED558CCDull;
+  x ^= x >> 33;
+  x *= 0xC4CEB9FE1A85EC53ull;
+  x ^= x >> 33;
+  return x;
+}
+__device__ __forceinline__ uint64_t key_hash64(uint64_t v, uint64_t w) {
+  return fmix64(v ^ fmix64(w ^ 0x9E3779B97F4A7C15ull));
+}
+
 // 2*x, exact (exponent increment); falls back to x+x for zero, subnormal, huge or non-finite x.
 __device__ __forceinline__ double twice(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);

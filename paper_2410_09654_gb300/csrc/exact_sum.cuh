@@ -149,13 +149,7 @@ __device__ __forceinline__ void block_flush(Win acc, long long* gwin) {
     atomicAdd((unsigned long long*)&gwin[threadIdx.x], (unsigned long long)s_dig[threadIdx.x]);
 }
 
-__device__ __forceinline__ uint32_t mix_key(uint64_t v, uint64_t w) {
-  uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w * 0xC2B2AE3D27D4EB4Full + 0x27D4EB2F165667C5ull);
-  h ^= h >> 31;
-  h *= 0x94D049BB133111EBull;
-  h ^= h >> 29;
-  return (uint32_t)h;
-}
+__device__ __forceinline__ uint64_t mix_key(uint64_t v, uint64_t w) { return key_hash64(v, w); }
 
 __device__ __forceinline__ ulonglong2 cas128_g(ulonglong2* p, ulonglong2 expect, ulonglong2 desired) {
   ulonglong2 old;

@@ -74,19 +74,6 @@ constexpr int kBatch = 2;           // entries per thread with loads in flight t
 constexpr int kBatchFull = 4;       // the same for full records (one load round per pass of 2048)
 static_assert(kCap <= 2048, "order key packs the entry index in 11 bits");
 
-// Shared-table slot hash of a string: the four 32-bit words folded with odd multipliers,
-// then a multiply-xorshift finaliser (32-bit multiplies only).
-__device__ __forceinline__ uint32_t table_hash(uint64_t v, uint64_t w) {
-  uint32_t h = (uint32_t)v * 0x9E3779B1u ^ (uint32_t)(v >> 32) * 0x85EBCA77u ^ (uint32_t)w * 0xC2B2AE3Du ^
-               (uint32_t)(w >> 32) * 0x27D4EB2Fu;
-  h ^= h >> 15;
-  h *= 0x2C1B3C6Du;
-  h ^= h >> 12;
-  h *= 0x297A2D39u;
-  h ^= h >> 15;
-  return h;
-}
-
 __device__ __forceinline__ ulonglong2 cas128_shared(ulonglong2* p, ulonglong2 expect, ulonglong2 desired) {
   ulonglong2 old;
   unsigned addr = (unsigned)__cvta_generic_to_shared(p);
@@ -818,9 +805,9 @@ __device__ __forceinline__ int table_insert(SM& s, ulonglong2 c, ulonglong2 sent
   fresh = false;
   // double hashing: an odd step from the hash's high bits (every slot is reachable), so
   // that neighbouring home slots do not build the long clusters of linear probing
-  const uint32_t h = table_hash(c.x, c.y);
-  uint32_t slot = h & (TAB - 1);
-  const uint32_t step = (h >> 20) | 1u;
+  const uint64_t h = key_hash64(c.x, c.y);
+  uint32_t slot = (uint32_t)h & (TAB - 1);
+  const uint32_t step = (uint32_t)(h >> 32) | 1u;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
     ulonglong2 k = s.key[slot];
     if (k.x == c.x && k.y == c.y) return (int)slot;

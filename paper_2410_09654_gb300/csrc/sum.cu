@@ -224,45 +224,32 @@ void host_key_with_hash(uint32_t target, int bits, uint64_t* v, uint64_t* w) {
 
 // ----------------------------------------------------------------------------- coefficient class
 // ----------------------------------------------------------------------------- validation kernels
-__device__ __forceinline__ uint32_t mix32(uint64_t v, uint64_t w) {
-  uint64_t h = v * 0x9E3779B97F4A7C15ull ^ (w + 0x632BE59BD9B4E019ull);
-  h ^= h >> 32;
-  h *= 0xD6E8FEB86659FD93ull;
-  h ^= h >> 32;
-  return (uint32_t)h;
-}
 
-__device__ __forceinline__ void cas128_global(ulonglong2* p, ulonglong2 expect, ulonglong2 desired, ulonglong2& old) {
-  asm volatile(
-      "{\n\t.reg .b128 d, b, c;\n\t"
-      "mov.b128 b, {%2, %3};\n\t"
-      "mov.b128 c, {%4, %5};\n\t"
-      "atom.global.cas.b128 d, [%6], b, c;\n\t"
-      "mov.b128 {%0, %1}, d;\n\t}"
-      : "=l"(old.x), "=l"(old.y)
-      : "l"(expect.x), "l"(expect.y), "l"(desired.x), "l"(desired.y), "l"(p)
-      : "memory");
-}
-
-// Insert every key into an open-addressing table of 2^k slots (empty = all ones);
-// a key found already present is a duplicate.  The all-ones key itself is counted aside.
-__global__ void k_distinct(const Rec* __restrict__ d, int64_t n, ulonglong2* table, uint64_t tmask, int* dup,
-                           int* ones) {
+// Insert every key into an open-addressing table of 2^k 64-bit slots (empty = 0).  A slot
+// holds the key's 24-bit fingerprint and its record index + 1 (40 bits), so that the table
+// (8 bytes a slot, at most half full) stays small enough for L2; a slot with the same
+// fingerprint is resolved by comparing the two records.  A key found already present is a
+// duplicate.
+__global__ void k_distinct(const Rec* __restrict__ d, int64_t n, unsigned long long* table, uint64_t tmask,
+                           int* dup) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const ulonglong2 empty = make_ulonglong2(~0ull, ~0ull);
   for (; i < n; i += stride) {
-    ulonglong2 k = make_ulonglong2(d[i].v, d[i].w);
-    if (k.x == ~0ull && k.y == ~0ull) {
-      if (atomicAdd(ones, 1) > 0) atomicOr(dup, 1);
-      continue;
-    }
-    uint64_t slot = mix32(k.x, k.y) & tmask;
+    const uint64_t kv = d[i].v, kw = d[i].w;
+    const uint64_t h = key_hash64(kv, kw);  // low bits: the slot; top 24 bits: the fingerprint
+    const unsigned long long fp = h >> 40;
+    const unsigned long long mine = (fp << 40) | (unsigned long long)(i + 1);
+    uint64_t slot = h & tmask;
     for (uint64_t probe = 0; probe <= tmask; ++probe) {
-      ulonglong2 old;
-      cas128_global(&table[slot], empty, k, old);
-      if (old.x == empty.x && old.y == empty.y) break;     // inserted
-      if (old.x == k.x && old.y == k.y) { atomicOr(dup, 1); break; }
+      const unsigned long long old = atomicCAS(&table[slot], 0ull, mine);
+      if (old == 0ull) break;  // inserted
+      if ((old >> 40) == fp) {
+        const int64_t j = (int64_t)(old & ((1ull << 40) - 1)) - 1;
+        if (d[j].v == kv && d[j].w == kw) {
+          atomicOr(dup, 1);
+          break;
+        }
+      }
       slot = (slot + 1) & tmask;
     }
   }
@@ -270,17 +257,34 @@ __global__ void k_distinct(const Rec* __restrict__ d, int64_t n, ulonglong2* tab
 
 // The distinctness check without its synchronisation: *dup is set if two keys are equal
 // (the table is sized and filled here and must live until the stream has run the kernel).
-int distinct_launch(const Rec* d, int64_t n, cudaStream_t s, Buf<ulonglong2>& table, int* dup, int* ones) {
+int distinct_launch(const Rec* d, int64_t n, cudaStream_t s, Buf<unsigned long long>& table, int* dup) {
+  if (n >= (int64_t)(1ull << 40) - 1) return PS_ERR_INVALID;  // record indices must fit the slot
   uint64_t slots = 1;
   while (slots < (uint64_t)(2 * n)) slots <<= 1;
   PS_TRY(table.alloc(slots, s));
-  PS_CUDA(cudaMemsetAsync(table.p, 0xFF, slots * sizeof(ulonglong2), s));
+  PS_CUDA(cudaMemsetAsync(table.p, 0, slots * sizeof(unsigned long long), s));
   int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
-  PS_LAUNCH("k_distinct", s, k_distinct<<<blocks, 256, 0, s>>>(d, n, table.p, slots - 1, dup, ones));
+  PS_LAUNCH("k_distinct", s, k_distinct<<<blocks, 256, 0, s>>>(d, n, table.p, slots - 1, dup));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 
+// Device address of caller memory the device can read or write directly: device memory, or
+// pinned host memory mapped into the device's address space (its device alias).  Null for
+// pageable host memory and for memory of another device.
+void* device_alias(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return at.device == dev ? at.devicePointer : nullptr;
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+  return nullptr;
+}
 
 }  // namespace ps
 
@@ -409,31 +413,43 @@ int pauli_sum_upload(pauli_sum* s, const uint64_t* v, const uint64_t* w, const d
   if (s->W > 1) return wide_api::upload(s, v, w, re, im, n, true);
   PS_TRY(sum_reserve(s, n, false));
   s->n = 0;
-  // four host->device copies into a staging area; one pass packs the records and checks the
-  // key bits and the coefficient class, one inserts the keys for the distinctness check; a
-  // single synchronisation reads every flag (the caller's host arrays may be released then)
+  // The records are packed by one pass that also checks the key bits and the coefficient
+  // class: straight from the caller's arrays when they are pinned host memory mapped into the
+  // device's address space (the pass reads them over the host link), else from a staging
+  // copy.  One pass inserts the keys for the distinctness check; a single synchronisation
+  // reads every flag (the caller's host arrays may be released then).
   Buf<uint64_t> stage;
   Buf<int> flags;
-  Buf<ulonglong2> table;
+  Buf<unsigned long long> table;
   PS_TRY(flags.alloc(4, s->stream));
   PS_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int), s->stream));
   if (n > 0) {
-    PS_TRY(stage.alloc((size_t)n * 4, s->stream));
-    uint64_t* dv = stage.p;
-    uint64_t* dw = stage.p + n;
-    double* dre = reinterpret_cast<double*>(stage.p + 2 * n);
-    double* dim = reinterpret_cast<double*>(stage.p + 3 * n);
-    const size_t bytes = (size_t)n * sizeof(uint64_t);
-    PS_CUDA(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, s->stream));
-    PS_CUDA(cudaMemcpyAsync(dw, w, bytes, cudaMemcpyHostToDevice, s->stream));
-    PS_CUDA(cudaMemcpyAsync(dre, re, bytes, cudaMemcpyHostToDevice, s->stream));
-    PS_CUDA(cudaMemcpyAsync(dim, im, bytes, cudaMemcpyHostToDevice, s->stream));
+    const uint64_t* dv = static_cast<const uint64_t*>(device_alias(v));
+    const uint64_t* dw = static_cast<const uint64_t*>(device_alias(w));
+    const double* dre = static_cast<const double*>(device_alias(re));
+    const double* dim = static_cast<const double*>(device_alias(im));
+    if (!dv || !dw || !dre || !dim) {
+      PS_TRY(stage.alloc((size_t)n * 4, s->stream));
+      uint64_t* sv = stage.p;
+      uint64_t* sw = stage.p + n;
+      double* sre = reinterpret_cast<double*>(stage.p + 2 * n);
+      double* sim = reinterpret_cast<double*>(stage.p + 3 * n);
+      const size_t bytes = (size_t)n * sizeof(uint64_t);
+      PS_CUDA(cudaMemcpyAsync(sv, v, bytes, cudaMemcpyHostToDevice, s->stream));
+      PS_CUDA(cudaMemcpyAsync(sw, w, bytes, cudaMemcpyHostToDevice, s->stream));
+      PS_CUDA(cudaMemcpyAsync(sre, re, bytes, cudaMemcpyHostToDevice, s->stream));
+      PS_CUDA(cudaMemcpyAsync(sim, im, bytes, cudaMemcpyHostToDevice, s->stream));
+      dv = sv;
+      dw = sw;
+      dre = sre;
+      dim = sim;
+    }
     int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
     PS_LAUNCH("k_pack", s->stream,
               k_pack<<<blocks, 256, 0, s->stream>>>(s->d, dv, dw, dre, dim, n, ~key_mask(s->n_sites), flags.p));
     PS_CUDA(cudaGetLastError());
   }
-  if (n > 1) PS_TRY(distinct_launch(s->d, n, s->stream, table, flags.p + 2, flags.p + 3));
+  if (n > 1) PS_TRY(distinct_launch(s->d, n, s->stream, table, flags.p + 2));
   int h[4] = {0, 0, 0, 0};
   PS_CUDA(cudaMemcpyAsync(h, flags.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
   PS_CUDA(cudaStreamSynchronize(s->stream));
@@ -459,6 +475,13 @@ __global__ void k_unpack(const Rec* __restrict__ d, uint64_t* __restrict__ v, ui
 int pauli_sum_upload_device(pauli_sum* s, const uint64_t* v, const uint64_t* w, const double* re,
                             const double* im, int64_t n) {
   if (!s || n < 0 || (n > 0 && (!v || !w || !re || !im))) return PS_ERR_INVALID;
+  if (n > 0) {  // device memory, or mapped pinned host memory (read over the host link)
+    v = static_cast<const uint64_t*>(device_alias(v));
+    w = static_cast<const uint64_t*>(device_alias(w));
+    re = static_cast<const double*>(device_alias(re));
+    im = static_cast<const double*>(device_alias(im));
+    if (!v || !w || !re || !im) return PS_ERR_INVALID;
+  }
   if (s->W > 1) return wide_api::upload(s, v, w, re, im, n, false);
   PS_TRY(sum_reserve(s, n, false));
   s->n = 0;
@@ -509,9 +532,16 @@ int pauli_sum_download_device(const pauli_sum* s, uint64_t* v, uint64_t* w, doub
   if (cap < s->n) return PS_ERR_CAPACITY;
   if (s->n == 0) return PS_OK;
   if (!v || !w || !re || !im) return PS_ERR_INVALID;
-  if (s->W > 1) return wide_api::download_device(s, v, w, re, im);
+  // device memory, or pinned host memory mapped into the device's address space (written
+  // over the host link by the unpacking pass itself)
+  uint64_t* dv = static_cast<uint64_t*>(device_alias(v));
+  uint64_t* dw = static_cast<uint64_t*>(device_alias(w));
+  double* dre = static_cast<double*>(device_alias(re));
+  double* dim = static_cast<double*>(device_alias(im));
+  if (!dv || !dw || !dre || !dim) return PS_ERR_INVALID;
+  if (s->W > 1) return wide_api::download_device(s, dv, dw, dre, dim);
   int blocks = (int)std::min<int64_t>(ceil_div(s->n, 256), 8 * num_sms());
-  PS_LAUNCH("k_unpack", s->stream, k_unpack<<<blocks, 256, 0, s->stream>>>(s->d, v, w, re, im, s->n));
+  PS_LAUNCH("k_unpack", s->stream, k_unpack<<<blocks, 256, 0, s->stream>>>(s->d, dv, dw, dre, dim, s->n));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

@@ -154,14 +154,10 @@ __device__ __forceinline__ int w_weight(const KeyW<W>& k) {
 
 template <int W>
 __device__ __forceinline__ uint32_t thash(const KeyW<W>& k) {
-  uint64_t h = 0x2545F4914F6CDD1Dull;
+  uint64_t h = 0x2545F4914F6CDD1Dull;  // every word through the full-avalanche finaliser
 #pragma unroll
-  for (int i = 0; i < W; ++i) {
-    h = (h ^ k.v[i]) * 0x9E3779B97F4A7C15ull;
-    h = (h ^ (h >> 29) ^ k.w[i]) * 0xBF58476D1CE4E5B9ull;
-  }
-  h ^= h >> 31;
-  return (uint32_t)h ^ (uint32_t)(h >> 32);
+  for (int i = 0; i < W; ++i) h = fmix64(fmix64(h ^ k.v[i]) ^ k.w[i]);
+  return (uint32_t)h;
 }
 
 // Canonical order of keys: v as a W-word unsigned integer (most significant word last in

@@ -710,15 +710,25 @@ def pauli_sum_download(S: PauliSum):
     return S.download()
 
 
-def pauli_sum_download_device(S: PauliSum):
-    """(v, w, re, im) CUDA tensors (int64 bit patterns of the masks, float64) in storage order."""
+def pauli_sum_download_device(S: PauliSum, out=None):
+    """(v, w, re, im) in storage order: int64 bit patterns of the masks and float64, as new CUDA
+    tensors, or written into `out` (four tensors of at least the sum's size: CUDA tensors or
+    pinned host tensors, which the library writes over the host link; complete once the sum's
+    stream has run the call).  Returns the four tensors cut to the sum's size."""
     import torch
     m = len(S)
-    t = [torch.empty(m * S.W, dtype=torch.int64, device="cuda"), torch.empty(m * S.W, dtype=torch.int64, device="cuda"),
-         torch.empty(m, dtype=torch.float64, device="cuda"), torch.empty(m, dtype=torch.float64, device="cuda")]
+    if out is None:
+        t = [torch.empty(m * S.W, dtype=torch.int64, device="cuda"), torch.empty(m * S.W, dtype=torch.int64, device="cuda"),
+             torch.empty(m, dtype=torch.float64, device="cuda"), torch.empty(m, dtype=torch.float64, device="cuda")]
+        cap = m
+    else:
+        t = list(out)
+        cap = min(int(t[2].numel()), int(t[3].numel()), int(t[0].numel()) // S.W, int(t[1].numel()) // S.W)
     got = ctypes.c_int64()
-    _check(load().pauli_sum_download_device(S.handle, *[ctypes.c_void_p(x.data_ptr()) for x in t], m,
+    _check(load().pauli_sum_download_device(S.handle, *[ctypes.c_void_p(x.data_ptr()) for x in t], cap,
                                             ctypes.byref(got)), "pauli_sum_download_device")
+    if out is not None:
+        t = [t[0][:m * S.W], t[1][:m * S.W], t[2][:m], t[3][:m]]
     if S.W > 1:
         t[0], t[1] = t[0].view(m, S.W), t[1].view(m, S.W)
     return tuple(t)

@@ -42,3 +42,62 @@ def test_module_level_bindings(tmp_path):
     ps.pauli_batch_destroy(B)
     for x in (S, D, C, E, H):
         ps.pauli_sum_destroy(x)
+
+
+def _pinned(a):
+    """A copy of numpy array a in pinned host memory (mapped into the device's address space)."""
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+def test_upload_rejects_a_repeated_string_and_keeps_distinct_ones():
+    n = 64
+    v, w, re, im = I.random_sum(3, n, 20000, kind="real")
+    ones = np.uint64(0xFFFFFFFFFFFFFFFF)  # Y on every site
+    v2, w2 = np.append(v, ones), np.append(w, ones)
+    re2, im2 = np.append(re, 1.0), np.append(im, 0.0)
+    S = ps.PauliSum.from_arrays(n, v2, w2, re2, im2)  # all distinct, the all-ones key once
+    assert len(S) == len(re2)
+    for dup in (17, len(re2) - 1):  # a random string, then the all-ones key, repeated
+        with pytest.raises(ps.PauliError):
+            ps.PauliSum.from_arrays(n, np.append(v2, v2[dup]), np.append(w2, w2[dup]),
+                                    np.append(re2, 2.0), np.append(im2, 0.0))
+    with pytest.raises(ps.PauliError):  # the same through pinned host arrays
+        ps.PauliSum.from_arrays(n, *[_pinned(np.append(x, x[5])) for x in (v2, w2, re2, im2)])
+
+
+def test_upload_from_pinned_host_arrays_equals_pageable():
+    n = 64
+    arr = I.random_sum(4, n, 300000, kind="complex")
+    A = ps.PauliSum.from_arrays(n, *arr)
+    B = ps.PauliSum.from_arrays(n, *[_pinned(x) for x in arr])
+    a, b = A.download(), B.download()
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    # storage order is the given order on both paths
+    da, db = ps.pauli_sum_download_device(A), ps.pauli_sum_download_device(B)
+    assert all(torch.equal(x, y) for x, y in zip(da, db))
+
+
+def test_download_device_into_pinned_host_memory_and_refusals():
+    import ctypes
+    n = 64
+    arr = I.random_sum(5, n, 100000, kind="complex")
+    S = ps.PauliSum.from_arrays(n, *arr)
+    m = len(S)
+    host = [torch.empty(m, dtype=dt).pin_memory() for dt in (torch.int64, torch.int64, torch.float64, torch.float64)]
+    got = ctypes.c_int64()
+    ps._check(ps.load().pauli_sum_download_device(S.handle, *[ctypes.c_void_p(t.data_ptr()) for t in host], m,
+                                                   ctypes.byref(got)), "download_device")
+    torch.cuda.synchronize()
+    dev = ps.pauli_sum_download_device(S)  # the same storage order
+    assert got.value == m
+    for h, d in zip(host, dev):
+        assert torch.equal(h, d.cpu().view(h.dtype))
+    # pageable host memory is refused, nothing written
+    page = [np.full(m, 7, np.int64), np.full(m, 7, np.int64), np.full(m, 7.0), np.full(m, 7.0)]
+    rc = ps.load().pauli_sum_download_device(S.handle, *[ctypes.c_void_p(x.ctypes.data) for x in page], m,
+                                             ctypes.byref(got))
+    assert rc == ps.PS_ERR_INVALID and all((x == 7).all() for x in page)
+    # and the device upload refuses pageable arrays too
+    rc = ps.load().pauli_sum_upload_device(S.handle, *[ctypes.c_void_p(x.ctypes.data) for x in page], m)
+    assert rc == ps.PS_ERR_INVALID
+    assert len(S) == m
