@@ -458,6 +458,12 @@ int pauli_debug_divide(double* x, int64_t n, double b, void* cuda_stream);
  * wait_limit polls (default 2^26).  For tests of the PS_ERR_TIMEOUT path; it never leaves work
  * in flight. */
 int pauli_debug_mlp_wait(int no_products, int64_t wait_limit);
+/* on != 0: every truncation takes the general path (division of every candidate before the
+ * ranking).  By default the Lanczos truncation of a single-component FP64 sum by top-k alone
+ * ranks the undivided values (the rank value |RN(x/b)|^2 is non-decreasing in |x|: the k-th
+ * value and its ties are found exactly) and divides only the kept strings; both paths give
+ * the same strings and coefficients.  For tests comparing the two. */
+int pauli_debug_general_truncation(int on);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,7 @@ struct SelState {
   unsigned long long need;
   int done;
   int pass;
+  int exact;            // 1: never stop early (every digit of the need-th key is fixed)
 };
 
 __device__ __forceinline__ bool matches_prefix(const uint64_t k[3], const SelState& st, int pass) {
@@ -114,7 +115,7 @@ __device__ __forceinline__ void sel_pick_block(SelState* st_p, int pass, unsigne
     int b = top - (t * per + k);
     if (b >= 0 && b == s_sel) {
       const int lo = hi - width;
-      if (h[k] == st.need - s_above || lo == 0) st_p->done = 1;
+      if (lo == 0 || (!st.exact && h[k] == st.need - s_above)) st_p->done = 1;
     }
   }
 }

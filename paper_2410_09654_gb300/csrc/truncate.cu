@@ -11,6 +11,7 @@
 // (the learned truncation ranks by ln|c| - gamma dt wt + z).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -224,7 +225,8 @@ __global__ void __launch_bounds__(256) k_sel_pick(SelState* st_p, int pass, unsi
 __global__ void __launch_bounds__(kTT) k_sel_compact(const Rec* __restrict__ in, const uint64_t* __restrict__ ab,
                                                      int64_t n, const SelState* __restrict__ st_p,
                                                      const ulonglong2* __restrict__ keep, int64_t nkeep,
-                                                     Rec* __restrict__ out, unsigned long long* __restrict__ n_out) {
+                                                     Rec* __restrict__ out, unsigned long long* __restrict__ n_out,
+                                                     int use_div, DivConst dc, int cls) {
   __shared__ TileRes s_res;
   const SelState st = *st_p;
   const int64_t tiles = ceil_div_dev(n, kTile);
@@ -258,6 +260,14 @@ __global__ void __launch_bounds__(kTT) k_sel_compact(const Rec* __restrict__ in,
         }
       }
     }
+    if (use_div) {  // the Lanczos division of the kept strings (rank values were taken before it)
+#pragma unroll
+      for (int k = 0; k < kTI; ++k) {
+        if (!kp[k]) continue;
+        if (cls & 1) r[k].re = div_const(r[k].re, dc);
+        if (cls & 2) r[k].im = div_const(r[k].im, dc);
+      }
+    }
     unsigned long long pos[kTI];
     tile_positions(kp, s_res, n_out, pos);
 #pragma unroll
@@ -266,9 +276,223 @@ __global__ void __launch_bounds__(kTT) k_sel_compact(const Rec* __restrict__ in,
   }
 }
 
+// ---- Lanczos truncation without a division per candidate (single-component FP64 sums,
+// top-k only).  The rank value |RN(x/b)|^2 (rounded square of the rounded quotient) is a
+// non-decreasing function of |x|, so the top-k by it is found from |x| itself: an exact
+// select on the bit pattern of |x| gives the k-th largest x_k; the host finds the interval
+// [g_lo, g_hi] of |x| whose rank value equals that of x_k; the strings in the interval are
+// tied and ordered by key (~v, ~w) exactly as in the plain truncation, those above it are
+// kept.  Only the kept strings are divided (in the compaction).
+
+// |x| of the non-zero component as a 64-bit rank value (non-negative doubles order like
+// their bit patterns), with the histogram of its top digit (warp-aggregated per digit).
+__global__ void __launch_bounds__(kTT) k_abskey(const Rec* __restrict__ in, int64_t n, int cls,
+                                                uint64_t* __restrict__ ab, unsigned* __restrict__ hist0) {
+  __shared__ unsigned s_hist[kBins];
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+    const int64_t i = b0 + lane;  // b0 is uniform across the warp
+    uint32_t dgt = 0xFFFFFFFFu;
+    if (i < n) {
+      const double x = cls == 2 ? in[i].im : in[i].re;
+      const uint64_t g = (uint64_t)__double_as_longlong(x) & ~(1ull << 63);
+      ab[i] = g;
+      dgt = (uint32_t)(g >> (64 - kDigitBits));
+    }
+    const unsigned m = __match_any_sync(0xffffffffu, dgt);
+    if (i < n && lane == __ffs(m) - 1) atomicAdd(&s_hist[dgt], (unsigned)__popc(m));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(&hist0[i], s_hist[i]);
+}
+
+__global__ void k_sel_init_ex(SelState* st, unsigned long long need, int exact, uint64_t prefix0) {
+  SelState z{};
+  z.need = need;
+  z.exact = exact;
+  z.prefix[0] = prefix0;
+  *st = z;
+}
+
+// Strings whose rank value lies in [g_lo, g_hi] (tied with the k-th) take the common rank
+// value g_hi and are listed; those above the interval are counted.
+__global__ void __launch_bounds__(kTT) k_tie_prep(uint64_t* __restrict__ ab, int64_t n, uint64_t g_lo, uint64_t g_hi,
+                                                  uint32_t* __restrict__ list, unsigned long long* __restrict__ n_list,
+                                                  unsigned long long* __restrict__ n_above) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long above = 0;
+  for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+    const int64_t i = b0 + lane;
+    bool tie = false;
+    if (i < n) {
+      const uint64_t g = ab[i];
+      if (g > g_hi) {
+        ++above;
+      } else if (g >= g_lo) {
+        tie = true;
+        ab[i] = g_hi;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, tie);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(n_list, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (tie) list[base + __popc(m & ((1u << lane) - 1))] = (uint32_t)i;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) above += __shfl_down_sync(0xffffffffu, above, d);
+  if (lane == 0 && above) atomicAdd(n_above, above);
+}
+
+// The tie-break digits for a small tie set in one block: the keys (~v, ~w) of the listed
+// strings are held in shared memory and every remaining pass (histogram, pick) runs here.
+constexpr int kTieSmem = 2048;
+__global__ void __launch_bounds__(256) k_sel_tie_block(const Rec* __restrict__ d, const uint32_t* __restrict__ list,
+                                                       const unsigned long long* __restrict__ n_list, uint64_t gkey,
+                                                       SelState* st_p, int pass0) {
+  __shared__ ulonglong2 s_key[kTieSmem];
+  __shared__ unsigned s_hist[kBins];
+  const int T = (int)min(*n_list, (unsigned long long)kTieSmem);  // the host checked T <= kTieSmem
+  for (int j = threadIdx.x; j < T; j += blockDim.x) {
+    const Rec r = d[list[j]];
+    s_key[j] = make_ulonglong2(~r.v, ~r.w);
+  }
+  for (int pass = pass0; pass < kPasses; ++pass) {
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    const SelState st = *st_p;
+    if (st.done) break;  // every thread reads the same state after the barrier
+    for (int j = threadIdx.x; j < T; j += blockDim.x) {
+      const uint64_t k[3] = {gkey, s_key[j].x, s_key[j].y};
+      if (matches_prefix(k, st, pass)) atomicAdd(&s_hist[rank_digit(k, pass)], 1u);
+    }
+    __syncthreads();
+    sel_pick_block(st_p, pass, s_hist);
+    __syncthreads();
+  }
+}
+
 __global__ void k_debug_divide(double* __restrict__ x, int64_t n, DivConst dc) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = div_const(x[i], dc);
+}
+
+}  // namespace
+
+bool g_general_truncation = false;  // test hook: always take the general truncation path
+
+namespace {
+
+// |RN(x/b)|^2 as the truncation computes it (the correctly rounded quotient, then the rounded
+// square), in IEEE double arithmetic on the host; b > 0.
+double sq_of_quotient(double x, double b) {
+  volatile double q = x / b;
+  volatile double r = q * q;
+  return r;
+}
+
+double from_bits(uint64_t g) {
+  double x;
+  std::memcpy(&x, &g, sizeof(x));
+  return x;
+}
+
+constexpr int kFallback = 1 << 20;  // not an error: the caller takes the general path
+
+// Top-k after the Lanczos division for a single-component FP64 sum O of n > k strings,
+// without dividing the candidates (see k_abskey): returns a status, or kFallback when the
+// threshold's rank value is zero or not finite.
+int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor) {
+  cudaStream_t s = O->stream;
+  const int64_t n = O->n;
+  const int nsm = num_sms();
+  auto grid = [&](int64_t m) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, kTT), 8 * nsm)); };
+  Buf<uint64_t> ab;
+  Buf<unsigned> hist;
+  Buf<SelState> st;
+  Buf<uint32_t> list;
+  Buf<unsigned long long> cnt;
+  PS_TRY(ab.alloc((size_t)n, s));
+  PS_TRY(hist.alloc(kBins, s));
+  PS_TRY(st.alloc(2, s));
+  PS_TRY(list.alloc((size_t)n, s));
+  PS_TRY(cnt.alloc(4, s));
+  PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
+  PS_CUDA(cudaMemsetAsync(cnt.p, 0, 4 * sizeof(unsigned long long), s));
+  // stage 1: the exact rank value |x_k| of the k-th largest |x|
+  PS_LAUNCH("k_abskey", s, k_abskey<<<grid(n), kTT, 0, s>>>(O->d, n, a.cls, ab.p, hist.p));
+  PS_LAUNCH("k_sel_init", s, k_sel_init_ex<<<1, 1, 0, s>>>(st.p, (unsigned long long)k, 1, 0ull));
+  PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 0, hist.p));
+  PS_LAUNCH("k_sel_narrow", s, k_sel_narrow<<<grid(n), kTT, 0, s>>>(ab.p, n, st.p, list.p, cnt.p));
+  const int hb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4 * nsm));
+  for (int pass = 1; pass <= 5; ++pass) {  // pass 5 fixes the last bits of |x_k|
+    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list.p, cnt.p, st.p, pass, hist.p));
+    PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, pass, hist.p));
+  }
+  SelState hs;
+  PS_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  const uint64_t gk = hs.prefix[0];
+  const double b = std::fabs(divisor);
+  const double fk = sq_of_quotient(from_bits(gk), b);
+  if (!(fk > 0.0) || !std::isfinite(fk)) return kFallback;
+  // the interval of |x| with the same rank value (the rank value is non-decreasing in |x|)
+  uint64_t lo = gk, hi = 0x7FF0000000000000ull;  // rank value of +inf: inf > fk
+  while (hi - lo > 1) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (sq_of_quotient(from_bits(mid), b) <= fk) lo = mid; else hi = mid;
+  }
+  const uint64_t g_hi = lo;
+  lo = 0;  // rank value 0 < fk
+  hi = gk;
+  while (hi - lo > 1) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (sq_of_quotient(from_bits(mid), b) < fk) lo = mid; else hi = mid;
+  }
+  const uint64_t g_lo = hi;
+  // stage 2: the tied strings by key
+  PS_LAUNCH("k_tie_prep", s, k_tie_prep<<<grid(n), kTT, 0, s>>>(ab.p, n, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
+  unsigned long long hc[3];
+  PS_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  const int64_t T = (int64_t)hc[1], above = (int64_t)hc[2];
+  const int64_t need = k - above;
+  if (need < 1 || need > T) return kFallback;  // cannot happen for a non-decreasing rank value
+  SelState* st2 = st.p + 1;
+  const uint64_t fixed55 = g_hi & ~((1ull << (64 - 5 * kDigitBits)) - 1);  // the digits of passes 0-4
+  PS_LAUNCH("k_sel_init", s, k_sel_init_ex<<<1, 1, 0, s>>>(st2, (unsigned long long)need, 0, fixed55));
+  if (T <= kTieSmem) {
+    PS_LAUNCH("k_sel_tie_block", s, k_sel_tie_block<<<1, 256, 0, s>>>(O->d, list.p, cnt.p + 1, g_hi, st2, 5));
+  } else {
+    for (int pass = 5; pass < kPasses; ++pass) {
+      PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list.p, cnt.p + 1, st2, pass, hist.p));
+      PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st2, pass, hist.p));
+    }
+  }
+  // compaction: kept = above the interval, or tied and at or above the key threshold; the
+  // kept strings are divided here
+  const int64_t cap = above + T;
+  Rec* outb = nullptr;
+  PS_TRY(dev_alloc((void**)&outb, (size_t)std::max<int64_t>(cap, 1) * sizeof(Rec), s));
+  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<grid(n), kTT, 0, s>>>(O->d, ab.p, n, st2, nullptr, 0, outb, cnt.p + 3,
+                                                                      1, a.dc, a.cls));
+  cudaError_t e = cudaGetLastError();
+  unsigned long long nk = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nk, cnt.p + 3, sizeof(nk), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    dev_free(outb, s);
+    set_cuda_error(e, "truncate select");
+    return PS_ERR_CUDA;
+  }
+  return sum_adopt(O, outb, std::max<int64_t>(cap, 1), (int64_t)nk);
 }
 
 }  // namespace
@@ -300,6 +524,14 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   if (use_gamma) {
     const double x = P->gamma * dt;
     for (int wt = 0; wt <= 64; ++wt) a.factor[wt] = std::exp(-(x * (double)wt));
+  }
+  // the Lanczos truncation (division, then top-k alone) of a single-component FP64 sum: ranked
+  // without dividing every candidate
+  if (divisor && use_top && !use_gamma && !use_w && !use_cut && !score && !(keep && keep->n > 0) && !O->f32 &&
+      (a.cls == 1 || a.cls == 2) && *divisor != 0.0 && std::isfinite(*divisor) && O->n > P->top_k &&
+      O->n < (int64_t)0xFFFFFFFF && !g_general_truncation) {
+    const int rc = truncate_div_top(O, P->top_k, a, *divisor);
+    if (rc != kFallback) return rc;
   }
   Rec* cand = nullptr;
   PS_TRY(dev_alloc((void**)&cand, (size_t)O->n * sizeof(Rec), s));
@@ -364,7 +596,7 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   Rec* outb = nullptr;
   int64_t ocap = (int64_t)nc;  // kept <= top_k + |keep| <= nc
   PS_TRY(dev_alloc((void**)&outb, (size_t)std::max<int64_t>(ocap, 1) * sizeof(Rec), s));
-  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<tile_grid((int64_t)nc), kTT, 0, s>>>(cand, ab.p, (int64_t)nc, st.p, keepk.p, nkeep, outb, cnt.p + 1));
+  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<tile_grid((int64_t)nc), kTT, 0, s>>>(cand, ab.p, (int64_t)nc, st.p, keepk.p, nkeep, outb, cnt.p + 1, 0, DivConst{}, 0));
   e = cudaGetLastError();
   unsigned long long nk = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nk, cnt.p + 1, sizeof(nk), cudaMemcpyDeviceToHost, s);
@@ -390,5 +622,10 @@ extern "C" int pauli_debug_divide(double* x, int64_t n, double b, void* cuda_str
   PS_LAUNCH("k_debug_divide", s, ps::k_debug_divide<<<blocks, 256, 0, s>>>(x, n, ps::make_divconst(b)));
   PS_CUDA(cudaGetLastError());
   PS_CUDA(cudaStreamSynchronize(s));
+  return PS_OK;
+}
+
+extern "C" int pauli_debug_general_truncation(int on) {
+  ps::g_general_truncation = on != 0;
   return PS_OK;
 }

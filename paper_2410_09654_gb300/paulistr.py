@@ -113,6 +113,7 @@ def load(build_if_missing: bool = False):
         "pauli_debug_fail_alloc_after": ([I64], ctypes.c_int),
         "pauli_debug_output_hash": ([P, P, I64, P], ctypes.c_int),
         "pauli_debug_mlp_wait": ([ctypes.c_int, I64], ctypes.c_int),
+        "pauli_debug_general_truncation": ([ctypes.c_int], ctypes.c_int),
         "pauli_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "pauli_profile_report": ([ctypes.c_char_p, I64, ctypes.POINTER(I64)], ctypes.c_int),
         "pauli_launch_count": ([], I64),
@@ -466,6 +467,10 @@ def pauli_debug_fail_alloc_after(n: int):
 
 def pauli_debug_mlp_wait(no_products: int = 0, wait_limit: int = 1 << 26):
     _check(load().pauli_debug_mlp_wait(int(no_products), int(wait_limit)), "pauli_debug_mlp_wait")
+
+
+def pauli_debug_general_truncation(on: int = 1):
+    _check(load().pauli_debug_general_truncation(int(on)), "pauli_debug_general_truncation")
 
 
 def pauli_debug_output_hash(v, w) -> np.ndarray:
