@@ -351,6 +351,72 @@ __global__ void __launch_bounds__(kTT) k_tie_prep(uint64_t* __restrict__ ab, int
   if (lane == 0 && above) atomicAdd(n_above, above);
 }
 
+// Second narrowing: the listed candidates whose top `bits` bits of the rank value equal the
+// threshold's (the prefix fixed so far).
+__global__ void __launch_bounds__(kTT) k_sel_renarrow(const uint64_t* __restrict__ ab, const uint32_t* __restrict__ list,
+                                                      const unsigned long long* __restrict__ n_list, int bits,
+                                                      const SelState* __restrict__ st_p, uint32_t* __restrict__ out,
+                                                      unsigned long long* __restrict__ n_out) {
+  const int64_t n = (int64_t)*n_list;
+  const uint64_t want = st_p->prefix[0] >> (64 - bits);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+    const int64_t j = b0 + lane;
+    uint32_t i = 0;
+    bool f = false;
+    if (j < n) {
+      i = list[j];
+      f = (ab[i] >> (64 - bits)) == want;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(n_out, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (f) out[base + __popc(m & ((1u << lane) - 1))] = i;
+    }
+  }
+}
+
+// k_tie_prep over the listed candidates only (the interval lies inside their common prefix).
+__global__ void __launch_bounds__(kTT) k_tie_prep_list(uint64_t* __restrict__ ab, const uint32_t* __restrict__ list,
+                                                       const unsigned long long* __restrict__ n_list, uint64_t g_lo,
+                                                       uint64_t g_hi, uint32_t* __restrict__ ties,
+                                                       unsigned long long* __restrict__ n_ties,
+                                                       unsigned long long* __restrict__ n_above) {
+  const int64_t n = (int64_t)*n_list;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long above = 0;
+  for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+    const int64_t j = b0 + lane;
+    bool tie = false;
+    uint32_t i = 0;
+    if (j < n) {
+      i = list[j];
+      const uint64_t g = ab[i];
+      if (g > g_hi) {
+        ++above;
+      } else if (g >= g_lo) {
+        tie = true;
+        ab[i] = g_hi;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, tie);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(n_ties, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (tie) ties[base + __popc(m & ((1u << lane) - 1))] = i;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) above += __shfl_down_sync(0xffffffffu, above, d);
+  if (lane == 0 && above) atomicAdd(n_above, above);
+}
+
 // The tie-break digits for a small tie set in one block: the keys (~v, ~w) of the listed
 // strings are held in shared memory and every remaining pass (histogram, pick) runs here.
 constexpr int kTieSmem = 2048;
@@ -416,30 +482,37 @@ int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor
   auto grid = [&](int64_t m) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, kTT), 8 * nsm)); };
   Buf<uint64_t> ab;
   Buf<unsigned> hist;
-  Buf<SelState> st;
-  Buf<uint32_t> list;
-  Buf<unsigned long long> cnt;
+  Buf<SelState> st;     // [0] stage 1, [1] stage 2, [2] stage 1 after its second digit
+  Buf<uint32_t> list;   // [0, n): first-digit list, later the tied strings; [n, 2n): second narrowing
+  Buf<unsigned long long> cnt;  // listed, tied, above the interval, kept, second narrowing
   PS_TRY(ab.alloc((size_t)n, s));
   PS_TRY(hist.alloc(kBins, s));
-  PS_TRY(st.alloc(2, s));
-  PS_TRY(list.alloc((size_t)n, s));
-  PS_TRY(cnt.alloc(4, s));
+  PS_TRY(st.alloc(3, s));
+  PS_TRY(list.alloc((size_t)n * 2, s));
+  PS_TRY(cnt.alloc(5, s));
   PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
-  PS_CUDA(cudaMemsetAsync(cnt.p, 0, 4 * sizeof(unsigned long long), s));
-  // stage 1: the exact rank value |x_k| of the k-th largest |x|
+  PS_CUDA(cudaMemsetAsync(cnt.p, 0, 5 * sizeof(unsigned long long), s));
+  uint32_t* list2 = list.p + n;
+  // stage 1: the exact rank value |x_k| of the k-th largest |x|; the candidates are narrowed
+  // to those sharing the threshold's first digit, then its first two digits (22 bits)
   PS_LAUNCH("k_abskey", s, k_abskey<<<grid(n), kTT, 0, s>>>(O->d, n, a.cls, ab.p, hist.p));
   PS_LAUNCH("k_sel_init", s, k_sel_init_ex<<<1, 1, 0, s>>>(st.p, (unsigned long long)k, 1, 0ull));
   PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 0, hist.p));
   PS_LAUNCH("k_sel_narrow", s, k_sel_narrow<<<grid(n), kTT, 0, s>>>(ab.p, n, st.p, list.p, cnt.p));
   const int hb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4 * nsm));
-  for (int pass = 1; pass <= 5; ++pass) {  // pass 5 fixes the last bits of |x_k|
-    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list.p, cnt.p, st.p, pass, hist.p));
+  PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list.p, cnt.p, st.p, 1, hist.p));
+  PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 1, hist.p));
+  PS_CUDA(cudaMemcpyAsync(st.p + 2, st.p, sizeof(SelState), cudaMemcpyDeviceToDevice, s));
+  constexpr int kBits2 = 2 * kDigitBits;
+  PS_LAUNCH("k_sel_narrow", s, k_sel_renarrow<<<hb, kTT, 0, s>>>(ab.p, list.p, cnt.p, kBits2, st.p, list2, cnt.p + 4));
+  for (int pass = 2; pass <= 5; ++pass) {  // pass 5 fixes the last bits of |x_k|
+    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list2, cnt.p + 4, st.p, pass, hist.p));
     PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, pass, hist.p));
   }
-  SelState hs;
-  PS_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  SelState hs[3];
+  PS_CUDA(cudaMemcpyAsync(hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
   PS_CUDA(cudaStreamSynchronize(s));
-  const uint64_t gk = hs.prefix[0];
+  const uint64_t gk = hs[0].prefix[0];
   const double b = std::fabs(divisor);
   const double fk = sq_of_quotient(from_bits(gk), b);
   if (!(fk > 0.0) || !std::isfinite(fk)) return kFallback;
@@ -457,12 +530,22 @@ int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor
     if (sq_of_quotient(from_bits(mid), b) < fk) lo = mid; else hi = mid;
   }
   const uint64_t g_lo = hi;
-  // stage 2: the tied strings by key
-  PS_LAUNCH("k_tie_prep", s, k_tie_prep<<<grid(n), kTT, 0, s>>>(ab.p, n, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
+  // stage 2: the tied strings by key.  When the interval shares the threshold's first two
+  // digits, only the second list can hold tied strings or strings above the interval inside
+  // that prefix; the strings above the prefix are counted by the select itself (k minus the
+  // rank still needed after the second digit).
+  const bool in_prefix = (g_lo >> (64 - kBits2)) == (gk >> (64 - kBits2)) && (g_hi >> (64 - kBits2)) == (gk >> (64 - kBits2));
+  int64_t above_prefix = 0;
+  if (in_prefix) {
+    above_prefix = k - (int64_t)hs[2].need;
+    PS_LAUNCH("k_tie_prep", s, k_tie_prep_list<<<hb, kTT, 0, s>>>(ab.p, list2, cnt.p + 4, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
+  } else {
+    PS_LAUNCH("k_tie_prep", s, k_tie_prep<<<grid(n), kTT, 0, s>>>(ab.p, n, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
+  }
   unsigned long long hc[3];
   PS_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
   PS_CUDA(cudaStreamSynchronize(s));
-  const int64_t T = (int64_t)hc[1], above = (int64_t)hc[2];
+  const int64_t T = (int64_t)hc[1], above = above_prefix + (int64_t)hc[2];
   const int64_t need = k - above;
   if (need < 1 || need > T) return kFallback;  // cannot happen for a non-decreasing rank value
   SelState* st2 = st.p + 1;
@@ -481,8 +564,9 @@ int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor
   const int64_t cap = above + T;
   Rec* outb = nullptr;
   PS_TRY(dev_alloc((void**)&outb, (size_t)std::max<int64_t>(cap, 1) * sizeof(Rec), s));
-  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<grid(n), kTT, 0, s>>>(O->d, ab.p, n, st2, nullptr, 0, outb, cnt.p + 3,
-                                                                      1, a.dc, a.cls));
+  const int cb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTile), 8 * nsm));
+  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<cb, kTT, 0, s>>>(O->d, ab.p, n, st2, nullptr, 0, outb, cnt.p + 3, 1, a.dc,
+                                                                 a.cls));
   cudaError_t e = cudaGetLastError();
   unsigned long long nk = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nk, cnt.p + 3, sizeof(nk), cudaMemcpyDeviceToHost, s);
