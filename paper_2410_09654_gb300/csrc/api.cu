@@ -358,19 +358,33 @@ int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, 
     sp.nsrc = 1;
   }
   PS_TRY(merge_into(sp, O_cur->stream, &A.s));
-  double n2 = 0.0;
-  PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2));
-  double b = std::sqrt(n2);
-  *b_out = b;
-  if (!std::isfinite(b)) return PS_ERR_NONFINITE;
-  if (b == 0.0) return PS_ERR_KRYLOV_EXHAUSTED;
   pauli_trunc_policy p{-1, 0.0, 0, 0.0, 0};
   if (policy) {
     p.max_weight = policy->max_weight;
     p.cutoff = policy->cutoff;
     p.top_k = policy->top_k;
   }
-  PS_TRY(truncate_run(&A.s, &p, nullptr, 0.0, &b));
+  // b_n = ||A||; for the division-free truncation the norm's first pass also writes the rank
+  // keys |x| of A (one read of A for both)
+  const bool keys = lanczos_keys_eligible(&A.s, &p);
+  Buf<uint64_t> ab;
+  Buf<unsigned> hist;
+  double n2 = 0.0;
+  if (keys) {
+    PS_TRY(ab.alloc((size_t)A.s.n, A.s.stream));
+    PS_TRY(hist.alloc(kKeyBins, A.s.stream));
+    PS_TRY(exact_norm2_keys(A.s.d, A.s.n, A.s.stream, &n2, A.s.cls, ab.p, hist.p));
+  } else {
+    PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2));
+  }
+  double b = std::sqrt(n2);
+  *b_out = b;
+  if (!std::isfinite(b)) return PS_ERR_NONFINITE;
+  if (b == 0.0) return PS_ERR_KRYLOV_EXHAUSTED;
+  if (keys)
+    PS_TRY(truncate_lanczos_keys(&A.s, &p, b, ab.p, hist.p));
+  else
+    PS_TRY(truncate_run(&A.s, &p, nullptr, 0.0, &b));
   // rotate: O_prev <- O_cur, O_cur <- O_n
   swap_contents(O_prev, O_cur);
   swap_contents(O_cur, &A.s);

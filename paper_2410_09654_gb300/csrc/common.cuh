@@ -395,6 +395,13 @@ void record_merge_stats(const pauli_merge_stats& st);
 int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor,
                  const double* score = nullptr);
 int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring = 0);
+// The Lanczos truncation of a single-component FP64 sum by top-k alone ranks the undivided
+// values |x| (truncate.cu).  Its rank keys (bit patterns of |x|) and their first-digit
+// histogram (kKeyBins counters) can be produced by the first pass of the norm.
+constexpr int kKeyBins = 2048;
+bool lanczos_keys_eligible(const pauli_sum* A, const pauli_trunc_policy* P);
+int exact_norm2_keys(const Rec* d, int64_t n, cudaStream_t s, double* out, int cls, uint64_t* ab, unsigned* hist);
+int truncate_lanczos_keys(pauli_sum* A, const pauli_trunc_policy* P, double divisor, uint64_t* ab, unsigned* hist);
 int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cudaStream_t s, double* re, double* im);
 int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw, int64_t nq, cudaStream_t s,
                  double* re, double* im);

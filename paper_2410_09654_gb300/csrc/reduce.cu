@@ -35,6 +35,38 @@ __global__ void k_norm_top(const Rec* __restrict__ d, int64_t n, int* top) {
   if ((threadIdx.x & 31) == 0) atomicMax(top, m);
 }
 
+// The same pass for a single-component sum whose Lanczos truncation ranks |x| (component
+// cls): it also writes the rank key of every string (the bit pattern of |x|) and the
+// histogram of its top 11 bits (warp-aggregated per bin).
+__global__ void __launch_bounds__(kRedThreads) k_norm_top_key(const Rec* __restrict__ d, int64_t n, int* top, int cls,
+                                                              uint64_t* __restrict__ ab, unsigned* __restrict__ hist0) {
+  __shared__ unsigned s_hist[kKeyBins];
+  for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  int m = -100000;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+    const int64_t i = b0 + lane;  // b0 is uniform across the warp
+    uint32_t dgt = 0xFFFFFFFFu;
+    if (i < n) {
+      const Rec r = d[i];
+      m = max(m, max(prod_top(r.re, r.re), prod_top(r.im, r.im)));
+      m = max(m, max(nonfinite_top(r.re), nonfinite_top(r.im)));
+      const uint64_t g = (uint64_t)__double_as_longlong(cls == kClsImag ? r.im : r.re) & ~(1ull << 63);
+      ab[i] = g;
+      dgt = (uint32_t)(g >> 53);
+    }
+    const unsigned mm = __match_any_sync(0xffffffffu, dgt);
+    if (i < n && lane == __ffs(mm) - 1) atomicAdd(&s_hist[dgt], (unsigned)__popc(mm));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if (lane == 0) atomicMax(top, m);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(&hist0[i], s_hist[i]);
+}
+
 // TS: a translation-symmetric generator on a ring of `ring` sites; a string of period p
 // stands for ring/p copies of each translate, so its |c|^2 is added ring/p times.
 template <bool TS>
@@ -149,7 +181,9 @@ __global__ void __launch_bounds__(kRedThreads) k_tp_acc(const Rec* __restrict__ 
 
 }  // namespace
 
-int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) {
+namespace {
+int exact_norm2_impl(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring, int cls, uint64_t* ab,
+                     unsigned* hist) {
   *out = 0.0;
   if (n == 0) return PS_OK;
   Buf<long long> acc;  // [0..7] window, [8..8+kFullDigits) full
@@ -161,7 +195,10 @@ int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) 
   // synchronise the stream)
   PS_CUDA(cudaMemsetAsync(ints.p, 0x80, 2 * sizeof(int), s));
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kRedThreads), 4 * num_sms()));
-  PS_LAUNCH("k_norm_top", s, k_norm_top<<<blocks, kRedThreads, 0, s>>>(d, n, ints.p));
+  if (ab)
+    PS_LAUNCH("k_norm_top", s, k_norm_top_key<<<blocks, kRedThreads, 0, s>>>(d, n, ints.p, cls, ab, hist));
+  else
+    PS_LAUNCH("k_norm_top", s, k_norm_top<<<blocks, kRedThreads, 0, s>>>(d, n, ints.p));
   PS_CUDA(cudaGetLastError());
   if (ring > 0)
     PS_LAUNCH("k_norm_acc", s, k_norm_acc<true><<<blocks, kRedThreads, 0, s>>>(d, n, ints.p, acc.p, acc.p + kWinDigits,
@@ -183,6 +220,17 @@ int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) 
   std::vector<long long> full(h.begin() + kWinDigits, h.end());
   *out = round_exact(full, h.data(), hi[1]);
   return PS_OK;
+}
+}  // namespace
+
+int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) {
+  return exact_norm2_impl(d, n, s, out, ring, 0, nullptr, nullptr);
+}
+
+// ab: n rank keys; hist: kKeyBins counters, zeroed here.
+int exact_norm2_keys(const Rec* d, int64_t n, cudaStream_t s, double* out, int cls, uint64_t* ab, unsigned* hist) {
+  PS_CUDA(cudaMemsetAsync(hist, 0, kKeyBins * sizeof(unsigned), s));
+  return exact_norm2_impl(d, n, s, out, 0, cls, ab, hist);
 }
 
 int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cudaStream_t s, double* re, double* im) {

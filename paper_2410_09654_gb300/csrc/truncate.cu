@@ -452,7 +452,9 @@ __global__ void k_debug_divide(double* __restrict__ x, int64_t n, DivConst dc) {
 
 }  // namespace
 
+static_assert(kBins == kKeyBins, "the norm's key histogram has the select's first-digit bins");
 bool g_general_truncation = false;  // test hook: always take the general truncation path
+bool lanczos_keys_eligible(const pauli_sum* A, const pauli_trunc_policy* P);
 
 namespace {
 
@@ -475,7 +477,10 @@ constexpr int kFallback = 1 << 20;  // not an error: the caller takes the genera
 // Top-k after the Lanczos division for a single-component FP64 sum O of n > k strings,
 // without dividing the candidates (see k_abskey): returns a status, or kFallback when the
 // threshold's rank value is zero or not finite.
-int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor) {
+// ab_in / hist_in: the rank keys and their first-digit histogram when the norm's first pass
+// has produced them (else computed here).
+int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor, uint64_t* ab_in = nullptr,
+                     unsigned* hist_in = nullptr) {
   cudaStream_t s = O->stream;
   const int64_t n = O->n;
   const int nsm = num_sms();
@@ -485,29 +490,35 @@ int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor
   Buf<SelState> st;     // [0] stage 1, [1] stage 2, [2] stage 1 after its second digit
   Buf<uint32_t> list;   // [0, n): first-digit list, later the tied strings; [n, 2n): second narrowing
   Buf<unsigned long long> cnt;  // listed, tied, above the interval, kept, second narrowing
-  PS_TRY(ab.alloc((size_t)n, s));
-  PS_TRY(hist.alloc(kBins, s));
+  if (!ab_in) {
+    PS_TRY(ab.alloc((size_t)n, s));
+    PS_TRY(hist.alloc(kBins, s));
+  }
+  uint64_t* abp = ab_in ? ab_in : ab.p;
+  unsigned* histp = ab_in ? hist_in : hist.p;
   PS_TRY(st.alloc(3, s));
   PS_TRY(list.alloc((size_t)n * 2, s));
   PS_TRY(cnt.alloc(5, s));
-  PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
   PS_CUDA(cudaMemsetAsync(cnt.p, 0, 5 * sizeof(unsigned long long), s));
   uint32_t* list2 = list.p + n;
   // stage 1: the exact rank value |x_k| of the k-th largest |x|; the candidates are narrowed
   // to those sharing the threshold's first digit, then its first two digits (22 bits)
-  PS_LAUNCH("k_abskey", s, k_abskey<<<grid(n), kTT, 0, s>>>(O->d, n, a.cls, ab.p, hist.p));
+  if (!ab_in) {
+    PS_CUDA(cudaMemsetAsync(hist.p, 0, kBins * sizeof(unsigned), s));
+    PS_LAUNCH("k_abskey", s, k_abskey<<<grid(n), kTT, 0, s>>>(O->d, n, a.cls, ab.p, hist.p));
+  }
   PS_LAUNCH("k_sel_init", s, k_sel_init_ex<<<1, 1, 0, s>>>(st.p, (unsigned long long)k, 1, 0ull));
-  PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 0, hist.p));
-  PS_LAUNCH("k_sel_narrow", s, k_sel_narrow<<<grid(n), kTT, 0, s>>>(ab.p, n, st.p, list.p, cnt.p));
+  PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 0, histp));
+  PS_LAUNCH("k_sel_narrow", s, k_sel_narrow<<<grid(n), kTT, 0, s>>>(abp, n, st.p, list.p, cnt.p));
   const int hb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4 * nsm));
-  PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list.p, cnt.p, st.p, 1, hist.p));
-  PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 1, hist.p));
+  PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, abp, list.p, cnt.p, st.p, 1, histp));
+  PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, 1, histp));
   PS_CUDA(cudaMemcpyAsync(st.p + 2, st.p, sizeof(SelState), cudaMemcpyDeviceToDevice, s));
   constexpr int kBits2 = 2 * kDigitBits;
-  PS_LAUNCH("k_sel_narrow", s, k_sel_renarrow<<<hb, kTT, 0, s>>>(ab.p, list.p, cnt.p, kBits2, st.p, list2, cnt.p + 4));
+  PS_LAUNCH("k_sel_narrow", s, k_sel_renarrow<<<hb, kTT, 0, s>>>(abp, list.p, cnt.p, kBits2, st.p, list2, cnt.p + 4));
   for (int pass = 2; pass <= 5; ++pass) {  // pass 5 fixes the last bits of |x_k|
-    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list2, cnt.p + 4, st.p, pass, hist.p));
-    PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, pass, hist.p));
+    PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, abp, list2, cnt.p + 4, st.p, pass, histp));
+    PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st.p, pass, histp));
   }
   SelState hs[3];
   PS_CUDA(cudaMemcpyAsync(hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -538,9 +549,9 @@ int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor
   int64_t above_prefix = 0;
   if (in_prefix) {
     above_prefix = k - (int64_t)hs[2].need;
-    PS_LAUNCH("k_tie_prep", s, k_tie_prep_list<<<hb, kTT, 0, s>>>(ab.p, list2, cnt.p + 4, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
+    PS_LAUNCH("k_tie_prep", s, k_tie_prep_list<<<hb, kTT, 0, s>>>(abp, list2, cnt.p + 4, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
   } else {
-    PS_LAUNCH("k_tie_prep", s, k_tie_prep<<<grid(n), kTT, 0, s>>>(ab.p, n, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
+    PS_LAUNCH("k_tie_prep", s, k_tie_prep<<<grid(n), kTT, 0, s>>>(abp, n, g_lo, g_hi, list.p, cnt.p + 1, cnt.p + 2));
   }
   unsigned long long hc[3];
   PS_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -555,8 +566,8 @@ int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor
     PS_LAUNCH("k_sel_tie_block", s, k_sel_tie_block<<<1, 256, 0, s>>>(O->d, list.p, cnt.p + 1, g_hi, st2, 5));
   } else {
     for (int pass = 5; pass < kPasses; ++pass) {
-      PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, ab.p, list.p, cnt.p + 1, st2, pass, hist.p));
-      PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st2, pass, hist.p));
+      PS_LAUNCH("k_sel_hist", s, k_sel_hist<<<hb, 256, 0, s>>>(O->d, abp, list.p, cnt.p + 1, st2, pass, histp));
+      PS_LAUNCH("k_sel_pick", s, k_sel_pick<<<1, 256, 0, s>>>(st2, pass, histp));
     }
   }
   // compaction: kept = above the interval, or tied and at or above the key threshold; the
@@ -565,7 +576,7 @@ int truncate_div_top(pauli_sum* O, int64_t k, const TruncArgs& a, double divisor
   Rec* outb = nullptr;
   PS_TRY(dev_alloc((void**)&outb, (size_t)std::max<int64_t>(cap, 1) * sizeof(Rec), s));
   const int cb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTile), 8 * nsm));
-  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<cb, kTT, 0, s>>>(O->d, ab.p, n, st2, nullptr, 0, outb, cnt.p + 3, 1, a.dc,
+  PS_LAUNCH("k_sel_compact", s, k_sel_compact<<<cb, kTT, 0, s>>>(O->d, abp, n, st2, nullptr, 0, outb, cnt.p + 3, 1, a.dc,
                                                                  a.cls));
   cudaError_t e = cudaGetLastError();
   unsigned long long nk = 0;
@@ -611,9 +622,8 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
   }
   // the Lanczos truncation (division, then top-k alone) of a single-component FP64 sum: ranked
   // without dividing every candidate
-  if (divisor && use_top && !use_gamma && !use_w && !use_cut && !score && !(keep && keep->n > 0) && !O->f32 &&
-      (a.cls == 1 || a.cls == 2) && *divisor != 0.0 && std::isfinite(*divisor) && O->n > P->top_k &&
-      O->n < (int64_t)0xFFFFFFFF && !g_general_truncation) {
+  if (divisor && !score && !(keep && keep->n > 0) && lanczos_keys_eligible(O, P) && *divisor != 0.0 &&
+      std::isfinite(*divisor)) {
     const int rc = truncate_div_top(O, P->top_k, a, *divisor);
     if (rc != kFallback) return rc;
   }
@@ -692,6 +702,31 @@ int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* kee
     return PS_ERR_CUDA;
   }
   return sum_adopt(O, outb, std::max<int64_t>(ocap, 1), (int64_t)nk);
+}
+
+// The conditions of the division-free Lanczos truncation, the divisor aside: top-k alone
+// (no weight filter, cutoff or dissipation), FP64, single-component values, more strings than
+// kept, 32-bit candidate indices.
+bool lanczos_keys_eligible(const pauli_sum* A, const pauli_trunc_policy* P) {
+  const int cls = A->cls ? A->cls : kClsComplex;
+  return P && P->top_k > 0 && P->max_weight < 0 && !(P->cutoff > 0.0) && P->gamma == 0.0 && !A->f32 &&
+         (cls == kClsReal || cls == kClsImag) && A->n > P->top_k && A->n < (int64_t)0xFFFFFFFF &&
+         !g_general_truncation;
+}
+
+// The Lanczos truncation O = trunc(A / divisor) with rank keys already produced by the norm's
+// first pass (exact_norm2_keys); the general path when the conditions do not hold.
+int truncate_lanczos_keys(pauli_sum* A, const pauli_trunc_policy* P, double divisor, uint64_t* ab, unsigned* hist) {
+  if (lanczos_keys_eligible(A, P) && divisor != 0.0 && std::isfinite(divisor)) {
+    TruncArgs a{};
+    a.max_weight = -1;
+    a.use_div = 1;
+    a.dc = make_divconst(divisor);
+    a.cls = A->cls;
+    const int rc = truncate_div_top(A, P->top_k, a, divisor, ab, hist);
+    if (rc != kFallback) return rc;
+  }
+  return truncate_run(A, P, nullptr, 0.0, &divisor);
 }
 
 int round_f32(pauli_sum* s) { return s->f32 ? truncate_run(s, nullptr, nullptr, 0.0, nullptr) : PS_OK; }
