@@ -1307,11 +1307,15 @@ constexpr int kMaskBits = 32 * kMaskWords;
 
 // Geometry of a ranked merge with W mask words: W = 8 (256 order codes) keeps 1024 slots and
 // passes of up to kCap entries; W = 16 (512 codes, for larger H) halves both so that two
-// blocks still fit an SM.
+// blocks still fit an SM.  W = 0 is the chained rank for any number of order codes: no masks;
+// each slot chains its entries, and an entry's rank is the number of entries of its chain with
+// a smaller order code (a string's order codes are distinct), so the geometry stays at 1024
+// slots and kCap entries whatever the number of codes.  kBits is then the number of run-length
+// classes of the phase-4 ordering (longer runs share the last class).
 template <int W>
 struct RankGeom {
   static constexpr int kWords = W;
-  static constexpr int kBits = 32 * W;
+  static constexpr int kBits = W == 0 ? 64 : 32 * W;
   static constexpr int kTab = W <= 8 ? kTable : kTable / 2;
   static constexpr int kEnt = W <= 8 ? kCap : kCap / 2;
 };
@@ -1325,6 +1329,7 @@ struct PfGeom {
   static constexpr int kBins = W <= 6 ? 256 : 1;  // bins of a prefetchable group
   static constexpr bool kOn = W <= 6;
 };
+constexpr uint32_t kNone32 = 0xFFFFFFFFu;
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)), "l"(gsrc)
@@ -1348,14 +1353,16 @@ struct RankSmem {
   uint64_t pfcpre[PfGeom<W>::kBins + 1];      // its bins' entry prefix
   uint32_t pf_g;                              // the group whose header and bins are in pf*, or kNone
   ulonglong2 key[G::kTab];
-  uint32_t mask[G::kTab][G::kWords];  // order codes present per slot
+  uint32_t mask[W > 0 ? G::kTab : 1][W > 0 ? G::kWords : 1];  // order codes present per slot (W > 0)
+  uint32_t head[W == 0 ? G::kTab : 1];            // W = 0: last entry of the slot's chain, or kNone32
+  uint16_t enext[W == 0 ? G::kEnt : 1];           // W = 0: previous entry of the same slot, or kNone16
   uint16_t pre[G::kTab];
   uint16_t ulist[G::kTab];
   uint16_t run[G::kTab];        // start of the slot's run in seg[]
   uint16_t rlen[G::kTab];       // length of the slot's run (popcount of its mask)
   double ere[G::kEnt];
   double eim[S ? 1 : G::kEnt];
-  uint16_t ebit[G::kEnt];         // order bit of the entry (kNone16: pre operand)
+  uint16_t ebit[G::kEnt];         // order bit (W = 0: order code) of the entry (kNone16: pre operand)
   uint16_t eslot[G::kEnt];
   double seg[G::kEnt];            // contributions ordered by (string, order code)
   double segim[S ? 1 : G::kEnt];
@@ -1380,8 +1387,12 @@ __device__ __forceinline__ void rank_release(RankSmem<S, W>& s, ulonglong2 sent)
   for (uint32_t u = threadIdx.x; u < n_u; u += kMergeThreads) {
     const uint32_t slot = s.ulist[u];
     s.key[slot] = sent;
+    if constexpr (W == 0) {
+      s.head[slot] = kNone32;
+    } else {
 #pragma unroll
-    for (int w = 0; w < G::kWords; ++w) s.mask[slot][w] = 0u;
+      for (int w = 0; w < G::kWords; ++w) s.mask[slot][w] = 0u;
+    }
     s.pre[slot] = kNone16;
   }
   __syncthreads();
@@ -1410,8 +1421,12 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
   const uint32_t ngroups = *a.ngroups;
   for (int i = tid; i < G::kTab; i += kMergeThreads) {
     s.key[i] = a.sent_lo;
+    if constexpr (W == 0) {
+      s.head[i] = kNone32;
+    } else {
 #pragma unroll
-    for (int w = 0; w < G::kWords; ++w) s.mask[i][w] = 0u;
+      for (int w = 0; w < G::kWords; ++w) s.mask[i][w] = 0u;
+    }
     s.pre[i] = kNone16;
   }
   if (tid == 0) {
@@ -1579,7 +1594,12 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
             } else {
               const uint32_t bit = code_bit(code, a.nH);
               s.ebit[e] = (uint16_t)bit;
-              atomicOr(&s.mask[slot][bit >> 5], 1u << (bit & 31));
+              if constexpr (W == 0) {
+                const uint32_t prev = atomicExch(&s.head[slot], e);
+                s.enext[e] = prev == kNone32 ? kNone16 : (uint16_t)prev;
+              } else {
+                atomicOr(&s.mask[slot][bit >> 5], 1u << (bit & 31));
+              }
             }
           }
         }
@@ -1608,8 +1628,16 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         uint32_t c = 0, slot = 0;
         if (u < n_u) {
           slot = s.ulist[u];
+          if constexpr (W == 0) {
+            for (uint32_t y = s.head[slot]; y != kNone32;) {
+              ++c;
+              const uint16_t nx = s.enext[y];
+              y = nx == kNone16 ? kNone32 : (uint32_t)nx;
+            }
+          } else {
 #pragma unroll
-          for (int w = 0; w < G::kWords; ++w) c += __popc(s.mask[slot][w]);
+            for (int w = 0; w < G::kWords; ++w) c += __popc(s.mask[slot][w]);
+          }
         }
         // warp-inclusive scan of c, one shared-memory reservation per warp
         uint32_t incl = c;
@@ -1624,7 +1652,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         if (u < n_u) {
           s.run[slot] = (uint16_t)(wb + incl - c);
           s.rlen[slot] = (uint16_t)c;
-          atomicAdd(&s_hist[G::kBits - c], 1u);  // longest runs first
+          atomicAdd(&s_hist[G::kBits - min(c, (uint32_t)G::kBits)], 1u);  // longest runs first
         }
       }
       __syncthreads();
@@ -1665,11 +1693,20 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
         const uint32_t bit = s.ebit[e];
         if (bit == kNone16) continue;
         const uint32_t slot = s.eslot[e];
-        const uint32_t wi = bit >> 5;
-        uint32_t rank = __popc(s.mask[slot][wi] & ((1u << (bit & 31)) - 1u));
+        uint32_t rank = 0;
+        if constexpr (W == 0) {  // entries of the chain with a smaller order code
+          for (uint32_t y = s.head[slot]; y != kNone32;) {
+            rank += s.ebit[y] < bit ? 1u : 0u;
+            const uint16_t nx = s.enext[y];
+            y = nx == kNone16 ? kNone32 : (uint32_t)nx;
+          }
+        } else {
+          const uint32_t wi = bit >> 5;
+          rank = __popc(s.mask[slot][wi] & ((1u << (bit & 31)) - 1u));
 #pragma unroll
-        for (int w = 0; w < G::kWords; ++w)
-          if ((uint32_t)w < wi) rank += __popc(s.mask[slot][w]);
+          for (int w = 0; w < G::kWords; ++w)
+            if ((uint32_t)w < wi) rank += __popc(s.mask[slot][w]);
+        }
         const uint32_t pos = s.run[slot] + rank;
         s.seg[pos] = s.ere[e];
         if constexpr (!S) s.segim[pos] = s.eim[e];
@@ -1684,7 +1721,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       for (uint32_t u = tid; u < n_u; u += kMergeThreads) {
         const uint32_t slot = s.ulist[u];
         const uint32_t n = s.rlen[slot];
-        s_order[atomicAdd(&s_hist[G::kBits - n], 1u)] = (uint16_t)slot;
+        s_order[atomicAdd(&s_hist[G::kBits - min(n, (uint32_t)G::kBits)], 1u)] = (uint16_t)slot;
       }
       __syncthreads();
       if (pf_first) {  // the next group's entries into L2; its header and bins are ready
@@ -1902,12 +1939,15 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   // ranked merge when the order codes fit the slot masks (256 codes; 512 with the wide
   // geometry), chained merge otherwise
   const bool ranked = ncode_h + sp.nsrc <= kMaskBits;
-  const bool ranked_wide = !ranked && !has_ts && ncode_h + sp.nsrc <= RankGeom<16>::kBits;
+  // beyond 256 codes: single-component merges rank by slot chains (any number of codes),
+  // complex ones by 512-bit masks up to 512 codes, else the chained merge
+  const bool chained_rank = !ranked && !has_ts && structured;
+  const bool ranked_wide = !ranked && !chained_rank && !has_ts && ncode_h + sp.nsrc <= RankGeom<16>::kBits;
   const bool full = structured && ranked && (uint64_t)bound_total * sizeof(Contrib) <= kFullBudget;
   if (has_ts && !full) return PS_ERR_INVALID;  // representatives need full records: one component
   // FP32 arithmetic with compensated sums: single-component ranked merges
   const int f32c = out->f32 == 2 ? 1 : 0;
-  if (f32c && !(structured && (ranked || ranked_wide))) return PS_ERR_INVALID;
+  if (f32c && !(structured && (ranked || ranked_wide || chained_rank))) return PS_ERR_INVALID;
   // per-instance H coefficients ride on the table emission of full records
   if (sp.hbatch && nX > 0 && !(full && sp.nH <= kMaskBits && !sp.product)) return PS_ERR_INVALID;
 
@@ -2119,10 +2159,14 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     sm = structured ? sizeof(RankSmem<true, 8>) : sizeof(RankSmem<false, 8>);
     kern = full ? k_merge_rank<true, true, 8> : (structured ? k_merge_rank<true, false, 8> : k_merge_rank<false, false, 8>);
     kname = full ? "k_merge_rank_f" : (structured ? "k_merge_rank_s" : "k_merge_rank");
+  } else if (chained_rank) {
+    sm = sizeof(RankSmem<true, 0>);
+    kern = k_merge_rank<true, false, 0>;
+    kname = "k_merge_rank_c";
   } else if (ranked_wide) {
-    sm = structured ? sizeof(RankSmem<true, 16>) : sizeof(RankSmem<false, 16>);
-    kern = structured ? k_merge_rank<true, false, 16> : k_merge_rank<false, false, 16>;
-    kname = structured ? "k_merge_rank_ws" : "k_merge_rank_w";
+    sm = sizeof(RankSmem<false, 16>);
+    kern = k_merge_rank<false, false, 16>;
+    kname = "k_merge_rank_w";
   } else {
     sm = structured ? sizeof(MergeSmem<true>) : sizeof(MergeSmem<false>);
     kern = structured ? k_merge<true> : k_merge<false>;
