@@ -527,20 +527,23 @@ def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3,
                       fixed_geometry: bool = False):
     """All instances in one tagged sum (pauli_batch_rk4_step) against the single-instance
     path looped over a sample of the instances (scaled to all): instance-steps/s and
-    products/s of both."""
+    products/s of both.  Under N ranks each rank takes the instances b with b mod N = rank
+    (independent problems, no exchange); rates are the ranks' sums over the slowest rank."""
     import torch
-    from paper_2410_09654_gb300 import inputs as I, paulistr as ps
+    from paper_2410_09654_gb300 import inputs as I, paulistr as ps, replicas as R
     n, shift = 32, 32
     N = shift + 9
+    mine = R.instance_share(n_inst)       # this rank's instances (global ids)
     W = [0.5 if b <= 170 else (2.0 if b <= 341 else 5.0) for b in range(n_inst)]
-    Hs = [I.random_field_xxz_chain(n, W[b], b).arrays() for b in range(n_inst)]
-    caps = np.array([1 << (8 + b % 7) for b in range(n_inst)], np.int64)
+    Hs = [I.random_field_xxz_chain(n, W[b], b).arrays() for b in mine]
+    caps = np.array([1 << (8 + b % 7) for b in mine], np.int64)
+    m = len(mine)
     hcoef = np.stack([h[2] for h in Hs])
     Hc = ps.PauliSum.from_arrays(N, Hs[0][0], Hs[0][1], np.ones(len(Hs[0][0])), np.zeros(len(Hs[0][0])))
     B = ps.PauliBatch(Hc, hcoef, shift, caps)
     z = I.single(n, "Z", 16).arrays()
-    v = np.array([int(z[0][0]) | (b << shift) for b in range(n_inst)], np.uint64)
-    O = ps.PauliSum.from_arrays(N, v, np.zeros(n_inst, np.uint64), np.ones(n_inst), np.zeros(n_inst))
+    v = np.array([int(z[0][0]) | (j << shift) for j in range(m)], np.uint64)
+    O = ps.PauliSum.from_arrays(N, v, np.zeros(m, np.uint64), np.ones(m), np.zeros(m))
     for _ in range(ramp):
         ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
     tune = None if fixed_geometry else ps.pauli_autotune_commutator(Hc, O, reps=2)  # batched commutators
@@ -552,9 +555,10 @@ def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3,
         prod += 4 * len(Hs[0][0]) * len(O)
         ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
     torch.cuda.synchronize()
-    t_b = (time.perf_counter() - t0) / timed
+    t_b = R.reduce_scalar((time.perf_counter() - t0) / timed, "max")
+    prod = R.reduce_scalar(prod, "sum")
     # the single-instance path on a sample spread over the caps and disorder strengths
-    pick = np.linspace(0, n_inst - 1, loop_sample).astype(int)
+    pick = np.linspace(0, m - 1, min(loop_sample, m)).astype(int)
     t_loop, prod_loop = 0.0, 0
     for b in pick:
         H = ps.PauliSum.from_arrays(n, *Hs[b])
@@ -569,18 +573,21 @@ def batched_instances(stream, n_inst: int = 512, ramp: int = 12, timed: int = 3,
             ps.pauli_rk4_step(H, Ob, 0.05, pol)
         torch.cuda.synchronize()
         t_loop += time.perf_counter() - t0
-    scale = n_inst / loop_sample
-    t_loop_all = t_loop / timed * scale  # seconds per step of all instances, looped
-    return {"workload": BATCH_WORKLOAD, "instances": n_inst, "strings": int(sizes.sum()),
-            "strings_per_instance_min_max": [int(sizes.min()), int(sizes.max())],
+    scale = m / len(pick)
+    t_loop_all = R.reduce_scalar(t_loop / timed * scale, "max")  # seconds per step of this rank's instances, looped
+    prod_loop = R.reduce_scalar(prod_loop, "sum")
+    t_loop = R.reduce_scalar(t_loop, "max")
+    return {"workload": BATCH_WORKLOAD, "instances": n_inst, "strings": int(R.reduce_scalar(sizes.sum(), "sum")),
+            "strings_per_instance_min_max": [int(R.reduce_scalar(sizes.min(), "min")), int(R.reduce_scalar(sizes.max(), "max"))],
             "batched": {"ms_per_step": 1e3 * t_b, "instance_steps_per_s": n_inst / t_b,
                         "products_per_s": prod / timed / t_b},
             "looped_single_instance": {"ms_per_step": 1e3 * t_loop_all, "instance_steps_per_s": n_inst / t_loop_all,
                                        "products_per_s": prod_loop / t_loop * 1.0,
                                        "sample": f"{loop_sample} instances spread over the caps, scaled to {n_inst}"},
             "speedup": t_loop_all / t_b, "merge_geometry_autotuned": tune,
-            "not_built": "one persistent graph-captured launch and the autotuner: each step is a sequence of "
-                         "launches with host synchronisation on data-dependent sizes"}
+            "ranks": R.world(), "instances_per_rank": "b mod ranks = rank",
+            "not_built": "one persistent graph-captured launch: each step is a sequence of launches with host "
+                         "synchronisation on data-dependent sizes"}
 
 
 BATCH_FULL_WORKLOAD = ("the same 512 realisations with the description's caps 2^(14 + instance mod 7) (16384 to "
@@ -591,15 +598,17 @@ BATCH_FULL_WORKLOAD = ("the same 512 realisations with the description's caps 2^
 
 def batched_instances_full(stream, n_inst: int = 512, ramp: int = 16, timed: int = 2, group_cap: int = 1 << 22):
     """The batched realisations at the full per-instance caps, grouped by cap, against the
-    single-instance path looped over two instances of every cap (scaled to all)."""
+    single-instance path looped over two instances of every cap (scaled to all).  Under N
+    ranks each rank takes the instances b with b mod N = rank."""
     import torch
-    from paper_2410_09654_gb300 import inputs as I, paulistr as ps
+    from paper_2410_09654_gb300 import inputs as I, paulistr as ps, replicas as R
     n, shift = 32, 32
     W = [0.5 if b <= 170 else (2.0 if b <= 341 else 5.0) for b in range(n_inst)]
     caps = np.array([1 << (14 + b % 7) for b in range(n_inst)], np.int64)
     z = I.single(n, "Z", 16).arrays()
+    mine = R.instance_share(n_inst)
     # groups: instances sorted by cap, filled greedily up to group_cap strings of caps
-    order = sorted(range(n_inst), key=lambda b: (caps[b], b))
+    order = sorted(mine, key=lambda b: (caps[b], b))
     groups, cur, tot = [], [], 0
     for b in order:
         if cur and tot + caps[b] > group_cap:
@@ -631,12 +640,18 @@ def batched_instances_full(stream, n_inst: int = 512, ramp: int = 16, timed: int
             prod += 4 * nh * len(O)
             ps.pauli_batch_rk4_step(B, Hc, O, 0.05, trim_stages=1)
     torch.cuda.synchronize()
-    t_b = (time.perf_counter() - t0) / timed
+    t_b = R.reduce_scalar((time.perf_counter() - t0) / timed, "max")
+    prod = R.reduce_scalar(prod, "sum")
+    strings = R.reduce_scalar(strings, "sum")
+    n_groups = R.reduce_scalar(len(groups), "sum")
     del runs
     # single-instance path: two instances of every cap class, scaled by the class sizes
     t_loop_all, prod_loop, t_loop = 0.0, 0, 0.0
+    per_class = {}
     for c in range(7):
-        members = [b for b in range(n_inst) if b % 7 == c]
+        members = [b for b in mine if b % 7 == c]
+        if not members:
+            continue
         t_c = 0.0
         for b in (members[0], members[len(members) // 2]):
             H = ps.PauliSum.from_arrays(n, *I.random_field_xxz_chain(n, W[b], b).arrays())
@@ -654,12 +669,17 @@ def batched_instances_full(stream, n_inst: int = 512, ramp: int = 16, timed: int
             t_c += dt_
             t_loop += dt_
         t_loop_all += t_c / 2 / timed * len(members)
-    return {"workload": BATCH_FULL_WORKLOAD, "instances": n_inst, "groups": len(groups), "strings": int(strings),
+        per_class[str(1 << (14 + c))] = 1e3 * t_c / 2 / timed * len(members)
+    t_loop_all = R.reduce_scalar(t_loop_all, "max")
+    prod_loop = R.reduce_scalar(prod_loop, "sum")
+    t_loop = R.reduce_scalar(t_loop, "max")
+    return {"workload": BATCH_FULL_WORKLOAD, "instances": n_inst, "groups": int(n_groups), "strings": int(strings),
             "batched": {"ms_per_step": 1e3 * t_b, "instance_steps_per_s": n_inst / t_b,
                         "products_per_s": prod / timed / t_b},
             "looped_single_instance": {"ms_per_step": 1e3 * t_loop_all, "instance_steps_per_s": n_inst / t_loop_all,
                                        "products_per_s": prod_loop / t_loop,
-                                       "sample": "two instances per cap class, scaled to the 512"},
+                                       "sample": "two instances per cap class, scaled to the 512",
+                                       "ms_per_step_by_cap": per_class},
             "speedup": t_loop_all / t_b}
 
 

@@ -357,22 +357,34 @@ int pauli_lanczos_step(const pauli_sum* H, pauli_sum* O_prev, pauli_sum* O_cur, 
     sp.src[0] = source(O_prev, Cx{-b_prev, 0.0});
     sp.nsrc = 1;
   }
+  // A = [H, O_n] - b_{n-1} O_{n-1}; a single-component merge also writes the rank keys |x| of
+  // A and the exact norm's exponent bound from its output stage
+  Buf<int> ktop;
+  PS_TRY(ktop.alloc(1, O_cur->stream));
+  PS_CUDA(cudaMemsetAsync(ktop.p, 0x80, sizeof(int), O_cur->stream));  // below every bound
+  uint64_t* mkeys = nullptr;
+  sp.keys_out = &mkeys;
+  sp.keys_top = ktop.p;
   PS_TRY(merge_into(sp, O_cur->stream, &A.s));
+  Buf<uint64_t> ab;
+  if (mkeys) ab.adopt(mkeys, (size_t)A.s.n, A.s.stream);
   pauli_trunc_policy p{-1, 0.0, 0, 0.0, 0};
   if (policy) {
     p.max_weight = policy->max_weight;
     p.cutoff = policy->cutoff;
     p.top_k = policy->top_k;
   }
-  // b_n = ||A||; for the division-free truncation the norm's first pass also writes the rank
-  // keys |x| of A (one read of A for both)
+  // b_n = ||A||: from the merge's keys (one read of 8 bytes per string, which also gives the
+  // division-free truncation its first-digit histogram), else from the records, where the
+  // norm's first pass writes the keys when the truncation can use them
   const bool keys = lanczos_keys_eligible(&A.s, &p);
-  Buf<uint64_t> ab;
   Buf<unsigned> hist;
   double n2 = 0.0;
-  if (keys) {
+  if (keys) PS_TRY(hist.alloc(kKeyBins, A.s.stream));
+  if (ab.p) {
+    PS_TRY(exact_norm2_keys_top(ab.p, A.s.n, ktop.p, A.s.stream, &n2, keys ? hist.p : nullptr));
+  } else if (keys) {
     PS_TRY(ab.alloc((size_t)A.s.n, A.s.stream));
-    PS_TRY(hist.alloc(kKeyBins, A.s.stream));
     PS_TRY(exact_norm2_keys(A.s.d, A.s.n, A.s.stream, &n2, A.s.cls, ab.p, hist.p));
   } else {
     PS_TRY(exact_norm2(A.s.d, A.s.n, A.s.stream, &n2));

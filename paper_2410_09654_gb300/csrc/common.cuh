@@ -67,6 +67,13 @@ struct Buf {
     p = nullptr;
     n = 0;
   }
+  // take ownership of a buffer from dev_alloc
+  void adopt(T* q, size_t count, cudaStream_t stream) {
+    reset();
+    p = q;
+    n = count;
+    s = stream;
+  }
 };
 
 }  // namespace ps
@@ -380,6 +387,15 @@ struct MergeSpec {
   // coefficients only fix the class.  Needs the table emission of full records.
   const double* hbatch = nullptr;
   int hb_shift = 0;
+  // Rank keys of a single-component output (optional): when keys_out is set and the merge runs
+  // in single-component mode on a ranked merge, its output stage also writes, per output
+  // string in storage order, the bit pattern of |x| of its non-zero component into a device
+  // array it allocates (*keys_out; the caller frees it with dev_free), and raises *keys_top
+  // (device int, set to a value below every bound beforehand) to the exponent bound of the
+  // exact norm, max prod_top(x, x) (kTopInf / kTopNaN for a non-finite x).  *keys_out stays
+  // null when the merge cannot provide them.
+  uint64_t** keys_out = nullptr;
+  int* keys_top = nullptr;
 };
 int merge_run(const MergeSpec& spec, cudaStream_t s, pauli_sum* out);
 int autotune_commutator(const MergeSpec& sp, pauli_sum* out, int reps, int* best_bin, int* best_quota,
@@ -395,6 +411,10 @@ void record_merge_stats(const pauli_merge_stats& st);
 int truncate_run(pauli_sum* O, const pauli_trunc_policy* P, const pauli_sum* keep, double dt, const double* divisor,
                  const double* score = nullptr);
 int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring = 0);
+// The exact norm of a single-component sum from its rank keys (bit patterns of |x|, see
+// MergeSpec::keys_out) and the exponent bound top (device int); with hist non-null, the keys'
+// first-digit histogram (kKeyBins counters, zeroed here) in the same pass.
+int exact_norm2_keys_top(const uint64_t* ab, int64_t n, const int* top, cudaStream_t s, double* out, unsigned* hist);
 // The Lanczos truncation of a single-component FP64 sum by top-k alone ranks the undivided
 // values |x| (truncate.cu).  Its rank keys (bit patterns of |x|) and their first-digit
 // histogram (kKeyBins counters) can be produced by the first pass of the norm.

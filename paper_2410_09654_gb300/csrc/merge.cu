@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "exact_sum.cuh"
 
 namespace ps {
 
@@ -768,6 +769,8 @@ struct MergeArgs {
   double post_s;          // post = post_s * i^(post_q - u(acc))
   int post_q;             // u(post) + u(acc)
   int out_imag;           // the output's non-zero component: 0 real, 1 imaginary
+  uint64_t* okeys;        // optional (single-component mode): per output, the bit pattern of |x|
+  int* otop;              // with okeys: max prod_top(x, x) over the outputs (exact norm's bound)
 };
 
 // Shared memory of one merge block.  S: single-component mode (no imaginary array).
@@ -1419,6 +1422,7 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const uint32_t ngroups = *a.ngroups;
+  int top_acc = -100000;  // okeys: this thread's largest exponent bound
   for (int i = tid; i < G::kTab; i += kMergeThreads) {
     s.key[i] = a.sent_lo;
     if constexpr (W == 0) {
@@ -1826,6 +1830,10 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
           if constexpr (S) {
             const double x = s.ore[i];
             a.out[ob + i] = a.out_imag ? Rec{k.x, k.y, 0.0, x} : Rec{k.x, k.y, x, 0.0};
+            if (a.okeys) {  // the norm's first pass, folded in: rank key and exponent bound
+              a.okeys[ob + i] = (uint64_t)__double_as_longlong(x) & ~(1ull << 63);
+              top_acc = max(top_acc, max(exact::prod_top(x, x), exact::nonfinite_top(x)));
+            }
           } else {
             a.out[ob + i] = Rec{k.x, k.y, s.ore[i], s.oim[i]};
           }
@@ -1834,6 +1842,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) k_merge_rank(MergeArgs a) {
       __syncthreads();
       rank_release(s, sent);
      }
+    }
+  }
+  if constexpr (S) {
+    if (a.okeys) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) top_acc = max(top_acc, __shfl_down_sync(0xffffffffu, top_acc, o));
+      if (lane == 0 && top_acc > -100000) atomicMax(a.otop, top_acc);
     }
   }
 }
@@ -1886,6 +1901,7 @@ void record_merge_stats(const pauli_merge_stats& st) {
 }
 
 int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
+  if (sp.keys_out) *sp.keys_out = nullptr;
   PS_TRY(upload_hash_tables());
   if (sp.nH > kMaxH || sp.nsrc > 4) return PS_ERR_INVALID;
   const int64_t nX = (sp.X && sp.nH > 0) ? sp.nX : 0;
@@ -2172,24 +2188,58 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     kern = structured ? k_merge<true> : k_merge<false>;
     kname = structured ? "k_merge_s" : "k_merge";
   }
-  PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  // rank keys and the norm's exponent bound from the output stage (single-component ranked
+  // merges): the caller's norm then reads 8 bytes per string instead of two passes over records
+  uint64_t* okeys = nullptr;
+  const bool ranked_s = structured && (ranked || chained_rank);  // a k_merge_rank<true, ...> runs
+  if (sp.keys_out && sp.keys_top && ranked_s) {
+    const int rk = dev_alloc((void**)&okeys, (size_t)out_cap * sizeof(uint64_t), s);
+    if (rk != PS_OK) {
+      dev_free(outbuf, s);
+      return rk;
+    }
+    a.okeys = okeys;
+    a.otop = sp.keys_top;
+  }
+  auto fail = [&](int rc) {
+    if (okeys) dev_free(okeys, s);
+    dev_free(outbuf, s);
+    return rc;
+  };
+  cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int per_sm = 0;
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMergeThreads, sm));
+  if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMergeThreads, sm);
+  if (ce != cudaSuccess) {
+    set_cuda_error(ce, "merge launch setup");
+    return fail(PS_ERR_CUDA);
+  }
   int grid = std::max(1, per_sm) * nsm;
   PS_LAUNCH(kname, s, kern<<<grid, kMergeThreads, sm, s>>>(a));
-  PS_CUDA(cudaGetLastError());
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) {
+    set_cuda_error(ce, "merge launch");
+    return fail(PS_ERR_CUDA);
+  }
   unsigned long long hres[2];
   unsigned hmisc[3];
   int herr = 0;
-  PS_CUDA(cudaMemcpyAsync(hres, counters.p, sizeof(hres), cudaMemcpyDeviceToHost, s));
-  PS_CUDA(cudaMemcpyAsync(hmisc, misc.p, sizeof(hmisc), cudaMemcpyDeviceToHost, s));
-  PS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PS_CUDA(cudaStreamSynchronize(s));
-  if (herr) {
-    dev_free(outbuf, s);
-    return (herr & 2) ? PS_ERR_TABLE_FULL : PS_ERR_CAPACITY;
+  ce = cudaMemcpyAsync(hres, counters.p, sizeof(hres), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hmisc, misc.p, sizeof(hmisc), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    set_cuda_error(ce, "merge results");
+    return fail(PS_ERR_CUDA);
   }
-  PS_TRY(sum_adopt(out, outbuf, out_cap, (int64_t)hres[1]));
+  if (herr) return fail((herr & 2) ? PS_ERR_TABLE_FULL : PS_ERR_CAPACITY);
+  {
+    const int ra = sum_adopt(out, outbuf, out_cap, (int64_t)hres[1]);
+    if (ra != PS_OK) {
+      if (okeys) dev_free(okeys, s);
+      return ra;
+    }
+  }
+  if (okeys) *sp.keys_out = okeys;
   out->cls = out_cls;
   st.merged = (int64_t)hres[1];
   st.groups = hmisc[1];

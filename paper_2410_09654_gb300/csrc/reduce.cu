@@ -89,6 +89,47 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_acc(const Rec* __restrict_
   block_flush(acc, gwin);
 }
 
+// The accumulation pass from rank keys: g = bit pattern of |x| of a single-component sum's
+// non-zero component, so x^2 = |x|^2 is added exactly (the other component is zero); with
+// HIST, the histogram of the keys' top 11 bits in the same read (warp-aggregated per bin).
+template <bool HIST>
+__global__ void __launch_bounds__(kRedThreads) k_norm_acc_keys(const uint64_t* __restrict__ ab, int64_t n,
+                                                               const int* top, long long* gwin, long long* full,
+                                                               int* wlo_out, unsigned* __restrict__ hist0) {
+  __shared__ unsigned s_hist[HIST ? kKeyBins : 1];
+  if constexpr (HIST) {
+    for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+  }
+  const int t = *top;
+  const bool acc_on = !(t <= -100000 || t >= kTopInf);  // uniform over the grid
+  const int wlo = ((t - 190 + kBias) & ~31) - kBias;
+  if (acc_on && blockIdx.x == 0 && threadIdx.x == 0) *wlo_out = wlo;
+  Win acc{{0, 0, 0, 0}};
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+    const int64_t i = b0 + lane;  // b0 is uniform across the warp
+    uint32_t dgt = 0xFFFFFFFFu;
+    if (i < n) {
+      const uint64_t g = ab[i];
+      const double x = __longlong_as_double((long long)g);
+      if (acc_on) add_product(acc, x, x, wlo, full);
+      dgt = (uint32_t)(g >> 53);
+    }
+    if constexpr (HIST) {
+      const unsigned mm = __match_any_sync(0xffffffffu, dgt);
+      if (i < n && lane == __ffs(mm) - 1) atomicAdd(&s_hist[dgt], (unsigned)__popc(mm));
+    }
+  }
+  if (acc_on) block_flush(acc, gwin);
+  if constexpr (HIST) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x)
+      if (s_hist[i]) atomicAdd(&hist0[i], s_hist[i]);
+  }
+}
+
 // ---------------------------------------------------------------- trace product
 // Table of B's keys (empty = all ones; the all-ones key itself is kept aside in *ones_idx).
 __global__ void k_tp_build(const Rec* __restrict__ B, int64_t n, ulonglong2* tkey, int64_t* tidx, uint64_t tmask,
@@ -222,6 +263,37 @@ int exact_norm2_impl(const Rec* d, int64_t n, cudaStream_t s, double* out, int r
   return PS_OK;
 }
 }  // namespace
+
+int exact_norm2_keys_top(const uint64_t* ab, int64_t n, const int* top, cudaStream_t s, double* out, unsigned* hist) {
+  *out = 0.0;
+  if (hist) PS_CUDA(cudaMemsetAsync(hist, 0, kKeyBins * sizeof(unsigned), s));
+  if (n == 0) return PS_OK;
+  Buf<long long> acc;  // [0..7] window, [8..8+kFullDigits) full
+  Buf<int> wlo;
+  PS_TRY(acc.alloc(kWinDigits + kFullDigits, s));
+  PS_TRY(wlo.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(acc.p, 0, (kWinDigits + kFullDigits) * sizeof(long long), s));
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kRedThreads), 4 * num_sms()));
+  if (hist)
+    PS_LAUNCH("k_norm_acc", s, k_norm_acc_keys<true><<<blocks, kRedThreads, 0, s>>>(ab, n, top, acc.p, acc.p + kWinDigits, wlo.p, hist));
+  else
+    PS_LAUNCH("k_norm_acc", s, k_norm_acc_keys<false><<<blocks, kRedThreads, 0, s>>>(ab, n, top, acc.p, acc.p + kWinDigits, wlo.p, nullptr));
+  PS_CUDA(cudaGetLastError());
+  std::vector<long long> h(kWinDigits + kFullDigits);
+  int hi[2];
+  PS_CUDA(cudaMemcpyAsync(h.data(), acc.p, h.size() * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaMemcpyAsync(&hi[0], top, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaMemcpyAsync(&hi[1], wlo.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  if (hi[0] <= -100000) return PS_OK;
+  if (hi[0] >= kTopInf) {
+    *out = hi[0] == kTopNaN ? std::nan("") : HUGE_VAL;
+    return PS_OK;
+  }
+  std::vector<long long> full(h.begin() + kWinDigits, h.end());
+  *out = round_exact(full, h.data(), hi[1]);
+  return PS_OK;
+}
 
 int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) {
   return exact_norm2_impl(d, n, s, out, ring, 0, nullptr, nullptr);

@@ -15,14 +15,32 @@ def _dist():
     return dist if dist.is_available() and dist.is_initialized() else None
 
 
+def world() -> int:
+    dist = _dist()
+    return 1 if dist is None else dist.get_world_size()
+
+
+def rank() -> int:
+    dist = _dist()
+    return 0 if dist is None else dist.get_rank()
+
+
+def instance_share(n_inst: int, r: int | None = None, w: int | None = None) -> list[int]:
+    """The independent instances (disorder realisations) rank r runs out of n_inst: every
+    instance b with b mod w == r, so that the caps, which cycle with b, spread evenly."""
+    r = rank() if r is None else r
+    w = world() if w is None else w
+    return [b for b in range(n_inst) if b % w == r]
+
+
 def reduce_scalar(x: float, op: str, device: str = "cuda") -> float:
-    """x reduced over all ranks ("max" or "sum"); x itself without a process group."""
+    """x reduced over all ranks ("max", "min" or "sum"); x itself without a process group."""
     dist = _dist()
     if dist is None or dist.get_world_size() == 1:
         return float(x)
     import torch
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "min": dist.ReduceOp.MIN, "sum": dist.ReduceOp.SUM}[op])
     return float(t.item())
 
 

@@ -84,3 +84,19 @@ def test_reference_arm_json_contract():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_instance_share_partitions_the_instances():
+    # the batched realisations are split over ranks without an exchange: every instance on
+    # exactly one rank, shares of equal size up to one, and every cap class (b mod 7) on each
+    from paper_2410_09654_gb300 import replicas as R
+    n = 512
+    for w in (1, 2, 3, 4, 8):
+        shares = [R.instance_share(n, r, w) for r in range(w)]
+        flat = sorted(b for sh in shares for b in sh)
+        assert flat == list(range(n))
+        sizes = [len(sh) for sh in shares]
+        assert max(sizes) - min(sizes) <= 1
+        for sh in shares:
+            assert {b % 7 for b in sh} == set(range(7))
+    assert R.instance_share(n) == list(range(n))  # one process: every instance
