@@ -37,7 +37,9 @@ MergeSource source(const pauli_sum* p, Cx alpha) {
 }
 
 // k = i[H, X] (rot = 1) or [H, X] (rot = 0) into out.
-int commutator_into(const pauli_sum* H, const pauli_sum* X, int rot, pauli_sum* out) {
+// keys (optional): receives the output's rank keys |x| when the merge can write them (see
+// MergeSpec::keys_out; null otherwise), owned by the caller.
+int commutator_into(const pauli_sum* H, const pauli_sum* X, int rot, pauli_sum* out, uint64_t** keys = nullptr) {
   MergeSpec sp;
   sp.H = H->d;
   sp.nH = (int)H->n;
@@ -46,6 +48,13 @@ int commutator_into(const pauli_sum* H, const pauli_sum* X, int rot, pauli_sum* 
   sp.rot = rot;
   sp.clsH = H->cls;
   sp.clsX = X->cls;
+  Buf<int> top;
+  if (keys) {
+    PS_TRY(top.alloc(1, out->stream));
+    PS_CUDA(cudaMemsetAsync(top.p, 0x80, sizeof(int), out->stream));
+    sp.keys_out = keys;
+    sp.keys_top = top.p;
+  }
   return merge_into(sp, out->stream, out);
 }
 
@@ -260,9 +269,21 @@ int rk4_impl(const pauli_sum* H, pauli_sum* O, double dt, const pauli_trunc_poli
   Tmp k1(O), k2(O), k3(O), k4(O), X(O);
   auto L = [&](const pauli_sum* in, pauli_sum* k) -> int {
     NvtxRange r("k_j = i[H, X]");
-    PS_TRY(commutator_into(H, in, 1, k));
-    if (trim) PS_TRY(truncate_run(k, &stage, nullptr, dt, nullptr));
-    return PS_OK;
+    if (!trim) return commutator_into(H, in, 1, k);
+    // the stage trim is top-k alone: on a single-component k_j it ranks the rank keys |x| that
+    // the merge writes (the division-free top-k of the Lanczos step with divisor 1, which keeps
+    // the same strings as the general path), else the general path
+    uint64_t* keys = nullptr;
+    PS_TRY(commutator_into(H, in, 1, k, &keys));
+    Buf<uint64_t> kb;
+    if (keys) kb.adopt(keys, (size_t)k->n, k->stream);
+    if (kb.p && k->n > stage.top_k) {
+      Buf<unsigned> hist;
+      PS_TRY(hist.alloc(kKeyBins, k->stream));
+      PS_TRY(key_first_digits(kb.p, k->n, k->stream, hist.p));
+      return truncate_top_keys(k, &stage, kb.p, hist.p);
+    }
+    return truncate_run(k, &stage, nullptr, dt, nullptr);
   };
   auto stage_input = [&](const pauli_sum* k, double a) -> int {  // X = O + a k
     NvtxRange r("stage input");

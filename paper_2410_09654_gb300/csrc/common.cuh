@@ -415,6 +415,8 @@ int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring =
 // MergeSpec::keys_out) and the exponent bound top (device int); with hist non-null, the keys'
 // first-digit histogram (kKeyBins counters, zeroed here) in the same pass.
 int exact_norm2_keys_top(const uint64_t* ab, int64_t n, const int* top, cudaStream_t s, double* out, unsigned* hist);
+// The first-digit histogram (kKeyBins counters, zeroed here) of n rank keys, without a norm.
+int key_first_digits(const uint64_t* ab, int64_t n, cudaStream_t s, unsigned* hist);
 // The Lanczos truncation of a single-component FP64 sum by top-k alone ranks the undivided
 // values |x| (truncate.cu).  Its rank keys (bit patterns of |x|) and their first-digit
 // histogram (kKeyBins counters) can be produced by the first pass of the norm.
@@ -422,6 +424,8 @@ constexpr int kKeyBins = 2048;
 bool lanczos_keys_eligible(const pauli_sum* A, const pauli_trunc_policy* P);
 int exact_norm2_keys(const Rec* d, int64_t n, cudaStream_t s, double* out, int cls, uint64_t* ab, unsigned* hist);
 int truncate_lanczos_keys(pauli_sum* A, const pauli_trunc_policy* P, double divisor, uint64_t* ab, unsigned* hist);
+// Top-k alone from the merge's rank keys (the RK4 stage trim); the general path otherwise.
+int truncate_top_keys(pauli_sum* A, const pauli_trunc_policy* P, uint64_t* ab, unsigned* hist);
 int exact_trace_product(const Rec* A, int64_t na, const Rec* B, int64_t nb, cudaStream_t s, double* re, double* im);
 int coefficients(const Rec* O, int64_t n, const uint64_t* qv, const uint64_t* qw, int64_t nq, cudaStream_t s,
                  double* re, double* im);

@@ -295,6 +295,18 @@ int exact_norm2_keys_top(const uint64_t* ab, int64_t n, const int* top, cudaStre
   return PS_OK;
 }
 
+int key_first_digits(const uint64_t* ab, int64_t n, cudaStream_t s, unsigned* hist) {
+  PS_CUDA(cudaMemsetAsync(hist, 0, kKeyBins * sizeof(unsigned), s));
+  if (n == 0) return PS_OK;
+  Buf<int> top;  // below every bound: the pass only counts
+  PS_TRY(top.alloc(1, s));
+  PS_CUDA(cudaMemsetAsync(top.p, 0x80, sizeof(int), s));
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kRedThreads), 4 * num_sms()));
+  PS_LAUNCH("k_key_hist", s, k_norm_acc_keys<true><<<blocks, kRedThreads, 0, s>>>(ab, n, top.p, nullptr, nullptr, nullptr, hist));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
 int exact_norm2(const Rec* d, int64_t n, cudaStream_t s, double* out, int ring) {
   return exact_norm2_impl(d, n, s, out, ring, 0, nullptr, nullptr);
 }

@@ -729,6 +729,27 @@ int truncate_lanczos_keys(pauli_sum* A, const pauli_trunc_policy* P, double divi
   return truncate_run(A, P, nullptr, 0.0, &divisor);
 }
 
+// Top-k alone (the RK4 stage trim) of a single-component sum from the rank keys |x| that its
+// merge wrote: the division-free top-k above with divisor 1 (x / 1 = x, and RN(x^2) is the
+// general path's |c|^2 of a single-component string), also for FP32 sums, whose stored values
+// are FP32 numbers already; the general path when the conditions do not hold.
+int truncate_top_keys(pauli_sum* A, const pauli_trunc_policy* P, uint64_t* ab, unsigned* hist) {
+  const int cls = A->cls ? A->cls : kClsComplex;
+  const bool ok = P && P->top_k > 0 && P->max_weight < 0 && !(P->cutoff > 0.0) && P->gamma == 0.0 &&
+                  (cls == kClsReal || cls == kClsImag) && A->n > P->top_k && A->n < (int64_t)0xFFFFFFFF &&
+                  !g_general_truncation && ab && hist;
+  if (ok) {
+    TruncArgs a{};
+    a.max_weight = -1;
+    a.use_div = 1;
+    a.dc = make_divconst(1.0);
+    a.cls = A->cls;
+    const int rc = truncate_div_top(A, P->top_k, a, 1.0, ab, hist);
+    if (rc != kFallback) return rc;
+  }
+  return truncate_run(A, P, nullptr, 0.0, nullptr);
+}
+
 int round_f32(pauli_sum* s) { return s->f32 ? truncate_run(s, nullptr, nullptr, 0.0, nullptr) : PS_OK; }
 
 }  // namespace ps
