@@ -1925,7 +1925,9 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     return PS_OK;
   }
   const MergeGeom geom = geometry_for(bound_total);
-  const int bits = choose_bits(bound_total, geom.bin_target);
+  // without a product operand the bound is the exact entry count, which fills a bin to the
+  // target and leaves no room in a pass for the bin's neighbours: quarter-size bins then
+  const int bits = choose_bits(bound_total, nX > 0 ? geom.bin_target : std::max(64, geom.bin_target / 4));
   const uint32_t nbins = 1u << bits;
   const int nsm = num_sms();
   auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
