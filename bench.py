@@ -62,7 +62,61 @@ def parse():
                    help="only the Lanczos headline (profiling runs): no RK4, lattice or pattern lines")
     p.add_argument("--merge-geometry", default=None,
                    help="BIN_TARGET,QUOTA: fix the merge geometry instead of tuning it (profiling runs)")
+    p.add_argument("--lattice-only", action="store_true",
+                   help="only the 8x8 lattice RK4 line (profiling runs), at --lattice-cap strings")
+    p.add_argument("--lattice-cap", type=int, default=1 << 23)
+    p.add_argument("--profile-window", action="store_true",
+                   help="cudaProfilerStart/Stop around the first timed step (ncu --profile-from-start off)")
     return p.parse_args()
+
+
+def lattice_only(args):
+    """The 2D workload alone (profiling runs): ramp to the cap, one untimed step, then the timed
+    steps (the first inside the profiler window when asked), then the same steps again from the
+    same state with per-kernel events."""
+    import torch
+    from paper_2410_09654_gb300 import inputs as I, paulistr as ps
+    ps.load(build_if_missing=True)
+    if args.merge_geometry:
+        bt, q = (int(x) for x in args.merge_geometry.split(","))
+        ps.pauli_merge_geometry_fix(bt, q)
+    cap = args.lattice_cap
+    Hl = ps.PauliSum.from_arrays(N_SITES, *I.heisenberg_2d(8, 8).arrays())
+    Ol = ps.PauliSum.from_arrays(N_SITES, *I.single(N_SITES, "Z", 28).arrays())
+    pol = ps.policy(top_k=cap, gamma=0.1, trim_stages=1)
+    ramp = 0
+    for i in range(40):
+        ps.pauli_rk4_step(Hl, Ol, 0.02, pol)
+        ramp += 1
+        if len(Ol) >= cap and i >= 24:
+            break
+    ps.pauli_rk4_step(Hl, Ol, 0.02, pol)
+    start = Ol.copy()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in range(args.steps):
+        if j == 0 and args.profile_window:
+            torch.cuda.profiler.start()
+        ps.pauli_rk4_step(Hl, Ol, 0.02, pol)
+        if j == 0 and args.profile_window:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    Ol = start
+    ps.pauli_profile_enable(True)
+    for j in range(args.steps):
+        ps.pauli_rk4_step(Hl, Ol, 0.02, pol)
+    prof = ps.pauli_profile_report()
+    ps.pauli_profile_enable(False)
+    print(json.dumps({"workload": LATTICE_WORKLOAD.replace("2^23", f"{cap}"), "profile_only": True,
+                      "ramp_steps": ramp, "steps": args.steps, "ms_per_step": ms, "size": len(Ol),
+                      "kernels_per_step_ms": {k: round(v[1] / args.steps, 4)
+                                              for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}), flush=True)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -184,6 +238,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.lattice_only:
+        lattice_only(args)
         return
     import torch
     import torch.distributed as dist
