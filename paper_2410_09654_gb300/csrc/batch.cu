@@ -9,6 +9,7 @@
 // the truncation cap (a top-k per instance, selected in one pass sequence for all).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -20,6 +21,7 @@ struct pauli_batch {
   int nH;
   cudaStream_t stream;
   double* hcoef;             // device [n_inst][nH]
+  double* huni;              // device [nH]: a term's coefficient when every instance has it, else NaN
   std::vector<int64_t> cap;  // per-instance cap (<= 0: none)
 };
 
@@ -67,30 +69,102 @@ __global__ void __launch_bounds__(kBT) k_bnorm(const Rec* __restrict__ d, int64_
     if (s_acc[i] != 0.0) atomicAdd(&acc[i], s_acc[i]);
 }
 
-// |c|^2 bit pattern of every string (non-negative doubles order like their bits).
-__global__ void k_bkeys(const Rec* __restrict__ d, int64_t n, uint64_t* __restrict__ ab) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const Rec r = d[i];
-    const double a = is_zero(r.re) ? 0.0 : __dmul_rn(r.re, r.re);
-    const double b = is_zero(r.im) ? 0.0 : __dmul_rn(r.im, r.im);
-    ab[i] = (uint64_t)__double_as_longlong(add_rn(a, b));
+// Rank keys (|c|^2 bit patterns: non-negative doubles order like their bits), instance tags
+// and per-instance string counts in one read of the records (the tags of the library's own merges are in range: every step validates them first).
+__global__ void __launch_bounds__(kBT) k_bkeys_tags(const Rec* __restrict__ d, int64_t n, int shift, int n_inst,
+                                                    uint64_t* __restrict__ ab, uint16_t* __restrict__ tag,
+                                                    unsigned long long* __restrict__ cnt) {
+  extern __shared__ unsigned long long s_cnt[];
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    uint32_t b = 0xFFFFFFFFu;
+    if (i < n) {
+      const Rec r = d[i];
+      const double x = is_zero(r.re) ? 0.0 : __dmul_rn(r.re, r.re);
+      const double y = is_zero(r.im) ? 0.0 : __dmul_rn(r.im, r.im);
+      ab[i] = (uint64_t)__double_as_longlong(add_rn(x, y));
+      b = inst_of(r, shift);
+      tag[i] = (uint16_t)b;
+    }
+    // one shared-memory add per instance present in the warp (few instances: hot counters)
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (i < n && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[b], (unsigned long long)__popc(peers));
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
 }
 
 // One digit pass for every instance still selecting: hist[b][digit] over the strings whose
-// rank key matches b's prefix.
-__global__ void k_bhist(const Rec* __restrict__ d, const uint64_t* __restrict__ ab, int64_t n, int shift,
-                        const SelState* __restrict__ st, const int* __restrict__ act, int pass,
-                        unsigned* __restrict__ hist) {
+// rank key matches b's prefix; over all strings (list null) or over a candidate list.  The
+// record is read only for the digits beyond the |c|^2 bits.  One global add per distinct
+// (instance, digit) in the warp: with few instances and clustered exponents the plain adds
+// pile up on a few counters.
+__global__ void __launch_bounds__(kBT) k_bhist(const Rec* __restrict__ d, const uint64_t* __restrict__ ab,
+                                               const uint16_t* __restrict__ tag, int64_t n,
+                                               const uint32_t* __restrict__ list,
+                                               const unsigned long long* __restrict__ nlist,
+                                               const SelState* __restrict__ st, const int* __restrict__ act, int pass,
+                                               unsigned* __restrict__ hist) {
   const bool need_key = (pass + 1) * kDigitBits > 64;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const Rec r = d[i];
-    const uint32_t b = inst_of(r, shift);
-    if (!act[b] || st[b].done) continue;
-    uint64_t k[3];
-    rank_key(ab[i], need_key ? &r : nullptr, k);
-    if (!matches_prefix(k, st[b], pass)) continue;
-    atomicAdd(&hist[(size_t)b * kBins + rank_digit(k, pass)], 1u);
+  const int64_t m = list ? (int64_t)*nlist : n;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; j0 < m; j0 += stride) {
+    const int64_t j = j0 + lane;
+    uint32_t code = 0xFFFFFFFFu, b = 0, dg = 0;
+    if (j < m) {
+      const int64_t i = list ? (int64_t)list[j] : j;
+      b = tag[i];
+      if (act[b] && !st[b].done) {
+        uint64_t k[3];
+        const uint64_t g = ab[i];
+        if (need_key) {
+          const Rec r = d[i];
+          rank_key(g, &r, k);
+        } else {
+          rank_key(g, nullptr, k);
+        }
+        if (matches_prefix(k, st[b], pass)) {
+          dg = rank_digit(k, pass);
+          code = (b << kDigitBits) | dg;
+        }
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, code);
+    if (code != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+      atomicAdd(&hist[(size_t)b * kBins + dg], (unsigned)__popc(peers));
+  }
+}
+
+// The candidates still selecting after the first digits: every string of a selecting instance
+// whose rank key matches the instance's prefix (warp-aggregated appends).
+__global__ void __launch_bounds__(kBT) k_bnarrow(const uint64_t* __restrict__ ab, const uint16_t* __restrict__ tag,
+                                                 int64_t n, const SelState* __restrict__ st,
+                                                 const int* __restrict__ act, int pass, uint32_t* __restrict__ list,
+                                                 unsigned long long* __restrict__ nlist) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    bool keep = false;
+    if (i < n) {
+      const uint32_t b = tag[i];
+      if (act[b] && !st[b].done) {
+        uint64_t k[3];
+        rank_key(ab[i], nullptr, k);
+        keep = matches_prefix(k, st[b], pass);
+      }
+    }
+    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+    unsigned long long base = 0;
+    if (lane == 0 && mk) base = atomicAdd(nlist, (unsigned long long)__popc(mk));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) list[base + __popc(mk & ((1u << lane) - 1u))] = (uint32_t)i;
   }
 }
 
@@ -162,11 +236,27 @@ int counts_run(const pauli_batch* B, const pauli_sum* O, std::vector<unsigned lo
   return hbad ? PS_ERR_INVALID : PS_OK;
 }
 
-// Per-instance top-k by |c|^2 (ties to the smaller key) for every instance over its cap.
+// Per-instance top-k by |c|^2 (ties to the smaller key) for every instance over its cap: one
+// read of the records gives the rank keys, the instance tags and the counts; the first two
+// digit passes run over keys and tags (10 bytes per string); the strings still tied with
+// their instance's threshold after them are listed, and the remaining passes run over the list.
 int batch_truncate(const pauli_batch* B, pauli_sum* O) {
   cudaStream_t s = O->stream;
-  std::vector<unsigned long long> cnt;
-  PS_TRY(counts_run(B, O, cnt));
+  if (O->n == 0) return PS_OK;
+  Buf<uint64_t> ab;
+  Buf<uint16_t> tag;
+  Buf<unsigned long long> dcnt;
+  PS_TRY(ab.alloc((size_t)O->n, s));
+  PS_TRY(tag.alloc((size_t)O->n, s));
+  PS_TRY(dcnt.alloc((size_t)B->n_inst, s));
+  PS_CUDA(cudaMemsetAsync(dcnt.p, 0, (size_t)B->n_inst * sizeof(unsigned long long), s));
+  PS_LAUNCH("k_bkeys", s,
+            k_bkeys_tags<<<grid_of(O->n), kBT, (size_t)B->n_inst * sizeof(unsigned long long), s>>>(
+                O->d, O->n, B->tag_shift, B->n_inst, ab.p, tag.p, dcnt.p));
+  PS_CUDA(cudaGetLastError());
+  std::vector<unsigned long long> cnt((size_t)B->n_inst);
+  PS_CUDA(cudaMemcpyAsync(cnt.data(), dcnt.p, cnt.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
   std::vector<int> act((size_t)B->n_inst, 0);
   std::vector<SelState> st((size_t)B->n_inst);
   int n_act = 0;
@@ -182,21 +272,30 @@ int batch_truncate(const pauli_batch* B, pauli_sum* O) {
   if (n_act == 0) return PS_OK;
   Buf<int> dact;
   Buf<SelState> dst;
-  Buf<uint64_t> ab;
   Buf<unsigned> hist, ndone;
+  Buf<uint32_t> list;
+  Buf<unsigned long long> nlist;
   PS_TRY(dact.alloc((size_t)B->n_inst, s));
   PS_TRY(dst.alloc((size_t)B->n_inst, s));
-  PS_TRY(ab.alloc((size_t)O->n, s));
   PS_TRY(hist.alloc((size_t)B->n_inst * kBins, s));
   PS_TRY(ndone.alloc(1, s));
+  PS_TRY(nlist.alloc(1, s));
+  const bool narrow = O->n <= (int64_t)0xFFFFFFFF;  // 32-bit candidate indices
+  if (narrow) PS_TRY(list.alloc((size_t)O->n, s));
   PS_CUDA(cudaMemcpyAsync(dact.p, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   PS_CUDA(cudaMemcpyAsync(dst.p, st.data(), st.size() * sizeof(SelState), cudaMemcpyHostToDevice, s));
   PS_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)B->n_inst * kBins * sizeof(unsigned), s));
   PS_CUDA(cudaMemsetAsync(ndone.p, 0, sizeof(unsigned), s));
-  PS_LAUNCH("k_bkeys", s, k_bkeys<<<grid_of(O->n), kBT, 0, s>>>(O->d, O->n, ab.p));
+  PS_CUDA(cudaMemsetAsync(nlist.p, 0, sizeof(unsigned long long), s));
+  constexpr int kNarrowAt = 2;  // digits fixed over all strings before the candidates are listed
   for (int pass = 0; pass < kPasses; ++pass) {
+    if (narrow && pass == kNarrowAt)
+      PS_LAUNCH("k_bnarrow", s,
+                k_bnarrow<<<grid_of(O->n), kBT, 0, s>>>(ab.p, tag.p, O->n, dst.p, dact.p, pass, list.p, nlist.p));
+    const bool listed = narrow && pass >= kNarrowAt;
     PS_LAUNCH("k_bhist", s,
-              k_bhist<<<grid_of(O->n), kBT, 0, s>>>(O->d, ab.p, O->n, B->tag_shift, dst.p, dact.p, pass, hist.p));
+              k_bhist<<<grid_of(O->n), kBT, 0, s>>>(O->d, ab.p, tag.p, O->n, listed ? list.p : nullptr,
+                                                    listed ? nlist.p : nullptr, dst.p, dact.p, pass, hist.p));
     PS_LAUNCH("k_bpick", s, k_bpick<<<B->n_inst, 256, 0, s>>>(dst.p, dact.p, pass, hist.p, ndone.p));
     if (pass == 4 || pass == 8 || pass == 12) {  // every instance usually settles within the |c|^2 digits
       unsigned nd = 0;
@@ -275,15 +374,29 @@ int pauli_batch_create(const pauli_sum* H, const double* hcoef, int n_inst, int 
   b->cap.assign((size_t)n_inst, 0);
   if (caps)
     for (int i = 0; i < n_inst; ++i) b->cap[(size_t)i] = caps[i];
+  // terms whose coefficient is the same (bit for bit) in every instance
+  std::vector<double> uni((size_t)H->n);
+  for (size_t h = 0; h < (size_t)H->n; ++h) {
+    uni[h] = hcoef[h];
+    for (int i = 1; i < n_inst; ++i)
+      if (std::memcmp(&hcoef[(size_t)i * (size_t)H->n + h], &uni[h], sizeof(double)) != 0) {
+        uni[h] = std::nan("");
+        break;
+      }
+  }
   int st = dev_alloc((void**)&b->hcoef, nc * sizeof(double), b->stream);
+  if (st == PS_OK) st = dev_alloc((void**)&b->huni, uni.size() * sizeof(double), b->stream);
   if (st != PS_OK) {
+    dev_free(b->hcoef, b->stream);
     delete b;
     return st;
   }
   cudaError_t e = cudaMemcpyAsync(b->hcoef, hcoef, nc * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->huni, uni.data(), uni.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     dev_free(b->hcoef, b->stream);
+    dev_free(b->huni, b->stream);
     delete b;
     set_cuda_error(e, "pauli_batch_create");
     return PS_ERR_CUDA;
@@ -295,6 +408,7 @@ int pauli_batch_create(const pauli_sum* H, const double* hcoef, int n_inst, int 
 int pauli_batch_destroy(pauli_batch* b) {
   if (!b) return PS_OK;
   dev_free(b->hcoef, b->stream);
+  dev_free(b->huni, b->stream);
   delete b;
   return PS_OK;
 }
@@ -366,6 +480,7 @@ int pauli_batch_rk4_step(const pauli_batch* b, const pauli_sum* H, pauli_sum* O,
     sp.clsH = H->cls;
     sp.clsX = in->cls;
     sp.hbatch = b->hcoef;
+    sp.hbatch_uniform = b->huni;
     sp.hb_shift = b->tag_shift;
     PS_TRY(merge_r(sp, k));
     if (trim_stages) PS_TRY(batch_truncate(b, k));

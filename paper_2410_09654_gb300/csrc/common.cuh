@@ -387,6 +387,9 @@ struct MergeSpec {
   // coefficients only fix the class.  Needs the table emission of full records.
   const double* hbatch = nullptr;
   int hb_shift = 0;
+  // With hbatch (optional): per H term, the coefficient shared by every instance, or NaN when
+  // the instances differ; shared terms skip the per-instance table.
+  const double* hbatch_uniform = nullptr;
   // Rank keys of a single-component output (optional): when keys_out is set and the merge runs
   // in single-component mode on a ranked merge, its output stage also writes, per output
   // string in storage order, the bit pattern of |x| of its non-zero component into a device

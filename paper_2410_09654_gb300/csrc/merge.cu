@@ -177,7 +177,7 @@ struct __align__(16) HScal {
   int e;
   int pvw;   // popcount(v & w) of the H term (its share of the product phase)
   float sf;  // s rounded to FP32 (the factor of the FP32 arithmetic)
-  int pad;
+  int per_inst;  // batched instances: 1 when the term's coefficient differs between instances
 };
 
 // Scalars of the single-component arithmetic (see build_scalar).
@@ -193,17 +193,25 @@ struct EmitScalars {
 // Per H term: its output-hash bits and (single-component mode, hscal non-null) its real factor
 // with the exponent of |s| when s is a power of two (kNoPow2 otherwise).
 __global__ void k_h_prep(const Rec* __restrict__ H, int nh, int bits, int uH, uint32_t* __restrict__ fH,
-                         HScal* __restrict__ hscal) {
+                         HScal* __restrict__ hscal, const double* __restrict__ huni) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nh) return;
   const Rec h = H[i];
   fH[i] = dev_hash(h.v, h.w, 0, bits);
   if (hscal) {
-    const double v = uH ? h.im : h.re;
+    // batched instances: a term whose coefficient is the same in every instance (huni[i],
+    // NaN when it differs) takes that value here, so the emission treats it as a plain term
+    double v = uH ? h.im : h.re;
+    int per_inst = 0;
+    if (huni) {
+      const double u = huni[i];
+      if (u != u) per_inst = 1;
+      else v = u;
+    }
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int E = (int)((b >> 52) & 0x7FF);
     const bool p2 = (b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046;
-    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, __popcll(h.v & h.w), __double2float_rn(v), 0};
+    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, __popcll(h.v & h.w), __double2float_rn(v), per_inst};
   }
 }
 
@@ -577,11 +585,12 @@ __global__ void __launch_bounds__(kEmitThreads, 4) k_emit_blk(const Rec* __restr
             const int ph = (__popcll(r.v & r.w) - hs.pvw - s_xp[xl] + 2 * __popcll(hk.y & x.x)) & 3;
             double hsv = hs.s;
             int hse = hs.e;
-            if (hb) {  // batched instances: the H coefficients of x's instance (tag = v >> hb_shift)
+            const bool inst = hb && hs.per_inst;
+            if (inst) {  // batched instances: the H coefficient of x's instance (tag = v >> hb_shift)
               hsv = hb[(size_t)(x.x >> hb_shift) * (size_t)nh + h];
               hse = kNoPow2;
             }
-            r.val = neg_if(es.f32c ? prod32(hb ? __double2float_rn(hsv) : hs.sf, s_xs[xl], 1) : scaled(hsv, hse, s_xs[xl], 1),
+            r.val = neg_if(es.f32c ? prod32(inst ? __double2float_rn(hsv) : hs.sf, s_xs[xl], 1) : scaled(hsv, hse, s_xs[xl], 1),
                            (ph & 2) != 0);
             r.code = h;
             r.pad = 0;
@@ -2041,7 +2050,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
     PS_CUDA(cudaGetLastError());
     PS_TRY(fH.alloc(sp.nH, s));
-    PS_LAUNCH("k_h_prep", s, k_h_prep<<<(int)ceil_div(sp.nH, 256), 256, 0, s>>>(sp.H, sp.nH, bits, a.uH, fH.p, hscal.p));
+    PS_LAUNCH("k_h_prep", s, k_h_prep<<<(int)ceil_div(sp.nH, 256), 256, 0, s>>>(sp.H, sp.nH, bits, a.uH, fH.p, hscal.p, sp.hbatch ? sp.hbatch_uniform : nullptr));
     PS_CUDA(cudaGetLastError());
   }
   for (int i = 0; i < sp.nsrc; ++i)
