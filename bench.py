@@ -457,7 +457,7 @@ def main():
                               "merge_groups_per_step": groups / args.steps,
                               "merge_split_groups_per_step": split_groups / args.steps,
                               "launches_before_timed": launches0, "gpu_launches": launches,
-                              "roofline": roof}), flush=True)
+                              "roofline": roof, "e2e": e2e}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
