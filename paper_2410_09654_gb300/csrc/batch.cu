@@ -181,35 +181,43 @@ __global__ void __launch_bounds__(256) k_bpick(SelState* st, const int* __restri
 }
 
 // Keep a string iff its instance is not capped or its rank key reaches the instance's
-// threshold.  Warp-aggregated output reservation (output order unspecified).
+// threshold.  Tiles of kBT * kBTI strings, one output reservation per tile: the kept strings
+// keep their order within a tile (the merge's bin order, on which the next emission's slot
+// reservations rely).
+constexpr int kBTI = 4;
 __global__ void __launch_bounds__(kBT) k_bcompact(const Rec* __restrict__ d, const uint64_t* __restrict__ ab,
-                                                  int64_t n, int shift, const SelState* __restrict__ st,
-                                                  const int* __restrict__ act, Rec* __restrict__ out,
-                                                  unsigned long long* __restrict__ n_out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; i0 < n; i0 += stride) {
-    const int64_t i = i0 + lane;
-    bool keep = false;
-    Rec r{0, 0, 0.0, 0.0};
-    if (i < n) {
-      r = d[i];
-      const uint32_t b = inst_of(r, shift);
-      if (!act[b]) {
-        keep = true;
-      } else {
-        uint64_t k[3];
-        rank_key(ab[i], &r, k);
-        const SelState& s = st[b];
-        keep = k[0] > s.prefix[0] ||
-               (k[0] == s.prefix[0] && (k[1] > s.prefix[1] || (k[1] == s.prefix[1] && k[2] >= s.prefix[2])));
+                                                  const uint16_t* __restrict__ tag, int64_t n,
+                                                  const SelState* __restrict__ st, const int* __restrict__ act,
+                                                  Rec* __restrict__ out, unsigned long long* __restrict__ n_out) {
+  __shared__ TileSlots<kBT, kBTI> s_res;
+  const int64_t tile_n = (int64_t)kBT * kBTI;
+  const int64_t tiles = (n + tile_n - 1) / tile_n;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    bool kp[kBTI];
+    Rec r[kBTI];
+#pragma unroll
+    for (int k = 0; k < kBTI; ++k) {
+      const int64_t i = tile * tile_n + (int64_t)k * kBT + threadIdx.x;
+      kp[k] = false;
+      if (i < n) {
+        r[k] = d[i];
+        const uint32_t b = tag[i];
+        if (!act[b]) {
+          kp[k] = true;
+        } else {
+          uint64_t key[3];
+          rank_key(ab[i], &r[k], key);
+          const SelState& s = st[b];
+          kp[k] = key[0] > s.prefix[0] ||
+                  (key[0] == s.prefix[0] && (key[1] > s.prefix[1] || (key[1] == s.prefix[1] && key[2] >= s.prefix[2])));
+        }
       }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    unsigned long long base = 0;
-    if (lane == 0 && m) base = atomicAdd(n_out, (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (keep) out[base + __popc(m & ((1u << lane) - 1u))] = r;
+    unsigned long long pos[kBTI];
+    tile_slots<kBT, kBTI>(kp, s_res, n_out, pos);
+#pragma unroll
+    for (int k = 0; k < kBTI; ++k)
+      if (kp[k]) out[pos[k]] = r[k];
   }
 }
 
@@ -311,7 +319,7 @@ int batch_truncate(const pauli_batch* B, pauli_sum* O) {
   PS_CUDA(cudaMemsetAsync(nout.p, 0, sizeof(unsigned long long), s));
   PS_TRY(dev_alloc((void**)&outb, (size_t)O->n * sizeof(Rec), s));
   PS_LAUNCH("k_bcompact", s,
-            k_bcompact<<<grid_of(O->n), kBT, 0, s>>>(O->d, ab.p, O->n, B->tag_shift, dst.p, dact.p, outb, nout.p));
+            k_bcompact<<<grid_of(O->n), kBT, 0, s>>>(O->d, ab.p, tag.p, O->n, dst.p, dact.p, outb, nout.p));
   cudaError_t e = cudaGetLastError();
   unsigned long long nk = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nk, nout.p, sizeof(nk), cudaMemcpyDeviceToHost, s);

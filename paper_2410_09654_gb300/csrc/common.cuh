@@ -245,7 +245,11 @@ __device__ __forceinline__ Cx rot(Cx a, int k) {  // multiply by i^k (exact)
 // t = |a|/|b|; the remainder rho = |a| - Q|b| is exact (one FMA); comparing rho with the exact
 // products |b| * (half gaps to Q's neighbours), powers of two times |b|, decides RN(t) among
 // Q and its two neighbours.  Whenever an operand or result leaves the normal range, or Q is
-// more than one ulp away, it falls back to the IEEE division.
+// more than one ulp away, it falls back to the IEEE division.  The exact FMA remainder and the
+// rounding decision from it are those of Markstein's correction step for division (P. Markstein,
+// IA-64 and Elementary Functions, 2000); the remainder's exactness when Q is within an ulp is
+// Boldo and Daumas' result (Representable correcting terms for possibly underflowing floating
+// point operations, ARITH 2003).
 struct DivConst {
   double b;       // divisor
   double rabs;    // RN(1 / |b|)

@@ -120,5 +120,41 @@ __device__ __forceinline__ void sel_pick_block(SelState* st_p, int pass, unsigne
   }
 }
 
+// Order-keeping compaction of a tile of TT * TI elements (element k * TT + thread of the tile
+// at f[k]): one output reservation per tile, positions in tile order, so runs of neighbouring
+// strings stay neighbours in the output (the emission's slot reservations rely on it).
+template <int TT, int TI>
+struct TileSlots {
+  uint32_t wcnt[TT / 32][TI];
+  unsigned long long base;
+};
+
+template <int TT, int TI>
+__device__ __forceinline__ void tile_slots(const bool (&f)[TI], TileSlots<TT, TI>& sm, unsigned long long* counter,
+                                           unsigned long long (&pos)[TI]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned m[TI];
+#pragma unroll
+  for (int k = 0; k < TI; ++k) {
+    m[k] = __ballot_sync(0xffffffffu, f[k]);
+    if (lane == 0) sm.wcnt[warp][k] = __popc(m[k]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < TI; ++k)
+      for (int w = 0; w < TT / 32; ++w) {
+        const uint32_t c = sm.wcnt[w][k];
+        sm.wcnt[w][k] = run;
+        run += c;
+      }
+    sm.base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < TI; ++k) pos[k] = sm.base + sm.wcnt[warp][k] + __popc(m[k] & ((1u << lane) - 1));
+  __syncthreads();
+}
+
 }  // namespace
 }  // namespace ps
