@@ -431,7 +431,8 @@ def main():
         for hp, hc, sb in host:  # the timed loop's first states, each from host arrays
             e_prev.upload(*hp)
             e_cur.upload(*hc)
-            e_prev.sort_by_hash()  # operands into the merge's hash order (canonical order is slower)
+            # the product operand into the merge's hash order (canonical order is slower); O_{n-1}
+            # enters the merge as a source term, whose emission does not depend on its order
             e_cur.sort_by_hash()
             e_prod += nH * len(hc[0])
             h2d += 32 * (len(hc[0]) + len(hp[0]))
@@ -446,7 +447,7 @@ def main():
                "h2d_bytes_per_step": int(h2d / len(host)), "d2h_bytes_per_step": int(d2h / len(host)),
                "states": f"the first {len(host)} input states of the timed loop, uploaded from pinned host arrays",
                "api": "pauli_sum_upload x2 (pinned host arrays, read by the packing kernel over the host link) + "
-                      "pauli_sum_sort_by_hash x2 + pauli_lanczos_step (b_n to host) + pauli_sum_download_device of "
+                      "pauli_sum_sort_by_hash of O_n + pauli_lanczos_step (b_n to host) + pauli_sum_download_device of "
                       "O_{n+1} into pinned host arrays"}
 
     if args.lanczos_only:
