@@ -135,3 +135,21 @@ def test_batch_rk4_steps_equals_single_steps():
     before = O.download()
     ps.pauli_batch_rk4_steps(B, Hc, O, 0.05, 0)  # zero steps: unchanged
     assert all(np.array_equal(x, y) for x, y in zip(O.download(), before))
+
+
+def test_batch_truncate_all_ties_many_instances():
+    # every coefficient equal: every rank is decided by the keys (~v, ~w), so the selection
+    # runs past the |c|^2 digits through the listed candidates; instances of several sizes,
+    # caps below, at and above their sizes
+    n, n_inst = 16, 40
+    N, Hs, Hc, B, caps = _setup(n, n_inst, lambda b: [3, 50, 400, 0, 1, 2000, 257][b % 7])
+    O0 = []
+    for b in range(n_inst):
+        v, w, _re, _im = I.random_sum(500 + b, n, 200 + 37 * b, kind="real")
+        O0.append((v, w, np.full(len(v), 0.5), np.zeros(len(v))))
+    O = ps.PauliSum.from_arrays(N, *_tagged(O0, n))
+    ps.pauli_batch_truncate(B, O)
+    got = _untag(O.download(), n, n_inst)
+    for b in range(n_inst):
+        want = orc.truncate(orc.Op(n, *O0[b]), top_k=int(max(caps[b], 0)))
+        assert_match(got[b], want, exact=True, what=f"instance {b}")

@@ -478,6 +478,22 @@ def test_rk4_trim_stages():
         assert_match(O.download(), Or, what=f"rk4 trim step {step}")
 
 
+def test_rk4_trim_stages_dyadic_ties():
+    # dyadic data and dt = 1/4 keep every sum exact, so the stage trims meet many exactly tied
+    # |c| (their top-k is decided by the keys); a single-component k_j takes the trim from the
+    # merge's rank keys
+    n = 12
+    Ha = I.xx_chain(n).arrays()
+    O0 = I.random_sum(77, n, 300, kind="real", dyadic=True)
+    H, Hr = dev(n, Ha), ref(n, Ha)
+    O, Or = dev(n, O0), ref(n, O0)
+    pol = ps.policy(top_k=150, trim_stages=1)
+    for step in range(3):
+        ps.pauli_rk4_step(H, O, 0.25, pol)
+        Or = orc.rk4_step(Hr, Or, 0.25, top_k=150, trim_stages=1)
+        assert_match(O.download(), Or, exact=True, what=f"rk4 trim ties step {step}")
+
+
 # ----------------------------------------------------------------------------- Lanczos
 def test_lanczos_paper_example():
     n = 10
