@@ -424,21 +424,21 @@ constexpr int kTabPos = 32, kTabVals = 16;
 __host__ __device__ constexpr int tab_stride(int nw) { return nw <= 2 ? 2 : (nw <= 6 ? 6 : 10); }
 
 // T[p][val][k]: bit b of word k is the parity of popcount(val & nibble_p(h = 32k + b)).
+// One thread per word T[p][val][k].
 __global__ void k_anti_table(const Rec* __restrict__ H, int nH, int stride, uint32_t* __restrict__ T) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= kTabPos * kTabVals) return;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= kTabPos * kTabVals * stride) return;
+  const int t = u / stride, k = u % stride;
   const int p = t / kTabVals, val = t % kTabVals;
-  for (int k = 0; k < stride; ++k) {
-    uint32_t word = 0;
-    for (int b = 0; b < 32; ++b) {
-      const int h = 32 * k + b;
-      if (h >= nH) break;
-      const uint64_t m = p < 16 ? H[h].w : H[h].v;
-      const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
-      word |= (uint32_t)(__popc(nib & (uint32_t)val) & 1) << b;
-    }
-    T[t * stride + k] = word;
+  uint32_t word = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int h = 32 * k + b;
+    if (h >= nH) break;
+    const uint64_t m = p < 16 ? H[h].w : H[h].v;
+    const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
+    word |= (uint32_t)(__popc(nib & (uint32_t)val) & 1) << b;
   }
+  T[u] = word;
 }
 
 // Block-level table emission.  A block takes 256 neighbouring x (hash order), one per
@@ -732,6 +732,140 @@ __global__ void k_group_heads(const uint32_t* __restrict__ gstart, const uint64_
     const uint32_t lo = gstart[g], hi = gstart[g + 1];
     const uint64_t e0 = cpre[lo];
     heads[g] = GroupHead{lo, hi, e0, cpre[hi] - e0, 0};
+  }
+}
+
+// ---- small merges: the bin bounds and the group plan each in one block of 1024 threads (each
+// thread owns up to 16 consecutive bins), in place of the device-wide kernels and scans that
+// cost a launch each; the same definitions, so the same groups.
+constexpr int kPlanThreads = 1024;
+constexpr uint32_t kSmallPlanBins = 16u * kPlanThreads;
+
+// Exclusive scan of one value per thread over the block of kPlanThreads; *total gets the sum.
+__device__ __forceinline__ uint64_t plan_scan(uint64_t v, uint64_t* s_w, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t t = s_w[lane];  // kPlanThreads / 32 = 32 warps
+    uint64_t ti = t;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t u = __shfl_up_sync(0xffffffffu, ti, d);
+      if (lane >= d) ti += u;
+    }
+    s_w[lane] = ti - t;
+    if (lane == 31) s_w[32] = ti;
+  }
+  __syncthreads();
+  const uint64_t r = s_w[warp] + incl - v;
+  *total = s_w[32];
+  __syncthreads();
+  return r;
+}
+
+// bound[p] as k_bound, its exclusive prefix base[0..nbins] and the cursors cur = base.
+__global__ void __launch_bounds__(kPlanThreads) k_bound_small(const uint32_t* __restrict__ histX,
+                                                              const uint32_t* __restrict__ histY,
+                                                              const uint32_t* __restrict__ fH, int nH, uint32_t nbins,
+                                                              uint64_t* __restrict__ base,
+                                                              unsigned long long* __restrict__ cur) {
+  __shared__ uint64_t s_w[33];
+  const uint32_t per = (nbins + kPlanThreads - 1) / kPlanThreads;
+  const uint32_t p0 = threadIdx.x * per;
+  uint64_t b[16];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint32_t p = p0 + (uint32_t)k;
+    b[k] = 0;
+    if ((uint32_t)k < per && p < nbins) {
+      uint64_t x = histY ? histY[p] : 0;
+      if (histX)
+        for (int h = 0; h < nH; ++h) x += histX[p ^ __ldg(&fH[h])];
+      b[k] = x;
+    }
+    sum += b[k];
+  }
+  uint64_t total;
+  uint64_t run = plan_scan(sum, s_w, &total);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint32_t p = p0 + (uint32_t)k;
+    if ((uint32_t)k < per && p < nbins) {
+      base[p] = run;
+      cur[p] = run;
+      run += b[k];
+    }
+  }
+  if (threadIdx.x == 0) base[nbins] = total;
+}
+
+// The group plan from the filled bins: cpre (as k_bin_counts + the scan), the group starts
+// (as k_group_flags + the scan + k_group_scatter) and the group heads (as k_group_heads).
+__global__ void __launch_bounds__(kPlanThreads) k_plan_small(const unsigned long long* __restrict__ cur,
+                                                             const uint64_t* __restrict__ base, uint32_t nbins,
+                                                             uint64_t quota, uint64_t* __restrict__ cpre,
+                                                             uint32_t* __restrict__ gstart,
+                                                             uint32_t* __restrict__ ngroups,
+                                                             GroupHead* __restrict__ heads) {
+  __shared__ uint64_t s_w[33];
+  const uint32_t per = (nbins + kPlanThreads - 1) / kPlanThreads;
+  const uint32_t p0 = threadIdx.x * per;
+  uint64_t c[16];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint32_t p = p0 + (uint32_t)k;
+    c[k] = ((uint32_t)k < per && p < nbins) ? (uint64_t)(cur[p] - base[p]) : 0;
+    sum += c[k];
+  }
+  uint64_t total;
+  uint64_t run = plan_scan(sum, s_w, &total);
+  uint64_t pre[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    pre[k] = run;
+    const uint32_t p = p0 + (uint32_t)k;
+    if ((uint32_t)k < per && p < nbins) cpre[p] = run;
+    run += c[k];
+  }
+  if (threadIdx.x == 0) cpre[nbins] = total;
+  // the predecessor of a thread's first bin belongs to the thread before: its prefix is read
+  // back from cpre after the barrier
+  __syncthreads();
+  uint32_t nf = 0;
+  bool f[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint32_t p = p0 + (uint32_t)k;
+    f[k] = false;
+    if ((uint32_t)k < per && p < nbins) {
+      const uint64_t prev = p == 0 ? 0 : (k > 0 ? pre[k - 1] : cpre[p - 1]);
+      f[k] = (p == 0) || (p == nbins / 2) || (p % kMaxGroupBins == 0) || (pre[k] / quota != prev / quota);
+      nf += f[k] ? 1u : 0u;
+    }
+  }
+  uint64_t ng;
+  uint64_t g = plan_scan(nf, s_w, &ng);
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    if (f[k]) gstart[g++] = p0 + (uint32_t)k;
+  if (threadIdx.x == 0) {
+    gstart[ng] = nbins;
+    *ngroups = (uint32_t)ng;
+  }
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < (uint32_t)ng; q += kPlanThreads) {
+    const uint32_t lo = gstart[q], hi = gstart[q + 1];
+    const uint64_t e0 = cpre[lo];
+    heads[q] = GroupHead{lo, hi, e0, cpre[hi] - e0, 0};
   }
 }
 
@@ -1938,6 +2072,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   // target and leaves no room in a pass for the bin's neighbours: quarter-size bins then
   const int bits = choose_bits(bound_total, nX > 0 ? geom.bin_target : std::max(64, geom.bin_target / 4));
   const uint32_t nbins = 1u << bits;
+  const bool small_plan = nbins <= kSmallPlanBins;  // one block each for the bin bounds and the group plan
   const int nsm = num_sms();
   auto grid_for = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16 * nsm)); };
   // shared-memory histograms: fewer, fuller blocks (one flush of the bins per block)
@@ -2031,8 +2166,10 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   Buf<unsigned> misc;                // [0] next_group, [1] ngroups, [2] split groups
   Buf<int> err;
   PS_TRY(histY.alloc(nbins, s));
-  PS_TRY(cnt.alloc(nbins, s));
-  PS_TRY(bound.alloc(nbins, s));
+  if (!small_plan) {
+    PS_TRY(cnt.alloc(nbins, s));
+    PS_TRY(bound.alloc(nbins, s));
+  }
   PS_TRY(base.alloc(nbins + 1, s));
   PS_TRY(counters.alloc(2, s));
   PS_TRY(misc.alloc(3, s));
@@ -2065,26 +2202,33 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, nullptr, histY.p));
     PS_CUDA(cudaGetLastError());
   }
+  // bin regions from the bounds; the emission's bin cursors start at the bins' first slots
+  Buf<unsigned long long> cur;
+  PS_TRY(cur.alloc(nbins, s));
   {
     int nh = nX > 0 ? sp.nH : 0;
-    int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
-    PS_LAUNCH("k_bound", s, k_bound<<<blocks, 256, 0, s>>>(nX > 0 ? histX.p : nullptr, histY.p, fH.p, nh, nbins, bound.p));
-    PS_CUDA(cudaGetLastError());
+    if (small_plan) {
+      PS_LAUNCH("k_bound", s, k_bound_small<<<1, kPlanThreads, 0, s>>>(nX > 0 ? histX.p : nullptr, histY.p, fH.p, nh, nbins,
+                                                                         base.p, cur.p));
+      PS_CUDA(cudaGetLastError());
+    } else {
+      int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
+      PS_LAUNCH("k_bound", s, k_bound<<<blocks, 256, 0, s>>>(nX > 0 ? histX.p : nullptr, histY.p, fH.p, nh, nbins, bound.p));
+      PS_CUDA(cudaGetLastError());
+      PS_TRY(scan_u64(bound.p, base.p, nbins, s));
+      PS_CUDA(cudaMemcpyAsync(cur.p, base.p, nbins * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    }
   }
-  PS_TRY(scan_u64(bound.p, base.p, nbins, s));
   if (full) PS_TRY(fent.alloc((size_t)bound_total, s));
   else PS_TRY(entries.alloc((size_t)bound_total, s));
 
-  // ---- 2. emission (bin cursors start at the bins' first slots)
-  Buf<unsigned long long> cur;
-  PS_TRY(cur.alloc(nbins, s));
-  PS_CUDA(cudaMemcpyAsync(cur.p, base.p, nbins * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  // ---- 2. emission
   Buf<uint32_t> tab;
   if (nX > 0 && sp.nH <= kMaskBits && !sp.product) {
     // |H| <= 256: anticommutation bitmaps from the nibble table
     const int stride = tab_stride((sp.nH + 31) / 32);
     PS_TRY(tab.alloc((size_t)kTabPos * kTabVals * stride, s));
-    PS_LAUNCH("k_anti_table", s, k_anti_table<<<(kTabPos * kTabVals + 255) / 256, 256, 0, s>>>(sp.H, sp.nH, stride, tab.p));
+    PS_LAUNCH("k_anti_table", s, k_anti_table<<<(kTabPos * kTabVals * stride + 255) / 256, 256, 0, s>>>(sp.H, sp.nH, stride, tab.p));
     PS_CUDA(cudaGetLastError());
     if (full) PS_TRY(emit_tab<true>(sp.X, fX.p, nX, sp.H, fH.p, hscal.p, sp.nH, tab.p, es, cur.p, nullptr, fent.p, counters.p, nsm, s, sp.hbatch, sp.hb_shift));
     else PS_TRY(emit_tab<false>(sp.X, fX.p, nX, sp.H, fH.p, nullptr, sp.nH, tab.p, es, cur.p, entries.p, nullptr, counters.p, nsm, s));
@@ -2109,7 +2253,7 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   for (int i = 0; i < sp.nsrc; ++i)
     if (sp.src[i].n > 0) PS_TRY(emit_source(sp.src[i].rec, sp.src[i].n, kCodeSrc + i, sp.src[i].ts));
   if (sp.npre > 0) PS_TRY(emit_source(sp.pre, sp.npre, kCodePre, 0));
-  {
+  if (!small_plan) {
     int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
     PS_LAUNCH("k_bin_counts", s, k_bin_counts<<<blocks, 256, 0, s>>>(cur.p, base.p, nbins, cnt.p));
     PS_CUDA(cudaGetLastError());
@@ -2122,11 +2266,17 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
 
   // ---- 3. groups
   PS_TRY(cpre.alloc(nbins + 1, s));
-  PS_TRY(scan_u32_to_u64(cnt.p, cpre.p, nbins, s));
-  PS_TRY(flag.alloc(nbins, s));
-  PS_TRY(fpre.alloc(nbins + 1, s));
   PS_TRY(gstart.alloc(nbins + 1, s));
-  {
+  if (small_plan) {
+    PS_TRY(heads.alloc(nbins, s));  // at most one group per bin
+    PS_LAUNCH("k_group_heads", s, k_plan_small<<<1, kPlanThreads, 0, s>>>(cur.p, base.p, nbins,
+                                                                          (uint64_t)(ranked_wide ? geom.quota / 2 : geom.quota),
+                                                                          cpre.p, gstart.p, misc.p + 1, heads.p));
+    PS_CUDA(cudaGetLastError());
+  } else {
+    PS_TRY(scan_u32_to_u64(cnt.p, cpre.p, nbins, s));
+    PS_TRY(flag.alloc(nbins, s));
+    PS_TRY(fpre.alloc(nbins + 1, s));
     int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
     PS_LAUNCH("k_group_flags", s, k_group_flags<<<blocks, 256, 0, s>>>(cpre.p, nbins, (uint64_t)(ranked_wide ? geom.quota / 2 : geom.quota), flag.p));
     PS_CUDA(cudaGetLastError());
