@@ -688,6 +688,84 @@ __global__ void k_emit_source(const Rec* __restrict__ Y, int64_t n, int bits, ui
   }
 }
 
+// All plain (not translation-symmetric) sources and the pre operand of a merge in one launch:
+// the concatenation of up to five operands, each with its order code.
+struct SrcSet {
+  const Rec* rec[5];
+  int64_t off[6];  // operand j covers [off[j], off[j + 1]) of the concatenation
+  uint32_t code[5];
+  int cnt;
+};
+
+__device__ __forceinline__ int src_of_index(const SrcSet& ss, int64_t i) {
+  int j = 0;
+  while (j + 1 < ss.cnt && i >= ss.off[j + 1]) ++j;
+  return j;
+}
+
+// The histogram of the operands' bins (as k_hash_hist without the per-string hashes).
+__global__ void k_hash_hist_set(SrcSet ss, int bits, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[1 << kHistSmemBits];
+  const bool local = bits <= kHistSmemBits;
+  const uint32_t nb = 1u << bits;
+  if (local) {
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+  }
+  const int64_t n = ss.off[ss.cnt];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = src_of_index(ss, i);
+    const Rec& r = ss.rec[j][i - ss.off[j]];
+    atomicAdd(local ? &sh[dev_hash(r.v, r.w, 0, bits)] : &hist[dev_hash(r.v, r.w, 0, bits)], 1u);
+  }
+  if (local) {
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+      if (sh[b]) atomicAdd(&hist[b], sh[b]);
+  }
+}
+
+// The emission of k_emit_source for every operand of the set (warp-strided over the
+// concatenation; a warp may straddle two operands).
+template <bool FULL>
+__global__ void k_emit_source_set(SrcSet ss, int bits, EmitScalars es, unsigned long long* __restrict__ cur,
+                                  uint64_t* __restrict__ entries, Contrib* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = ss.off[ss.cnt];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    const bool act = i < n;
+    Rec y = Rec{0, 0, 0.0, 0.0};
+    uint32_t code = 0;
+    int64_t idx = 0;
+    if (act) {
+      const int j = src_of_index(ss, i);
+      idx = i - ss.off[j];
+      y = ss.rec[j][idx];
+      code = ss.code[j];
+    }
+    if constexpr (FULL) {
+      double val = 0.0;
+      if (act) {
+        if (code == kCodePre) {
+          val = es.pre_u ? y.im : y.re;
+        } else {
+          const uint32_t si = code - kCodeSrc;
+          const double sy = es.src_uy[si] ? y.im : y.re;
+          val = neg_if(es.f32c ? prod32(es.src_sf[si], sy, 0) : scaled(es.src_s[si], es.src_e[si], sy, 0),
+                       (es.src_q[si] & 2) != 0);
+        }
+      }
+      const uint64_t at = reserve_slot(cur, dev_hash(y.v, y.w, 0, bits), act, lane);
+      if (act) out[at] = Contrib{y.v, y.w, val, code, 0};
+    } else {
+      const uint64_t at = reserve_slot(cur, dev_hash(y.v, y.w, 0, bits), act, lane);
+      if (act) entries[at] = ((uint64_t)idx << 16) | code;
+    }
+  }
+}
+
 // Slots used per bin: cnt[p] = cur[p] - base[p].
 __global__ void k_bin_counts(const unsigned long long* __restrict__ cur, const uint64_t* __restrict__ base,
                              uint32_t nbins, uint32_t* __restrict__ cnt) {
@@ -2190,16 +2268,30 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_LAUNCH("k_h_prep", s, k_h_prep<<<(int)ceil_div(sp.nH, 256), 256, 0, s>>>(sp.H, sp.nH, bits, a.uH, fH.p, hscal.p, sp.hbatch ? sp.hbatch_uniform : nullptr));
     PS_CUDA(cudaGetLastError());
   }
+  // the plain sources and the pre operand as one set (one launch each for their histogram and
+  // their emission); translation-symmetric sources one by one
+  SrcSet sset{};
   for (int i = 0; i < sp.nsrc; ++i)
-    if (sp.src[i].n > 0) {
-      if (sp.src[i].ts)
-        PS_LAUNCH("k_hash_hist", s, k_hash_hist_ts<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, sp.src[i].ts, sp.ring, histY.p));
-      else
-        PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, nullptr, histY.p));
-      PS_CUDA(cudaGetLastError());
+    if (sp.src[i].n > 0 && !sp.src[i].ts) {
+      sset.rec[sset.cnt] = sp.src[i].rec;
+      sset.code[sset.cnt] = kCodeSrc + (uint32_t)i;
+      sset.off[sset.cnt + 1] = sset.off[sset.cnt] + sp.src[i].n;
+      ++sset.cnt;
     }
   if (sp.npre > 0) {
-    PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(sp.npre), 256, 0, s>>>(sp.pre, sp.npre, bits, nullptr, histY.p));
+    sset.rec[sset.cnt] = sp.pre;
+    sset.code[sset.cnt] = kCodePre;
+    sset.off[sset.cnt + 1] = sset.off[sset.cnt] + sp.npre;
+    ++sset.cnt;
+  }
+  const int64_t nset = sset.off[sset.cnt];
+  for (int i = 0; i < sp.nsrc; ++i)
+    if (sp.src[i].n > 0 && sp.src[i].ts) {
+      PS_LAUNCH("k_hash_hist", s, k_hash_hist_ts<<<grid_for(sp.src[i].n), 256, 0, s>>>(sp.src[i].rec, sp.src[i].n, bits, sp.src[i].ts, sp.ring, histY.p));
+      PS_CUDA(cudaGetLastError());
+    }
+  if (nset > 0) {
+    PS_LAUNCH("k_hash_hist", s, k_hash_hist_set<<<hist_grid(nset), 256, 0, s>>>(sset, bits, histY.p));
     PS_CUDA(cudaGetLastError());
   }
   // bin regions from the bounds; the emission's bin cursors start at the bins' first slots
@@ -2251,8 +2343,14 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     return PS_OK;
   };
   for (int i = 0; i < sp.nsrc; ++i)
-    if (sp.src[i].n > 0) PS_TRY(emit_source(sp.src[i].rec, sp.src[i].n, kCodeSrc + i, sp.src[i].ts));
-  if (sp.npre > 0) PS_TRY(emit_source(sp.pre, sp.npre, kCodePre, 0));
+    if (sp.src[i].n > 0 && sp.src[i].ts) PS_TRY(emit_source(sp.src[i].rec, sp.src[i].n, kCodeSrc + i, sp.src[i].ts));
+  if (nset > 0) {
+    if (full)
+      PS_LAUNCH("k_emit_source", s, k_emit_source_set<true><<<grid_for(nset), 256, 0, s>>>(sset, bits, es, cur.p, nullptr, fent.p));
+    else
+      PS_LAUNCH("k_emit_source", s, k_emit_source_set<false><<<grid_for(nset), 256, 0, s>>>(sset, bits, es, cur.p, entries.p, nullptr));
+    PS_CUDA(cudaGetLastError());
+  }
   if (!small_plan) {
     int blocks = (int)std::min<int64_t>(ceil_div(nbins, 256), 4 * nsm);
     PS_LAUNCH("k_bin_counts", s, k_bin_counts<<<blocks, 256, 0, s>>>(cur.p, base.p, nbins, cnt.p));
