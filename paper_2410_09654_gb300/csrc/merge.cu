@@ -424,21 +424,45 @@ constexpr int kTabPos = 32, kTabVals = 16;
 __host__ __device__ constexpr int tab_stride(int nw) { return nw <= 2 ? 2 : (nw <= 6 ? 6 : 10); }
 
 // T[p][val][k]: bit b of word k is the parity of popcount(val & nibble_p(h = 32k + b)).
-// One thread per word T[p][val][k].
-__global__ void k_anti_table(const Rec* __restrict__ H, int nH, int stride, uint32_t* __restrict__ T) {
+// The anticommutation table T[p][val][k] (one thread per word) and the preparation of the H
+// terms as in k_h_prep, in one launch: threads [0, table words) build the table, the next nh
+// threads prepare the terms.
+__global__ void k_h_prep_table(const Rec* __restrict__ H, int nh, int bits, int uH, uint32_t* __restrict__ fH,
+                               HScal* __restrict__ hscal, const double* __restrict__ huni, int stride,
+                               uint32_t* __restrict__ T) {
+  const int words = kTabPos * kTabVals * stride;
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= kTabPos * kTabVals * stride) return;
-  const int t = u / stride, k = u % stride;
-  const int p = t / kTabVals, val = t % kTabVals;
-  uint32_t word = 0;
-  for (int b = 0; b < 32; ++b) {
-    const int h = 32 * k + b;
-    if (h >= nH) break;
-    const uint64_t m = p < 16 ? H[h].w : H[h].v;
-    const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
-    word |= (uint32_t)(__popc(nib & (uint32_t)val) & 1) << b;
+  if (u < words) {
+    const int t = u / stride, k = u % stride;
+    const int p = t / kTabVals, val = t % kTabVals;
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int h = 32 * k + b;
+      if (h >= nh) break;
+      const uint64_t m = p < 16 ? H[h].w : H[h].v;
+      const uint32_t nib = (uint32_t)(m >> (4 * (p & 15))) & 15u;
+      word |= (uint32_t)(__popc(nib & (uint32_t)val) & 1) << b;
+    }
+    T[u] = word;
+    return;
   }
-  T[u] = word;
+  const int i = u - words;
+  if (i >= nh) return;
+  const Rec h = H[i];
+  fH[i] = dev_hash(h.v, h.w, 0, bits);
+  if (hscal) {
+    double v = uH ? h.im : h.re;
+    int per_inst = 0;
+    if (huni) {
+      const double w = huni[i];
+      if (w != w) per_inst = 1;
+      else v = w;
+    }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const bool p2 = (b & ((1ull << 52) - 1)) == 0 && E >= 1 && E <= 2046;
+    hscal[i] = HScal{v, p2 ? E - 1023 : kNoPow2, __popcll(h.v & h.w), __double2float_rn(v), per_inst};
+  }
 }
 
 // Block-level table emission.  A block takes 256 neighbouring x (hash order), one per
@@ -2258,6 +2282,8 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   PS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
 
   // ---- 1. hashes, histograms and bin bounds
+  const bool use_tab = nX > 0 && sp.nH <= kMaskBits && !sp.product;  // table emission (|H| <= 256)
+  Buf<uint32_t> tab;
   if (nX > 0) {
     PS_TRY(fX.alloc(nX, s));
     PS_TRY(histX.alloc(nbins, s));
@@ -2265,7 +2291,15 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
     PS_LAUNCH("k_hash_hist", s, k_hash_hist<<<hist_grid(nX), 256, 0, s>>>(sp.X, nX, bits, fX.p, histX.p));
     PS_CUDA(cudaGetLastError());
     PS_TRY(fH.alloc(sp.nH, s));
-    PS_LAUNCH("k_h_prep", s, k_h_prep<<<(int)ceil_div(sp.nH, 256), 256, 0, s>>>(sp.H, sp.nH, bits, a.uH, fH.p, hscal.p, sp.hbatch ? sp.hbatch_uniform : nullptr));
+    if (use_tab) {  // the H terms and the anticommutation table in one launch
+      const int words = kTabPos * kTabVals * tab_stride((sp.nH + 31) / 32);
+      PS_TRY(tab.alloc((size_t)words, s));
+      PS_LAUNCH("k_h_prep", s, k_h_prep_table<<<(int)ceil_div(words + sp.nH, 256), 256, 0, s>>>(
+                                   sp.H, sp.nH, bits, a.uH, fH.p, hscal.p, sp.hbatch ? sp.hbatch_uniform : nullptr,
+                                   tab_stride((sp.nH + 31) / 32), tab.p));
+    } else {
+      PS_LAUNCH("k_h_prep", s, k_h_prep<<<(int)ceil_div(sp.nH, 256), 256, 0, s>>>(sp.H, sp.nH, bits, a.uH, fH.p, hscal.p, sp.hbatch ? sp.hbatch_uniform : nullptr));
+    }
     PS_CUDA(cudaGetLastError());
   }
   // the plain sources and the pre operand as one set (one launch each for their histogram and
@@ -2315,13 +2349,8 @@ int merge_run(const MergeSpec& sp, cudaStream_t s, pauli_sum* out) {
   else PS_TRY(entries.alloc((size_t)bound_total, s));
 
   // ---- 2. emission
-  Buf<uint32_t> tab;
-  if (nX > 0 && sp.nH <= kMaskBits && !sp.product) {
-    // |H| <= 256: anticommutation bitmaps from the nibble table
-    const int stride = tab_stride((sp.nH + 31) / 32);
-    PS_TRY(tab.alloc((size_t)kTabPos * kTabVals * stride, s));
-    PS_LAUNCH("k_anti_table", s, k_anti_table<<<(kTabPos * kTabVals * stride + 255) / 256, 256, 0, s>>>(sp.H, sp.nH, stride, tab.p));
-    PS_CUDA(cudaGetLastError());
+  if (use_tab) {
+    // |H| <= 256: anticommutation bitmaps from the nibble table (built with the H terms)
     if (full) PS_TRY(emit_tab<true>(sp.X, fX.p, nX, sp.H, fH.p, hscal.p, sp.nH, tab.p, es, cur.p, nullptr, fent.p, counters.p, nsm, s, sp.hbatch, sp.hb_shift));
     else PS_TRY(emit_tab<false>(sp.X, fX.p, nX, sp.H, fH.p, nullptr, sp.nH, tab.p, es, cur.p, entries.p, nullptr, counters.p, nsm, s));
   } else if (nX > 0) {
