@@ -59,3 +59,22 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     assert_match(got.download(), want, exact=True, what="tuned")
     with pytest.raises(ps.PauliError):
         ps.pauli_merge_geometry_fix(10, 1536)
+
+
+@pytest.mark.parametrize("m", [8000, 9000, 300])
+def test_plan_boundary_bins(m):
+    # 120 terms x m strings at 64 entries per bin: 2^14 bins for m = 8000 (the largest merge
+    # planned in one block, 16 bins per thread), 2^15 for m = 9000 (the device-wide plan),
+    # a few hundred bins for m = 300; the results do not depend on the path
+    n = 40
+    Ha = I.random_sum(13, n, 120, kind="real", max_support=5)
+    Oa = I.random_sum(14, n, m, kind="real", max_support=9)
+    ps.pauli_merge_geometry_fix(64, 64)
+    try:
+        got = ps.pauli_commutator(ps.PauliSum.from_arrays(n, *Ha), ps.PauliSum.from_arrays(n, *Oa))
+        ga = ps.pauli_add(ps.PauliSum.from_arrays(n, *Oa), -0.25, got)
+    finally:
+        ps.pauli_autotune_reset()
+    want = orc.commutator(orc.Op(n, *Ha), orc.Op(n, *Oa))
+    assert_match(got.download(), want, exact=True, what=f"plan m={m}")
+    assert_match(ga.download(), orc.axpy(orc.Op(n, *Oa), -0.25, want), exact=True, what=f"add m={m}")

@@ -494,6 +494,25 @@ def test_rk4_trim_stages_dyadic_ties():
         assert_match(O.download(), Or, exact=True, what=f"rk4 trim ties step {step}")
 
 
+def test_rk4_commuting_and_partly_commuting():
+    # H commuting with O: every k_j is empty, the final merge holds the pre operand alone and
+    # O is returned unchanged; then an O of which only some strings commute with H
+    n = 8
+    Ha = I.single(n, "Z", 3).arrays()
+    O0 = I.single(n, "Z", 3).arrays()
+    H, Hr = dev(n, Ha), ref(n, Ha)
+    O, Or = dev(n, O0), ref(n, O0)
+    ps.pauli_rk4_step(H, O, 0.1, ps.policy(top_k=4))
+    Or = orc.rk4_step(Hr, Or, 0.1, top_k=4)
+    assert_match(O.download(), Or, exact=True, what="commuting")
+    v, w, re, im = I.random_sum(21, n, 60, kind="real", dyadic=True)
+    O, Or = dev(n, (v, w, re, im)), ref(n, (v, w, re, im))
+    for step in range(2):
+        ps.pauli_rk4_step(H, O, 0.25, ps.policy(top_k=40, trim_stages=1))
+        Or = orc.rk4_step(Hr, Or, 0.25, top_k=40, trim_stages=1)
+        assert_match(O.download(), Or, exact=True, what=f"partly commuting step {step}")
+
+
 # ----------------------------------------------------------------------------- Lanczos
 def test_lanczos_paper_example():
     n = 10
